@@ -1,0 +1,645 @@
+/*
+ * vsr_oracle.c -- plain FP64 CPU oracle of the visual-sphere rasterizer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file.  The product (the CUDA
+ * library and its Python binding) never calls it, includes it or shares code
+ * with it.
+ *
+ * Everything here is computed in double precision, by brute force over every
+ * (pixel, triangle) pair, in the order the paper states the method:
+ *
+ *   map      Universal perspective 2D->3D transform (Sec. 2 "Universal
+ *            perspective", eq. of the 2D->3D transformation) with the
+ *            parameter limits (Sec. "Universal perspective parameters and
+ *            limits") and the view-coordinate normalisation of the AOV remark
+ *            (Sec. 2, remark on AOV types).  The global delta (Sec. 1.1.1,
+ *            "Global delta") is the reciprocal of the largest per-component
+ *            fwidth of the map.
+ *   setup    edge-plane normals ||A x B||, ||B x C||, ||C x A|| (Sec. 1.1),
+ *            the miter / smallest-circle vector S (Sec. 1.1.2), the hard
+ *            normal N and plane offset d = A.N (Sec. 1.1.5, depth equation).
+ *   raster   the four plane distances of the rasterization equation
+ *            (Sec. 1.1.2, eq. "rasterization"), gpstep / gbpxstep (Sec. 1.1.1),
+ *            bstep for the centre test, ray-plane depth r = (A.N)/(G.N), and
+ *            the front-to-back mask merge of Sec. 1.3 (hidden surface
+ *            occlusion).
+ *
+ * The only shortcut is that the miter-plane test of gbpxstep is evaluated
+ * before the three edge-plane tests: a pair that fails it is not a fragment
+ * by definition, so skipping the remaining arithmetic changes no result.
+ *
+ * Readings where the paper is silent or inconsistent (each one is listed
+ * with its reason in the design notes of the repository):
+ *   R1  R = sqrt(x^2 + l*y^2) as in the equation (the listing squares l).
+ *   R3  pixel centres f = ((i+1/2)/W, (j+1/2)/H), aspect a = W/H.
+ *   R5  s is clamped to [0.5, 1] unless strict limits ask for [0.8, 1].
+ *   R6  pixels where asin is undefined are invalid: map (0,0,0,0).
+ *   R7  R = 0 uses the limit of sin(theta)/R.
+ *   R8  fwidth = |central difference along i| + |along j| of the map
+ *       function at the neighbouring pixel centres, one-sided next to an
+ *       invalid neighbour, 0 when both are invalid.
+ *   R10 two-sided triangles: sigma = sign(A'.(B' x C')) orients all normals.
+ *   R11 ties g == 0 in the centre test count as inside iff the first
+ *       nonzero component of the edge normal is positive; each edge's cross
+ *       product is taken with its vertices in a canonical order (bit pattern
+ *       of the world-space FP32 coordinates) so shared edges get exactly
+ *       opposite normals.
+ *   R15 front-to-back order = ascending (r, t); id/depth from the nearest
+ *       centre-inside fragment; fragments with r <= 0 or non-finite r are
+ *       dropped.
+ *   R17 the miter plane's distance G.S-hat - |S| is divided by sin(rho),
+ *       rho the cap's angular radius, before the global-delta step.  The
+ *       edge distances G.n are sines of angular distances (unit slope at the
+ *       edge) but the miter distance has slope sin(rho) at its rim; the
+ *       per-fragment pstep of the paper's listing divides by fwidth(g),
+ *       which removes any such scale, and the global delta stands in for
+ *       that denominator only for unit-slope distances.  Without the factor
+ *       the miter ramp is 1/sin(rho) pixels wide and a small triangle never
+ *       reaches full coverage.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* Record layout of one set-up triangle (doubles). */
+enum {
+    REC_N1 = 0,  /* edge normal of A,B (3) */
+    REC_N2 = 3,  /* edge normal of B,C (3) */
+    REC_N3 = 6,  /* edge normal of C,A (3) */
+    REC_S = 9,   /* miter unit vector S-hat (3) */
+    REC_C = 12,  /* |S| = cosine of the cap radius rho */
+    REC_N = 13,  /* hard normal N (3) */
+    REC_D = 16,  /* A'.N */
+    REC_VALID = 17,
+    REC_SIGMA = 18,
+    REC_SR = 19, /* sin(rho) = sqrt(1 - |S|^2) */
+    ORC_REC = 20
+};
+
+int orc_record_size(void) { return ORC_REC; }
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double* a, const double* b, double* o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ------------------------------------------------------------------------
+ * Parameter limits (Sec. "Universal perspective parameters and limits").
+ * k in [-1,1], l in [0,1], s in [0.8,1] (strict) or [0.5,1] (reading R5),
+ * Omega in degrees clamped to [1, Omega_max] with
+ * Omega_max = (k > 0 ? 179 : 180) / max(|k|, 1/2).
+ * out = {k, l, s, omega_deg}.
+ */
+void orc_limits(double k, double l, double s, double omega_deg, int strict, double* out)
+{
+    k = clampd(k, -1.0, 1.0);
+    l = clampd(l, 0.0, 1.0);
+    s = clampd(s, strict ? 0.8 : 0.5, 1.0);
+    double kmag = fabs(k) > 0.5 ? fabs(k) : 0.5;
+    double omax = (k > 0.0 ? 179.0 : 180.0) / kmag;
+    omega_deg = clampd(omega_deg, 1.0, omax);
+    out[0] = k;
+    out[1] = l;
+    out[2] = s;
+    out[3] = omega_deg;
+}
+
+/* ------------------------------------------------------------------------
+ * View coordinates from texture coordinates (remark on AOV types, Sec. 2):
+ * centred 2f-1, then normalised for the AOV type.
+ * aov: 0 horizontal, 1 diagonal, 2 vertical, 3 horizontal 4x3.
+ */
+void orc_view_coord(double fs, double ft, double aspect, int aov, double* xy)
+{
+    double x = 2.0 * fs - 1.0, y = 2.0 * ft - 1.0;
+    switch (aov) {
+    case 1: /* diagonal: [a, 1] / sqrt(1 + a^2) */
+        x = x * aspect / sqrt(1.0 + aspect * aspect);
+        y = y / sqrt(1.0 + aspect * aspect);
+        break;
+    case 2: /* vertical: [a, 1] */
+        x = x * aspect;
+        break;
+    case 3: /* horizontal 4x3: [a, 1] / (4/3) */
+        x = x * aspect / (4.0 / 3.0);
+        y = y / (4.0 / 3.0);
+        break;
+    default: /* horizontal: [1, 1/a] */
+        y = y / aspect;
+        break;
+    }
+    xy[0] = x;
+    xy[1] = y;
+}
+
+/* ------------------------------------------------------------------------
+ * Universal perspective 2D->3D (Sec. "Transformation of 2D->3D"):
+ *   R     = sqrt(x^2 + l y^2)                                   (reading R1)
+ *   theta = atan(tan(k Omega/2) R)/k   k > 0
+ *           Omega/2 R                  k = 0
+ *           asin(sin(k Omega/2) R)/k   k < 0
+ *   v     = normalize(x sin(theta)/R, y sin(theta)/R / (l(1-s)+s), cos(theta))
+ * p = {k, l, s, omega_deg} after limits.  Returns 0 where asin is undefined
+ * (reading R6), 1 otherwise.
+ */
+int orc_map_dir(double x, double y, const double* p, double* v)
+{
+    double k = p[0], l = p[1], s = p[2];
+    double half = p[3] * ORC_PI / 360.0; /* Omega/2 in radians */
+    double R = sqrt(x * x + l * y * y);
+    double theta, sin_over_R;
+    if (k > 0.0) {
+        double tk = tan(k * half);
+        theta = atan(tk * R) / k;
+        sin_over_R = R > 0.0 ? sin(theta) / R : tk / k; /* reading R7 */
+    } else if (k == 0.0) {
+        theta = half * R;
+        sin_over_R = R > 0.0 ? sin(theta) / R : half;
+    } else {
+        double sk = sin(k * half);
+        double arg = sk * R;
+        if (arg > 1.0 || arg < -1.0) {
+            v[0] = v[1] = v[2] = 0.0;
+            return 0;
+        }
+        theta = asin(arg) / k;
+        sin_over_R = R > 0.0 ? sin(theta) / R : sk / k;
+    }
+    double w[3] = {x * sin_over_R, y * sin_over_R / (l * (1.0 - s) + s), cos(theta)};
+    double n = sqrt(dot3(w, w));
+    v[0] = w[0] / n;
+    v[1] = w[1] / n;
+    v[2] = w[2] / n;
+    return 1;
+}
+
+/* Map direction at a texture coordinate (fs, ft) of a W x H picture. */
+static int map_at(double fs, double ft, double aspect, int aov, const double* p, double* v)
+{
+    double xy[2];
+    orc_view_coord(fs, ft, aspect, aov, xy);
+    return orc_map_dir(xy[0], xy[1], p, v);
+}
+
+/* Vectorised map function at arbitrary texture coordinates (used by the
+ * supersampling and area pins).  v: n x 3, valid: n. */
+void orc_map_dirs(int64_t n, const double* fs, const double* ft, int W, int H, const double* p, int aov,
+                  double* v, int32_t* valid)
+{
+    double aspect = (double)W / (double)H;
+    for (int64_t q = 0; q < n; ++q) valid[q] = map_at(fs[q], ft[q], aspect, aov, p, v + 3 * q);
+}
+
+/* ------------------------------------------------------------------------
+ * Universal perspective 3D->2D (Sec. "Transformation of 3D->2D"):
+ *   theta = acos(v_z / sqrt(v_x^2 + l v_y^2 + v_z^2))
+ *   R     = tan(k theta)/tan(k Omega/2)   k > 0
+ *           theta/(Omega/2)               k = 0
+ *           sin(k theta)/sin(k Omega/2)   k < 0
+ *   (x,y) = (v_x, v_y) R / sqrt(v_x^2 + l v_y^2) * (1, l(1-s)+s)
+ * Used only as a round-trip pin of the 2D->3D map.
+ */
+void orc_map_inverse(const double* v, const double* p, double* xy)
+{
+    double k = p[0], l = p[1], s = p[2];
+    double half = p[3] * ORC_PI / 360.0;
+    double theta = acos(v[2] / sqrt(v[0] * v[0] + l * v[1] * v[1] + v[2] * v[2]));
+    double R;
+    if (k > 0.0)
+        R = tan(k * theta) / tan(k * half);
+    else if (k == 0.0)
+        R = theta / half;
+    else
+        R = sin(k * theta) / sin(k * half);
+    double rho = sqrt(v[0] * v[0] + l * v[1] * v[1]);
+    if (rho == 0.0) {
+        xy[0] = xy[1] = 0.0;
+        return;
+    }
+    xy[0] = v[0] * R / rho;
+    xy[1] = v[1] * R / rho * (l * (1.0 - s) + s);
+}
+
+/* ------------------------------------------------------------------------
+ * Perspective map with global delta (Sec. 1.1.1 "Global delta"):
+ *   out[(j*W + i)*4 + 0..2] = v(i, j),  out[...+3] = delta(i, j)
+ *   delta = 1 / max_c (|d_i v_c| + |d_j v_c|)           (reading R8)
+ * Invalid pixels are (0,0,0,0).  The map function is evaluated on the
+ * (W+2) x (H+2) grid of pixel centres including a one-pixel border.
+ */
+typedef struct {
+    int W, H, aov;
+    const double* p;
+    double* grid; /* (H+2)*(W+2)*3 */
+    int* gvalid;
+    double* out;
+    int next_row;
+    int phase;
+} map_job;
+
+static void* map_worker(void* arg)
+{
+    map_job* J = (map_job*)arg;
+    const int W = J->W, H = J->H, GW = W + 2;
+    const double aspect = (double)W / (double)H;
+    for (;;) {
+        int row = __atomic_fetch_add(&J->next_row, 1, __ATOMIC_RELAXED);
+        if (J->phase == 0) {
+            if (row >= H + 2) break;
+            int j = row - 1;
+            for (int gi = 0; gi < GW; ++gi) {
+                int i = gi - 1;
+                double* v = J->grid + ((size_t)row * GW + gi) * 3;
+                J->gvalid[(size_t)row * GW + gi] =
+                    map_at((i + 0.5) / W, (j + 0.5) / H, aspect, J->aov, J->p, v);
+            }
+        } else {
+            if (row >= H) break;
+            int j = row;
+            for (int i = 0; i < W; ++i) {
+                double* o = J->out + ((size_t)j * W + i) * 4;
+                size_t c0 = (size_t)(j + 1) * GW + (i + 1);
+                if (!J->gvalid[c0]) {
+                    o[0] = o[1] = o[2] = o[3] = 0.0;
+                    continue;
+                }
+                const double* vc = J->grid + c0 * 3;
+                double di[3], dj[3];
+                /* derivative along i (columns) */
+                size_t cl = c0 - 1, cr = c0 + 1, cu = c0 - GW, cd = c0 + GW;
+                for (int c = 0; c < 3; ++c) {
+                    if (J->gvalid[cl] && J->gvalid[cr])
+                        di[c] = (J->grid[cr * 3 + c] - J->grid[cl * 3 + c]) * 0.5;
+                    else if (J->gvalid[cr])
+                        di[c] = J->grid[cr * 3 + c] - vc[c];
+                    else if (J->gvalid[cl])
+                        di[c] = vc[c] - J->grid[cl * 3 + c];
+                    else
+                        di[c] = 0.0;
+                    if (J->gvalid[cu] && J->gvalid[cd])
+                        dj[c] = (J->grid[cd * 3 + c] - J->grid[cu * 3 + c]) * 0.5;
+                    else if (J->gvalid[cd])
+                        dj[c] = J->grid[cd * 3 + c] - vc[c];
+                    else if (J->gvalid[cu])
+                        dj[c] = vc[c] - J->grid[cu * 3 + c];
+                    else
+                        dj[c] = 0.0;
+                }
+                double fw = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double f = fabs(di[c]) + fabs(dj[c]);
+                    if (f > fw) fw = f;
+                }
+                if (fw > 0.0) {
+                    o[0] = vc[0];
+                    o[1] = vc[1];
+                    o[2] = vc[2];
+                    o[3] = 1.0 / fw;
+                } else {
+                    o[0] = o[1] = o[2] = o[3] = 0.0;
+                }
+            }
+        }
+    }
+    return NULL;
+}
+
+static int ncores(int nthreads)
+{
+    if (nthreads > 0) return nthreads;
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int)n : 1;
+}
+
+static void run_threads(int n, void* (*fn)(void*), void* arg)
+{
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)n);
+    for (int t = 0; t < n; ++t) pthread_create(&th[t], NULL, fn, arg);
+    for (int t = 0; t < n; ++t) pthread_join(th[t], NULL);
+    free(th);
+}
+
+int orc_map(int W, int H, const double* p, int aov, double* out, int nthreads)
+{
+    if (W <= 0 || H <= 0) return -1;
+    size_t gn = (size_t)(W + 2) * (size_t)(H + 2);
+    map_job J;
+    J.W = W;
+    J.H = H;
+    J.aov = aov;
+    J.p = p;
+    J.grid = (double*)malloc(gn * 3 * sizeof(double));
+    J.gvalid = (int*)malloc(gn * sizeof(int));
+    J.out = out;
+    if (!J.grid || !J.gvalid) {
+        free(J.grid);
+        free(J.gvalid);
+        return -2;
+    }
+    int n = ncores(nthreads);
+    J.phase = 0;
+    J.next_row = 0;
+    run_threads(n, map_worker, &J);
+    J.phase = 1;
+    J.next_row = 0;
+    run_threads(n, map_worker, &J);
+    free(J.grid);
+    free(J.gvalid);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Triangle setup.
+ *
+ * Camera: cam = {O_x, O_y, O_z, M (3x3 row-major)}; camera-space vertex
+ * X' = M (X - O).
+ *
+ * Edge normals (Sec. 1.1): n_AB = sigma ||A' x B'||, n_BC, n_CA with
+ * sigma = sign(A'.(B' x C')) (reading R10).  The cross product of each edge
+ * is formed with the edge's vertices in canonical order and negated when the
+ * triangle lists them the other way (reading R11).
+ *
+ * Miter (Sec. 1.1.2): with A-hat, B-hat, C-hat the normalised vertices,
+ *   a^2 = |B-C|^2, b^2 = |C-A|^2, c^2 = |A-B|^2,
+ *   O_s = a^2(b^2+c^2-a^2), O_t = b^2(c^2+a^2-b^2), O_p = c^2(a^2+b^2-c^2),
+ *   S = (B+C)/2 if O_s <= 0, else (C+A)/2 if O_t <= 0, else (A+B)/2 if
+ *   O_p <= 0, else (O_s A + O_t B + O_p C)/(O_s+O_t+O_p);
+ *   stored as S-hat, |S| = cos(rho) and sin(rho) = sqrt(1 - |S|^2).
+ *
+ * Plane (Sec. 1.1.5): N = (A'-B') x (C'-B'), d = A'.N.
+ *
+ * Culled (valid = 0): a vertex at the eye, A'.(B' x C') == 0, or a cap whose
+ * sin(rho) rounds to zero (a triangle far below a pixel).
+ */
+static int vertex_less(const float* P, const float* Q)
+{
+    /* lexicographic order of the FP32 bit patterns of (x, y, z) */
+    for (int c = 0; c < 3; ++c) {
+        uint32_t a, b;
+        memcpy(&a, &P[c], 4);
+        memcpy(&b, &Q[c], 4);
+        if (a != b) return a < b;
+    }
+    return 0;
+}
+
+static void edge_normal(const float* Pw, const float* Qw, const double* Pc, const double* Qc, double sigma,
+                        double* n)
+{
+    double x[3];
+    if (vertex_less(Qw, Pw)) {
+        /* canonical order is (Q, P): n = -(Q' x P') */
+        cross3(Qc, Pc, x);
+        x[0] = -x[0];
+        x[1] = -x[1];
+        x[2] = -x[2];
+    } else {
+        cross3(Pc, Qc, x);
+    }
+    double len = sqrt(dot3(x, x));
+    for (int c = 0; c < 3; ++c) n[c] = sigma * x[c] / len;
+}
+
+void orc_setup(int64_t T, const float* tris, const float* cam, double* rec)
+{
+    const double O[3] = {cam[0], cam[1], cam[2]};
+    double M[9];
+    for (int q = 0; q < 9; ++q) M[q] = cam[3 + q];
+    for (int64_t t = 0; t < T; ++t) {
+        const float* w = tris + 9 * t;
+        double* r = rec + ORC_REC * t;
+        memset(r, 0, sizeof(double) * ORC_REC);
+        double V[3][3];
+        int at_eye = 0;
+        for (int q = 0; q < 3; ++q) {
+            double d[3] = {(double)w[3 * q] - O[0], (double)w[3 * q + 1] - O[1], (double)w[3 * q + 2] - O[2]};
+            for (int c = 0; c < 3; ++c) V[q][c] = M[3 * c] * d[0] + M[3 * c + 1] * d[1] + M[3 * c + 2] * d[2];
+            if (V[q][0] == 0.0 && V[q][1] == 0.0 && V[q][2] == 0.0) at_eye = 1;
+        }
+        double bxc[3];
+        cross3(V[1], V[2], bxc);
+        double det = dot3(V[0], bxc);
+        if (at_eye || det == 0.0 || !isfinite(det)) continue; /* culled */
+        double sigma = det > 0.0 ? 1.0 : -1.0;
+        edge_normal(w + 0, w + 3, V[0], V[1], sigma, r + REC_N1);
+        edge_normal(w + 3, w + 6, V[1], V[2], sigma, r + REC_N2);
+        edge_normal(w + 6, w + 0, V[2], V[0], sigma, r + REC_N3);
+
+        /* miter: smallest circle over the projected vertices */
+        double U[3][3];
+        for (int q = 0; q < 3; ++q) {
+            double len = sqrt(dot3(V[q], V[q]));
+            for (int c = 0; c < 3; ++c) U[q][c] = V[q][c] / len;
+        }
+        double e_a[3], e_b[3], e_c[3];
+        for (int c = 0; c < 3; ++c) {
+            e_a[c] = U[1][c] - U[2][c];
+            e_b[c] = U[2][c] - U[0][c];
+            e_c[c] = U[0][c] - U[1][c];
+        }
+        double a2 = dot3(e_a, e_a), b2 = dot3(e_b, e_b), c2 = dot3(e_c, e_c);
+        double Os = a2 * (b2 + c2 - a2), Ot = b2 * (c2 + a2 - b2), Op = c2 * (a2 + b2 - c2);
+        double S[3];
+        for (int c = 0; c < 3; ++c) {
+            if (Os <= 0.0)
+                S[c] = 0.5 * (U[1][c] + U[2][c]);
+            else if (Ot <= 0.0)
+                S[c] = 0.5 * (U[2][c] + U[0][c]);
+            else if (Op <= 0.0)
+                S[c] = 0.5 * (U[0][c] + U[1][c]);
+            else
+                S[c] = (Os * U[0][c] + Ot * U[1][c] + Op * U[2][c]) / (Os + Ot + Op);
+        }
+        double slen = sqrt(dot3(S, S));
+        double sr = sqrt((1.0 - slen) * (1.0 + slen)); /* sin(rho), reading R17 */
+        if (!(slen > 0.0) || !(sr > 0.0)) continue; /* degenerate: det == 0, or a point-sized cap */
+        for (int c = 0; c < 3; ++c) r[REC_S + c] = S[c] / slen;
+        r[REC_C] = slen;
+        r[REC_SR] = sr;
+
+        /* plane for depth */
+        double ab[3], cb[3];
+        for (int c = 0; c < 3; ++c) {
+            ab[c] = V[0][c] - V[1][c];
+            cb[c] = V[2][c] - V[1][c];
+        }
+        cross3(ab, cb, r + REC_N);
+        r[REC_D] = dot3(V[0], r + REC_N);
+        r[REC_VALID] = 1.0;
+        r[REC_SIGMA] = sigma;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Rasterization of one pixel against every triangle.
+ *
+ * For pixel direction G and global delta delta:
+ *   g_1..3 = G . n_i, g_4 = (G . S-hat - |S|) / sin(rho)
+ *                                   (eq. "rasterization"; reading R17)
+ *   fragment  iff  g_i > -1/(2 delta) for all four (gbpxstep) and r > 0
+ *   m^f       = min_i clamp(delta g_i + 1/2, 0, 1)        (gpstep, min)
+ *   r         = d / (G . N)                               (depth)
+ *   centre-inside iff bstep on g_1..3 with the tie rule R11
+ * Fragments are merged front to back in ascending (r, t)  (reading R15):
+ *   m^fc = min(m^f, 1 - m^b);  m^b = m^b + m^fc          (Sec. 1.3)
+ * cov = final m^b; id, depth = the first centre-inside fragment.
+ */
+typedef struct {
+    double r, m;
+    uint32_t t;
+    int inside;
+} frag;
+
+static int frag_cmp(const void* a, const void* b)
+{
+    const frag* x = (const frag*)a;
+    const frag* y = (const frag*)b;
+    if (x->r < y->r) return -1;
+    if (x->r > y->r) return 1;
+    return x->t < y->t ? -1 : (x->t > y->t ? 1 : 0);
+}
+
+static int tie_inside(double g, const double* n)
+{
+    if (g > 0.0) return 1;
+    if (g < 0.0) return 0;
+    /* g == 0: perturbed sample (eps, eps^2, eps^3) */
+    for (int c = 0; c < 3; ++c) {
+        if (n[c] > 0.0) return 1;
+        if (n[c] < 0.0) return 0;
+    }
+    return 0;
+}
+
+typedef struct {
+    int W, H;
+    const double* map;
+    int64_t T;
+    const double* rec;
+    int64_t npix;
+    const int64_t* pix;
+    uint32_t* id;
+    double* depth;
+    double* cov;
+    double* sum_mf;
+    int32_t* n_inside;
+    int32_t* n_frag;
+    int64_t next;
+    int64_t n_alg;
+} raster_job;
+
+static void* raster_worker(void* arg)
+{
+    raster_job* J = (raster_job*)arg;
+    size_t cap = 64;
+    frag* F = (frag*)malloc(cap * sizeof(frag));
+    int64_t n_alg = 0;
+    const int64_t chunk = 64;
+    for (;;) {
+        int64_t q0 = __atomic_fetch_add(&J->next, chunk, __ATOMIC_RELAXED);
+        if (q0 >= J->npix) break;
+        int64_t q1 = q0 + chunk < J->npix ? q0 + chunk : J->npix;
+        for (int64_t q = q0; q < q1; ++q) {
+            int64_t p = J->pix ? J->pix[q] : q;
+            const double* G = J->map + 4 * p;
+            double delta = G[3];
+            size_t nf = 0;
+            if (delta > 0.0) {
+                double lim = -0.5 / delta;
+                for (int64_t t = 0; t < J->T; ++t) {
+                    const double* r = J->rec + ORC_REC * t;
+                    if (r[REC_VALID] == 0.0) continue;
+                    double g4 = (dot3(G, r + REC_S) - r[REC_C]) / r[REC_SR];
+                    if (!(g4 > lim)) continue;
+                    ++n_alg; /* G inside the enlarged cap: one algorithmic test */
+                    double g1 = dot3(G, r + REC_N1), g2 = dot3(G, r + REC_N2), g3 = dot3(G, r + REC_N3);
+                    if (!(g1 > lim && g2 > lim && g3 > lim)) continue;
+                    double rr = r[REC_D] / dot3(G, r + REC_N);
+                    if (!(rr > 0.0) || !isfinite(rr)) continue;
+                    double m = 1.0;
+                    double gs[4] = {g1, g2, g3, g4};
+                    for (int i = 0; i < 4; ++i) {
+                        double st = clampd(delta * gs[i] + 0.5, 0.0, 1.0);
+                        if (st < m) m = st;
+                    }
+                    if (nf == cap) {
+                        cap *= 2;
+                        F = (frag*)realloc(F, cap * sizeof(frag));
+                    }
+                    F[nf].r = rr;
+                    F[nf].m = m;
+                    F[nf].t = (uint32_t)t;
+                    F[nf].inside = tie_inside(g1, r + REC_N1) && tie_inside(g2, r + REC_N2) &&
+                                   tie_inside(g3, r + REC_N3);
+                    ++nf;
+                }
+            }
+            qsort(F, nf, sizeof(frag), frag_cmp);
+            double mb = 0.0, sum = 0.0;
+            uint32_t best = 0xFFFFFFFFu;
+            double bdepth = INFINITY;
+            int32_t ninside = 0;
+            for (size_t f = 0; f < nf; ++f) {
+                double mfc = F[f].m < 1.0 - mb ? F[f].m : 1.0 - mb;
+                mb = mb + mfc;
+                sum += F[f].m;
+                if (F[f].inside) {
+                    if (ninside == 0) {
+                        best = F[f].t;
+                        bdepth = F[f].r;
+                    }
+                    ++ninside;
+                }
+            }
+            J->id[q] = best;
+            J->depth[q] = bdepth;
+            J->cov[q] = mb;
+            if (J->sum_mf) J->sum_mf[q] = sum;
+            if (J->n_inside) J->n_inside[q] = ninside;
+            if (J->n_frag) J->n_frag[q] = (int32_t)nf;
+        }
+    }
+    free(F);
+    __atomic_fetch_add(&J->n_alg, n_alg, __ATOMIC_RELAXED);
+    return NULL;
+}
+
+/* map: H*W*4 doubles; rec: T*ORC_REC; pix: npix pixel indices (j*W+i) or
+ * NULL for all pixels in order (then npix must be W*H).  Outputs have npix
+ * entries; sum_mf, n_inside, n_frag may be NULL.  Returns the number of
+ * algorithmic tests (pairs inside the enlarged cap), or -1 on bad sizes. */
+int64_t orc_raster(int W, int H, const double* map, int64_t T, const double* rec, int64_t npix,
+                   const int64_t* pix, uint32_t* id, double* depth, double* cov, double* sum_mf,
+                   int32_t* n_inside, int32_t* n_frag, int nthreads)
+{
+    if (W <= 0 || H <= 0 || T < 0 || npix < 0) return -1;
+    if (!pix && npix != (int64_t)W * H) return -1;
+    raster_job J;
+    J.W = W;
+    J.H = H;
+    J.map = map;
+    J.T = T;
+    J.rec = rec;
+    J.npix = npix;
+    J.pix = pix;
+    J.id = id;
+    J.depth = depth;
+    J.cov = cov;
+    J.sum_mf = sum_mf;
+    J.n_inside = n_inside;
+    J.n_frag = n_frag;
+    J.next = 0;
+    J.n_alg = 0;
+    run_threads(ncores(nthreads), raster_worker, &J);
+    return J.n_alg;
+}
