@@ -1,0 +1,338 @@
+"""Benchmark of the visual-sphere rasterizer on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vsr|reference]
+
+Workload: the single-view frame -- a 1920x1080 Universal-perspective map
+(k=0.32, l=0.62, s=0.86, Omega=270 deg, horizontal AOV) of a level-5
+icosphere of radius 50 around the eye (20,480 triangles) plus 200,000 seeded
+random triangles (radius U[1, 40], edge ~0.02 rad); synthetic, seeded.
+
+One step is the whole hot path over that frame: perspective map + tile cones
+(a1), triangle set-up (a2), tile binning (a3), tile coverage / depth /
+visibility and the front-to-back merge (a4 + a5), all inputs resident in
+HBM.  The metric is pixel x triangle tests/s: algorithmic tests (pixel
+inside a triangle's enlarged miter cap, counted by the raster kernel) per
+second of step time.  L2 is flushed (a 256 MB write) before every timed
+step, outside its CUDA events.
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its
+own replica of the frame ("replicas only": the path has no exchange step)
+and the value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel x triangle tests/s"
+UNIT = "tests/s"
+OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
+LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vsr", choices=["vsr", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=200000, help="pixels of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_2003_10558_gb300 import scenes
+    lens, tris, cam = scenes.single_view_scene()
+    return lens, tris, cam
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) < 9:
+                        continue
+                    try:
+                        sm.append(float(p[1]))
+                        smax.append(float(p[2]))
+                    except ValueError:
+                        continue
+                    for n, v in zip(names, p[5:9]):
+                        if v.lower() in ("active", "0x1", "1"):
+                            reasons.add(n)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(lens, tris, cam, n_pix, seed=123):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    its raster stage (brute force over every triangle) on n_pix seeded pixels
+    of the oracle's own map.  Returns (tests/s, seconds, n_alg, threads)."""
+    import oracle
+    m64, _ = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    rec = oracle.setup(tris, cam)
+    rng = np.random.default_rng(seed)
+    pix = rng.integers(0, lens["W"] * lens["H"], n_pix)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    out = oracle.raster(m64, rec, pixels=pix, nthreads=threads)
+    dt = time.perf_counter() - t0
+    # extrapolate nothing: tests/s of the sampled pixels
+    return out["n_alg"] / dt, dt, out["n_alg"], threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    lens, tris, cam = workload()
+    # each step: a bounded sample of the frame, so K + W steps end in minutes
+    n_pix = max(256, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        cpu_baseline(lens, tris, cam, 64)
+    vals, tot_alg, tot_t = [], 0, 0.0
+    threads = os.cpu_count() or 1
+    for k in range(args.steps):
+        v, dt, n_alg, threads = cpu_baseline(lens, tris, cam, n_pix, seed=1000 + k)
+        vals.append(v)
+        tot_alg += n_alg
+        tot_t += dt
+    value = tot_alg / tot_t
+    sample = (f"{n_pix} seeded pixels per step of the 1920x1080 single-view frame; oracle raster stage, "
+              f"brute force over all {len(tris)} triangles per pixel")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "single-view 1920x1080, icosphere L5 + 200k triangles",
+                                            "W": lens["W"], "H": lens["H"], "T": int(len(tris))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_vsr(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2003_10558_gb300 import vsr as V
+    from paper_2003_10558_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    B.build()
+    V.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    lens, tris_np, cam = workload()
+    W, H = lens["W"], lens["H"]
+    T = int(len(tris_np))
+    tris = torch.from_numpy(tris_np).to(dev)
+    m = V.Map(W, H, lens["k"], lens["l"], lens["s"], lens["omega"])
+    sc = V.Scene(tris, cam)
+    out = {"id": torch.empty((H, W), dtype=torch.int32, device=dev),
+           "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+           "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        m.update(W, H, lens["k"], lens["l"], lens["s"], lens["omega"])  # a1
+        sc.update(tris, cam)  # a2
+        V.bin(m, sc)  # a3
+        ev_r0.record(stream)
+        V.raster(m, sc, out=out, binned=True)  # a4 + a5
+        ev_r1.record(stream)
+
+    ev_r0, ev_r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # algorithmic units of one step (counted once, untimed)
+    V.bin(m, sc)
+    st = V.raster(m, sc, stats=True)
+    n_alg, n_exec = st["n_alg"], st["n_exec"]
+    pairs = sc.bin_pairs()
+    assert V.last_device_status() == 0
+
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    r0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    r1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev0[k].record(stream)
+            ev_r0, ev_r1 = r0[k], r1[k]
+            step()
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    assert V.last_device_status() == 0
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    rast_ms = [a.elapsed_time(b) for a, b in zip(r0, r1)]
+    tot_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([tot_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    ms_per_step = 1000.0 * tot_s / K
+    value = world * n_alg * K / tot_s
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        work = V.Scene()
+        tris_pin = torch.from_numpy(tris_np).pin_memory()
+        outs = {"id": torch.empty((H, W), dtype=torch.int32).pin_memory(),
+                "depth": torch.empty((H, W), dtype=torch.float32).pin_memory(),
+                "cov": torch.empty((H, W), dtype=torch.float32).pin_memory()}
+        host_out = {"id": outs["id"].numpy().view(np.uint32), "depth": outs["depth"].numpy(),
+                    "cov": outs["cov"].numpy()}
+        tris_host = tris_pin.numpy()
+
+        def e2e_step():
+            m.update(W, H, lens["k"], lens["l"], lens["s"], lens["omega"])
+            V.render_host(m, work, tris_host, cam, out=host_out)
+
+        for _ in range(max(3, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n_alg * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * 36,
+               "d2h_bytes_per_step": W * H * 12, "ms_per_step": 1000.0 * e2e_s / K}
+
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6
+    rast_mean_s = statistics.mean(rast_ms) / 1000.0
+    achieved = n_alg * OPS_PER_TEST / rast_mean_s
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "raster_traffic.json")) as f:
+            traffic = json.load(f).get("bytes_per_launch_1080p")
+    except Exception:
+        pass
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded scene generator)",
+        "config": {"workload": "single-view 1920x1080, k=0.32 l=0.62 s=0.86 Omega=270, icosphere L5 + 200k triangles",
+                   "W": W, "H": H, "T": T, "l2": "flushed before every step (256 MB write, outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "frames_per_s": world * K / tot_s,
+        "raster_kernel_ms": statistics.mean(rast_ms),
+        "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32)",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "raster_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
+                     f"{LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} sm_max_mhz)"},
+        "clocks": clk.summary(),
+        "gpu_launches": 7 * K,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, na, thr = cpu_baseline(lens, tris_np, cam, args.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"{args.cpu_sample} seeded pixels of the frame, oracle raster stage "
+                                          f"(brute force over all {T} triangles), {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_vsr(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * vsr.h -- C ABI of the GB300 visual-sphere rasterizer.
+ *
+ * The library rasterizes triangles directly into a per-pixel direction map
+ * ("perspective map") as described in J. M. Fober, "Perspective picture from
+ * Visual Sphere: a new approach to image rasterization" (arXiv 2003.10558):
+ * every pixel carries a unit view direction G from the Universal perspective
+ * model (Sec. 2), a triangle ABC seen from the eye O is bounded by the three
+ * great-circle planes OAB, OBC, OCA (Sec. 1.1) plus the miter cap of its
+ * smallest enclosing circle (Sec. 1.1.2), coverage uses the analytic
+ * global-delta step (Sec. 1.1.1), depth is the ray-plane distance (Sec.
+ * 1.1.5) and fragments merge front to back (Sec. 1.3).
+ *
+ * Conventions shared by every entry point:
+ *   - All device pointers are CUDA global-memory pointers on the current
+ *     device; host pointers are ordinary (pageable or pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is asynchronous on that stream unless stated.
+ *   - Handles (vsr_map, vsr_scene) are owned by the library; free them with
+ *     their *_free function.  Output buffers are owned by the caller.
+ *   - No call aborts or exits.  Every error is a vsr_status.  Errors raised
+ *     by device code (e.g. bin overflow) are recorded in a per-device status
+ *     word and returned by vsr_last_device_status(), which synchronises.
+ *   - Inputs are never modified.
+ *   - Images are row-major [H][W]; pixel (i, j) is column i, row j, row 0
+ *     first in memory.
+ */
+#ifndef VSR_H
+#define VSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VSR_OK = 0,
+    VSR_ERR_INVALID_ARG = -1,  /* bad size, NULL pointer, non-finite parameter */
+    VSR_ERR_OOM = -2,          /* device or host allocation failed */
+    VSR_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    VSR_ERR_BIN_OVERFLOW = -4, /* a tile bin exceeded its capacity (device-side) */
+    VSR_ERR_FRAG_OVERFLOW = -5,/* reserved: the merge is order-free and keeps no fragment list */
+    VSR_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+    VSR_ERR_BUDGET = -7,       /* a request does not fit the memory budget */
+    VSR_ERR_CANCELLED = -8
+} vsr_status;
+
+/* Angle-of-view types of the view-coordinate normalisation (Sec. 2, remark
+ * on AOV types): x = 2 f_s - 1, y = 2 f_t - 1, then
+ *   HORIZONTAL  y /= a              (a = W/H)
+ *   DIAGONAL    (x a, y) / sqrt(1 + a^2)
+ *   VERTICAL    x *= a
+ *   H4X3        (x a, y) / (4/3)                                         */
+typedef enum { VSR_AOV_HORIZONTAL = 0, VSR_AOV_DIAGONAL = 1, VSR_AOV_VERTICAL = 2, VSR_AOV_H4X3 = 3 } vsr_aov;
+
+typedef struct vsr_map_s* vsr_map;
+typedef struct vsr_scene_s* vsr_scene;
+
+/* Universal perspective parameters (Sec. 2, "Universal perspective
+ * parameters and limits").  k in [-1, 1] picks the azimuthal projection
+ * (1 gnomonic, 0.5 stereographic, 0 equidistant, -0.5 equisolid,
+ * -1 orthographic); l in [0, 1] cylindricity; s anamorphic correction;
+ * omega_deg the angle of view in degrees.  The limits of the paper are
+ * applied on creation: k, l clamped; omega clamped to
+ * [1, (k > 0 ? 179 : 180) / max(|k|, 1/2)]; s clamped to [0.8, 1] when
+ * strict_limits != 0, else to [0.5, 1]. */
+typedef struct {
+    float k, l, s, omega_deg;
+    int W, H;
+    int aov;           /* vsr_aov */
+    int strict_limits; /* 0 or 1 */
+} vsr_map_params;
+
+/* ---- perspective map ------------------------------------------------------
+ * vsr_make_map: build the direction map of a W x H picture on `stream`
+ * (Universal perspective 2D->3D transform, Sec. 2): for pixel centre
+ * f = ((i + 1/2)/W, (j + 1/2)/H) with view coordinates (x, y),
+ *   R = sqrt(x^2 + l y^2),
+ *   theta = atan(tan(k Omega/2) R)/k | Omega/2 R | asin(sin(k Omega/2) R)/k
+ *           for k > 0 | k = 0 | k < 0,
+ *   G = normalize(x sin(theta)/R, y sin(theta)/R / (l(1-s)+s), cos(theta)),
+ * and the global delta delta = 1 / max_c fwidth(G_c) (Sec. 1.1.1) from
+ * central differences of the map function at the neighbouring pixel
+ * centres.  Stored as float4 (G_x, G_y, G_z, delta) per pixel; pixels where
+ * asin is undefined are (0, 0, 0, 0) and are never covered.  Also builds the
+ * per-tile view cones used by the binner.
+ * Horizontal AOV, non-strict limits.  1 <= W, H <= 32768.
+ * Returns VSR_ERR_INVALID_ARG for bad sizes or non-finite parameters. */
+vsr_status vsr_make_map(float k, float l, float s, float omega_deg, int W, int H, void* stream, vsr_map* out);
+vsr_status vsr_make_map_ex(const vsr_map_params* p, void* stream, vsr_map* out);
+
+/* Build a map from a caller-supplied float4 [H][W] (G_x, G_y, G_z, delta)
+ * array in DEVICE memory (copied; the caller keeps ownership).  Directions
+ * must be unit length where delta > 0; delta <= 0 marks an invalid pixel.
+ * Tile cones are computed from the data.  Lets a user rasterize into a map
+ * made elsewhere (the paper's "perspective pixel-shader pass", Sec. 1.1.6). */
+vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream, vsr_map* out);
+
+/* Regenerate an existing map in place for new parameters (reallocates
+ * only when W or H change).  Same semantics as vsr_make_map_ex. */
+vsr_status vsr_map_update(vsr_map m, const vsr_map_params* p, void* stream);
+
+/* Effective parameters after the limits (omega in degrees). */
+vsr_status vsr_map_params_effective(vsr_map m, vsr_map_params* out);
+
+/* Device pointer of the map's float4 [H][W] array (owned by the map). */
+vsr_status vsr_map_data(vsr_map m, const float** xyzd_dev, int* W, int* H);
+
+/* Synchronous copy of the map into host memory (W*H*4 floats). */
+vsr_status vsr_map_download(vsr_map m, float* host_xyzd);
+
+void vsr_map_free(vsr_map m);
+
+/* ---- triangle set-up --------------------------------------------------------
+ * vsr_setup: per-triangle set-up (Sec. 1.1, 1.1.2, 1.1.5) of T world-space
+ * triangles `tris_dev` (device, FP32, [T][3 vertices][xyz]) seen by the
+ * camera `cam` (host, 12 floats: eye O xyz, then the 3x3 world->camera
+ * rotation M row-major; X' = M (X - O)).  Computes in FP32-pair arithmetic
+ * the edge-plane normals ||A' x B'||, ||B' x C'||, ||C' x A'|| oriented by
+ * sign(A'.(B' x C')), the miter cap (smallest circle centre S-hat, cos and
+ * sin of its radius), and the plane (unit normal of (A'-B') x (C'-B'),
+ * offset).  Triangles with a vertex at the eye or with A'.(B' x C') = 0 are
+ * culled.  The scene keeps a pointer-free copy of the records; `tris_dev`
+ * may be freed once the call has completed on `stream`.
+ * 0 <= T < 2^31 - 1. */
+vsr_status vsr_setup(const float* tris_dev, int64_t T, const float cam[12], void* stream, vsr_scene* out);
+
+/* An empty scene (T = 0) to be filled by vsr_scene_update or
+ * vsr_render_host. */
+vsr_status vsr_scene_create(vsr_scene* out);
+
+/* Re-run the set-up of an existing scene for new triangles and/or camera,
+ * reusing its device memory when T does not grow. */
+vsr_status vsr_scene_update(vsr_scene s, const float* tris_dev, int64_t T, const float cam[12], void* stream);
+
+void vsr_scene_free(vsr_scene s);
+int64_t vsr_scene_size(vsr_scene s);
+
+/* ---- rasterization ---------------------------------------------------------
+ * vsr_raster: rasterize the scene into the map (Sec. 1.1.2 eq.
+ * "rasterization", Sec. 1.1.1 gpstep/gbpxstep, Sec. 1.1.5 depth, Sec. 1.3
+ * merge).  For pixel direction G with global delta delta and triangle t:
+ *   g_1..3 = G.n_i, g_4 = miter distance (G.S-hat - cos rho)/sin rho,
+ *   fragment iff every g_i > -1/(2 delta) and depth r = (A'.N)/(G.N) > 0,
+ *   m^f = min_i clamp(delta g_i + 1/2, 0, 1),
+ *   centre-inside iff g_1..3 >= 0 (ties: inside iff the first nonzero
+ *   component of the edge normal is positive).
+ * Outputs (caller-owned DEVICE buffers of W*H elements, any may be NULL):
+ *   id    uint32: the nearest centre-inside triangle (ties: lower index),
+ *         0xFFFFFFFF if none;
+ *   depth float: its r, +inf if none;
+ *   cov   float: the front-to-back merged mask m^b = min(1, sum of m^f).
+ * The merge of Sec. 1.3 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
+ * to min(1, sum m^f), so the result does not depend on fragment order; it is
+ * accumulated in 2^-24 fixed point and is bit-reproducible.
+ * Scratch (tile bins) is held by the scene handle; the first call for a new
+ * (map, scene) pair synchronises `stream` once to size it.  A scene must not
+ * be rasterized on two streams at the same time. */
+vsr_status vsr_raster(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev, void* stream);
+
+/* The two halves of vsr_raster, for callers that reuse one binning:
+ * vsr_bin builds the tile bins of (m, s) (count, scan, fill; the first call
+ * for a new pair synchronises `stream` once to size them);
+ * vsr_raster_tiles runs the tile coverage/depth kernel on the current bins
+ * and returns VSR_ERR_INVALID_ARG if they were built for another map or an
+ * older set-up of the scene. */
+vsr_status vsr_bin(vsr_map m, vsr_scene s, void* stream);
+
+/* Diagnostics of one rasterization (all optional, NULL to skip). */
+typedef struct {
+    uint64_t* n_alg_dev;     /* device: += pairs with G inside the enlarged cap */
+    uint64_t* n_exec_dev;    /* device: += pixel x triangle pairs evaluated */
+    int32_t* n_inside_dev;   /* device [H][W]: count of centre-inside triangles */
+} vsr_raster_stats;
+
+vsr_status vsr_raster_ex(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                         const vsr_raster_stats* stats, void* stream);
+vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            const vsr_raster_stats* stats, void* stream);
+
+/* Number of (tile, triangle) pairs in the last binning of this scene
+ * (synchronises `stream`). */
+vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
+
+/* ---- end to end from host memory ------------------------------------------
+ * vsr_render_host: one call from host buffers: copies `tris_host` ([T][3][3]
+ * FP32, host) to the device, re-runs the set-up of the work scene `s` (a
+ * handle from vsr_scene_create, whose device buffers are reused across
+ * calls), rasterizes into the map and copies id/depth/cov (W*H each, host;
+ * any may be NULL) back, then synchronises `stream`.  Same outputs as
+ * vsr_raster. */
+vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
+                           uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
+
+/* ---- status ---------------------------------------------------------------- */
+const char* vsr_status_str(vsr_status s);
+/* Synchronises the device, returns and clears the device-side status word
+ * (VSR_OK when nothing was raised). */
+vsr_status vsr_last_device_status(void);
+/* Library version string. */
+const char* vsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSR_H */

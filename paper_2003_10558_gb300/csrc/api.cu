@@ -1,0 +1,499 @@
+// api.cu -- host side of the C ABI declared in include/vsr.h: handles,
+// device memory, argument checks and the launch sequence of one frame
+//   map (once per lens) -> set-up (once per scene/camera) -> bin count ->
+//   scan -> bin fill -> tile raster.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "vsr_internal.cuh"
+
+namespace {
+
+std::atomic<uint64_t> g_gen{1};
+std::mutex g_status_mu;
+int* g_status[256] = {};
+
+// The device-side status word of the current device (allocated and zeroed
+// on first use).
+int* status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc((void**)&p, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+template <class Tp>
+vsr_status dalloc(Tp** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc((void**)p, n * sizeof(Tp)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return VSR_ERR_OOM;
+    }
+    return VSR_OK;
+}
+
+}  // namespace
+
+struct vsr_map_s {
+    vsr_map_params p;  // effective parameters
+    float4* map = nullptr;
+    Cone* tiles = nullptr;
+    Cone* supers = nullptr;
+    int tx = 0, ty = 0, sx = 0, sy = 0;
+    uint64_t gen = 0;
+};
+
+struct vsr_scene_s {
+    int64_t T = 0;
+    int64_t T_alloc = 0;
+    float4* rec = nullptr;
+    uint64_t gen = 0;
+    // bin workspace
+    int ws_tiles = 0;
+    uint32_t* counts = nullptr;
+    uint32_t* offsets = nullptr;
+    uint32_t* ids = nullptr;
+    uint32_t cap = 0;
+    uint64_t sized_map = 0, sized_scene = 0;
+    uint32_t* h_total = nullptr;  // pinned
+    int last_ntiles = 0;
+    uint64_t binned_map = 0, binned_scene = 0;  // generations the current bins belong to
+    // host-path buffers (vsr_render_host)
+    float* tris_dev = nullptr;
+    int64_t tris_alloc = 0;
+    void* out_dev = nullptr;  // id | depth | cov staging, 12 B per pixel
+    size_t out_alloc = 0;
+};
+
+namespace {
+
+bool finite4(float a, float b, float c, float d) { return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d); }
+
+void apply_limits(vsr_map_params* p)
+{
+    // Sec. 2, "Universal perspective parameters and limits"
+    float k = fminf(1.0f, fmaxf(-1.0f, p->k));
+    float l = fminf(1.0f, fmaxf(0.0f, p->l));
+    float s = fminf(1.0f, fmaxf(p->strict_limits ? 0.8f : 0.5f, p->s));
+    float kmag = fabsf(k) > 0.5f ? fabsf(k) : 0.5f;
+    float omax = (k > 0.0f ? 179.0f : 180.0f) / kmag;
+    float om = fminf(omax, fmaxf(1.0f, p->omega_deg));
+    p->k = k;
+    p->l = l;
+    p->s = s;
+    p->omega_deg = om;
+}
+
+vsr_status map_alloc(vsr_map m, int W, int H)
+{
+    m->tx = (W + TILE - 1) / TILE;
+    m->ty = (H + TILE - 1) / TILE;
+    m->sx = (m->tx + SUPER - 1) / SUPER;
+    m->sy = (m->ty + SUPER - 1) / SUPER;
+    vsr_status st;
+    if ((st = dalloc(&m->map, (size_t)W * H)) != VSR_OK) return st;
+    if ((st = dalloc(&m->tiles, (size_t)m->tx * m->ty)) != VSR_OK) return st;
+    if ((st = dalloc(&m->supers, (size_t)m->sx * m->sy)) != VSR_OK) return st;
+    return VSR_OK;
+}
+
+void map_release(vsr_map m)
+{
+    if (!m) return;
+    cudaFree(m->map);
+    cudaFree(m->tiles);
+    cudaFree(m->supers);
+    m->map = nullptr;
+    m->tiles = m->supers = nullptr;
+}
+
+bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 32768 && H <= 32768; }
+
+vsr_status check_params(const vsr_map_params* p)
+{
+    if (!p) return VSR_ERR_INVALID_ARG;
+    if (!size_ok(p->W, p->H)) return VSR_ERR_INVALID_ARG;
+    if (!finite4(p->k, p->l, p->s, p->omega_deg)) return VSR_ERR_INVALID_ARG;
+    if (p->aov < 0 || p->aov > 3) return VSR_ERR_INVALID_ARG;
+    return VSR_OK;
+}
+
+vsr_status map_generate(vsr_map m, cudaStream_t st)
+{
+    vsr_status s = launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles, st);
+    if (s != VSR_OK) return s;
+    s = launch_super_cones(m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, st);
+    m->gen = g_gen.fetch_add(1);
+    return s;
+}
+
+vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const float cam[12], cudaStream_t st)
+{
+    if (T > sc->T_alloc) {
+        cudaFree(sc->rec);
+        sc->rec = nullptr;
+        sc->T_alloc = 0;
+        vsr_status s = dalloc(&sc->rec, (size_t)REC_F * (size_t)T);
+        if (s != VSR_OK) return s;
+        sc->T_alloc = T;
+    }
+    sc->T = T;
+    // the record layout is field-major with stride T: keep it dense
+    vsr_status s = launch_setup(tris_dev, (int)T, cam, sc->rec, st);
+    sc->gen = g_gen.fetch_add(1);
+    return s;
+}
+
+vsr_status ensure_ws(vsr_scene sc, int ntiles)
+{
+    if (ntiles <= sc->ws_tiles) return VSR_OK;
+    cudaFree(sc->counts);
+    cudaFree(sc->offsets);
+    sc->counts = sc->offsets = nullptr;
+    sc->ws_tiles = 0;
+    vsr_status s;
+    if ((s = dalloc(&sc->counts, (size_t)ntiles)) != VSR_OK) return s;
+    if ((s = dalloc(&sc->offsets, (size_t)ntiles + 1)) != VSR_OK) return s;
+    sc->ws_tiles = ntiles;
+    sc->sized_map = 0;
+    return VSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vsr_version(void) { return "vsr 0.1 (sm_103a)"; }
+
+const char* vsr_status_str(vsr_status s)
+{
+    switch (s) {
+    case VSR_OK: return "ok";
+    case VSR_ERR_INVALID_ARG: return "invalid argument";
+    case VSR_ERR_OOM: return "out of memory";
+    case VSR_ERR_CUDA: return "CUDA error";
+    case VSR_ERR_BIN_OVERFLOW: return "tile bin overflow";
+    case VSR_ERR_FRAG_OVERFLOW: return "fragment list overflow";
+    case VSR_ERR_TIMEOUT: return "device wait timed out";
+    case VSR_ERR_BUDGET: return "memory budget exceeded";
+    case VSR_ERR_CANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+vsr_status vsr_last_device_status(void)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return VSR_ERR_CUDA;
+    int* w = status_word();
+    if (!w) return VSR_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VSR_ERR_CUDA;
+    if (cudaMemset(w, 0, sizeof(int)) != cudaSuccess) return VSR_ERR_CUDA;
+    return (vsr_status)v;
+}
+
+vsr_status vsr_make_map_ex(const vsr_map_params* p, void* stream, vsr_map* out)
+{
+    if (!out) return VSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    vsr_status s = check_params(p);
+    if (s != VSR_OK) return s;
+    vsr_map m = new (std::nothrow) vsr_map_s;
+    if (!m) return VSR_ERR_OOM;
+    m->p = *p;
+    apply_limits(&m->p);
+    if ((s = map_alloc(m, p->W, p->H)) != VSR_OK || (s = map_generate(m, (cudaStream_t)stream)) != VSR_OK) {
+        map_release(m);
+        delete m;
+        return s;
+    }
+    *out = m;
+    return VSR_OK;
+}
+
+vsr_status vsr_make_map(float k, float l, float s, float omega_deg, int W, int H, void* stream, vsr_map* out)
+{
+    vsr_map_params p;
+    p.k = k;
+    p.l = l;
+    p.s = s;
+    p.omega_deg = omega_deg;
+    p.W = W;
+    p.H = H;
+    p.aov = VSR_AOV_HORIZONTAL;
+    p.strict_limits = 0;
+    return vsr_make_map_ex(&p, stream, out);
+}
+
+vsr_status vsr_map_update(vsr_map m, const vsr_map_params* p, void* stream)
+{
+    if (!m) return VSR_ERR_INVALID_ARG;
+    vsr_status s = check_params(p);
+    if (s != VSR_OK) return s;
+    if (p->W != m->p.W || p->H != m->p.H) {
+        map_release(m);
+        if ((s = map_alloc(m, p->W, p->H)) != VSR_OK) return s;
+    }
+    m->p = *p;
+    apply_limits(&m->p);
+    return map_generate(m, (cudaStream_t)stream);
+}
+
+vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream, vsr_map* out)
+{
+    if (!out) return VSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!xyzd_dev || !size_ok(W, H)) return VSR_ERR_INVALID_ARG;
+    vsr_map m = new (std::nothrow) vsr_map_s;
+    if (!m) return VSR_ERR_OOM;
+    memset(&m->p, 0, sizeof(m->p));
+    m->p.W = W;
+    m->p.H = H;
+    m->p.k = m->p.l = m->p.s = m->p.omega_deg = NAN;
+    vsr_status s = map_alloc(m, W, H);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s == VSR_OK && cudaMemcpyAsync(m->map, xyzd_dev, sizeof(float4) * (size_t)W * H, cudaMemcpyDeviceToDevice,
+                                       st) != cudaSuccess)
+        s = VSR_ERR_CUDA;
+    if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, st);
+    if (s == VSR_OK) s = launch_super_cones(m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, st);
+    if (s != VSR_OK) {
+        map_release(m);
+        delete m;
+        return s;
+    }
+    m->gen = g_gen.fetch_add(1);
+    *out = m;
+    return VSR_OK;
+}
+
+vsr_status vsr_map_params_effective(vsr_map m, vsr_map_params* out)
+{
+    if (!m || !out) return VSR_ERR_INVALID_ARG;
+    *out = m->p;
+    return VSR_OK;
+}
+
+vsr_status vsr_map_data(vsr_map m, const float** xyzd_dev, int* W, int* H)
+{
+    if (!m) return VSR_ERR_INVALID_ARG;
+    if (xyzd_dev) *xyzd_dev = (const float*)m->map;
+    if (W) *W = m->p.W;
+    if (H) *H = m->p.H;
+    return VSR_OK;
+}
+
+vsr_status vsr_map_download(vsr_map m, float* host_xyzd)
+{
+    if (!m || !host_xyzd) return VSR_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return VSR_ERR_CUDA;
+    if (cudaMemcpy(host_xyzd, m->map, sizeof(float4) * (size_t)m->p.W * m->p.H, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return VSR_ERR_CUDA;
+    return VSR_OK;
+}
+
+void vsr_map_free(vsr_map m)
+{
+    if (!m) return;
+    map_release(m);
+    delete m;
+}
+
+vsr_status vsr_scene_create(vsr_scene* out)
+{
+    if (!out) return VSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    vsr_scene sc = new (std::nothrow) vsr_scene_s;
+    if (!sc) return VSR_ERR_OOM;
+    if (cudaMallocHost((void**)&sc->h_total, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete sc;
+        return VSR_ERR_OOM;
+    }
+    *sc->h_total = 0;
+    *out = sc;
+    return VSR_OK;
+}
+
+static bool setup_args_ok(const float* tris, int64_t T, const float* cam)
+{
+    if (T < 0 || T >= 0x7fffffffLL || (T > 0 && !tris) || !cam) return false;
+    for (int q = 0; q < 12; ++q)
+        if (!isfinite(cam[q])) return false;
+    return true;
+}
+
+vsr_status vsr_setup(const float* tris_dev, int64_t T, const float cam[12], void* stream, vsr_scene* out)
+{
+    if (!out) return VSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!setup_args_ok(tris_dev, T, cam)) return VSR_ERR_INVALID_ARG;
+    vsr_scene sc;
+    vsr_status s = vsr_scene_create(&sc);
+    if (s != VSR_OK) return s;
+    s = scene_setup(sc, tris_dev, T, cam, (cudaStream_t)stream);
+    if (s != VSR_OK) {
+        vsr_scene_free(sc);
+        return s;
+    }
+    *out = sc;
+    return VSR_OK;
+}
+
+vsr_status vsr_scene_update(vsr_scene sc, const float* tris_dev, int64_t T, const float cam[12], void* stream)
+{
+    if (!sc || !setup_args_ok(tris_dev, T, cam)) return VSR_ERR_INVALID_ARG;
+    return scene_setup(sc, tris_dev, T, cam, (cudaStream_t)stream);
+}
+
+void vsr_scene_free(vsr_scene sc)
+{
+    if (!sc) return;
+    cudaFree(sc->rec);
+    cudaFree(sc->counts);
+    cudaFree(sc->offsets);
+    cudaFree(sc->ids);
+    cudaFree(sc->tris_dev);
+    cudaFree(sc->out_dev);
+    if (sc->h_total) cudaFreeHost(sc->h_total);
+    delete sc;
+}
+
+int64_t vsr_scene_size(vsr_scene sc) { return sc ? sc->T : -1; }
+
+vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
+{
+    if (!m || !sc) return VSR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ntiles = m->tx * m->ty;
+    vsr_status s = ensure_ws(sc, ntiles);
+    if (s != VSR_OK) return s;
+    const int T = (int)sc->T;
+    sc->last_ntiles = ntiles;
+    VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_count(sc->rec, T, m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, sc->counts, st)) != VSR_OK)
+        return s;
+    if ((s = launch_scan(sc->counts, ntiles, sc->offsets, st)) != VSR_OK) return s;
+    if (sc->sized_map != m->gen || sc->sized_scene != sc->gen || sc->cap == 0) {
+        // first binning of this (map, scene) pair: size the bins once
+        VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        VSR_CUDA_TRY(cudaStreamSynchronize(st));
+        const uint32_t total = *sc->h_total;
+        if (total > sc->cap || sc->cap == 0) {
+            cudaFree(sc->ids);
+            sc->ids = nullptr;
+            sc->cap = 0;
+            uint64_t want = (uint64_t)total + total / 4 + 4096;
+            if (want > 0xffffffffull) want = 0xffffffffull;
+            if ((s = dalloc(&sc->ids, (size_t)want)) != VSR_OK) return s;
+            sc->cap = (uint32_t)want;
+        }
+        sc->sized_map = m->gen;
+        sc->sized_scene = sc->gen;
+    }
+    VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_fill(sc->rec, T, m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, sc->offsets, sc->counts,
+                             sc->ids, sc->cap, status_word(), st)) != VSR_OK)
+        return s;
+    sc->binned_map = m->gen;
+    sc->binned_scene = sc->gen;
+    return VSR_OK;
+}
+
+vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            const vsr_raster_stats* stats, void* stream)
+{
+    if (!m || !sc) return VSR_ERR_INVALID_ARG;
+    if (sc->binned_map != m->gen || sc->binned_scene != sc->gen) return VSR_ERR_INVALID_ARG;
+    return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
+                         depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
+                         stats ? (unsigned long long*)stats->n_exec_dev : nullptr,
+                         stats ? stats->n_inside_dev : nullptr, status_word(), (cudaStream_t)stream);
+}
+
+vsr_status vsr_raster_ex(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                         const vsr_raster_stats* stats, void* stream)
+{
+    vsr_status s = vsr_bin(m, sc, stream);
+    if (s != VSR_OK) return s;
+    return vsr_raster_tiles(m, sc, id_dev, depth_dev, cov_dev, stats, stream);
+}
+
+vsr_status vsr_raster(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev, void* stream)
+{
+    return vsr_raster_ex(m, sc, id_dev, depth_dev, cov_dev, nullptr, stream);
+}
+
+vsr_status vsr_scene_bin_pairs(vsr_scene sc, void* stream, int64_t* pairs)
+{
+    if (!sc || !pairs || sc->last_ntiles == 0) return VSR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + sc->last_ntiles, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st));
+    VSR_CUDA_TRY(cudaStreamSynchronize(st));
+    *pairs = *sc->h_total;
+    return VSR_OK;
+}
+
+vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int64_t T, const float cam[12],
+                           uint32_t* id_host, float* depth_host, float* cov_host, void* stream)
+{
+    if (!m || !sc || !setup_args_ok(tris_host, T, cam)) return VSR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    vsr_status s;
+    if (T > sc->tris_alloc) {
+        cudaFree(sc->tris_dev);
+        sc->tris_dev = nullptr;
+        sc->tris_alloc = 0;
+        if ((s = dalloc(&sc->tris_dev, (size_t)T * 9)) != VSR_OK) return s;
+        sc->tris_alloc = T;
+    }
+    const size_t npix = (size_t)m->p.W * m->p.H;
+    if (12 * npix > sc->out_alloc) {
+        cudaFree(sc->out_dev);
+        sc->out_dev = nullptr;
+        sc->out_alloc = 0;
+        if (cudaMalloc(&sc->out_dev, 12 * npix) != cudaSuccess) {
+            cudaGetLastError();
+            return VSR_ERR_OOM;
+        }
+        sc->out_alloc = 12 * npix;
+    }
+    uint32_t* id_d = (uint32_t*)sc->out_dev;
+    float* depth_d = (float*)((char*)sc->out_dev + 4 * npix);
+    float* cov_d = (float*)((char*)sc->out_dev + 8 * npix);
+    if (T > 0)
+        VSR_CUDA_TRY(cudaMemcpyAsync(sc->tris_dev, tris_host, sizeof(float) * 9 * (size_t)T, cudaMemcpyHostToDevice,
+                                     st));
+    if ((s = scene_setup(sc, sc->tris_dev, T, cam, st)) != VSR_OK) return s;
+    if ((s = vsr_raster_ex(m, sc, id_host ? id_d : nullptr, depth_host ? depth_d : nullptr,
+                           cov_host ? cov_d : nullptr, nullptr, stream)) != VSR_OK)
+        return s;
+    if (id_host) VSR_CUDA_TRY(cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+    if (depth_host) VSR_CUDA_TRY(cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+    if (cov_host) VSR_CUDA_TRY(cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+    VSR_CUDA_TRY(cudaStreamSynchronize(st));
+    return VSR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// map.cu -- perspective-map generation (Universal perspective 2D->3D,
+// Sec. 2 "Transformation of 2D->3D coordinates"; global delta, Sec. 1.1.1)
+// and per-tile / per-super-tile view cones for the binner.
+//
+// One CTA per 16x16 tile.  The map function is evaluated once per pixel
+// centre of the tile plus a one-pixel halo into shared memory (18x18 = 324
+// evaluations for 256 pixels), the global delta comes from central
+// differences of those values, and the tile's view cone is reduced in the
+// same CTA, so the map is written exactly once (16 B/px, HBM-write bound).
+#include <math.h>
+
+#include "vsr_internal.cuh"
+
+namespace {
+
+struct MapP {
+    float k, l;
+    float tk;      // tan(k Omega/2)              (k > 0)
+    float sk;      // sin(k Omega/2)              (k < 0)
+    float half;    // Omega/2 in radians
+    float inv_ls;  // 1 / (l (1 - s) + s)
+    float sc;      // view-coordinate scale: x = (2i + 1 - W) sc, y = (2j + 1 - H) sc
+    int kind;      // 1: k > 0, 0: k == 0, -1: k < 0
+};
+
+// Map function at pixel centre (i, j) (may lie outside the picture).
+__device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p, float3& v)
+{
+    float x = (float)(2 * i + 1 - W) * p.sc;
+    float y = (float)(2 * j + 1 - H) * p.sc;
+    float R = sqrtf(fmaf(x, x, p.l * y * y));
+    float th, sor;
+    if (p.kind > 0) {
+        th = atanf(p.tk * R) / p.k;
+        sor = R > 0.0f ? sinf(th) / R : p.tk / p.k;
+    } else if (p.kind == 0) {
+        th = p.half * R;
+        sor = R > 0.0f ? sinf(th) / R : p.half;
+    } else {
+        float arg = p.sk * R;
+        if (arg > 1.0f || arg < -1.0f) return false;
+        th = asinf(arg) / p.k;
+        sor = R > 0.0f ? sinf(th) / R : p.sk / p.k;
+    }
+    float wx = x * sor, wy = y * sor * p.inv_ls, wz = cosf(th);
+    float inv = rsqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    // one Newton step on the reciprocal square root keeps |v| = 1 to ~1 ulp
+    float n2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+    inv = inv * fmaf(-0.5f * n2 * inv, inv, 1.5f);
+    v = make_float3(wx * inv, wy * inv, wz * inv);
+    return true;
+}
+
+// Block-wide reduction of the tile cone from per-thread (valid, G, h).
+// blockDim.x == TILE_PIX.
+__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
+{
+    __shared__ float red[4][TILE_PIX / 32];
+    __shared__ float axis_s[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float sx = valid ? G.x : 0.0f, sy = valid ? G.y : 0.0f, sz = valid ? G.z : 0.0f, cnt = valid ? 1.0f : 0.0f;
+    for (int o = 16; o; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = sx;
+        red[1][warp] = sy;
+        red[2][warp] = sz;
+        red[3][warp] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0, b = 0, c = 0, n = 0;
+        for (int w = 0; w < TILE_PIX / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            c += red[2][w];
+            n += red[3][w];
+        }
+        float len = sqrtf(a * a + b * b + c * c);
+        if (len > 1e-6f * fmaxf(n, 1.0f)) {
+            axis_s[0] = a / len;
+            axis_s[1] = b / len;
+            axis_s[2] = c / len;
+        } else {
+            axis_s[0] = 0.0f;
+            axis_s[1] = 0.0f;
+            axis_s[2] = 1.0f;
+        }
+        axis_s[3] = n;
+    }
+    __syncthreads();
+    float ax = axis_s[0], ay = axis_s[1], az = axis_s[2], n = axis_s[3];
+    float cmin = valid ? G.x * ax + G.y * ay + G.z * az : 2.0f;
+    float hmax = valid ? h : 0.0f;
+    for (int o = 16; o; o >>= 1) {
+        cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+        hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[0][warp] = cmin;
+        red[1][warp] = hmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float c = 2.0f, hh = 0.0f;
+        for (int w = 0; w < TILE_PIX / 32; ++w) {
+            c = fminf(c, red[0][w]);
+            hh = fmaxf(hh, red[1][w]);
+        }
+        // widen by a margin that covers the FP32 rounding of the dot products
+        float ca = fmaxf(-1.0f, fminf(1.0f, c - 2e-6f));
+        if (n == 0.0f) ca = 1.0f;
+        float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
+        out->c0 = make_float4(ax, ay, az, ca);
+        out->c1 = make_float4(sa, hh, n, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(TILE_PIX) map_kernel(int W, int H, MapP p, float4* __restrict__ map,
+                                                        Cone* __restrict__ tiles)
+{
+    constexpr int HW = TILE + 2;
+    __shared__ float3 sv[HW * HW];
+    __shared__ unsigned char sok[HW * HW];
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
+    for (int q = threadIdx.x; q < HW * HW; q += blockDim.x) {
+        int qi = q % HW, qj = q / HW;
+        float3 v = make_float3(0.0f, 0.0f, 0.0f);
+        bool ok = map_fn(i0 + qi, j0 + qj, W, H, p, v);
+        sv[q] = v;
+        sok[q] = ok;
+    }
+    __syncthreads();
+    const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
+    const int i = tx * TILE + li, j = ty * TILE + lj;
+    const int c = (lj + 1) * HW + (li + 1);
+    bool valid = false;
+    float3 G = make_float3(0.0f, 0.0f, 0.0f);
+    float h = 0.0f;
+    if (i < W && j < H) {
+        float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (sok[c]) {
+            const float3 vc = sv[c];
+            const int L = c - 1, Rr = c + 1, U = c - HW, D = c + HW;
+            float fw = 0.0f;
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                auto get = [&](int q) { return comp == 0 ? sv[q].x : (comp == 1 ? sv[q].y : sv[q].z); };
+                float vcc = comp == 0 ? vc.x : (comp == 1 ? vc.y : vc.z);
+                float di, dj;
+                if (sok[L] && sok[Rr])
+                    di = (get(Rr) - get(L)) * 0.5f;
+                else if (sok[Rr])
+                    di = get(Rr) - vcc;
+                else if (sok[L])
+                    di = vcc - get(L);
+                else
+                    di = 0.0f;
+                if (sok[U] && sok[D])
+                    dj = (get(D) - get(U)) * 0.5f;
+                else if (sok[D])
+                    dj = get(D) - vcc;
+                else if (sok[U])
+                    dj = vcc - get(U);
+                else
+                    dj = 0.0f;
+                fw = fmaxf(fw, fabsf(di) + fabsf(dj));
+            }
+            if (fw > 0.0f) {
+                o = make_float4(vc.x, vc.y, vc.z, 1.0f / fw);
+                valid = true;
+                G = vc;
+                h = 0.5f * fw;
+            }
+        }
+        map[(size_t)j * W + i] = o;
+    }
+    reduce_cone(valid, G, h, &tiles[ty * gridDim.x + tx]);
+}
+
+// Cones of a map supplied by the caller.
+__global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict__ map, int W, int H,
+                                                         Cone* __restrict__ tiles)
+{
+    const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
+    const int i = blockIdx.x * TILE + li, j = blockIdx.y * TILE + lj;
+    bool valid = false;
+    float3 G = make_float3(0.0f, 0.0f, 0.0f);
+    float h = 0.0f;
+    if (i < W && j < H) {
+        float4 o = map[(size_t)j * W + i];
+        if (o.w > 0.0f) {
+            valid = true;
+            G = make_float3(o.x, o.y, o.z);
+            h = 0.5f / o.w;
+        }
+    }
+    reduce_cone(valid, G, h, &tiles[blockIdx.y * gridDim.x + blockIdx.x]);
+}
+
+// One thread per super-tile: a cone holding all of its tiles' cones.
+__global__ void super_kernel(const Cone* __restrict__ tiles, int tx, int ty, Cone* __restrict__ supers, int sx, int sy)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sx * sy) return;
+    int bx = (s % sx) * SUPER, by = (s / sx) * SUPER;
+    float ax = 0, ay = 0, az = 0, n = 0, hh = 0;
+    for (int y = by; y < min(by + SUPER, ty); ++y)
+        for (int x = bx; x < min(bx + SUPER, tx); ++x) {
+            Cone c = tiles[y * tx + x];
+            float w = c.c1.z;
+            ax += w * c.c0.x;
+            ay += w * c.c0.y;
+            az += w * c.c0.z;
+            n += w;
+            hh = fmaxf(hh, c.c1.y);
+        }
+    float len = sqrtf(ax * ax + ay * ay + az * az);
+    if (len > 1e-6f * fmaxf(n, 1.0f)) {
+        ax /= len;
+        ay /= len;
+        az /= len;
+    } else {
+        ax = 0.0f;
+        ay = 0.0f;
+        az = 1.0f;
+    }
+    float amax = 0.0f;
+    for (int y = by; y < min(by + SUPER, ty); ++y)
+        for (int x = bx; x < min(bx + SUPER, tx); ++x) {
+            Cone c = tiles[y * tx + x];
+            if (c.c1.z == 0.0f) continue;
+            float d = fmaxf(-1.0f, fminf(1.0f, ax * c.c0.x + ay * c.c0.y + az * c.c0.z));
+            float a = acosf(d) + acosf(fmaxf(-1.0f, fminf(1.0f, c.c0.w)));
+            amax = fmaxf(amax, a);
+        }
+    amax += 1e-5f;
+    float ca = amax >= 3.14159265f ? -1.0f : cosf(amax);
+    float sa = amax >= 3.14159265f ? 0.0f : sinf(amax);
+    if (n == 0.0f) {
+        ca = 1.0f;
+        sa = 0.0f;
+    }
+    supers[s].c0 = make_float4(ax, ay, az, ca);
+    supers[s].c1 = make_float4(sa, hh, n, 0.0f);
+}
+
+}  // namespace
+
+vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
+                      cudaStream_t st)
+{
+    // per-map scalars, formed once in double precision and rounded to float
+    MapP p;
+    double half = (double)omega_deg * M_PI / 360.0;
+    p.k = k;
+    p.l = l;
+    p.kind = k > 0.0f ? 1 : (k < 0.0f ? -1 : 0);
+    p.tk = (float)tan((double)k * half);
+    p.sk = (float)sin((double)k * half);
+    p.half = (float)half;
+    p.inv_ls = (float)(1.0 / ((double)l * (1.0 - (double)s) + (double)s));
+    double a = (double)W / (double)H;
+    switch (aov) {
+    case VSR_AOV_DIAGONAL: p.sc = (float)(1.0 / sqrt((double)W * W + (double)H * H)); break;
+    case VSR_AOV_VERTICAL: p.sc = (float)(1.0 / H); break;
+    case VSR_AOV_H4X3: p.sc = (float)(0.75 / H); break;
+    default: p.sc = (float)(1.0 / W); break;
+    }
+    (void)a;
+    dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
+    map_kernel<<<grid, TILE_PIX, 0, st>>>(W, H, p, map, tiles);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaStream_t st)
+{
+    dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
+    cone_kernel<<<grid, TILE_PIX, 0, st>>>(map, W, H, tiles);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_super_cones(const Cone* tiles, int tx, int ty, Cone* supers, int sx, int sy, cudaStream_t st)
+{
+    int n = sx * sy;
+    super_kernel<<<(n + 127) / 128, 128, 0, st>>>(tiles, tx, ty, supers, sx, sy);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}

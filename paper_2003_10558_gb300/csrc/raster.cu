@@ -1,0 +1,270 @@
+// raster.cu -- per-tile coverage / depth / visibility kernel.
+//
+// One CTA of 256 threads per 16x16 tile; warp w covers the 8x4 pixel block
+// (w & 1, w >> 1) of the tile and each lane one pixel of it.  For every
+// pixel G (unit direction, global delta) and every triangle t of the tile's
+// bin the kernel evaluates the four plane distances of the rasterization
+// equation (Sec. 1.1.2):
+//   g_1..3 = G.n_i                   edge planes through the eye (Sec. 1.1)
+//   g_4    = (G.S-hat - cos rho)/sin rho   miter cap, in the same angular
+//            units as the edge distances, computed in the chord form
+//            (4 sin^2(rho/2) - |G - S-hat|^2 + |G|^2 - 1) / (2 sin rho),
+//            which keeps its accuracy for caps far below a pixel
+// then   fragment   iff min g_i > -1/(2 delta) and r > 0   (gbpxstep)
+//        m^f        = clamp(delta min g_i + 1/2, 0, 1)       (gpstep)
+//        r          = (A'.N-hat)/(G.N-hat)                    (Sec. 1.1.5)
+//        centre-inside iff g_1..3 >= 0 (tie rule via the normal's sign)
+// and merges front to back (Sec. 1.3).  The merge
+//   m^fc = min(m^f, 1 - m^b),  m^b = m^b + m^fc
+// equals m^b = min(1, sum m^f) by induction, independent of the order, so
+// each pixel keeps a saturating 2^-24 fixed-point sum and the 64-bit key
+// (bits(r) << 32 | t) of its nearest centre-inside triangle.
+//
+// Accuracy in FP32: every distance is re-centred on the tile's cone axis a,
+//   G.n = a.n + (G - a).n,
+// with a.n formed once per (tile, triangle) from the FP32-pair normals in a
+// compensated dot product.  The per-pixel part is a plain 3-term FMA chain
+// on |G - a| <= the tile's angular radius, so its rounding error in units of
+// the ramp is ~(tile size in pixels) x 2^-23, a few 1e-6 of coverage.
+//
+// Work culling: the triangles of a chunk are first tested lane-parallel
+// (lane j <-> triangle j) against each warp's own 8x4-pixel view cone; the
+// surviving ones are then evaluated for all 32 pixels.
+#include "df.cuh"
+#include "vsr_internal.cuh"
+
+namespace {
+
+constexpr int CHUNK = TILE_PIX;  // triangles staged per pass
+
+struct __align__(16) Stage {
+    float4 s0[CHUNK];  // S-hat.hi xyz, tie flags (bits)
+    float4 s1[CHUNK];  // sin rho, 2(1 - cos rho), 1/(2 sin rho), A'.N-hat
+    float4 s2[CHUNK];  // n1.hi xyz, a.n1
+    float4 s3[CHUNK];  // n2.hi xyz, a.n2
+    float4 s4[CHUNK];  // n3.hi xyz, a.n3
+    float4 s5[CHUNK];  // N-hat.hi xyz, a.N-hat
+    float4 s6[CHUNK];  // S-hat.lo xyz, triangle index (bits)
+};
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(TILE_PIX) raster_kernel(
+    const float4* __restrict__ map, int W, int H, const Cone* __restrict__ tiles, int tiles_x,
+    const float4* __restrict__ rec, int T, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ids,
+    uint32_t cap, uint32_t* __restrict__ out_id, float* __restrict__ out_depth, float* __restrict__ out_cov,
+    unsigned long long* __restrict__ n_alg, unsigned long long* __restrict__ n_exec, int32_t* __restrict__ n_inside,
+    int* __restrict__ status)
+{
+    __shared__ Stage st;
+    __shared__ unsigned long long red[2][TILE_PIX / 32];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+    const int py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside_img = px < W && py < H;
+
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (inside_img) g = map[(size_t)py * W + px];
+    const bool pv = g.w > 0.0f;
+    const float delta = g.w;
+    const float h = pv ? 0.5f / delta : 0.0f;
+
+    // |G|^2 - 1, error-free (TwoProd / TwoSum): the chord form of the miter
+    // distance below equals (G.S-hat - cos rho)/sin rho for any G only with
+    // this term, and FP32 map directions are unit to ~1e-7, not exactly
+    float eg = 0.0f;
+    if (pv) {
+        const df px2 = two_prod(g.x, g.x), py2 = two_prod(g.y, g.y), pz2 = two_prod(g.z, g.z);
+        const df s1 = two_sum(px2.hi, py2.hi);
+        const df s2 = two_sum(s1.hi, pz2.hi);
+        const float tail = __fadd_rn(__fadd_rn(__fadd_rn(px2.lo, py2.lo), __fadd_rn(pz2.lo, s1.lo)), s2.lo);
+        eg = __fadd_rn(__fadd_rn(s2.hi, -1.0f), tail);
+    }
+
+    const Cone tc = tiles[tile];
+    const float ax = tc.c0.x, ay = tc.c0.y, az = tc.c0.z;
+    const float dgx = g.x - ax, dgy = g.y - ay, dgz = g.z - az;
+
+    // the warp's own view cone
+    float wsx = warp_sum(pv ? g.x : 0.0f), wsy = warp_sum(pv ? g.y : 0.0f), wsz = warp_sum(pv ? g.z : 0.0f);
+    const float wcnt = warp_sum(pv ? 1.0f : 0.0f);
+    float wl = sqrtf(wsx * wsx + wsy * wsy + wsz * wsz);
+    float wax = 0.0f, way = 0.0f, waz = 1.0f;
+    if (wl > 1e-6f * fmaxf(wcnt, 1.0f)) {
+        wax = wsx / wl;
+        way = wsy / wl;
+        waz = wsz / wl;
+    }
+    float wcos = warp_min(pv ? g.x * wax + g.y * way + g.z * waz : 2.0f);
+    wcos = fmaxf(-1.0f, fminf(1.0f, wcos - 2e-6f));
+    if (wl <= 1e-6f * fmaxf(wcnt, 1.0f)) wcos = -1.0f;
+    const float wsin = sqrtf(fmaxf(0.0f, 1.0f - wcos * wcos));
+    const float wh = warp_max(h);
+    const bool warp_active = wcnt > 0.0f;
+
+    uint32_t b0 = 0, b1 = 0;
+    if (tc.c1.z > 0.0f) {
+        b0 = offsets[tile];
+        b1 = offsets[tile + 1];
+        if (b1 > cap) {
+            if (threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
+            b1 = cap;
+            b0 = min(b0, cap);
+        }
+    }
+
+    uint32_t acc = 0;
+    unsigned long long key = ~0ull;
+    uint32_t cnt_alg = 0, cnt_exec = 0;
+    int32_t cnt_in = 0;
+    const size_t TT = (size_t)T;
+
+    for (uint32_t base = b0; base < b1; base += CHUNK) {
+        const int n = (int)min((uint32_t)CHUNK, b1 - base);
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t t = ids[base + threadIdx.x];
+            if (t >= (uint32_t)T) {
+                // never produced by a completed binning: a stale or overflowed
+                // bin must not index outside the records
+                raise_status(status, VSR_ERR_BIN_OVERFLOW);
+                st.s6[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(0xffffffffu));
+            } else {
+                const float4 cp = rec[RF_CAP * TT + t];
+                const float4 cp2 = rec[RF_CAP2 * TT + t];
+                const float4 n1 = rec[RF_N1 * TT + t], n2 = rec[RF_N2 * TT + t], n3 = rec[RF_N3 * TT + t];
+                const float4 pl = rec[RF_PL * TT + t];
+                const float4 l1 = rec[RF_N1L * TT + t], l2 = rec[RF_N2L * TT + t], l3 = rec[RF_N3L * TT + t];
+                const float4 ll = rec[RF_PLL * TT + t];
+                const float c1 = dot_f_df(ax, ay, az, {{n1.x, l1.x}, {n1.y, l1.y}, {n1.z, l1.z}});
+                const float c2 = dot_f_df(ax, ay, az, {{n2.x, l2.x}, {n2.y, l2.y}, {n2.z, l2.z}});
+                const float c3 = dot_f_df(ax, ay, az, {{n3.x, l3.x}, {n3.y, l3.y}, {n3.z, l3.z}});
+                const float cN = dot_f_df(ax, ay, az, {{pl.x, ll.x}, {pl.y, ll.y}, {pl.z, ll.z}});
+                st.s0[threadIdx.x] = make_float4(cp.x, cp.y, cp.z, n1.w);
+                st.s1[threadIdx.x] = make_float4(cp2.x, cp2.y, cp2.z, pl.w);
+                st.s2[threadIdx.x] = make_float4(n1.x, n1.y, n1.z, c1);
+                st.s3[threadIdx.x] = make_float4(n2.x, n2.y, n2.z, c2);
+                st.s4[threadIdx.x] = make_float4(n3.x, n3.y, n3.z, c3);
+                st.s5[threadIdx.x] = make_float4(pl.x, pl.y, pl.z, cN);
+                st.s6[threadIdx.x] = make_float4(l1.w, l2.w, l3.w, __uint_as_float(t));
+            }
+        }
+        __syncthreads();
+        if (!warp_active) continue;
+        for (int gbase = 0; gbase < n; gbase += 32) {
+            // lane-parallel cull of 32 triangles against this warp's cone
+            bool keep = false;
+            const int jj = gbase + lane;
+            if (jj < n && __float_as_uint(st.s6[jj].w) != 0xffffffffu) {
+                const float4 a = st.s0[jj];
+                const float4 b = st.s1[jj];
+                const float cos_rho = 1.0f - 0.5f * b.y;
+                keep = cap_hits_cone(make_float3(a.x, a.y, a.z), cos_rho, b.x, make_float3(wax, way, waz), wcos, wsin,
+                                     wh);
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            while (mask) {
+                const int j = gbase + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 a = st.s0[j];
+                const float4 b = st.s1[j];
+                const float4 e = st.s6[j];
+                // miter distance, chord form
+                const float mx = (g.x - a.x) - e.x, my = (g.y - a.y) - e.y, mz = (g.z - a.z) - e.z;
+                const float q = fmaf(mx, mx, fmaf(my, my, mz * mz));
+                const float g4 = ((b.y - q) + eg) * b.z;
+                const bool p4 = pv && g4 > -h;
+                ++cnt_exec;
+                if (!__any_sync(0xffffffffu, p4)) continue;
+                cnt_alg += p4;
+                const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
+                const float g1 = fmaf(dgx, n1.x, fmaf(dgy, n1.y, fmaf(dgz, n1.z, n1.w)));
+                const float g2 = fmaf(dgx, n2.x, fmaf(dgy, n2.y, fmaf(dgz, n2.z, n2.w)));
+                const float g3 = fmaf(dgx, n3.x, fmaf(dgy, n3.y, fmaf(dgz, n3.z, n3.w)));
+                const float gm = fminf(fminf(g1, g2), fminf(g3, g4));
+                bool frag = p4 && gm > -h;
+                if (!__any_sync(0xffffffffu, frag)) continue;
+                const float4 pl = st.s5[j];
+                const float D = fmaf(dgx, pl.x, fmaf(dgy, pl.y, fmaf(dgz, pl.z, pl.w)));
+                const float r = __fdiv_rn(b.w, D);
+                frag = frag && r > 0.0f && r < INFINITY;
+                if (frag) {
+                    const float m = __saturatef(fmaf(gm, delta, 0.5f));
+                    acc = min(acc + __float2uint_rn(m * 16777216.0f), 16777216u);
+                    const unsigned ties = __float_as_uint(a.w);
+                    const bool in1 = g1 > 0.0f || (g1 == 0.0f && (ties & 1u));
+                    const bool in2 = g2 > 0.0f || (g2 == 0.0f && (ties & 2u));
+                    const bool in3 = g3 > 0.0f || (g3 == 0.0f && (ties & 4u));
+                    if (in1 && in2 && in3) {
+                        const unsigned long long k =
+                            ((unsigned long long)__float_as_uint(r) << 32) | (unsigned long long)__float_as_uint(e.w);
+                        key = k < key ? k : key;
+                        ++cnt_in;
+                    }
+                }
+            }
+        }
+    }
+
+    if (inside_img) {
+        const size_t o = (size_t)py * W + px;
+        const bool hit = key != ~0ull;
+        if (out_id) out_id[o] = hit ? (uint32_t)(key & 0xffffffffull) : 0xffffffffu;
+        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
+        if (out_cov) out_cov[o] = (float)acc * (1.0f / 16777216.0f);
+        if (n_inside) n_inside[o] = cnt_in;
+    }
+    if (n_alg || n_exec) {
+        // cnt_exec counts warp-level evaluations: one per (warp, triangle) for 32 pixels
+        unsigned long long va = cnt_alg, ve = lane == 0 ? (unsigned long long)cnt_exec * 32ull : 0ull;
+        for (int o = 16; o; o >>= 1) {
+            va += __shfl_xor_sync(0xffffffffu, va, o);
+            ve += __shfl_xor_sync(0xffffffffu, ve, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = va;
+            red[1][warp] = ve;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long sa = 0, se = 0;
+            for (int w = 0; w < TILE_PIX / 32; ++w) {
+                sa += red[0][w];
+                se += red[1][w];
+            }
+            if (n_alg) atomicAdd(n_alg, sa);
+            if (n_exec) atomicAdd(n_exec, se);
+        }
+    }
+}
+
+}  // namespace
+
+vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
+                         const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
+                         float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
+                         int* status, cudaStream_t st)
+{
+    const int tx = (W + TILE - 1) / TILE, ty = (H + TILE - 1) / TILE;
+    raster_kernel<<<tx * ty, TILE_PIX, 0, st>>>(map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov,
+                                                 n_alg, n_exec, n_inside, status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}

@@ -1,0 +1,167 @@
+// setup.cu -- per-triangle set-up in FP32-pair arithmetic.
+//
+// For each world-space triangle ABC and camera (O, M):
+//   A' = M (A - O)                                 camera space (exact pairs)
+//   edge-plane normals  n_AB = s ||A' x B'||, n_BC, n_CA          (Sec. 1.1)
+//     with s = sign(A'.(B' x C')) so the triangle is on the positive side of
+//     all three (two-sided triangles), and each edge's cross product taken
+//     with its vertices in a canonical order (the lexicographic order of the
+//     FP32 bit patterns of the world coordinates) and negated when the
+//     triangle lists them the other way -- neighbours sharing an edge get
+//     bit-for-bit opposite normals, which makes the centre test watertight.
+//   miter cap: smallest circle over the projected vertices   (Sec. 1.1.2)
+//     a^2 = |B-C|^2, b^2 = |C-A|^2, c^2 = |A-B|^2 of the unit vertices,
+//     O_s = a^2(b^2+c^2-a^2), O_t = b^2(c^2+a^2-b^2), O_p = c^2(a^2+b^2-c^2),
+//     S = midpoint of the side opposite the first non-positive O, else the
+//     circumcentre (O_s A + O_t B + O_p C)/(O_s + O_t + O_p);
+//     kept as S-hat, cos rho = |S|, sin rho, 2(1 - cos rho), 1/(2 sin rho).
+//   plane: N = (A'-B') x (C'-B') (Sec. 1.1.5), kept as N-hat and A'.N-hat.
+// Culled: a vertex at the eye, A'.(B' x C') = 0, or sin rho = 0.
+//
+// Everything is FP32 arithmetic; the pairs (Dekker / Knuth error-free
+// transformations, see df.cuh) keep the normals accurate to ~2^-44 so that the
+// anti-aliasing ramp, whose slope is the global delta (hundreds per radian),
+// is placed to ~1e-6 of a pixel.
+#include "df.cuh"
+#include "vsr_internal.cuh"
+
+namespace {
+
+struct Cam {
+    float O[3];
+    float M[9];
+};
+
+__device__ __forceinline__ bool vless(const float* P, const float* Q)
+{
+    for (int c = 0; c < 3; ++c) {
+        unsigned a = __float_as_uint(P[c]), b = __float_as_uint(Q[c]);
+        if (a != b) return a < b;
+    }
+    return false;
+}
+
+__device__ __forceinline__ df3 normalize3(df3 v)
+{
+    df len = df_sqrt(df_dot(v, v));
+    return df3_div(v, len);
+}
+
+__device__ __forceinline__ df3 edge_normal(const float* Pw, const float* Qw, const df3& P, const df3& Q, bool flip)
+{
+    df3 x;
+    if (vless(Qw, Pw))
+        x = df3_neg(df_cross(Q, P));
+    else
+        x = df_cross(P, Q);
+    df3 n = normalize3(x);
+    return flip ? df3_neg(n) : n;
+}
+
+__device__ __forceinline__ unsigned first_positive(const df3& n)
+{
+    if (n.x.hi != 0.0f) return n.x.hi > 0.0f;
+    if (n.y.hi != 0.0f) return n.y.hi > 0.0f;
+    return n.z.hi > 0.0f;
+}
+
+__global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tris, int T, Cam cam,
+                                                     float4* __restrict__ rec)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    float w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = tris[(size_t)t * 9 + q];
+
+    df3 V[3];
+    bool at_eye = false;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        df d0 = two_sum(w[3 * q + 0], -cam.O[0]);
+        df d1 = two_sum(w[3 * q + 1], -cam.O[1]);
+        df d2 = two_sum(w[3 * q + 2], -cam.O[2]);
+        df c[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            c[r] = df_add(df_add(df_mul_f(d0, cam.M[3 * r + 0]), df_mul_f(d1, cam.M[3 * r + 1])),
+                          df_mul_f(d2, cam.M[3 * r + 2]));
+        V[q] = {c[0], c[1], c[2]};
+        at_eye |= (c[0].hi == 0.0f && c[1].hi == 0.0f && c[2].hi == 0.0f);
+    }
+    df det = df_dot(V[0], df_cross(V[1], V[2]));
+
+    const size_t TT = (size_t)T;
+    float4 invalid = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (at_eye || det.hi == 0.0f || !isfinite(det.hi)) {
+#pragma unroll
+        for (int f = 0; f < REC_F; ++f) rec[f * TT + t] = invalid;
+        return;
+    }
+    const bool flip = det.hi < 0.0f;
+    df3 n1 = edge_normal(w + 0, w + 3, V[0], V[1], flip);
+    df3 n2 = edge_normal(w + 3, w + 6, V[1], V[2], flip);
+    df3 n3 = edge_normal(w + 6, w + 0, V[2], V[0], flip);
+
+    // miter: smallest circle over the unit vertices
+    df3 U0 = normalize3(V[0]), U1 = normalize3(V[1]), U2 = normalize3(V[2]);
+    df3 ea = df3_sub(U1, U2), eb = df3_sub(U2, U0), ec = df3_sub(U0, U1);
+    df a2 = df_dot(ea, ea), b2 = df_dot(eb, eb), c2 = df_dot(ec, ec);
+    df Os = df_mul(a2, df_sub(df_add(b2, c2), a2));
+    df Ot = df_mul(b2, df_sub(df_add(c2, a2), b2));
+    df Op = df_mul(c2, df_sub(df_add(a2, b2), c2));
+    df3 S;
+    const df half = df_make(0.5f);
+    if (Os.hi <= 0.0f)
+        S = df3_scale(df3_add(U1, U2), half);
+    else if (Ot.hi <= 0.0f)
+        S = df3_scale(df3_add(U2, U0), half);
+    else if (Op.hi <= 0.0f)
+        S = df3_scale(df3_add(U0, U1), half);
+    else {
+        df3 num = df3_add(df3_add(df3_scale(U0, Os), df3_scale(U1, Ot)), df3_scale(U2, Op));
+        S = df3_div(num, df_add(df_add(Os, Ot), Op));
+    }
+    df slen = df_sqrt(df_dot(S, S));
+    df one = df_make(1.0f);
+    df omc = df_sub(one, slen);                    // 1 - cos rho
+    df sr = df_sqrt(df_mul(omc, df_add(one, slen)));  // sin rho
+    if (!(slen.hi > 0.0f) || !(sr.hi > 0.0f)) {
+#pragma unroll
+        for (int f = 0; f < REC_F; ++f) rec[f * TT + t] = invalid;
+        return;
+    }
+    df3 Sh = df3_div(S, slen);
+    float K = __fmul_rn(2.0f, omc.hi);                   // 2 (1 - cos rho) = 4 sin^2(rho/2)
+    float inv2sr = __fdiv_rn(1.0f, __fmul_rn(2.0f, sr.hi));
+
+    // plane
+    df3 N = df_cross(df3_sub(V[0], V[1]), df3_sub(V[2], V[1]));
+    df3 Nh = normalize3(N);
+    df dN = df_dot(V[0], Nh);
+
+    unsigned ties = first_positive(n1) | (first_positive(n2) << 1) | (first_positive(n3) << 2);
+    rec[RF_CAP * TT + t] = make_float4(Sh.x.hi, Sh.y.hi, Sh.z.hi, slen.hi);
+    rec[RF_CAP2 * TT + t] = make_float4(sr.hi, K, inv2sr, 1.0f);
+    rec[RF_N1 * TT + t] = make_float4(n1.x.hi, n1.y.hi, n1.z.hi, __uint_as_float(ties));
+    rec[RF_N2 * TT + t] = make_float4(n2.x.hi, n2.y.hi, n2.z.hi, 0.0f);
+    rec[RF_N3 * TT + t] = make_float4(n3.x.hi, n3.y.hi, n3.z.hi, 0.0f);
+    rec[RF_PL * TT + t] = make_float4(Nh.x.hi, Nh.y.hi, Nh.z.hi, dN.hi);
+    rec[RF_N1L * TT + t] = make_float4(n1.x.lo, n1.y.lo, n1.z.lo, Sh.x.lo);
+    rec[RF_N2L * TT + t] = make_float4(n2.x.lo, n2.y.lo, n2.z.lo, Sh.y.lo);
+    rec[RF_N3L * TT + t] = make_float4(n3.x.lo, n3.y.lo, n3.z.lo, Sh.z.lo);
+    rec[RF_PLL * TT + t] = make_float4(Nh.x.lo, Nh.y.lo, Nh.z.lo, 0.0f);
+}
+
+}  // namespace
+
+vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st)
+{
+    if (T == 0) return VSR_OK;
+    Cam c;
+    for (int q = 0; q < 3; ++q) c.O[q] = cam[q];
+    for (int q = 0; q < 9; ++q) c.M[q] = cam[3 + q];
+    setup_kernel<<<(T + 127) / 128, 128, 0, st>>>(tris, T, c, rec);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}

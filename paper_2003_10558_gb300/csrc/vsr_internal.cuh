@@ -1,0 +1,95 @@
+// vsr_internal.cuh -- layouts and helpers shared by the kernels and the host
+// library of the visual-sphere rasterizer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vsr.h"
+
+// ---------------------------------------------------------------------------
+// Tiling.  The map is cut into TILE x TILE pixel tiles (one raster CTA each);
+// SUPER x SUPER tiles form a super-tile, the coarse level of the binner.
+constexpr int TILE = 16;
+constexpr int TILE_PIX = TILE * TILE;
+constexpr int SUPER = 8;
+
+// ---------------------------------------------------------------------------
+// Per-triangle set-up record: REC_F float4 fields stored field-major
+// (field f of triangle t at rec[f * T + t]) so that the binner reads its two
+// cap fields coalesced.
+enum {
+    RF_CAP = 0,   // (S-hat.hi xyz, cos rho)            miter cap centre and radius
+    RF_CAP2 = 1,  // (sin rho, 2(1 - cos rho), 1/(2 sin rho), valid ? 1 : 0)
+    RF_N1 = 2,    // (n_AB.hi xyz, tie flags)          edge normals, FP32 high parts
+    RF_N2 = 3,    // (n_BC.hi xyz, 0)
+    RF_N3 = 4,    // (n_CA.hi xyz, 0)
+    RF_PL = 5,    // (N-hat.hi xyz, (A'.N)/|N|)         plane for the ray-plane depth
+    RF_N1L = 6,   // (n_AB.lo xyz, S-hat.lo.x)          low parts
+    RF_N2L = 7,   // (n_BC.lo xyz, S-hat.lo.y)
+    RF_N3L = 8,   // (n_CA.lo xyz, S-hat.lo.z)
+    RF_PLL = 9,   // (N-hat.lo xyz, 0)
+    REC_F = 10
+};
+
+// tie flags in RF_N1.w (as integer bits): bit i set <=> the first nonzero
+// component of edge normal i is positive (simulation-of-simplicity rule for
+// g_i == 0 in the centre test).
+
+// ---------------------------------------------------------------------------
+// Tile cones (per tile, 2 float4):
+//   c0 = (axis xyz, cos alpha)   all valid pixel directions of the tile lie
+//                                within alpha of the axis
+//   c1 = (sin alpha, h, n_valid, 0) with h = max over valid pixels of
+//                                1/(2 delta) (the widest ramp half-width)
+// An empty tile has n_valid = 0.
+struct Cone {
+    float4 c0, c1;
+};
+
+// Device-side status word (vsr_status values; 0 = OK), one int per device
+// owned by the host library and passed to the kernels that can fail.
+__device__ __forceinline__ void raise_status(int* status, int code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Conservative test: may a cap (centre S, cos/sin of radius, enlarged by the
+// ramp half-width h measured on the miter's normalised distance) reach a
+// direction inside the cone (axis, cos/sin alpha)?
+//   fragment region of the miter:  G.S - cos rho > -h sin rho
+//   i.e. a cap of cos(beta) = cos rho - h sin rho.
+__device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin_rho, float3 axis, float cos_a,
+                                              float sin_a, float h)
+{
+    const float eps = 2e-6f;
+    float cb = cos_rho - h * sin_rho;
+    if (cb + cos_a <= eps) return true;  // alpha + beta >= pi
+    if (cb <= -1.0f) return true;
+    float sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
+    float cg = S.x * axis.x + S.y * axis.y + S.z * axis.z;
+    return cg >= cos_a * cb - sin_a * sb - eps;
+}
+
+#define VSR_CUDA_TRY(expr)                                                                                              \
+    do {                                                                                                                \
+        cudaError_t _e = (expr);                                                                                        \
+        if (_e != cudaSuccess) return VSR_ERR_CUDA;                                                                     \
+    } while (0)
+
+// Kernel launchers (defined in the .cu files, called by the host library).
+vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
+                      cudaStream_t st);
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaStream_t st);
+vsr_status launch_super_cones(const Cone* tiles, int tx, int ty, Cone* supers, int sx, int sy, cudaStream_t st);
+vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
+vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
+                            int sy, uint32_t* counts, cudaStream_t st);
+vsr_status launch_scan(const uint32_t* counts, int n, uint32_t* offsets, cudaStream_t st);
+vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
+                           int sy, const uint32_t* offsets, uint32_t* cursors, uint32_t* ids, uint32_t cap,
+                           int* status, cudaStream_t st);
+vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
+                         const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
+                         float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
+                         int* status, cudaStream_t st);

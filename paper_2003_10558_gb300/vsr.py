@@ -1,0 +1,298 @@
+"""Python binding of libvsr.so (the C ABI in include/vsr.h).
+
+Argument marshalling only: every step of the rasterizer runs in the CUDA
+kernels of libvsr.so.  PyTorch provides device memory (tensors) and streams.
+There is no CPU fallback: if the library is missing or a call fails, an
+exception is raised.
+
+Low-level functions carry the C names (vsr_make_map, vsr_setup, vsr_raster,
+...) and take raw pointers; the classes Map and Scene and the function
+raster() wrap them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvsr.so")
+
+VSR_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "tile bin overflow",
+          -5: "fragment list overflow", -6: "device wait timed out", -7: "memory budget exceeded", -8: "cancelled"}
+NO_ID = 0xFFFFFFFF
+AOV_HORIZONTAL, AOV_DIAGONAL, AOV_VERTICAL, AOV_H4X3 = 0, 1, 2, 3
+
+# every symbol include/vsr.h declares
+EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
+           "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
+           "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
+           "vsr_scene_bin_pairs",
+           "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
+
+
+class VsrError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+
+
+class MapParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_float), ("l", ctypes.c_float), ("s", ctypes.c_float), ("omega_deg", ctypes.c_float),
+                ("W", ctypes.c_int), ("H", ctypes.c_int), ("aov", ctypes.c_int), ("strict_limits", ctypes.c_int)]
+
+
+class RasterStats(ctypes.Structure):
+    _fields_ = [("n_alg_dev", ctypes.c_void_p), ("n_exec_dev", ctypes.c_void_p), ("n_inside_dev", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libvsr.so (built by paper_2003_10558_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run `python -m paper_2003_10558_gb300.build` "
+                               "(the rasterizer has no CPU fallback)")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+        P = ctypes.POINTER
+        sig = {
+            "vsr_make_map": ([f32, f32, f32, f32, i32, i32, vp, P(vp)], i32),
+            "vsr_make_map_ex": ([P(MapParams), vp, P(vp)], i32),
+            "vsr_map_from_device": ([vp, i32, i32, vp, P(vp)], i32),
+            "vsr_map_update": ([vp, P(MapParams), vp], i32),
+            "vsr_map_params_effective": ([vp, P(MapParams)], i32),
+            "vsr_map_data": ([vp, P(vp), P(i32), P(i32)], i32),
+            "vsr_map_download": ([vp, vp], i32),
+            "vsr_map_free": ([vp], None),
+            "vsr_setup": ([vp, i64, vp, vp, P(vp)], i32),
+            "vsr_scene_create": ([P(vp)], i32),
+            "vsr_scene_update": ([vp, vp, i64, vp, vp], i32),
+            "vsr_scene_free": ([vp], None),
+            "vsr_scene_size": ([vp], i64),
+            "vsr_raster": ([vp, vp, vp, vp, vp, vp], i32),
+            "vsr_raster_ex": ([vp, vp, vp, vp, vp, P(RasterStats), vp], i32),
+            "vsr_bin": ([vp, vp, vp], i32),
+            "vsr_raster_tiles": ([vp, vp, vp, vp, vp, P(RasterStats), vp], i32),
+            "vsr_scene_bin_pairs": ([vp, vp, P(i64)], i32),
+            "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+            "vsr_status_str": ([i32], ctypes.c_char_p),
+            "vsr_last_device_status": ([], i32),
+            "vsr_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def check(code, what=""):
+    if code != VSR_OK:
+        raise VsrError(code, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _cam_array(cam):
+    c = np.ascontiguousarray(np.asarray(cam, dtype=np.float32).ravel())
+    if c.size != 12:
+        raise ValueError("camera must have 12 floats: eye xyz then 3x3 rotation")
+    return c
+
+
+def last_device_status():
+    """Synchronise and return (and clear) the device-side status word."""
+    return load().vsr_last_device_status()
+
+
+class Map:
+    """A device-resident perspective map (float4 [H, W] = G xyz, delta) with
+    its tile view cones."""
+
+    def __init__(self, W, H, k, l, s, omega_deg, aov=AOV_HORIZONTAL, strict=False, stream=None, _handle=None):
+        L = load()
+        self.h = ctypes.c_void_p()
+        if _handle is not None:
+            self.h = _handle
+        else:
+            p = MapParams(k, l, s, omega_deg, W, H, aov, int(strict))
+            check(L.vsr_make_map_ex(ctypes.byref(p), _stream_ptr(stream), ctypes.byref(self.h)), "vsr_make_map_ex")
+        self._keep = None
+
+    @classmethod
+    def from_tensor(cls, xyzd, stream=None):
+        """Map from a CUDA float32 tensor [H, W, 4] (copied)."""
+        import torch
+        if not (xyzd.is_cuda and xyzd.dtype == torch.float32 and xyzd.dim() == 3 and xyzd.shape[2] == 4):
+            raise ValueError("expected a CUDA float32 tensor [H, W, 4]")
+        xyzd = xyzd.contiguous()
+        h = ctypes.c_void_p()
+        H, W = xyzd.shape[:2]
+        check(load().vsr_map_from_device(_dptr(xyzd), W, H, _stream_ptr(stream), ctypes.byref(h)),
+              "vsr_map_from_device")
+        m = cls(W, H, 0, 0, 0, 0, _handle=h)
+        m._keep = xyzd  # alive until the async copy is done
+        return m
+
+    def update(self, W, H, k, l, s, omega_deg, aov=AOV_HORIZONTAL, strict=False, stream=None):
+        p = MapParams(k, l, s, omega_deg, W, H, aov, int(strict))
+        check(load().vsr_map_update(self.h, ctypes.byref(p), _stream_ptr(stream)), "vsr_map_update")
+
+    @property
+    def shape(self):
+        W, H = ctypes.c_int(), ctypes.c_int()
+        check(load().vsr_map_data(self.h, None, ctypes.byref(W), ctypes.byref(H)), "vsr_map_data")
+        return H.value, W.value
+
+    def params(self):
+        p = MapParams()
+        check(load().vsr_map_params_effective(self.h, ctypes.byref(p)), "vsr_map_params_effective")
+        return dict(k=p.k, l=p.l, s=p.s, omega_deg=p.omega_deg, W=p.W, H=p.H, aov=p.aov, strict=p.strict_limits)
+
+    def download(self):
+        H, W = self.shape
+        out = np.empty((H, W, 4), dtype=np.float32)
+        check(load().vsr_map_download(self.h, out.ctypes.data_as(ctypes.c_void_p)), "vsr_map_download")
+        return out
+
+    def tensor(self):
+        """A torch copy of the map, [H, W, 4] float32 on the device."""
+        import torch
+        H, W = self.shape
+        return torch.from_numpy(self.download()).cuda()
+
+    def free(self):
+        if self.h:
+            load().vsr_map_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Scene:
+    """Set-up records of T triangles for one camera (device-resident)."""
+
+    def __init__(self, tris=None, cam=None, stream=None):
+        L = load()
+        self.h = ctypes.c_void_p()
+        check(L.vsr_scene_create(ctypes.byref(self.h)), "vsr_scene_create")
+        if tris is not None:
+            self.update(tris, cam, stream)
+
+    def update(self, tris, cam=None, stream=None):
+        import torch
+        if cam is None:
+            cam = [0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1]
+        if not (tris.is_cuda and tris.dtype == torch.float32):
+            raise ValueError("triangles must be a CUDA float32 tensor [T, 3, 3]")
+        tris = tris.contiguous()
+        T = tris.numel() // 9
+        c = _cam_array(cam)
+        check(load().vsr_scene_update(self.h, _dptr(tris) if T else None, T, c.ctypes.data_as(ctypes.c_void_p),
+                                      _stream_ptr(stream)), "vsr_scene_update")
+        self._keep = tris
+
+    @property
+    def T(self):
+        return int(load().vsr_scene_size(self.h))
+
+    def bin_pairs(self, stream=None):
+        n = ctypes.c_int64()
+        check(load().vsr_scene_bin_pairs(self.h, _stream_ptr(stream), ctypes.byref(n)), "vsr_scene_bin_pairs")
+        return n.value
+
+    def free(self):
+        if self.h:
+            load().vsr_scene_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def bin(m: Map, sc: Scene, stream=None):
+    """Build the tile bins of (m, sc) (vsr_bin)."""
+    check(load().vsr_bin(m.h, sc.h, _stream_ptr(stream)), "vsr_bin")
+
+
+def raster(m: Map, sc: Scene, out=None, stats=False, n_inside=False, stream=None, binned=False):
+    """Rasterize: returns dict of CUDA tensors id (int32 view of uint32),
+    depth, cov [H, W]; with stats=True also n_alg, n_exec (python ints, sync);
+    with n_inside=True the per-pixel count of centre-inside triangles.
+    binned=True reuses the bins of the last bin() call (vsr_raster_tiles)."""
+    import torch
+    H, W = m.shape
+    dev = torch.device("cuda")
+    if out is None:
+        out = {"id": torch.empty((H, W), dtype=torch.int32, device=dev),
+               "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
+    st = None
+    cnt = None
+    if stats or n_inside:
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        if n_inside:
+            out["n_inside"] = torch.empty((H, W), dtype=torch.int32, device=dev)
+        st = RasterStats(cnt.data_ptr() if stats else None, cnt.data_ptr() + 8 if stats else None,
+                         out["n_inside"].data_ptr() if n_inside else None)
+    fn = load().vsr_raster_tiles if binned else load().vsr_raster_ex
+    check(fn(m.h, sc.h, _dptr(out.get("id")), _dptr(out.get("depth")), _dptr(out.get("cov")),
+             ctypes.byref(st) if st is not None else None, _stream_ptr(stream)), "vsr_raster")
+    if stats:
+        c = cnt.cpu()
+        out["n_alg"], out["n_exec"] = int(c[0]), int(c[1])
+    return out
+
+
+def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "depth", "cov"), out=None, stream=None):
+    """End to end from host memory (vsr_render_host): numpy triangles in,
+    numpy id (uint32) / depth / cov out.  `out` may hold preallocated
+    (ideally pinned) arrays."""
+    if cam is None:
+        cam = [0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1]
+    tris = np.ascontiguousarray(tris, dtype=np.float32)
+    T = tris.size // 9
+    H, W = m.shape
+    if out is None:
+        out = {}
+        if "id" in want:
+            out["id"] = np.empty((H, W), dtype=np.uint32)
+        if "depth" in want:
+            out["depth"] = np.empty((H, W), dtype=np.float32)
+        if "cov" in want:
+            out["cov"] = np.empty((H, W), dtype=np.float32)
+    c = _cam_array(cam)
+
+    def p(a):
+        return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+    check(load().vsr_render_host(m.h, sc.h, p(tris), T, c.ctypes.data_as(ctypes.c_void_p), p(out.get("id")),
+                                 p(out.get("depth")), p(out.get("cov")), _stream_ptr(stream)), "vsr_render_host")
+    return out

@@ -1,0 +1,266 @@
+"""CUDA path versus the FP64 oracle, through the C ABI (libvsr.so).
+
+Raster parity feeds both sides the same map: the oracle's FP64 map rounded
+to FP32 once, uploaded with vsr_map_from_device (the map is an input of the
+rasterizer).  Map parity compares the GPU's own map with the oracle's.
+The end-to-end check (GPU map + GPU raster against oracle map + oracle
+raster) carries the map's rounding into coverage and is held to the looser
+bound derived from it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_10558_gb300 import scenes
+
+from _util import compare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vsr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_10558_gb300 import build, vsr as V
+    build.build()
+    V.load()
+    return V
+
+
+def _gpu_outputs(out):
+    return {"id": out["id"].cpu().numpy().view(np.uint32), "depth": out["depth"].cpu().numpy(),
+            "cov": out["cov"].cpu().numpy()}
+
+
+def _oracle_map32(lens, aov=0):
+    m64, eff = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"], aov=aov)
+    return m64.astype(np.float32), eff
+
+
+def _raster_shared_map(V, lens, tris, cam, pixels=None, stats=False):
+    m32, _ = _oracle_map32(lens)
+    gm = V.Map.from_tensor(torch.from_numpy(m32).cuda())
+    sc = V.Scene(torch.from_numpy(tris).cuda(), cam)
+    out = V.raster(gm, sc, stats=stats)
+    assert V.last_device_status() == 0
+    rec = oracle.setup(tris, cam)
+    exp = oracle.raster(m32, rec, pixels=pixels)
+    return m32, rec, exp, out
+
+
+# ---------------------------------------------------------------------------
+# map
+
+MAP_CASES = [
+    dict(W=256, H=256, k=0.0, l=1.0, s=1.0, omega=180.0),
+    dict(W=1920, H=1080, k=0.32, l=0.62, s=0.86, omega=270.0),
+    dict(W=333, H=197, k=-1.0, l=1.0, s=1.0, omega=180.0),
+    dict(W=512, H=512, k=-0.5, l=0.8, s=0.6, omega=360.0),
+    dict(W=640, H=480, k=1.0, l=1.0, s=1.0, omega=120.0),
+    dict(W=300, H=200, k=0.0, l=0.5, s=0.7, omega=360.0),
+]
+
+# FP32 map function: tan/atan/asin/sin/cos each within a few ulp, so the
+# direction is off by at most ~8 ulp of theta (<= pi): 8 * 2^-24 * pi ~ 1.5e-6.
+MAP_ANGLE_TOL = 2e-6
+# delta is a central difference of neighbouring FP32 directions ~1/delta
+# apart: relative error ~ (2 x 1.5e-6 rad) x delta, bounded below at 1e-3 for
+# the resolutions tested.
+MAP_DELTA_TOL = 2e-3
+
+
+def _asin_condition(lens, eff):
+    """For k < 0, theta = asin(sin(k Omega/2) R)/k amplifies the FP32 rounding
+    of its argument by 1/sqrt(1 - arg^2) near the rim; 1 elsewhere."""
+    W, H = lens["W"], lens["H"]
+    i, j = np.meshgrid(np.arange(W), np.arange(H))
+    x = 2 * (i + 0.5) / W - 1
+    y = (2 * (j + 0.5) / H - 1) * H / W
+    R = np.sqrt(x * x + eff[1] * y * y)
+    if eff[0] >= 0:
+        return np.ones_like(R)
+    arg = np.abs(np.sin(eff[0] * math.radians(eff[3]) / 2) * R)
+    return np.maximum(1.0, 0.25 / np.sqrt(np.maximum(1e-12, 1 - np.minimum(arg, 1) ** 2)))
+
+
+def _angle(a, b):
+    """Angle between direction fields, insensitive to their lengths."""
+    c = np.linalg.norm(np.cross(a, b), axis=-1)
+    return np.arctan2(c, (a * b).sum(-1))
+
+
+@pytest.mark.parametrize("lens", MAP_CASES, ids=lambda d: f"{d['W']}x{d['H']}k{d['k']}")
+def test_map_parity(vsr, lens):
+    gm = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    got = gm.download().astype(np.float64)
+    exp, eff = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    p = gm.params()
+    assert abs(p["omega_deg"] - eff[3]) < 1e-4 and abs(p["k"] - eff[0]) < 1e-7
+    ve, vg = exp[..., 3] > 0, got[..., 3] > 0
+    both = ve & vg
+    # validity differs only on the asin domain edge (|sin(k Omega/2) R| ~ 1)
+    assert (ve != vg).sum() <= max(2, 1e-4 * ve.size)
+    ang = _angle(exp[..., :3], got[..., :3])
+    tol = MAP_ANGLE_TOL * _asin_condition(lens, eff)
+    assert (ang - tol)[both].max() < 0, (ang / tol)[both].max()
+    assert np.abs(np.linalg.norm(got[..., :3], axis=-1) - 1)[vg].max() < 4e-7
+    rel = np.abs(got[..., 3] / np.where(both, exp[..., 3], 1.0) - 1.0)
+    assert rel[both].max() < MAP_DELTA_TOL, rel[both].max()
+    assert np.all(got[~vg] == 0.0)
+
+
+def test_map_aov_types(vsr):
+    for aov in (1, 2, 3):
+        lens = dict(W=200, H=120, k=0.32, l=0.62, s=0.86, omega=200.0)
+        gm = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"], aov=aov)
+        got = gm.download().astype(np.float64)
+        exp, _ = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"], aov=aov)
+        both = (exp[..., 3] > 0) & (got[..., 3] > 0)
+        assert _angle(exp[..., :3], got[..., :3])[both].max() < MAP_ANGLE_TOL
+
+
+# ---------------------------------------------------------------------------
+# raster, shared FP32 map
+
+def test_raster_parity_tiny(vsr):
+    """256x256 equidistant view of 64 seeded triangles, full frame."""
+    lens, tris, cam = scenes.tiny_scene()
+    m32, rec, exp, out = _raster_shared_map(vsr, lens, tris, cam, stats=True)
+    rep = compare(m32, rec, exp, _gpu_outputs(out))
+    assert out["n_alg"] == exp["n_alg"] or abs(out["n_alg"] - exp["n_alg"]) <= 1e-5 * exp["n_alg"]
+    assert rep["n_valid"] == 256 * 256
+
+
+@pytest.mark.parametrize("lens", [dict(W=333, H=197, k=-1.0, l=1.0, s=1.0, omega=180.0),
+                                  dict(W=300, H=200, k=0.0, l=0.5, s=0.7, omega=360.0),
+                                  dict(W=97, H=61, k=1.0, l=1.0, s=1.0, omega=150.0),
+                                  dict(W=1, H=1, k=0.0, l=1.0, s=1.0, omega=90.0),
+                                  dict(W=17, H=300, k=0.6, l=0.9, s=0.9, omega=250.0)],
+                         ids=["ortho-invalid-corners", "wrap360", "ragged-pinhole", "1x1", "tall"])
+def test_raster_parity_lenses(vsr, lens):
+    """Ragged tiles, invalid pixels, wrap-around beyond 180 deg, degenerate
+    sizes; scenes with small, large and near-eye triangles."""
+    tris = np.concatenate([scenes.random_triangles(150, 1.0, 10.0, 0.25, seed=5),
+                           scenes.random_triangles(150, 2.0, 30.0, 0.03, seed=6),
+                           scenes.random_triangles(5, 0.05, 0.2, 1.2, seed=7)])
+    m32, rec, exp, out = _raster_shared_map(vsr, lens, tris, scenes.camera())
+    compare(m32, rec, exp, _gpu_outputs(out))
+
+
+def test_raster_parity_camera_and_culling(vsr):
+    """Moved and rotated camera; culled triangles (vertex at the eye,
+    collinear with the eye) are never drawn."""
+    lens = dict(W=320, H=240, k=0.5, l=0.8, s=0.9, omega=220.0)
+    tris = scenes.random_triangles(400, 1.0, 10.0, 0.2, seed=12)
+    O = np.array([0.3, -0.2, 0.5], dtype=np.float32)
+    th = 0.4
+    M = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    cam = scenes.camera(O, M)
+    bad = np.array([[O, O + [1, 0, 0], O + [0, 1, 0]], [O + [1, 0, 1], O + [2, 0, 2], O + [0, 1, 3]]],
+                   dtype=np.float32)
+    tris = np.concatenate([tris, bad])
+    m32, rec, exp, out = _raster_shared_map(vsr, lens, tris, cam)
+    compare(m32, rec, exp, _gpu_outputs(out))
+    ids = out["id"].cpu().numpy().view(np.uint32)
+    assert not np.isin(ids, [len(tris) - 2, len(tris) - 1]).any()
+
+
+def test_raster_empty_scene(vsr):
+    m = vsr.Map(64, 48, 0.0, 1.0, 1.0, 180.0)
+    sc = vsr.Scene(torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda"))
+    out = vsr.raster(m, sc)
+    assert (out["id"].cpu().numpy().view(np.uint32) == 0xFFFFFFFF).all()
+    assert torch.isinf(out["depth"]).all() and (out["cov"] == 0).all()
+
+
+def test_single_view_workload_sampled(vsr):
+    """The 1920x1080 single-view workload (icosphere + 200k triangles) in the
+    launch configuration the benchmark times; the oracle checks 4096 seeded
+    pixels and a 96x96 crop one by one."""
+    lens, tris, cam = scenes.single_view_scene()
+    rng = np.random.default_rng(99)
+    W, H = lens["W"], lens["H"]
+    pix = rng.integers(0, W * H, 4096)
+    cj, ci = 500, 900
+    crop = (np.arange(cj, cj + 96)[:, None] * W + np.arange(ci, ci + 96)[None, :]).ravel()
+    pixels = np.concatenate([pix, crop])
+    m32, rec, exp, out = _raster_shared_map(vsr, lens, tris, cam, pixels=pixels)
+    rep = compare(m32, rec, exp, _gpu_outputs(out), pixels=pixels)
+    assert rep["n_valid"] == len(pixels)
+
+
+def test_watertight_icosphere_gpu_map(vsr):
+    """Level-5 icosphere around the eye on the GPU's own 1080p map: exactly
+    one centre-inside triangle per pixel, coverage 1 away from vertices."""
+    W, H = 1920, 1080
+    tris = scenes.icosphere(5, 50.0)
+    m = vsr.Map(W, H, 0.32, 0.62, 0.86, 270.0)
+    sc = vsr.Scene(torch.from_numpy(tris).cuda())
+    out = vsr.raster(m, sc, n_inside=True)
+    n_in = out["n_inside"].cpu().numpy()
+    mp = m.download().astype(np.float64)
+    valid = mp[..., 3] > 0
+    assert (n_in[valid] == 1).all(), np.unique(n_in[valid], return_counts=True)
+    cov = out["cov"].cpu().numpy()
+    verts = np.unique(tris.reshape(-1, 3), axis=0).astype(np.float64)
+    verts /= np.linalg.norm(verts, axis=1, keepdims=True)
+    # distance to the nearest vertex direction, in pixels, on a sample
+    rng = np.random.default_rng(3)
+    pick = rng.integers(0, W * H, 20000)
+    G = mp.reshape(-1, 4)[pick, :3]
+    d = np.arccos(np.clip((G @ verts.T).max(1), -1, 1)) * mp.reshape(-1, 4)[pick, 3]
+    far = d > 2.5
+    assert far.mean() > 0.3
+    assert np.abs(cov.reshape(-1)[pick][far] - 1).max() < 1e-5
+
+
+def test_end_to_end_against_oracle(vsr):
+    """GPU map + GPU raster against oracle map + oracle raster.  The map's
+    FP32 rounding (<= 2e-6 rad) moves edge distances by as much, i.e. coverage
+    by delta x 2e-6 (delta ~ 80 here), and delta's own rounding scales ramps by
+    <= 2e-3: coverage is held to 2e-3 and ids to 99.9 %."""
+    lens, tris, cam = scenes.tiny_scene()
+    m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), cam)
+    got = _gpu_outputs(vsr.raster(m, sc))
+    m64, _ = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    exp = oracle.raster(m64, oracle.setup(tris, cam))
+    assert np.abs(got["cov"] - exp["cov"]).max() < 2e-3
+    assert (got["id"] == exp["id"]).mean() > 0.999
+
+
+def test_deterministic(vsr):
+    lens, tris, cam = scenes.tiny_scene()
+    m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), cam)
+    a = _gpu_outputs(vsr.raster(m, sc))
+    b = _gpu_outputs(vsr.raster(m, sc))
+    for k in a:
+        assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32))
+
+
+def test_render_host_matches_device_path(vsr):
+    lens, tris, cam = scenes.tiny_scene()
+    m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    dev = _gpu_outputs(vsr.raster(m, vsr.Scene(torch.from_numpy(tris).cuda(), cam)))
+    work = vsr.Scene()
+    for _ in range(2):
+        host = vsr.render_host(m, work, tris, cam)
+        for k in dev:
+            assert np.array_equal(dev[k].view(np.uint32), host[k].view(np.uint32))
+
+
+def test_invalid_arguments(vsr):
+    L = vsr.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert L.vsr_make_map(float("nan"), 1, 1, 90, 64, 64, None, ctypes.byref(h)) == -1
+    assert L.vsr_make_map(0.0, 1, 1, 90, 0, 64, None, ctypes.byref(h)) == -1
+    assert L.vsr_make_map(0.0, 1, 1, 90, 64, 40000, None, ctypes.byref(h)) == -1
+    assert L.vsr_raster(None, None, None, None, None, None) == -1
+    cam = (ctypes.c_float * 12)(*([float("inf")] + [0.0] * 11))
+    assert L.vsr_setup(None, 0, cam, None, ctypes.byref(h)) == -1
+    assert L.vsr_last_device_status() == 0
