@@ -58,8 +58,8 @@ struct vsr_map_s {
     vsr_map_params p;  // effective parameters
     float4* map = nullptr;
     Cone* tiles = nullptr;
-    Cone* supers = nullptr;
-    int tx = 0, ty = 0, sx = 0, sy = 0;
+    TileIndex idx = {};
+    int tx = 0, ty = 0;
     uint64_t gen = 0;
 };
 
@@ -108,12 +108,15 @@ vsr_status map_alloc(vsr_map m, int W, int H)
 {
     m->tx = (W + TILE - 1) / TILE;
     m->ty = (H + TILE - 1) / TILE;
-    m->sx = (m->tx + SUPER - 1) / SUPER;
-    m->sy = (m->ty + SUPER - 1) / SUPER;
+    const size_t nt = (size_t)m->tx * m->ty;
     vsr_status st;
     if ((st = dalloc(&m->map, (size_t)W * H)) != VSR_OK) return st;
-    if ((st = dalloc(&m->tiles, (size_t)m->tx * m->ty)) != VSR_OK) return st;
-    if ((st = dalloc(&m->supers, (size_t)m->sx * m->sy)) != VSR_OK) return st;
+    if ((st = dalloc(&m->tiles, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.hdr, 1)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.cell_start, (size_t)IDX_CELLS_MAX + 1)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.cell_tiles, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.big_tiles, nt)) != VSR_OK) return st;
     return VSR_OK;
 }
 
@@ -122,9 +125,14 @@ void map_release(vsr_map m)
     if (!m) return;
     cudaFree(m->map);
     cudaFree(m->tiles);
-    cudaFree(m->supers);
+    cudaFree(m->idx.hdr);
+    cudaFree(m->idx.cell_count);
+    cudaFree(m->idx.cell_start);
+    cudaFree(m->idx.cell_tiles);
+    cudaFree(m->idx.big_tiles);
     m->map = nullptr;
-    m->tiles = m->supers = nullptr;
+    m->tiles = nullptr;
+    m->idx = TileIndex{};
 }
 
 bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 32768 && H <= 32768; }
@@ -142,7 +150,7 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
     vsr_status s = launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles, st);
     if (s != VSR_OK) return s;
-    s = launch_super_cones(m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, st);
+    s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     m->gen = g_gen.fetch_add(1);
     return s;
 }
@@ -276,7 +284,7 @@ vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream
                                        st) != cudaSuccess)
         s = VSR_ERR_CUDA;
     if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, st);
-    if (s == VSR_OK) s = launch_super_cones(m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, st);
+    if (s == VSR_OK) s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     if (s != VSR_OK) {
         map_release(m);
         delete m;
@@ -391,9 +399,8 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     const int T = (int)sc->T;
     sc->last_ntiles = ntiles;
     VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_count(sc->rec, T, m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, sc->counts, st)) != VSR_OK)
-        return s;
-    if ((s = launch_scan(sc->counts, ntiles, sc->offsets, st)) != VSR_OK) return s;
+    if ((s = launch_bin_count(sc->rec, T, m->tiles, m->idx, sc->counts, st)) != VSR_OK) return s;
+    if ((s = launch_scan(sc->counts, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
     if (sc->sized_map != m->gen || sc->sized_scene != sc->gen || sc->cap == 0) {
         // first binning of this (map, scene) pair: size the bins once
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -412,8 +419,8 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->sized_scene = sc->gen;
     }
     VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_fill(sc->rec, T, m->tiles, m->tx, m->ty, m->supers, m->sx, m->sy, sc->offsets, sc->counts,
-                             sc->ids, sc->cap, status_word(), st)) != VSR_OK)
+    if ((s = launch_bin_fill(sc->rec, T, m->tiles, m->idx, sc->offsets, sc->counts, sc->ids, sc->cap, status_word(),
+                             st)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;

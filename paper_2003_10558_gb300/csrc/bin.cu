@@ -3,120 +3,278 @@
 //
 // A fragment of triangle t at pixel direction G needs G inside the miter
 // cap enlarged by the ramp half-width (the gbpxstep test of the miter plane,
-// Sec. 1.1.1/1.1.2): G.S-hat - cos rho > -h sin rho, h = 1/(2 delta).  The
+// Sec. 1.1.1 / 1.1.2): G.S-hat - cos rho > -h sin rho, h = 1/(2 delta).  The
 // binner keeps (tile, t) when that enlarged cap can reach the tile's view
-// cone (cap_hits_cone), first against 8x8-tile super-tiles, then against
-// the tiles of each super-tile that was hit.  The paper's analogue is the
-// low-resolution region mask widened by fwidth/2 (getPolygonRegion).
+// cone (cap_hits_cone).  The paper's analogue is the low-resolution region
+// mask widened by fwidth/2 (getPolygonRegion).
 //
-// count (one thread per triangle, atomic per-tile counters) -> exclusive
-// scan -> fill (atomic per-tile cursors).  The order of ids inside a bin is
-// not fixed; the raster kernel's result does not depend on it.
+// The candidate tiles of a triangle come from the map's tile index (a
+// latitude-longitude grid of the view sphere in which every tile is filed
+// once, see TileIndexHdr): only the cells within beta + alpha_small_max of
+// the cap centre are visited, so the work per triangle is a few dozen cone
+// tests whatever the map's size, and no tile is found twice.
+//
+// Per frame: count (one thread per triangle, atomic per-tile counters) ->
+// exclusive scan -> fill (atomic per-tile cursors).  The order of ids inside
+// a bin is not fixed; the raster kernel's result does not depend on it.
+#include <math.h>
+
 #include "vsr_internal.cuh"
 
 namespace {
 
+constexpr float PI_F = 3.14159265358979f;
+
+__device__ __forceinline__ int hist_bin(float a)
+{
+    // third-of-an-octave bins from 2^-17 rad
+    int b = (int)floorf((log2f(fmaxf(a, 1e-30f)) + 17.0f) * 3.0f);
+    return min(IDX_HIST - 1, max(0, b));
+}
+
+__device__ __forceinline__ float hist_upper(int b) { return exp2f((float)(b + 1) / 3.0f - 17.0f); }
+
+__device__ __forceinline__ float cone_half_angle(const Cone& c) { return acosf(fmaxf(-1.0f, fminf(1.0f, c.c0.w))); }
+
+__device__ __forceinline__ int cell_row(float lat, const TileIndexHdr& h)
+{
+    return min(h.nlat - 1, max(0, (int)floorf((lat + 0.5f * PI_F) / h.cell)));
+}
+
+__device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
+{
+    int c = (int)floorf((lon + PI_F) / h.cell);
+    c %= h.nlon;
+    return c < 0 ? c + h.nlon : c;
+}
+
+__device__ __forceinline__ int home_cell(float3 a, const TileIndexHdr& h)
+{
+    float lat = asinf(fmaxf(-1.0f, fminf(1.0f, a.y)));
+    float lon = atan2f(a.x, a.z);
+    return cell_row(lat, h) * h.nlon + cell_col(lon, h);
+}
+
+// ---- tile index -------------------------------------------------------------
+
+__global__ void idx_hist_kernel(const Cone* __restrict__ tiles, int ntiles, TileIndexHdr* hdr)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntiles) return;
+    Cone c = tiles[i];
+    if (c.c1.z == 0.0f) return;
+    atomicAdd(&hdr->hist[hist_bin(cone_half_angle(c))], 1u);
+    atomicAdd(&hdr->n_valid, 1u);
+    atomicMax(&hdr->h_max, __float_as_uint(c.c1.y));  // non-negative floats order as their bits
+}
+
+// one thread: grid size and small / big threshold from the 99th percentile
+// of tile half-angles
+__global__ void idx_plan_kernel(TileIndexHdr* hdr)
+{
+    unsigned target = (unsigned)ceilf(0.99f * (float)hdr->n_valid), run = 0;
+    int b = 0;
+    for (; b < IDX_HIST; ++b) {
+        run += hdr->hist[b];
+        if (run >= target) break;
+    }
+    float cut = hist_upper(min(b, IDX_HIST - 1));
+    float cell = fminf(PI_F / 8.0f, fmaxf(PI_F / IDX_NLAT_MAX, cut));
+    int nlat = min(IDX_NLAT_MAX, (int)ceilf(PI_F / cell));
+    hdr->nlat = nlat;
+    hdr->nlon = 2 * nlat;
+    hdr->ncell = nlat * 2 * nlat;
+    hdr->cell = PI_F / nlat;
+    hdr->alpha_cut = cut;
+}
+
+__global__ void idx_count_kernel(const Cone* __restrict__ tiles, int ntiles, TileIndexHdr* hdr,
+                                 uint32_t* __restrict__ cell_count, uint32_t* __restrict__ big)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntiles) return;
+    Cone c = tiles[i];
+    if (c.c1.z == 0.0f) return;
+    const TileIndexHdr h = *hdr;
+    float a = cone_half_angle(c);
+    if (a > h.alpha_cut) {
+        big[atomicAdd(&hdr->n_big, 1u)] = (uint32_t)i;
+    } else {
+        atomicAdd(&cell_count[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u);
+        atomicMax(&hdr->alpha_small_max, __float_as_uint(a));
+    }
+}
+
+__global__ void idx_fill_kernel(const Cone* __restrict__ tiles, int ntiles, const TileIndexHdr* hdr,
+                                const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ cursor,
+                                uint32_t* __restrict__ cell_tiles)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntiles) return;
+    Cone c = tiles[i];
+    if (c.c1.z == 0.0f) return;
+    const TileIndexHdr h = *hdr;
+    if (cone_half_angle(c) > h.alpha_cut) return;
+    int cell = home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h);
+    cell_tiles[cell_start[cell] + atomicAdd(&cursor[cell], 1u)] = (uint32_t)i;
+}
+
+// ---- per-triangle binning ---------------------------------------------------
+
 template <bool FILL>
 __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec, int T, const Cone* __restrict__ tiles,
-                                                   int tx, int ty, const Cone* __restrict__ supers, int sx, int sy,
+                                                   const TileIndexHdr* __restrict__ hdr,
+                                                   const uint32_t* __restrict__ cell_start,
+                                                   const uint32_t* __restrict__ cell_tiles,
+                                                   const uint32_t* __restrict__ big_tiles,
                                                    uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
                                                    uint32_t* __restrict__ ids, uint32_t cap, int* status)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const size_t TT = (size_t)T;
-    float4 c0 = rec[RF_CAP * TT + t];
-    float4 c1 = rec[RF_CAP2 * TT + t];
+    const float4 c0 = rec[RF_CAP * TT + t];
+    const float4 c1 = rec[RF_CAP2 * TT + t];
     if (c1.w == 0.0f) return;  // culled
     const float3 S = make_float3(c0.x, c0.y, c0.z);
     const float cr = c0.w, sr = c1.x;
-    for (int s = 0; s < sx * sy; ++s) {
-        Cone sc = supers[s];
-        if (sc.c1.z == 0.0f) continue;
-        if (!cap_hits_cone(S, cr, sr, make_float3(sc.c0.x, sc.c0.y, sc.c0.z), sc.c0.w, sc.c1.x, sc.c1.y)) continue;
-        int bx = (s % sx) * SUPER, by = (s / sx) * SUPER;
-        int ex = min(bx + SUPER, tx), ey = min(by + SUPER, ty);
-        for (int y = by; y < ey; ++y)
-            for (int x = bx; x < ex; ++x) {
-                int tile = y * tx + x;
-                Cone c = tiles[tile];
-                if (c.c1.z == 0.0f) continue;
-                if (!cap_hits_cone(S, cr, sr, make_float3(c.c0.x, c.c0.y, c.c0.z), c.c0.w, c.c1.x, c.c1.y)) continue;
-                if (!FILL) {
-                    atomicAdd(&counts[tile], 1u);
-                } else {
-                    uint32_t slot = atomicAdd(&counts[tile], 1u);
-                    uint32_t pos = offsets[tile] + slot;
-                    if (pos < cap && pos < offsets[tile + 1])
-                        ids[pos] = (uint32_t)t;
-                    else
-                        raise_status(status, VSR_ERR_BIN_OVERFLOW);
-                }
-            }
+    const TileIndexHdr& h = *hdr;
+    const int nlat = h.nlat, nlon = h.nlon;
+    const float cell = h.cell;
+    const float amax = __uint_as_float(h.alpha_small_max), hmax = __uint_as_float(h.h_max);
+
+    auto visit = [&](uint32_t tile) {
+        const Cone c = tiles[tile];
+        if (!cap_hits_cone(S, cr, sr, make_float3(c.c0.x, c.c0.y, c.c0.z), c.c0.w, c.c1.x, c.c1.y)) return;
+        if (!FILL) {
+            atomicAdd(&counts[tile], 1u);
+        } else {
+            uint32_t pos = offsets[tile] + atomicAdd(&counts[tile], 1u);
+            if (pos < cap && pos < offsets[tile + 1])
+                ids[pos] = (uint32_t)t;
+            else
+                raise_status(status, VSR_ERR_BIN_OVERFLOW);
+        }
+    };
+
+    // search radius: enlarged cap (widest ramp of the map) + largest small tile
+    const float cb = fmaxf(-1.0f, fminf(1.0f, cr - hmax * sr));
+    const float gamma = acosf(cb) + amax + 1e-4f;
+    int r0 = 0, r1 = nlat - 1, c0i = 0, ncol = nlon;
+    if (gamma < PI_F) {
+        const float lat = asinf(fmaxf(-1.0f, fminf(1.0f, S.y)));
+        const float lon = atan2f(S.x, S.z);
+        r0 = cell_row(lat - gamma, h);
+        r1 = cell_row(lat + gamma, h);
+        if (fabsf(lat) + gamma < 0.5f * PI_F - 1e-3f) {
+            // longitude half-width of a cap that holds no pole
+            const float dl = asinf(fminf(1.0f, sinf(gamma) / cosf(lat))) + 1e-4f;
+            c0i = (int)floorf((lon - dl + PI_F) / cell);
+            const int c1i = (int)floorf((lon + dl + PI_F) / cell);
+            ncol = min(nlon, c1i - c0i + 1);
+        }
     }
+    for (int r = r0; r <= r1; ++r)
+        for (int q = 0; q < ncol; ++q) {
+            int col = (c0i + q) % nlon;
+            if (col < 0) col += nlon;
+            const int cidx = r * nlon + col;
+            const uint32_t e = cell_start[cidx + 1];
+            for (uint32_t k = cell_start[cidx]; k < e; ++k) visit(cell_tiles[k]);
+        }
+    const uint32_t nb = h.n_big;
+    for (uint32_t k = 0; k < nb; ++k) visit(big_tiles[k]);
 }
 
-// Exclusive scan of n counts into offsets[0..n] by one CTA of 1024 threads,
-// each owning a contiguous segment.
-__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__ counts, int n,
-                                                     uint32_t* __restrict__ offsets)
+// Exclusive scan of n counts into offsets[0..n] by one CTA of 1024 threads:
+// chunks of 4096 (four consecutive elements per thread), carried across
+// chunks.  n comes from n_dev when it is not NULL.
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__ counts, int n_host,
+                                                     const int* __restrict__ n_dev, uint32_t* __restrict__ offsets)
 {
     __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry_s;
+    const int n = n_dev ? *n_dev : n_host;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + blockDim.x - 1) / blockDim.x;
-    const int b = min(n, tid * per), e = min(n, b + per);
-    uint32_t local = 0;
-    for (int q = b; q < e; ++q) local += counts[q];
-    uint32_t x = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
+    if (tid == 0) carry_s = 0;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t s = warp_sums[lane];
+    for (int base = 0; base < n; base += 4096) {
+        const int b = base + 4 * tid;
+        uint32_t v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = b + q < n ? counts[b + q] : 0u;
+        const uint32_t local = v[0] + v[1] + v[2] + v[3];
+        uint32_t x = local;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        warp_sums[lane] = s;
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        uint32_t run = carry_s + x - local + (warp > 0 ? warp_sums[warp - 1] : 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (b + q < n) offsets[b + q] = run;
+            run += v[q];
+        }
+        __syncthreads();
+        if (tid == 0) carry_s += warp_sums[31];
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = x - local + (warp > 0 ? warp_sums[warp - 1] : 0u);
-    for (int q = b; q < e; ++q) {
-        offsets[q] = run;
-        run += counts[q];
-    }
-    if (tid == blockDim.x - 1) offsets[n] = warp_sums[31];
+    if (tid == 0) offsets[n] = carry_s;
 }
 
 }  // namespace
 
-vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
-                            int sy, uint32_t* counts, cudaStream_t st)
+vsr_status launch_scan(const uint32_t* counts, int n, const int* n_dev, uint32_t* offsets, cudaStream_t st)
 {
-    if (T == 0) return VSR_OK;
-    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, tx, ty, supers, sx, sy, counts, nullptr, nullptr,
-                                                       0, nullptr);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, n, n_dev, offsets);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_scan(const uint32_t* counts, int n, uint32_t* offsets, cudaStream_t st)
+vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
-    scan_kernel<<<1, 1024, 0, st>>>(counts, n, offsets);
+    const int nb = (ntiles + 255) / 256;
+    VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
+    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
+    idx_hist_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr);
+    idx_plan_kernel<<<1, 1, 0, st>>>(idx.hdr);
+    idx_count_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_count, idx.big_tiles);
+    VSR_CUDA_TRY(cudaGetLastError());
+    vsr_status s = launch_scan(idx.cell_count, 0, &idx.hdr->ncell, idx.cell_start, st);
+    if (s != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
+    idx_fill_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.cell_tiles);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
-                           int sy, const uint32_t* offsets, uint32_t* cursors, uint32_t* ids, uint32_t cap,
-                           int* status, cudaStream_t st)
+vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, TileIndex idx, uint32_t* counts,
+                            cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, tx, ty, supers, sx, sy, cursors, offsets, ids,
-                                                      cap, status);
+    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, idx.hdr, idx.cell_start, idx.cell_tiles,
+                                                       idx.big_tiles, counts, nullptr, nullptr, 0, nullptr);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, TileIndex idx, const uint32_t* offsets,
+                           uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st)
+{
+    if (T == 0) return VSR_OK;
+    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, idx.hdr, idx.cell_start, idx.cell_tiles,
+                                                      idx.big_tiles, cursors, offsets, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

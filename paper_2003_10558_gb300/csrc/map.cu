@@ -1,6 +1,6 @@
 // map.cu -- perspective-map generation (Universal perspective 2D->3D,
 // Sec. 2 "Transformation of 2D->3D coordinates"; global delta, Sec. 1.1.1)
-// and per-tile / per-super-tile view cones for the binner.
+// and the per-tile view cones used by the binner.
 //
 // One CTA per 16x16 tile.  The map function is evaluated once per pixel
 // centre of the tile plus a one-pixel halo into shared memory (18x18 = 324
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(TILE_PIX) map_kernel(int W, int H, MapP p, flo
                 o = make_float4(vc.x, vc.y, vc.z, 1.0f / fw);
                 valid = true;
                 G = vc;
-                h = 0.5f * fw;
+                h = 0.5f / o.w;  // exactly the raster kernel's ramp half-width
             }
         }
         map[(size_t)j * W + i] = o;
@@ -202,53 +202,6 @@ __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict
         }
     }
     reduce_cone(valid, G, h, &tiles[blockIdx.y * gridDim.x + blockIdx.x]);
-}
-
-// One thread per super-tile: a cone holding all of its tiles' cones.
-__global__ void super_kernel(const Cone* __restrict__ tiles, int tx, int ty, Cone* __restrict__ supers, int sx, int sy)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= sx * sy) return;
-    int bx = (s % sx) * SUPER, by = (s / sx) * SUPER;
-    float ax = 0, ay = 0, az = 0, n = 0, hh = 0;
-    for (int y = by; y < min(by + SUPER, ty); ++y)
-        for (int x = bx; x < min(bx + SUPER, tx); ++x) {
-            Cone c = tiles[y * tx + x];
-            float w = c.c1.z;
-            ax += w * c.c0.x;
-            ay += w * c.c0.y;
-            az += w * c.c0.z;
-            n += w;
-            hh = fmaxf(hh, c.c1.y);
-        }
-    float len = sqrtf(ax * ax + ay * ay + az * az);
-    if (len > 1e-6f * fmaxf(n, 1.0f)) {
-        ax /= len;
-        ay /= len;
-        az /= len;
-    } else {
-        ax = 0.0f;
-        ay = 0.0f;
-        az = 1.0f;
-    }
-    float amax = 0.0f;
-    for (int y = by; y < min(by + SUPER, ty); ++y)
-        for (int x = bx; x < min(bx + SUPER, tx); ++x) {
-            Cone c = tiles[y * tx + x];
-            if (c.c1.z == 0.0f) continue;
-            float d = fmaxf(-1.0f, fminf(1.0f, ax * c.c0.x + ay * c.c0.y + az * c.c0.z));
-            float a = acosf(d) + acosf(fmaxf(-1.0f, fminf(1.0f, c.c0.w)));
-            amax = fmaxf(amax, a);
-        }
-    amax += 1e-5f;
-    float ca = amax >= 3.14159265f ? -1.0f : cosf(amax);
-    float sa = amax >= 3.14159265f ? 0.0f : sinf(amax);
-    if (n == 0.0f) {
-        ca = 1.0f;
-        sa = 0.0f;
-    }
-    supers[s].c0 = make_float4(ax, ay, az, ca);
-    supers[s].c1 = make_float4(sa, hh, n, 0.0f);
 }
 
 }  // namespace
@@ -288,10 +241,3 @@ vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaSt
     return VSR_OK;
 }
 
-vsr_status launch_super_cones(const Cone* tiles, int tx, int ty, Cone* supers, int sx, int sy, cudaStream_t st)
-{
-    int n = sx * sy;
-    super_kernel<<<(n + 127) / 128, 128, 0, st>>>(tiles, tx, ty, supers, sx, sy);
-    VSR_CUDA_TRY(cudaGetLastError());
-    return VSR_OK;
-}

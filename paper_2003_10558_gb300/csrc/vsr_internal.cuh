@@ -8,11 +8,9 @@
 #include "../../include/vsr.h"
 
 // ---------------------------------------------------------------------------
-// Tiling.  The map is cut into TILE x TILE pixel tiles (one raster CTA each);
-// SUPER x SUPER tiles form a super-tile, the coarse level of the binner.
+// Tiling.  The map is cut into TILE x TILE pixel tiles (one raster CTA each).
 constexpr int TILE = 16;
 constexpr int TILE_PIX = TILE * TILE;
-constexpr int SUPER = 8;
 
 // ---------------------------------------------------------------------------
 // Per-triangle set-up record: REC_F float4 fields stored field-major
@@ -45,6 +43,32 @@ enum {
 // An empty tile has n_valid = 0.
 struct Cone {
     float4 c0, c1;
+};
+
+// ---------------------------------------------------------------------------
+// Tile index of a map: a latitude-longitude grid over the view sphere
+// (latitude = asin(y), longitude = atan2(x, z), so the grid's poles are the
+// camera's +-y axis).  Every tile whose cone half-angle is at most alpha_cut
+// is filed once, in the cell holding its axis; larger ("big") tiles are kept
+// in a separate list that every triangle scans.  A triangle whose enlarged
+// cap has angular radius beta can only reach small tiles whose axis lies
+// within beta + alpha_small_max of the cap centre, i.e. in a small
+// latitude/longitude window of cells.  Grid size and alpha_cut are chosen on
+// the device from the distribution of tile half-angles.
+constexpr int IDX_NLAT_MAX = 128;
+constexpr int IDX_CELLS_MAX = IDX_NLAT_MAX * 2 * IDX_NLAT_MAX;
+constexpr int IDX_HIST = 64;
+
+struct TileIndexHdr {
+    int nlat, nlon;             // grid: nlon = 2 nlat, square cells of `cell` radians
+    int ncell;                  // nlat * nlon
+    float cell;
+    float alpha_cut;            // small / big tile threshold (radians)
+    unsigned alpha_small_max;   // float bits: largest half-angle of a small tile
+    unsigned h_max;             // float bits: largest ramp half-width 1/(2 delta)
+    unsigned n_big;
+    unsigned n_valid;
+    unsigned hist[IDX_HIST];    // third-of-an-octave histogram of half-angles
 };
 
 // Device-side status word (vsr_status values; 0 = OK), one int per device
@@ -81,14 +105,22 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
                       cudaStream_t st);
 vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaStream_t st);
-vsr_status launch_super_cones(const Cone* tiles, int tx, int ty, Cone* supers, int sx, int sy, cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
-vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
-                            int sy, uint32_t* counts, cudaStream_t st);
-vsr_status launch_scan(const uint32_t* counts, int n, uint32_t* offsets, cudaStream_t st);
-vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, int tx, int ty, const Cone* supers, int sx,
-                           int sy, const uint32_t* offsets, uint32_t* cursors, uint32_t* ids, uint32_t cap,
-                           int* status, cudaStream_t st);
+
+// Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
+struct TileIndex {
+    TileIndexHdr* hdr;
+    uint32_t* cell_count;  // IDX_CELLS_MAX
+    uint32_t* cell_start;  // IDX_CELLS_MAX + 1
+    uint32_t* cell_tiles;  // ntiles
+    uint32_t* big_tiles;   // ntiles
+};
+vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
+vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, TileIndex idx, uint32_t* counts,
+                            cudaStream_t st);
+vsr_status launch_scan(const uint32_t* counts, int n, const int* n_dev, uint32_t* offsets, cudaStream_t st);
+vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, TileIndex idx, const uint32_t* offsets,
+                           uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st);
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
