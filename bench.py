@@ -38,6 +38,9 @@ METRIC = "pixel x triangle tests/s"
 UNIT = "tests/s"
 OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
 LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
+# kernels of libvsr.so per step: map + 5 tile-index kernels (hist, plan, count,
+# scan, fill), set-up, bin count, bin scan, bin fill, raster
+LAUNCHES_PER_STEP = 11
 
 
 def parse():
@@ -203,15 +206,20 @@ def run_vsr(args, rank, world, local):
            "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(evs=None):
         m.update(W, H, lens["k"], lens["l"], lens["s"], lens["omega"])  # a1
+        if evs:
+            evs[0].record(stream)
         sc.update(tris, cam)  # a2
+        if evs:
+            evs[1].record(stream)
         V.bin(m, sc)  # a3
-        ev_r0.record(stream)
+        if evs:
+            evs[2].record(stream)
         V.raster(m, sc, out=out, binned=True)  # a4 + a5
-        ev_r1.record(stream)
+        if evs:
+            evs[3].record(stream)
 
-    ev_r0, ev_r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # algorithmic units of one step (counted once, untimed)
     V.bin(m, sc)
     st = V.raster(m, sc, stats=True)
@@ -227,24 +235,28 @@ def run_vsr(args, rank, world, local):
         dist.barrier()
 
     K = args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    r0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    r1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+
+    def evt():
+        return torch.cuda.Event(enable_timing=True)
+
+    ev0 = [evt() for _ in range(K)]
+    stage = [[evt() for _ in range(4)] for _ in range(K)]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for k in range(K):
             flush.fill_(float(k))
             ev0[k].record(stream)
-            ev_r0, ev_r1 = r0[k], r1[k]
-            step()
-            ev1[k].record(stream)
+            step(stage[k])
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     assert V.last_device_status() == 0
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    rast_ms = [a.elapsed_time(b) for a, b in zip(r0, r1)]
+    step_ms = [a.elapsed_time(s[3]) for a, s in zip(ev0, stage)]
+    rast_ms = [s[2].elapsed_time(s[3]) for s in stage]
+    stage_ms = {"map": statistics.mean(a.elapsed_time(s[0]) for a, s in zip(ev0, stage)),
+                "setup": statistics.mean(s[0].elapsed_time(s[1]) for s in stage),
+                "bin": statistics.mean(s[1].elapsed_time(s[2]) for s in stage),
+                "raster": statistics.mean(rast_ms)}
     tot_s = sum(step_ms) / 1000.0
     if world > 1:
         t = torch.tensor([tot_s], dtype=torch.float64, device=dev)
@@ -307,13 +319,14 @@ def run_vsr(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "frames_per_s": world * K / tot_s,
         "raster_kernel_ms": statistics.mean(rast_ms),
+        "stage_ms": stage_ms,
         "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32)",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "raster_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
                      f"{LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} sm_max_mhz)"},
         "clocks": clk.summary(),
-        "gpu_launches": 7 * K,
+        "gpu_launches": LAUNCHES_PER_STEP * K,
     }
     if e2e is not None:
         line["e2e"] = e2e

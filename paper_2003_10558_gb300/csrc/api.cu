@@ -74,6 +74,8 @@ struct vsr_scene_s {
     uint32_t* offsets = nullptr;
     uint32_t* ids = nullptr;
     uint32_t cap = 0;
+    uint32_t* hits = nullptr;  // per-triangle hit cache, (BIN_HIT_CACHE + 1) x T_alloc
+    int64_t hits_T = 0;
     uint64_t sized_map = 0, sized_scene = 0;
     uint32_t* h_total = nullptr;  // pinned
     int last_ntiles = 0;
@@ -115,8 +117,8 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.hdr, 1)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.cell_start, (size_t)IDX_CELLS_MAX + 1)) != VSR_OK) return st;
-    if ((st = dalloc(&m->idx.cell_tiles, nt)) != VSR_OK) return st;
-    if ((st = dalloc(&m->idx.big_tiles, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
     return VSR_OK;
 }
 
@@ -128,8 +130,8 @@ void map_release(vsr_map m)
     cudaFree(m->idx.hdr);
     cudaFree(m->idx.cell_count);
     cudaFree(m->idx.cell_start);
-    cudaFree(m->idx.cell_tiles);
-    cudaFree(m->idx.big_tiles);
+    cudaFree(m->idx.sorted);
+    cudaFree(m->idx.big);
     m->map = nullptr;
     m->tiles = nullptr;
     m->idx = TileIndex{};
@@ -381,6 +383,7 @@ void vsr_scene_free(vsr_scene sc)
     cudaFree(sc->counts);
     cudaFree(sc->offsets);
     cudaFree(sc->ids);
+    cudaFree(sc->hits);
     cudaFree(sc->tris_dev);
     cudaFree(sc->out_dev);
     if (sc->h_total) cudaFreeHost(sc->h_total);
@@ -399,7 +402,14 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     const int T = (int)sc->T;
     sc->last_ntiles = ntiles;
     VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_count(sc->rec, T, m->tiles, m->idx, sc->counts, st)) != VSR_OK) return s;
+    if (sc->T > sc->hits_T) {
+        cudaFree(sc->hits);
+        sc->hits = nullptr;
+        sc->hits_T = 0;
+        if ((s = dalloc(&sc->hits, (size_t)(BIN_HIT_CACHE + 1) * (size_t)sc->T)) != VSR_OK) return s;
+        sc->hits_T = sc->T;
+    }
+    if ((s = launch_bin_count(sc->rec, T, m->idx, sc->counts, sc->hits, st)) != VSR_OK) return s;
     if ((s = launch_scan(sc->counts, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
     if (sc->sized_map != m->gen || sc->sized_scene != sc->gen || sc->cap == 0) {
         // first binning of this (map, scene) pair: size the bins once
@@ -419,7 +429,7 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->sized_scene = sc->gen;
     }
     VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_fill(sc->rec, T, m->tiles, m->idx, sc->offsets, sc->counts, sc->ids, sc->cap, status_word(),
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->hits, sc->offsets, sc->counts, sc->ids, sc->cap, status_word(),
                              st)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;

@@ -88,8 +88,16 @@ __global__ void idx_plan_kernel(TileIndexHdr* hdr)
     hdr->alpha_cut = cut;
 }
 
+__device__ __forceinline__ Cone index_entry(const Cone& c, int i)
+{
+    Cone e;
+    e.c0 = c.c0;
+    e.c1 = make_float4(c.c1.x, c.c1.y, __uint_as_float((uint32_t)i), 0.0f);
+    return e;
+}
+
 __global__ void idx_count_kernel(const Cone* __restrict__ tiles, int ntiles, TileIndexHdr* hdr,
-                                 uint32_t* __restrict__ cell_count, uint32_t* __restrict__ big)
+                                 uint32_t* __restrict__ cell_count, Cone* __restrict__ big)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntiles) return;
@@ -98,7 +106,7 @@ __global__ void idx_count_kernel(const Cone* __restrict__ tiles, int ntiles, Til
     const TileIndexHdr h = *hdr;
     float a = cone_half_angle(c);
     if (a > h.alpha_cut) {
-        big[atomicAdd(&hdr->n_big, 1u)] = (uint32_t)i;
+        big[atomicAdd(&hdr->n_big, 1u)] = index_entry(c, i);
     } else {
         atomicAdd(&cell_count[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u);
         atomicMax(&hdr->alpha_small_max, __float_as_uint(a));
@@ -107,7 +115,7 @@ __global__ void idx_count_kernel(const Cone* __restrict__ tiles, int ntiles, Til
 
 __global__ void idx_fill_kernel(const Cone* __restrict__ tiles, int ntiles, const TileIndexHdr* hdr,
                                 const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ cursor,
-                                uint32_t* __restrict__ cell_tiles)
+                                Cone* __restrict__ sorted)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntiles) return;
@@ -116,26 +124,54 @@ __global__ void idx_fill_kernel(const Cone* __restrict__ tiles, int ntiles, cons
     const TileIndexHdr h = *hdr;
     if (cone_half_angle(c) > h.alpha_cut) return;
     int cell = home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h);
-    cell_tiles[cell_start[cell] + atomicAdd(&cursor[cell], 1u)] = (uint32_t)i;
+    sorted[cell_start[cell] + atomicAdd(&cursor[cell], 1u)] = index_entry(c, i);
 }
 
 // ---- per-triangle binning ---------------------------------------------------
 
 template <bool FILL>
-__global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec, int T, const Cone* __restrict__ tiles,
+__global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec, int T,
                                                    const TileIndexHdr* __restrict__ hdr,
                                                    const uint32_t* __restrict__ cell_start,
-                                                   const uint32_t* __restrict__ cell_tiles,
-                                                   const uint32_t* __restrict__ big_tiles,
-                                                   uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
-                                                   uint32_t* __restrict__ ids, uint32_t cap, int* status)
+                                                   const Cone* __restrict__ sorted, const Cone* __restrict__ big,
+                                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ hits,
+                                                   const uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
+                                                   uint32_t cap, int* status)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const size_t TT = (size_t)T;
+    uint32_t* my_hits = hits + (size_t)t * (BIN_HIT_CACHE + 1);
+    uint32_t nhit = 0;
+
+    auto emit = [&](uint32_t tile) {
+        if (!FILL) {
+            atomicAdd(&counts[tile], 1u);
+            if (nhit < BIN_HIT_CACHE) my_hits[1 + nhit] = tile;
+        } else {
+            uint32_t pos = offsets[tile] + atomicAdd(&counts[tile], 1u);
+            if (pos < cap && pos < offsets[tile + 1])
+                ids[pos] = (uint32_t)t;
+            else
+                raise_status(status, VSR_ERR_BIN_OVERFLOW);
+        }
+        ++nhit;
+    };
+
+    if (FILL) {
+        // the count pass cached up to BIN_HIT_CACHE hits per triangle
+        const uint32_t n = my_hits[0];
+        if (n <= BIN_HIT_CACHE) {
+            for (uint32_t q = 0; q < n; ++q) emit(my_hits[1 + q]);
+            return;
+        }
+    }
     const float4 c0 = rec[RF_CAP * TT + t];
     const float4 c1 = rec[RF_CAP2 * TT + t];
-    if (c1.w == 0.0f) return;  // culled
+    if (c1.w == 0.0f) {  // culled
+        if (!FILL) my_hits[0] = 0;
+        return;
+    }
     const float3 S = make_float3(c0.x, c0.y, c0.z);
     const float cr = c0.w, sr = c1.x;
     const TileIndexHdr& h = *hdr;
@@ -143,17 +179,11 @@ __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec
     const float cell = h.cell;
     const float amax = __uint_as_float(h.alpha_small_max), hmax = __uint_as_float(h.h_max);
 
-    auto visit = [&](uint32_t tile) {
-        const Cone c = tiles[tile];
-        if (!cap_hits_cone(S, cr, sr, make_float3(c.c0.x, c.c0.y, c.c0.z), c.c0.w, c.c1.x, c.c1.y)) return;
-        if (!FILL) {
-            atomicAdd(&counts[tile], 1u);
-        } else {
-            uint32_t pos = offsets[tile] + atomicAdd(&counts[tile], 1u);
-            if (pos < cap && pos < offsets[tile + 1])
-                ids[pos] = (uint32_t)t;
-            else
-                raise_status(status, VSR_ERR_BIN_OVERFLOW);
+    auto scan_range = [&](const Cone* __restrict__ list, uint32_t k0, uint32_t k1) {
+        for (uint32_t k = k0; k < k1; ++k) {
+            const Cone c = list[k];
+            if (cap_hits_cone(S, cr, sr, make_float3(c.c0.x, c.c0.y, c.c0.z), c.c0.w, c.c1.x, c.c1.y))
+                emit(__float_as_uint(c.c1.z));
         }
     };
 
@@ -172,18 +202,21 @@ __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec
             c0i = (int)floorf((lon - dl + PI_F) / cell);
             const int c1i = (int)floorf((lon + dl + PI_F) / cell);
             ncol = min(nlon, c1i - c0i + 1);
+            c0i %= nlon;
+            if (c0i < 0) c0i += nlon;
         }
     }
-    for (int r = r0; r <= r1; ++r)
-        for (int q = 0; q < ncol; ++q) {
-            int col = (c0i + q) % nlon;
-            if (col < 0) col += nlon;
-            const int cidx = r * nlon + col;
-            const uint32_t e = cell_start[cidx + 1];
-            for (uint32_t k = cell_start[cidx]; k < e; ++k) visit(cell_tiles[k]);
+    for (int r = r0; r <= r1; ++r) {
+        const uint32_t* row = cell_start + r * nlon;
+        if (c0i + ncol <= nlon) {
+            scan_range(sorted, row[c0i], row[c0i + ncol]);
+        } else {  // the window wraps across longitude +-pi
+            scan_range(sorted, row[c0i], row[nlon]);
+            scan_range(sorted, row[0], row[c0i + ncol - nlon]);
         }
-    const uint32_t nb = h.n_big;
-    for (uint32_t k = 0; k < nb; ++k) visit(big_tiles[k]);
+    }
+    scan_range(big, 0, h.n_big);
+    if (!FILL) my_hits[0] = nhit;
 }
 
 // Exclusive scan of n counts into offsets[0..n] by one CTA of 1024 threads:
@@ -249,32 +282,32 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
     VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
     idx_hist_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr);
     idx_plan_kernel<<<1, 1, 0, st>>>(idx.hdr);
-    idx_count_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_count, idx.big_tiles);
+    idx_count_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_count, idx.big);
     VSR_CUDA_TRY(cudaGetLastError());
     vsr_status s = launch_scan(idx.cell_count, 0, &idx.hdr->ncell, idx.cell_start, st);
     if (s != VSR_OK) return s;
     VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
-    idx_fill_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.cell_tiles);
+    idx_fill_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, TileIndex idx, uint32_t* counts,
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* hits,
                             cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, idx.hdr, idx.cell_start, idx.cell_tiles,
-                                                       idx.big_tiles, counts, nullptr, nullptr, 0, nullptr);
+    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, counts,
+                                                       hits, nullptr, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, TileIndex idx, const uint32_t* offsets,
+vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
                            uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, tiles, idx.hdr, idx.cell_start, idx.cell_tiles,
-                                                      idx.big_tiles, cursors, offsets, ids, cap, status);
+    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, cursors,
+                                                      const_cast<uint32_t*>(hits), offsets, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

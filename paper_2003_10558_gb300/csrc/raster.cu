@@ -1,7 +1,9 @@
 // raster.cu -- per-tile coverage / depth / visibility kernel.
 //
-// One CTA of 256 threads per 16x16 tile; warp w covers the 8x4 pixel block
-// (w & 1, w >> 1) of the tile and each lane one pixel of it.  For every
+// One CTA of 128 threads per 16x16 tile; warp w covers the 8x8 pixel block
+// (w & 1, w >> 1) of the tile and each lane two pixels of it, (x, y) and
+// (x, y + 4), so every shared-memory load, vote and branch per triangle
+// serves two pixels.  For every
 // pixel G (unit direction, global delta) and every triangle t of the tile's
 // bin the kernel evaluates the four plane distances of the rasterization
 // equation (Sec. 1.1.2):
@@ -28,14 +30,17 @@
 // the ramp is ~(tile size in pixels) x 2^-23, a few 1e-6 of coverage.
 //
 // Work culling: the triangles of a chunk are first tested lane-parallel
-// (lane j <-> triangle j) against each warp's own 8x4-pixel view cone; the
-// surviving ones are then evaluated for all 32 pixels.
+// (lane j <-> triangle j) against each warp's own 8x8-pixel view cone; the
+// surviving ones are then evaluated for all 64 pixels.
 #include "df.cuh"
 #include "vsr_internal.cuh"
 
 namespace {
 
-constexpr int CHUNK = TILE_PIX;  // triangles staged per pass
+constexpr int RT = 128;          // threads per CTA (one 16x16 tile)
+constexpr int PPT = 2;           // pixels per thread: (x, y) and (x, y + 4) of the warp's 8x8 block
+constexpr int CHUNK = RT;        // triangles staged per pass
+static_assert(RT * PPT == TILE_PIX, "one CTA covers one tile");
 
 struct __align__(16) Stage {
     float4 s0[CHUNK];  // S-hat.hi xyz, tie flags (bits)
@@ -63,7 +68,19 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(TILE_PIX) raster_kernel(
+// |G|^2 - 1, error-free (TwoProd / TwoSum): the chord form of the miter
+// distance equals (G.S-hat - cos rho)/sin rho for any G only with this term,
+// and FP32 map directions are unit to ~1e-7, not exactly.
+__device__ __forceinline__ float norm2_minus_one(float x, float y, float z)
+{
+    const df px2 = two_prod(x, x), py2 = two_prod(y, y), pz2 = two_prod(z, z);
+    const df s1 = two_sum(px2.hi, py2.hi);
+    const df s2 = two_sum(s1.hi, pz2.hi);
+    const float tail = __fadd_rn(__fadd_rn(__fadd_rn(px2.lo, py2.lo), __fadd_rn(pz2.lo, s1.lo)), s2.lo);
+    return __fadd_rn(__fadd_rn(s2.hi, -1.0f), tail);
+}
+
+__global__ void __launch_bounds__(RT, 8) raster_kernel(
     const float4* __restrict__ map, int W, int H, const Cone* __restrict__ tiles, int tiles_x,
     const float4* __restrict__ rec, int T, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ids,
     uint32_t cap, uint32_t* __restrict__ out_id, float* __restrict__ out_depth, float* __restrict__ out_cov,
@@ -71,52 +88,69 @@ __global__ void __launch_bounds__(TILE_PIX) raster_kernel(
     int* __restrict__ status)
 {
     __shared__ Stage st;
-    __shared__ unsigned long long red[2][TILE_PIX / 32];
+    __shared__ unsigned long long red[2][RT / 32];
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * TILE + (warp & 1) * 8 + (lane & 7);
-    const int py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside_img = px < W && py < H;
-
-    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (inside_img) g = map[(size_t)py * W + px];
-    const bool pv = g.w > 0.0f;
-    const float delta = g.w;
-    const float h = pv ? 0.5f / delta : 0.0f;
-
-    // |G|^2 - 1, error-free (TwoProd / TwoSum): the chord form of the miter
-    // distance below equals (G.S-hat - cos rho)/sin rho for any G only with
-    // this term, and FP32 map directions are unit to ~1e-7, not exactly
-    float eg = 0.0f;
-    if (pv) {
-        const df px2 = two_prod(g.x, g.x), py2 = two_prod(g.y, g.y), pz2 = two_prod(g.z, g.z);
-        const df s1 = two_sum(px2.hi, py2.hi);
-        const df s2 = two_sum(s1.hi, pz2.hi);
-        const float tail = __fadd_rn(__fadd_rn(__fadd_rn(px2.lo, py2.lo), __fadd_rn(pz2.lo, s1.lo)), s2.lo);
-        eg = __fadd_rn(__fadd_rn(s2.hi, -1.0f), tail);
-    }
+    const int py0 = ty * TILE + (warp >> 1) * 8 + (lane >> 3);
 
     const Cone tc = tiles[tile];
     const float ax = tc.c0.x, ay = tc.c0.y, az = tc.c0.z;
-    const float dgx = g.x - ax, dgy = g.y - ay, dgz = g.z - az;
 
-    // the warp's own view cone
-    float wsx = warp_sum(pv ? g.x : 0.0f), wsy = warp_sum(pv ? g.y : 0.0f), wsz = warp_sum(pv ? g.z : 0.0f);
-    const float wcnt = warp_sum(pv ? 1.0f : 0.0f);
-    float wl = sqrtf(wsx * wsx + wsy * wsy + wsz * wsz);
-    float wax = 0.0f, way = 0.0f, waz = 1.0f;
-    if (wl > 1e-6f * fmaxf(wcnt, 1.0f)) {
-        wax = wsx / wl;
-        way = wsy / wl;
-        waz = wsz / wl;
+    float gx[PPT], gy[PPT], gz[PPT], dgx[PPT], dgy[PPT], dgz[PPT], delta[PPT], h[PPT], eg[PPT];
+    bool pv[PPT], inimg[PPT];
+    uint32_t acc[PPT];
+    unsigned long long key[PPT];
+    int32_t cnt_in[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int py = py0 + 4 * p;
+        inimg[p] = px < W && py < H;
+        float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (inimg[p]) g = map[(size_t)py * W + px];
+        pv[p] = g.w > 0.0f;
+        gx[p] = g.x;
+        gy[p] = g.y;
+        gz[p] = g.z;
+        delta[p] = g.w;
+        h[p] = pv[p] ? 0.5f / g.w : 0.0f;
+        eg[p] = pv[p] ? norm2_minus_one(g.x, g.y, g.z) : 0.0f;
+        dgx[p] = g.x - ax;
+        dgy[p] = g.y - ay;
+        dgz[p] = g.z - az;
+        acc[p] = 0u;
+        key[p] = ~0ull;
+        cnt_in[p] = 0;
     }
-    float wcos = warp_min(pv ? g.x * wax + g.y * way + g.z * waz : 2.0f);
-    wcos = fmaxf(-1.0f, fminf(1.0f, wcos - 2e-6f));
-    if (wl <= 1e-6f * fmaxf(wcnt, 1.0f)) wcos = -1.0f;
+
+    // the warp's own view cone (its 8x8 pixels)
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f, cn = 0.0f, hw = 0.0f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+        if (pv[p]) {
+            sx += gx[p];
+            sy += gy[p];
+            sz += gz[p];
+            cn += 1.0f;
+            hw = fmaxf(hw, h[p]);
+        }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    sz = warp_sum(sz);
+    const float wcnt = warp_sum(cn);
+    const float wh = warp_max(hw);
+    const float wl = sqrtf(sx * sx + sy * sy + sz * sz);
+    const bool wdeg = !(wl > 1e-6f * fmaxf(wcnt, 1.0f));
+    const float wax = wdeg ? 0.0f : sx / wl, way = wdeg ? 0.0f : sy / wl, waz = wdeg ? 1.0f : sz / wl;
+    float cm = 2.0f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+        if (pv[p]) cm = fminf(cm, gx[p] * wax + gy[p] * way + gz[p] * waz);
+    float wcos = fmaxf(-1.0f, fminf(1.0f, warp_min(cm) - 2e-6f));
+    if (wdeg) wcos = -1.0f;
     const float wsin = sqrtf(fmaxf(0.0f, 1.0f - wcos * wcos));
-    const float wh = warp_max(h);
     const bool warp_active = wcnt > 0.0f;
 
     uint32_t b0 = 0, b1 = 0;
@@ -130,10 +164,7 @@ __global__ void __launch_bounds__(TILE_PIX) raster_kernel(
         }
     }
 
-    uint32_t acc = 0;
-    unsigned long long key = ~0ull;
     uint32_t cnt_alg = 0, cnt_exec = 0;
-    int32_t cnt_in = 0;
     const size_t TT = (size_t)T;
 
     for (uint32_t base = b0; base < b1; base += CHUNK) {
@@ -175,9 +206,8 @@ __global__ void __launch_bounds__(TILE_PIX) raster_kernel(
             if (jj < n && __float_as_uint(st.s6[jj].w) != 0xffffffffu) {
                 const float4 a = st.s0[jj];
                 const float4 b = st.s1[jj];
-                const float cos_rho = 1.0f - 0.5f * b.y;
-                keep = cap_hits_cone(make_float3(a.x, a.y, a.z), cos_rho, b.x, make_float3(wax, way, waz), wcos, wsin,
-                                     wh);
+                keep = cap_hits_cone(make_float3(a.x, a.y, a.z), 1.0f - 0.5f * b.y, b.x, make_float3(wax, way, waz),
+                                     wcos, wsin, wh);
             }
             unsigned mask = __ballot_sync(0xffffffffu, keep);
             while (mask) {
@@ -186,54 +216,70 @@ __global__ void __launch_bounds__(TILE_PIX) raster_kernel(
                 const float4 a = st.s0[j];
                 const float4 b = st.s1[j];
                 const float4 e = st.s6[j];
-                // miter distance, chord form
-                const float mx = (g.x - a.x) - e.x, my = (g.y - a.y) - e.y, mz = (g.z - a.z) - e.z;
-                const float q = fmaf(mx, mx, fmaf(my, my, mz * mz));
-                const float g4 = ((b.y - q) + eg) * b.z;
-                const bool p4 = pv && g4 > -h;
                 ++cnt_exec;
-                if (!__any_sync(0xffffffffu, p4)) continue;
-                cnt_alg += p4;
+                // miter distance, chord form
+                float g4[PPT];
+                bool p4[PPT], any4 = false;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const float mx = (gx[p] - a.x) - e.x, my = (gy[p] - a.y) - e.y, mz = (gz[p] - a.z) - e.z;
+                    const float q = fmaf(mx, mx, fmaf(my, my, mz * mz));
+                    g4[p] = ((b.y - q) + eg[p]) * b.z;
+                    p4[p] = pv[p] && g4[p] > -h[p];
+                    cnt_alg += p4[p];
+                    any4 |= p4[p];
+                }
+                if (!__any_sync(0xffffffffu, any4)) continue;
                 const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
-                const float g1 = fmaf(dgx, n1.x, fmaf(dgy, n1.y, fmaf(dgz, n1.z, n1.w)));
-                const float g2 = fmaf(dgx, n2.x, fmaf(dgy, n2.y, fmaf(dgz, n2.z, n2.w)));
-                const float g3 = fmaf(dgx, n3.x, fmaf(dgy, n3.y, fmaf(dgz, n3.z, n3.w)));
-                const float gm = fminf(fminf(g1, g2), fminf(g3, g4));
-                bool frag = p4 && gm > -h;
-                if (!__any_sync(0xffffffffu, frag)) continue;
+                float g1[PPT], g2[PPT], g3[PPT], gm[PPT];
+                bool frag[PPT], anyf = false;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    g1[p] = fmaf(dgx[p], n1.x, fmaf(dgy[p], n1.y, fmaf(dgz[p], n1.z, n1.w)));
+                    g2[p] = fmaf(dgx[p], n2.x, fmaf(dgy[p], n2.y, fmaf(dgz[p], n2.z, n2.w)));
+                    g3[p] = fmaf(dgx[p], n3.x, fmaf(dgy[p], n3.y, fmaf(dgz[p], n3.z, n3.w)));
+                    gm[p] = fminf(fminf(g1[p], g2[p]), fminf(g3[p], g4[p]));
+                    frag[p] = p4[p] && gm[p] > -h[p];
+                    anyf |= frag[p];
+                }
+                if (!__any_sync(0xffffffffu, anyf)) continue;
                 const float4 pl = st.s5[j];
-                const float D = fmaf(dgx, pl.x, fmaf(dgy, pl.y, fmaf(dgz, pl.z, pl.w)));
-                const float r = __fdiv_rn(b.w, D);
-                frag = frag && r > 0.0f && r < INFINITY;
-                if (frag) {
-                    const float m = __saturatef(fmaf(gm, delta, 0.5f));
-                    acc = min(acc + __float2uint_rn(m * 16777216.0f), 16777216u);
-                    const unsigned ties = __float_as_uint(a.w);
-                    const bool in1 = g1 > 0.0f || (g1 == 0.0f && (ties & 1u));
-                    const bool in2 = g2 > 0.0f || (g2 == 0.0f && (ties & 2u));
-                    const bool in3 = g3 > 0.0f || (g3 == 0.0f && (ties & 4u));
+                const unsigned ties = __float_as_uint(a.w);
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    if (!frag[p]) continue;
+                    const float D = fmaf(dgx[p], pl.x, fmaf(dgy[p], pl.y, fmaf(dgz[p], pl.z, pl.w)));
+                    const float r = __fdividef(b.w, D);
+                    if (!(r > 0.0f && r < INFINITY)) continue;
+                    const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
+                    acc[p] = min(acc[p] + __float2uint_rn(m * 16777216.0f), 16777216u);
+                    const bool in1 = g1[p] > 0.0f || (g1[p] == 0.0f && (ties & 1u));
+                    const bool in2 = g2[p] > 0.0f || (g2[p] == 0.0f && (ties & 2u));
+                    const bool in3 = g3[p] > 0.0f || (g3[p] == 0.0f && (ties & 4u));
                     if (in1 && in2 && in3) {
                         const unsigned long long k =
                             ((unsigned long long)__float_as_uint(r) << 32) | (unsigned long long)__float_as_uint(e.w);
-                        key = k < key ? k : key;
-                        ++cnt_in;
+                        key[p] = k < key[p] ? k : key[p];
+                        ++cnt_in[p];
                     }
                 }
             }
         }
     }
 
-    if (inside_img) {
-        const size_t o = (size_t)py * W + px;
-        const bool hit = key != ~0ull;
-        if (out_id) out_id[o] = hit ? (uint32_t)(key & 0xffffffffull) : 0xffffffffu;
-        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
-        if (out_cov) out_cov[o] = (float)acc * (1.0f / 16777216.0f);
-        if (n_inside) n_inside[o] = cnt_in;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if (!inimg[p]) continue;
+        const size_t o = (size_t)(py0 + 4 * p) * W + px;
+        const bool hit = key[p] != ~0ull;
+        if (out_id) out_id[o] = hit ? (uint32_t)(key[p] & 0xffffffffull) : 0xffffffffu;
+        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key[p] >> 32)) : INFINITY;
+        if (out_cov) out_cov[o] = (float)acc[p] * (1.0f / 16777216.0f);
+        if (n_inside) n_inside[o] = cnt_in[p];
     }
     if (n_alg || n_exec) {
-        // cnt_exec counts warp-level evaluations: one per (warp, triangle) for 32 pixels
-        unsigned long long va = cnt_alg, ve = lane == 0 ? (unsigned long long)cnt_exec * 32ull : 0ull;
+        // cnt_exec counts warp-level evaluations: one per (warp, triangle) for 64 pixels
+        unsigned long long va = cnt_alg, ve = lane == 0 ? (unsigned long long)cnt_exec * (32ull * PPT) : 0ull;
         for (int o = 16; o; o >>= 1) {
             va += __shfl_xor_sync(0xffffffffu, va, o);
             ve += __shfl_xor_sync(0xffffffffu, ve, o);
@@ -245,7 +291,7 @@ __global__ void __launch_bounds__(TILE_PIX) raster_kernel(
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long sa = 0, se = 0;
-            for (int w = 0; w < TILE_PIX / 32; ++w) {
+            for (int w = 0; w < RT / 32; ++w) {
                 sa += red[0][w];
                 se += red[1][w];
             }
@@ -263,7 +309,7 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
                          int* status, cudaStream_t st)
 {
     const int tx = (W + TILE - 1) / TILE, ty = (H + TILE - 1) / TILE;
-    raster_kernel<<<tx * ty, TILE_PIX, 0, st>>>(map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov,
+    raster_kernel<<<tx * ty, RT, 0, st>>>(map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov,
                                                  n_alg, n_exec, n_inside, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;

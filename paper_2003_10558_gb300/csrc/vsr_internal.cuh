@@ -108,18 +108,23 @@ vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaSt
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
+// The cones of the small tiles are stored sorted by home cell, so the cells
+// of one grid row form one contiguous range: (axis xyz, cos alpha),
+// (sin alpha, h, tile index bits, 0).  Big tiles are stored the same way.
 struct TileIndex {
     TileIndexHdr* hdr;
     uint32_t* cell_count;  // IDX_CELLS_MAX
     uint32_t* cell_start;  // IDX_CELLS_MAX + 1
-    uint32_t* cell_tiles;  // ntiles
-    uint32_t* big_tiles;   // ntiles
+    Cone* sorted;          // ntiles
+    Cone* big;             // ntiles
 };
+// per-triangle hit cache between the count and fill passes of the binner
+constexpr int BIN_HIT_CACHE = 8;
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
-vsr_status launch_bin_count(const float4* rec, int T, const Cone* tiles, TileIndex idx, uint32_t* counts,
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* hits,
                             cudaStream_t st);
 vsr_status launch_scan(const uint32_t* counts, int n, const int* n_dev, uint32_t* offsets, cudaStream_t st);
-vsr_status launch_bin_fill(const float4* rec, int T, const Cone* tiles, TileIndex idx, const uint32_t* offsets,
+vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
                            uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st);
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
