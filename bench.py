@@ -68,6 +68,30 @@ def workload():
     return lens, tris, cam
 
 
+RASTER_SOURCES = ("paper_2003_10558_gb300/csrc/raster.cu", "paper_2003_10558_gb300/csrc/df.cuh",
+                  "paper_2003_10558_gb300/csrc/vsr_internal.cuh")
+
+
+def raster_traffic():
+    """DRAM bytes per raster launch from the committed ncu summary, or None
+    when the kernel's sources changed since that capture."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "raster_kernel_1080p_single_view.md")) as f:
+            txt = f.read()
+        h = hashlib.sha256()
+        for p in RASTER_SOURCES:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        want = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt).group(1)
+        if h.hexdigest()[:16] != want:
+            return None
+        return int(re.search(r"traffic_bytes_per_launch:\s*(\d+)", txt).group(1))
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -304,12 +328,7 @@ def run_vsr(args, rank, world, local):
     peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6
     rast_mean_s = statistics.mean(rast_ms) / 1000.0
     achieved = n_alg * OPS_PER_TEST / rast_mean_s
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "raster_traffic.json")) as f:
-            traffic = json.load(f).get("bytes_per_launch_1080p")
-    except Exception:
-        pass
+    traffic = raster_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -97,6 +97,21 @@ __device__ __forceinline__ df df_sqrt(df x)
     return fast_two_sum(s, e);
 }
 
+// 1/sqrt(x) of a positive double-word: r0 = rsqrt(hi), one Newton step
+// r = r0 + r0 (1 - x r0^2) / 2 with the residual in double-word arithmetic.
+__device__ __forceinline__ df df_rsqrt(df x)
+{
+    if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+    float r0 = rsqrtf(x.hi);
+    r0 = __fmul_rn(r0, __fmaf_rn(__fmul_rn(-0.5f, __fmul_rn(x.hi, r0)), r0, 1.5f));  // ~1 ulp
+    df xr2 = df_mul_f(df_mul_f(x, r0), r0);
+    float e = __fadd_rn(__fadd_rn(1.0f, -xr2.hi), -xr2.lo);
+    return fast_two_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), e));
+}
+
+// reciprocal of a double-word
+__device__ __forceinline__ df df_recip(df y) { return df_div(df_make(1.0f), y); }
+
 struct df3 {
     df x, y, z;
 };

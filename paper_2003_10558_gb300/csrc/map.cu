@@ -15,6 +15,7 @@ namespace {
 
 struct MapP {
     float k, l;
+    float inv_k;   // 1 / k (k != 0)
     float tk;      // tan(k Omega/2)              (k > 0)
     float sk;      // sin(k Omega/2)              (k < 0)
     float half;    // Omega/2 in radians
@@ -29,20 +30,24 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
     float x = (float)(2 * i + 1 - W) * p.sc;
     float y = (float)(2 * j + 1 - H) * p.sc;
     float R = sqrtf(fmaf(x, x, p.l * y * y));
-    float th, sor;
+    float th;
+    float lim;  // lim_{R -> 0} sin(theta)/R
     if (p.kind > 0) {
-        th = atanf(p.tk * R) / p.k;
-        sor = R > 0.0f ? sinf(th) / R : p.tk / p.k;
+        th = atanf(p.tk * R) * p.inv_k;
+        lim = p.tk * p.inv_k;
     } else if (p.kind == 0) {
         th = p.half * R;
-        sor = R > 0.0f ? sinf(th) / R : p.half;
+        lim = p.half;
     } else {
         float arg = p.sk * R;
         if (arg > 1.0f || arg < -1.0f) return false;
-        th = asinf(arg) / p.k;
-        sor = R > 0.0f ? sinf(th) / R : p.sk / p.k;
+        th = asinf(arg) * p.inv_k;
+        lim = p.sk * p.inv_k;
     }
-    float wx = x * sor, wy = y * sor * p.inv_ls, wz = cosf(th);
+    float st, ct;
+    sincosf(th, &st, &ct);
+    const float sor = R > 0.0f ? __fdividef(st, R) : lim;
+    float wx = x * sor, wy = y * sor * p.inv_ls, wz = ct;
     float inv = rsqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
     // one Newton step on the reciprocal square root keeps |v| = 1 to ~1 ulp
     float n2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
@@ -52,10 +57,11 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
 }
 
 // Block-wide reduction of the tile cone from per-thread (valid, G, h).
-// blockDim.x == TILE_PIX.
+// Every thread of the block calls it; blockDim.x is a multiple of 32, <= 512.
 __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
 {
-    __shared__ float red[4][TILE_PIX / 32];
+    __shared__ float red[4][16];
+    const int nwarps = blockDim.x >> 5;
     __shared__ float axis_s[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float sx = valid ? G.x : 0.0f, sy = valid ? G.y : 0.0f, sz = valid ? G.z : 0.0f, cnt = valid ? 1.0f : 0.0f;
@@ -74,7 +80,7 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
     __syncthreads();
     if (threadIdx.x == 0) {
         float a = 0, b = 0, c = 0, n = 0;
-        for (int w = 0; w < TILE_PIX / 32; ++w) {
+        for (int w = 0; w < nwarps; ++w) {
             a += red[0][w];
             b += red[1][w];
             c += red[2][w];
@@ -108,7 +114,7 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
     __syncthreads();
     if (threadIdx.x == 0) {
         float c = 2.0f, hh = 0.0f;
-        for (int w = 0; w < TILE_PIX / 32; ++w) {
+        for (int w = 0; w < nwarps; ++w) {
             c = fminf(c, red[0][w]);
             hh = fmaxf(hh, red[1][w]);
         }
@@ -121,22 +127,29 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
     }
 }
 
-__global__ void __launch_bounds__(TILE_PIX) map_kernel(int W, int H, MapP p, float4* __restrict__ map,
-                                                        Cone* __restrict__ tiles)
+constexpr int HW = TILE + 2;
+constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation per thread
+
+__global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, float4* __restrict__ map,
+                                                           Cone* __restrict__ tiles)
 {
-    constexpr int HW = TILE + 2;
     __shared__ float3 sv[HW * HW];
     __shared__ unsigned char sok[HW * HW];
     const int tx = blockIdx.x, ty = blockIdx.y;
     const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
-    for (int q = threadIdx.x; q < HW * HW; q += blockDim.x) {
-        int qi = q % HW, qj = q / HW;
+    if (threadIdx.x < HW * HW) {
+        const int q = threadIdx.x, qi = q % HW, qj = q / HW;
         float3 v = make_float3(0.0f, 0.0f, 0.0f);
         bool ok = map_fn(i0 + qi, j0 + qj, W, H, p, v);
         sv[q] = v;
         sok[q] = ok;
     }
     __syncthreads();
+    if (threadIdx.x >= TILE_PIX) {
+        // the halo-only threads take part in the cone reduction's barriers
+        reduce_cone(false, make_float3(0.0f, 0.0f, 0.0f), 0.0f, &tiles[ty * gridDim.x + tx]);
+        return;
+    }
     const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
     const int i = tx * TILE + li, j = ty * TILE + lj;
     const int c = (lj + 1) * HW + (li + 1);
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(TILE_PIX) map_kernel(int W, int H, MapP p, flo
                 fw = fmaxf(fw, fabsf(di) + fabsf(dj));
             }
             if (fw > 0.0f) {
-                o = make_float4(vc.x, vc.y, vc.z, 1.0f / fw);
+                o = make_float4(vc.x, vc.y, vc.z, __frcp_rn(fw));
                 valid = true;
                 G = vc;
                 h = 0.5f / o.w;  // exactly the raster kernel's ramp half-width
@@ -215,6 +228,7 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
     p.k = k;
     p.l = l;
     p.kind = k > 0.0f ? 1 : (k < 0.0f ? -1 : 0);
+    p.inv_k = k != 0.0f ? (float)(1.0 / (double)k) : 0.0f;
     p.tk = (float)tan((double)k * half);
     p.sk = (float)sin((double)k * half);
     p.half = (float)half;
@@ -228,7 +242,7 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
     }
     (void)a;
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<<<grid, TILE_PIX, 0, st>>>(W, H, p, map, tiles);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, p, map, tiles);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

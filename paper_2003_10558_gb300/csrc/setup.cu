@@ -41,11 +41,7 @@ __device__ __forceinline__ bool vless(const float* P, const float* Q)
     return false;
 }
 
-__device__ __forceinline__ df3 normalize3(df3 v)
-{
-    df len = df_sqrt(df_dot(v, v));
-    return df3_div(v, len);
-}
+__device__ __forceinline__ df3 normalize3(df3 v) { return df3_scale(v, df_rsqrt(df_dot(v, v))); }
 
 __device__ __forceinline__ df3 edge_normal(const float* Pw, const float* Qw, const df3& P, const df3& Q, bool flip)
 {
@@ -120,9 +116,11 @@ __global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tr
         S = df3_scale(df3_add(U0, U1), half);
     else {
         df3 num = df3_add(df3_add(df3_scale(U0, Os), df3_scale(U1, Ot)), df3_scale(U2, Op));
-        S = df3_div(num, df_add(df_add(Os, Ot), Op));
+        S = df3_scale(num, df_recip(df_add(df_add(Os, Ot), Op)));
     }
-    df slen = df_sqrt(df_dot(S, S));
+    const df s2len = df_dot(S, S);
+    const df rs = df_rsqrt(s2len);
+    df slen = df_mul(s2len, rs);  // |S| = |S|^2 / |S|
     df one = df_make(1.0f);
     df omc = df_sub(one, slen);                    // 1 - cos rho
     df sr = df_sqrt(df_mul(omc, df_add(one, slen)));  // sin rho
@@ -131,7 +129,7 @@ __global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tr
         for (int f = 0; f < REC_F; ++f) rec[f * TT + t] = invalid;
         return;
     }
-    df3 Sh = df3_div(S, slen);
+    df3 Sh = df3_scale(S, rs);
     float K = __fmul_rn(2.0f, omc.hi);                   // 2 (1 - cos rho) = 4 sin^2(rho/2)
     float inv2sr = __fdiv_rn(1.0f, __fmul_rn(2.0f, sr.hi));
 
