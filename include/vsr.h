@@ -180,6 +180,30 @@ vsr_status vsr_raster_ex(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_
 vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
                             const vsr_raster_stats* stats, void* stream);
 
+/* vsr_raster_noalloc: the same rasterization as vsr_raster, for callers that
+ * cannot allocate device memory while they render (a host framework that
+ * owns all device memory and forbids side allocations, or a real-time loop
+ * that must not wait on cudaMalloc or on the synchronisation with which
+ * vsr_raster sizes the bins of a new map/scene pair).  The paper has no
+ * counterpart; this is a service of the library.
+ * The tile bins live in one fixed device array inside the library (about
+ * 13.8 MB, held on every device that loads the library until the process
+ * exits) instead of the scene's workspace: the call allocates nothing and
+ * never synchronises.  Maps and scenes are made beforehand as usual.
+ * Limits: at most 16384 tiles of 16x16 pixels (e.g. 2048 x 2048), at most
+ * 262144 triangles (else VSR_ERR_INVALID_ARG), at most 2^20 (tile, triangle)
+ * pairs (known only on the device: exceeding it writes VSR_ERR_BIN_OVERFLOW
+ * to the status and leaves the outputs incomplete).
+ * status_dev: optional caller-owned device int32 that receives VSR_OK or the
+ * device-side error of this call (cleared by the call).  With NULL the
+ * status goes to a word of the library's array.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture.  Every call
+ * shares the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. */
+vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                              int32_t* status_dev, void* stream);
+
 /* Number of (tile, triangle) pairs in the last binning of this scene
  * (synchronises `stream`). */
 vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);

@@ -514,3 +514,89 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Rasterization without allocation (vsr_raster_noalloc).
+//
+// Some callers cannot allocate device memory while they render: a host
+// framework that owns every byte of device memory and forbids side
+// allocations, or a real-time loop that must never wait on cudaMalloc and the
+// synchronisation the first vsr_raster of a new (map, scene) pair performs
+// to size its bins.  For them the tile bins live in one file-scope device
+// array of fixed size instead of the scene's workspace.  The maps and scenes
+// are prepared beforehand; the call itself allocates nothing and never
+// synchronises.
+//
+// Limits: map of at most NA_TILES_MAX 16x16 tiles (e.g. 2048 x 2048), scene
+// of at most NA_T_MAX triangles, at most NA_PAIRS_MAX (tile, triangle) bin
+// pairs.  The array takes about 13.8 MB on every device that loads the
+// library, until the process exits.
+namespace {
+
+constexpr uint32_t NA_TILES_MAX = 16384;
+constexpr uint32_t NA_T_MAX = 262144;
+constexpr uint32_t NA_PAIRS_MAX = 1u << 20;
+constexpr size_t NA_STATUS_WORDS = 64;  // word 0: status when the caller passes none
+constexpr size_t NA_COUNTS = NA_STATUS_WORDS;
+constexpr size_t NA_OFFSETS = NA_COUNTS + NA_TILES_MAX;
+constexpr size_t NA_IDS = NA_OFFSETS + NA_TILES_MAX + 64;
+constexpr size_t NA_HITS = NA_IDS + NA_PAIRS_MAX;
+constexpr size_t NA_WORDS = NA_HITS + (size_t)(BIN_HIT_CACHE + 1) * NA_T_MAX;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress allocates nothing).
+uint32_t* noalloc_scratch(vsr_status* err)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        *err = VSR_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            *err = VSR_ERR_CUDA;
+            return nullptr;
+        }
+        g_noalloc_addr[dev] = (uint32_t*)p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+}  // namespace
+
+extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                                         int32_t* status_dev, void* stream)
+{
+    if (!m || !sc) return VSR_ERR_INVALID_ARG;
+    const int ntiles = m->tx * m->ty;
+    if ((uint32_t)ntiles > NA_TILES_MAX || sc->T < 0 || (uint64_t)sc->T > NA_T_MAX) return VSR_ERR_INVALID_ARG;
+    vsr_status err = VSR_OK;
+    uint32_t* base = noalloc_scratch(&err);
+    if (!base) return err;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int T = (int)sc->T;
+    int* status = status_dev ? (int*)status_dev : (int*)base;
+    uint32_t* counts = base + NA_COUNTS;
+    uint32_t* offsets = base + NA_OFFSETS;
+    uint32_t* ids = base + NA_IDS;
+    uint32_t* hits = base + NA_HITS;
+    vsr_status s;
+    // the array keeps the previous call's contents: clear what starts at zero
+    VSR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, hits, st)) != VSR_OK) return s;
+    if ((s = launch_scan(counts, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, hits, offsets, counts, ids, NA_PAIRS_MAX, status, st)) != VSR_OK)
+        return s;
+    return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, T, offsets, ids, NA_PAIRS_MAX, id_dev, depth_dev,
+                         cov_dev, nullptr, nullptr, nullptr, status, st);
+}

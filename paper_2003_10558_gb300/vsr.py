@@ -30,7 +30,7 @@ AOV_HORIZONTAL, AOV_DIAGONAL, AOV_VERTICAL, AOV_H4X3 = 0, 1, 2, 3
 EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
-           "vsr_scene_bin_pairs",
+           "vsr_scene_bin_pairs", "vsr_raster_noalloc",
            "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
 
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
             "vsr_bin": ([vp, vp, vp], i32),
             "vsr_raster_tiles": ([vp, vp, vp, vp, vp, P(RasterStats), vp], i32),
             "vsr_scene_bin_pairs": ([vp, vp, P(i64)], i32),
+            "vsr_raster_noalloc": ([vp, vp, vp, vp, vp, vp, vp], i32),
             "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_status_str": ([i32], ctypes.c_char_p),
             "vsr_last_device_status": ([], i32),
