@@ -74,7 +74,7 @@ struct vsr_scene_s {
     uint32_t* offsets = nullptr;
     uint32_t* ids = nullptr;
     uint32_t cap = 0;
-    uint32_t* hits = nullptr;  // per-triangle hit cache, (BIN_HIT_CACHE + 1) x T_alloc
+    uint32_t* hits = nullptr;  // per-triangle hit cache, BIN_HIT_WORDS x T_alloc
     int64_t hits_T = 0;
     uint64_t sized_map = 0, sized_scene = 0;
     uint32_t* h_total = nullptr;  // pinned
@@ -115,7 +115,6 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->map, (size_t)W * H)) != VSR_OK) return st;
     if ((st = dalloc(&m->tiles, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.hdr, 1)) != VSR_OK) return st;
-    if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.cell_start, (size_t)IDX_CELLS_MAX + 1)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
@@ -128,7 +127,6 @@ void map_release(vsr_map m)
     cudaFree(m->map);
     cudaFree(m->tiles);
     cudaFree(m->idx.hdr);
-    cudaFree(m->idx.cell_count);
     cudaFree(m->idx.cell_start);
     cudaFree(m->idx.sorted);
     cudaFree(m->idx.big);
@@ -182,7 +180,7 @@ vsr_status ensure_ws(vsr_scene sc, int ntiles)
     sc->counts = sc->offsets = nullptr;
     sc->ws_tiles = 0;
     vsr_status s;
-    if ((s = dalloc(&sc->counts, (size_t)ntiles)) != VSR_OK) return s;
+    if ((s = dalloc(&sc->counts, 2 * (size_t)ntiles)) != VSR_OK) return s;  // counts | extra
     if ((s = dalloc(&sc->offsets, (size_t)ntiles + 1)) != VSR_OK) return s;
     sc->ws_tiles = ntiles;
     sc->sized_map = 0;
@@ -401,16 +399,19 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     if (s != VSR_OK) return s;
     const int T = (int)sc->T;
     sc->last_ntiles = ntiles;
-    VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    uint32_t* counts = sc->counts;
+    uint32_t* extra = sc->counts + sc->ws_tiles;
     if (sc->T > sc->hits_T) {
         cudaFree(sc->hits);
         sc->hits = nullptr;
         sc->hits_T = 0;
-        if ((s = dalloc(&sc->hits, (size_t)(BIN_HIT_CACHE + 1) * (size_t)sc->T)) != VSR_OK) return s;
+        if ((s = dalloc(&sc->hits, (size_t)BIN_HIT_WORDS * (size_t)sc->T)) != VSR_OK) return s;
         sc->hits_T = sc->T;
     }
-    if ((s = launch_bin_count(sc->rec, T, m->idx, sc->counts, sc->hits, st)) != VSR_OK) return s;
-    if ((s = launch_scan(sc->counts, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    VSR_CUDA_TRY(cudaMemsetAsync(extra, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, extra, sc->hits, st)) != VSR_OK) return s;
+    if ((s = launch_scan(counts, extra, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
     if (sc->sized_map != m->gen || sc->sized_scene != sc->gen || sc->cap == 0) {
         // first binning of this (map, scene) pair: size the bins once
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -428,9 +429,8 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->sized_map = m->gen;
         sc->sized_scene = sc->gen;
     }
-    VSR_CUDA_TRY(cudaMemsetAsync(sc->counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->hits, sc->offsets, sc->counts, sc->ids, sc->cap, status_word(),
-                             st)) != VSR_OK)
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->hits, sc->offsets, counts, extra, sc->ids, sc->cap,
+                             status_word(), st)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
@@ -538,10 +538,11 @@ constexpr uint32_t NA_T_MAX = 262144;
 constexpr uint32_t NA_PAIRS_MAX = 1u << 20;
 constexpr size_t NA_STATUS_WORDS = 64;  // word 0: status when the caller passes none
 constexpr size_t NA_COUNTS = NA_STATUS_WORDS;
-constexpr size_t NA_OFFSETS = NA_COUNTS + NA_TILES_MAX;
+constexpr size_t NA_EXTRA = NA_COUNTS + NA_TILES_MAX;
+constexpr size_t NA_OFFSETS = NA_EXTRA + NA_TILES_MAX;
 constexpr size_t NA_IDS = NA_OFFSETS + NA_TILES_MAX + 64;
 constexpr size_t NA_HITS = NA_IDS + NA_PAIRS_MAX;
-constexpr size_t NA_WORDS = NA_HITS + (size_t)(BIN_HIT_CACHE + 1) * NA_T_MAX;
+constexpr size_t NA_WORDS = NA_HITS + (size_t)BIN_HIT_WORDS * NA_T_MAX;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 
@@ -585,6 +586,7 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
     const int T = (int)sc->T;
     int* status = status_dev ? (int*)status_dev : (int*)base;
     uint32_t* counts = base + NA_COUNTS;
+    uint32_t* extra = base + NA_EXTRA;
     uint32_t* offsets = base + NA_OFFSETS;
     uint32_t* ids = base + NA_IDS;
     uint32_t* hits = base + NA_HITS;
@@ -592,10 +594,11 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
     // the array keeps the previous call's contents: clear what starts at zero
     VSR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, hits, st)) != VSR_OK) return s;
-    if ((s = launch_scan(counts, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_fill(sc->rec, T, m->idx, hits, offsets, counts, ids, NA_PAIRS_MAX, status, st)) != VSR_OK)
+    VSR_CUDA_TRY(cudaMemsetAsync(extra, 0, sizeof(uint32_t) * (size_t)ntiles, st));
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, extra, hits, st)) != VSR_OK) return s;
+    if ((s = launch_scan(counts, extra, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, hits, offsets, counts, extra, ids, NA_PAIRS_MAX, status, st)) !=
+        VSR_OK)
         return s;
     return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, T, offsets, ids, NA_PAIRS_MAX, id_dev, depth_dev,
                          cov_dev, nullptr, nullptr, nullptr, status, st);

@@ -56,37 +56,14 @@ __device__ __forceinline__ int home_cell(float3 a, const TileIndexHdr& h)
 }
 
 // ---- tile index -------------------------------------------------------------
+//
+// One CTA of IDX_THREADS threads builds the whole index: the histogram of
+// tile half-angles and the grid plan, the per-cell counts (in shared
+// memory), their exclusive scan, and the cell-sorted cone copies.  A tile
+// index holds one entry per tile, so a single CTA keeps every phase a few
+// loads per thread and saves the launch gaps of separate kernels.
 
-__global__ void idx_hist_kernel(const Cone* __restrict__ tiles, int ntiles, TileIndexHdr* hdr)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntiles) return;
-    Cone c = tiles[i];
-    if (c.c1.z == 0.0f) return;
-    atomicAdd(&hdr->hist[hist_bin(cone_half_angle(c))], 1u);
-    atomicAdd(&hdr->n_valid, 1u);
-    atomicMax(&hdr->h_max, __float_as_uint(c.c1.y));  // non-negative floats order as their bits
-}
-
-// one thread: grid size and small / big threshold from the 99th percentile
-// of tile half-angles
-__global__ void idx_plan_kernel(TileIndexHdr* hdr)
-{
-    unsigned target = (unsigned)ceilf(0.99f * (float)hdr->n_valid), run = 0;
-    int b = 0;
-    for (; b < IDX_HIST; ++b) {
-        run += hdr->hist[b];
-        if (run >= target) break;
-    }
-    float cut = hist_upper(min(b, IDX_HIST - 1));
-    float cell = fminf(PI_F / 8.0f, fmaxf(PI_F / IDX_NLAT_MAX, cut));
-    int nlat = min(IDX_NLAT_MAX, (int)ceilf(PI_F / cell));
-    hdr->nlat = nlat;
-    hdr->nlon = 2 * nlat;
-    hdr->ncell = nlat * 2 * nlat;
-    hdr->cell = PI_F / nlat;
-    hdr->alpha_cut = cut;
-}
+constexpr int IDX_THREADS = 1024;
 
 __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
 {
@@ -96,35 +73,113 @@ __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
     return e;
 }
 
-__global__ void idx_count_kernel(const Cone* __restrict__ tiles, int ntiles, TileIndexHdr* hdr,
-                                 uint32_t* __restrict__ cell_count, Cone* __restrict__ big)
+__global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __restrict__ tiles, int ntiles,
+                                                                 TileIndexHdr* __restrict__ hdr,
+                                                                 uint32_t* __restrict__ cell_start,
+                                                                 Cone* __restrict__ sorted, Cone* __restrict__ big)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntiles) return;
-    Cone c = tiles[i];
-    if (c.c1.z == 0.0f) return;
-    const TileIndexHdr h = *hdr;
-    float a = cone_half_angle(c);
-    if (a > h.alpha_cut) {
-        big[atomicAdd(&hdr->n_big, 1u)] = index_entry(c, i);
-    } else {
-        atomicAdd(&cell_count[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u);
-        atomicMax(&hdr->alpha_small_max, __float_as_uint(a));
-    }
-}
+    extern __shared__ uint32_t s_cell[];  // IDX_CELLS_MAX counts, then cursors
+    __shared__ unsigned s_hist[IDX_HIST];
+    __shared__ unsigned s_nvalid, s_hmax, s_amax, s_nbig;
+    __shared__ TileIndexHdr s_h;
+    __shared__ uint32_t s_warp[IDX_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-__global__ void idx_fill_kernel(const Cone* __restrict__ tiles, int ntiles, const TileIndexHdr* hdr,
-                                const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ cursor,
-                                Cone* __restrict__ sorted)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntiles) return;
-    Cone c = tiles[i];
-    if (c.c1.z == 0.0f) return;
-    const TileIndexHdr h = *hdr;
-    if (cone_half_angle(c) > h.alpha_cut) return;
-    int cell = home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h);
-    sorted[cell_start[cell] + atomicAdd(&cursor[cell], 1u)] = index_entry(c, i);
+    for (int q = tid; q < IDX_CELLS_MAX; q += IDX_THREADS) s_cell[q] = 0u;
+    if (tid < IDX_HIST) s_hist[tid] = 0u;
+    if (tid == 0) s_nvalid = s_hmax = s_amax = s_nbig = 0u;
+    __syncthreads();
+
+    // histogram of half-angles, widest ramp
+    for (int i = tid; i < ntiles; i += IDX_THREADS) {
+        const Cone c = tiles[i];
+        if (c.c1.z == 0.0f) continue;
+        atomicAdd(&s_hist[hist_bin(cone_half_angle(c))], 1u);
+        atomicAdd(&s_nvalid, 1u);
+        atomicMax(&s_hmax, __float_as_uint(c.c1.y));  // non-negative floats order as their bits
+    }
+    __syncthreads();
+
+    // grid size and small / big threshold from the 99th percentile
+    if (tid == 0) {
+        unsigned target = (unsigned)ceilf(0.99f * (float)s_nvalid), run = 0;
+        int b = 0;
+        for (; b < IDX_HIST; ++b) {
+            run += s_hist[b];
+            if (run >= target) break;
+        }
+        const float cut = hist_upper(min(b, IDX_HIST - 1));
+        const float cell = fminf(PI_F / 8.0f, fmaxf(PI_F / IDX_NLAT_MAX, cut));
+        const int nlat = min(IDX_NLAT_MAX, (int)ceilf(PI_F / cell));
+        s_h.nlat = nlat;
+        s_h.nlon = 2 * nlat;
+        s_h.ncell = 2 * nlat * nlat;
+        s_h.cell = PI_F / nlat;
+        s_h.alpha_cut = cut;
+    }
+    __syncthreads();
+    const TileIndexHdr h = s_h;
+
+    // per-cell counts of the small tiles; big tiles to their own list
+    for (int i = tid; i < ntiles; i += IDX_THREADS) {
+        const Cone c = tiles[i];
+        if (c.c1.z == 0.0f) continue;
+        const float a = cone_half_angle(c);
+        if (a > h.alpha_cut) {
+            big[atomicAdd(&s_nbig, 1u)] = index_entry(c, i);
+        } else {
+            atomicAdd(&s_cell[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u);
+            atomicMax(&s_amax, __float_as_uint(a));
+        }
+    }
+    __syncthreads();
+
+    // exclusive scan of the cell counts (contiguous segment per thread)
+    const int per = (h.ncell + IDX_THREADS - 1) / IDX_THREADS;
+    const int b0 = min(h.ncell, tid * per), b1 = min(h.ncell, b0 + per);
+    uint32_t local = 0;
+    for (int q = b0; q < b1; ++q) local += s_cell[q];
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        s_warp[lane] = v;
+    }
+    __syncthreads();
+    uint32_t run = x - local + (warp > 0 ? s_warp[warp - 1] : 0u);
+    for (int q = b0; q < b1; ++q) {
+        const uint32_t cnt = s_cell[q];
+        cell_start[q] = run;
+        s_cell[q] = run;  // becomes the fill cursor
+        run += cnt;
+    }
+    if (tid == IDX_THREADS - 1) cell_start[h.ncell] = s_warp[31];
+    __syncthreads();
+
+    // cell-sorted copies of the small tiles' cones
+    for (int i = tid; i < ntiles; i += IDX_THREADS) {
+        const Cone c = tiles[i];
+        if (c.c1.z == 0.0f || cone_half_angle(c) > h.alpha_cut) continue;
+        sorted[atomicAdd(&s_cell[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u)] = index_entry(c, i);
+    }
+    if (tid == 0) {
+        TileIndexHdr o = h;
+        o.alpha_small_max = s_amax;
+        o.h_max = s_hmax;
+        o.n_big = s_nbig;
+        o.n_valid = s_nvalid;
+        for (int q = 0; q < IDX_HIST; ++q) o.hist[q] = s_hist[q];
+        *hdr = o;
+    }
 }
 
 // ---- per-triangle binning ---------------------------------------------------
@@ -134,38 +189,52 @@ __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec
                                                    const TileIndexHdr* __restrict__ hdr,
                                                    const uint32_t* __restrict__ cell_start,
                                                    const Cone* __restrict__ sorted, const Cone* __restrict__ big,
-                                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ hits,
-                                                   const uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
-                                                   uint32_t cap, int* status)
+                                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ extra,
+                                                   uint32_t* __restrict__ hits, const uint32_t* __restrict__ offsets,
+                                                   uint32_t* __restrict__ ids, uint32_t cap, int* status)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const size_t TT = (size_t)T;
-    uint32_t* my_hits = hits + (size_t)t * (BIN_HIT_CACHE + 1);
+    uint32_t* my_hits = hits + (size_t)t * BIN_HIT_WORDS;
     uint32_t nhit = 0;
 
+    auto put = [&](uint32_t tile, uint32_t pos) {
+        if (pos < cap && pos < offsets[tile + 1])
+            ids[pos] = (uint32_t)t;
+        else
+            raise_status(status, VSR_ERR_BIN_OVERFLOW);
+    };
+
+    if (FILL) {
+        // the count pass recorded (tile, slot) for up to BIN_HIT_CACHE hits
+        const uint32_t n = my_hits[0];
+        const uint32_t nc = min(n, (uint32_t)BIN_HIT_CACHE);
+        for (uint32_t q = 0; q < nc; ++q) {
+            const uint32_t tile = my_hits[1 + 2 * q];
+            put(tile, offsets[tile] + my_hits[2 + 2 * q]);
+        }
+        if (n <= BIN_HIT_CACHE) return;
+    }
+
+    // count: the first BIN_HIT_CACHE hits take a slot in `counts`, the rest
+    // are counted in `extra`.  fill (only for triangles with more hits):
+    // search again, skip the cached hits, place the others after the slotted
+    // ones of their tile.
     auto emit = [&](uint32_t tile) {
         if (!FILL) {
-            atomicAdd(&counts[tile], 1u);
-            if (nhit < BIN_HIT_CACHE) my_hits[1 + nhit] = tile;
-        } else {
-            uint32_t pos = offsets[tile] + atomicAdd(&counts[tile], 1u);
-            if (pos < cap && pos < offsets[tile + 1])
-                ids[pos] = (uint32_t)t;
-            else
-                raise_status(status, VSR_ERR_BIN_OVERFLOW);
+            if (nhit < BIN_HIT_CACHE) {
+                my_hits[1 + 2 * nhit] = tile;
+                my_hits[2 + 2 * nhit] = atomicAdd(&counts[tile], 1u);
+            } else {
+                atomicAdd(&extra[tile], 1u);
+            }
+        } else if (nhit >= BIN_HIT_CACHE) {
+            put(tile, offsets[tile] + counts[tile] + atomicSub(&extra[tile], 1u) - 1u);
         }
         ++nhit;
     };
 
-    if (FILL) {
-        // the count pass cached up to BIN_HIT_CACHE hits per triangle
-        const uint32_t n = my_hits[0];
-        if (n <= BIN_HIT_CACHE) {
-            for (uint32_t q = 0; q < n; ++q) emit(my_hits[1 + q]);
-            return;
-        }
-    }
     const float4 c0 = rec[RF_CAP * TT + t];
     const float4 c1 = rec[RF_CAP2 * TT + t];
     if (c1.w == 0.0f) {  // culled
@@ -219,10 +288,12 @@ __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec
     if (!FILL) my_hits[0] = nhit;
 }
 
-// Exclusive scan of n counts into offsets[0..n] by one CTA of 1024 threads:
+// Exclusive scan of n counts (+ extra, when not NULL) into offsets[0..n] by
+// one CTA of 1024 threads:
 // chunks of 4096 (four consecutive elements per thread), carried across
 // chunks.  n comes from n_dev when it is not NULL.
-__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__ counts, int n_host,
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__ counts,
+                                                     const uint32_t* __restrict__ extra, int n_host,
                                                      const int* __restrict__ n_dev, uint32_t* __restrict__ offsets)
 {
     __shared__ uint32_t warp_sums[32];
@@ -235,7 +306,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__
         const int b = base + 4 * tid;
         uint32_t v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = b + q < n ? counts[b + q] : 0u;
+        for (int q = 0; q < 4; ++q) v[q] = b + q < n ? counts[b + q] + (extra ? extra[b + q] : 0u) : 0u;
         const uint32_t local = v[0] + v[1] + v[2] + v[3];
         uint32_t x = local;
         for (int o = 1; o < 32; o <<= 1) {
@@ -268,46 +339,40 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__
 
 }  // namespace
 
-vsr_status launch_scan(const uint32_t* counts, int n, const int* n_dev, uint32_t* offsets, cudaStream_t st)
+vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
+                       cudaStream_t st)
 {
-    scan_kernel<<<1, 1024, 0, st>>>(counts, n, n_dev, offsets);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, extra, n, n_dev, offsets);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
-    const int nb = (ntiles + 255) / 256;
-    VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
-    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
-    idx_hist_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr);
-    idx_plan_kernel<<<1, 1, 0, st>>>(idx.hdr);
-    idx_count_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_count, idx.big);
-    VSR_CUDA_TRY(cudaGetLastError());
-    vsr_status s = launch_scan(idx.cell_count, 0, &idx.hdr->ncell, idx.cell_start, st);
-    if (s != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
-    idx_fill_kernel<<<nb, 256, 0, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
+    const size_t smem = sizeof(uint32_t) * IDX_CELLS_MAX;  // 128 KB of per-cell counts
+    VSR_CUDA_TRY(cudaFuncSetAttribute(idx_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    idx_build_kernel<<<1, IDX_THREADS, smem, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.sorted, idx.big);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* hits,
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* extra, uint32_t* hits,
                             cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
     bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, counts,
-                                                       hits, nullptr, nullptr, 0, nullptr);
+                                                       extra, hits, nullptr, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
-                           uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st)
+                           uint32_t* counts, uint32_t* extra, uint32_t* ids, uint32_t cap, int* status,
+                           cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, cursors,
-                                                      const_cast<uint32_t*>(hits), offsets, ids, cap, status);
+    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, counts,
+                                                      extra, const_cast<uint32_t*>(hits), offsets, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -208,6 +208,16 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                 const float4 b = st.s1[jj];
                 keep = cap_hits_cone(make_float3(a.x, a.y, a.z), 1.0f - 0.5f * b.y, b.x, make_float3(wax, way, waz),
                                      wcos, wsin, wh);
+                // every pixel G of the warp is within alpha of the warp axis w, so
+                // G.n <= w.n + sin(alpha) + (1 - cos(alpha)) for a unit normal n;
+                // a triangle with some edge plane below -h there has no fragment
+                // (skipped while counting algorithmic tests, which are defined
+                // by the cap alone)
+                const float lim = -(wh + wsin + (1.0f - wcos) + 1e-6f);
+                const float4 n1 = st.s2[jj], n2 = st.s3[jj], n3 = st.s4[jj];
+                keep = keep && (n_alg != nullptr || (fmaf(wax, n1.x, fmaf(way, n1.y, waz * n1.z)) > lim &&
+                       fmaf(wax, n2.x, fmaf(way, n2.y, waz * n2.z)) > lim &&
+                       fmaf(wax, n3.x, fmaf(way, n3.y, waz * n3.z)) > lim));
             }
             unsigned mask = __ballot_sync(0xffffffffu, keep);
             while (mask) {
@@ -245,23 +255,26 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                 if (!__any_sync(0xffffffffu, anyf)) continue;
                 const float4 pl = st.s5[j];
                 const unsigned ties = __float_as_uint(a.w);
+                const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    if (!frag[p]) continue;
+                    // predicated: every lane computes, non-fragments add nothing
                     const float D = fmaf(dgx[p], pl.x, fmaf(dgy[p], pl.y, fmaf(dgz[p], pl.z, pl.w)));
                     const float r = __fdividef(b.w, D);
-                    if (!(r > 0.0f && r < INFINITY)) continue;
+                    const bool f = frag[p] && r > 0.0f && r < INFINITY;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
-                    acc[p] = min(acc[p] + __float2uint_rn(m * 16777216.0f), 16777216u);
-                    const bool in1 = g1[p] > 0.0f || (g1[p] == 0.0f && (ties & 1u));
-                    const bool in2 = g2[p] > 0.0f || (g2[p] == 0.0f && (ties & 2u));
-                    const bool in3 = g3[p] > 0.0f || (g3[p] == 0.0f && (ties & 4u));
-                    if (in1 && in2 && in3) {
-                        const unsigned long long k =
-                            ((unsigned long long)__float_as_uint(r) << 32) | (unsigned long long)__float_as_uint(e.w);
-                        key[p] = k < key[p] ? k : key[p];
-                        ++cnt_in[p];
-                    }
+                    acc[p] = min(acc[p] + (f ? __float2uint_rn(m * 16777216.0f) : 0u), 16777216u);
+                    // centre-inside: all three edge distances >= 0, exact zeros by the tie rule
+                    const float g3m = fminf(fminf(g1[p], g2[p]), g3[p]);
+                    bool in = g3m > 0.0f;
+                    if (g3m == 0.0f)
+                        in = (g1[p] > 0.0f || (g1[p] == 0.0f && (ties & 1u))) &&
+                             (g2[p] > 0.0f || (g2[p] == 0.0f && (ties & 2u))) &&
+                             (g3[p] > 0.0f || (g3[p] == 0.0f && (ties & 4u)));
+                    in = in && f;
+                    const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
+                    key[p] = in && k < key[p] ? k : key[p];
+                    cnt_in[p] += in;
                 }
             }
         }

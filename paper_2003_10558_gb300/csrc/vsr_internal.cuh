@@ -113,19 +113,24 @@ vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* r
 // (sin alpha, h, tile index bits, 0).  Big tiles are stored the same way.
 struct TileIndex {
     TileIndexHdr* hdr;
-    uint32_t* cell_count;  // IDX_CELLS_MAX
     uint32_t* cell_start;  // IDX_CELLS_MAX + 1
     Cone* sorted;          // ntiles
     Cone* big;             // ntiles
 };
-// per-triangle hit cache between the count and fill passes of the binner
-constexpr int BIN_HIT_CACHE = 8;
+// per-triangle hit cache between the count and fill passes of the binner:
+// word 0 = number of hits, then (tile, slot) for up to BIN_HIT_CACHE hits
+constexpr int BIN_HIT_CACHE = 4;
+constexpr int BIN_HIT_WORDS = 1 + 2 * BIN_HIT_CACHE;
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
-vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* hits,
+// binning of one frame: counts and extra zeroed by the caller ->
+// launch_bin_count -> launch_scan(counts, extra) -> launch_bin_fill
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* extra, uint32_t* hits,
                             cudaStream_t st);
-vsr_status launch_scan(const uint32_t* counts, int n, const int* n_dev, uint32_t* offsets, cudaStream_t st);
+vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
+                       cudaStream_t st);
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
-                           uint32_t* cursors, uint32_t* ids, uint32_t cap, int* status, cudaStream_t st);
+                           uint32_t* counts, uint32_t* extra, uint32_t* ids, uint32_t cap, int* status,
+                           cudaStream_t st);
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,

@@ -247,6 +247,8 @@ def raster(m: Map, sc: Scene, out=None, stats=False, n_inside=False, stream=None
     """Rasterize: returns dict of CUDA tensors id (int32 view of uint32),
     depth, cov [H, W]; with stats=True also n_alg, n_exec (python ints, sync);
     with n_inside=True the per-pixel count of centre-inside triangles.
+    stats="exec" counts only the evaluated pairs (the kernel then culls as in
+    a timed run; counting algorithmic tests disables the edge-plane cull).
     binned=True reuses the bins of the last bin() call (vsr_raster_tiles)."""
     import torch
     H, W = m.shape
@@ -261,7 +263,7 @@ def raster(m: Map, sc: Scene, out=None, stats=False, n_inside=False, stream=None
         cnt = torch.zeros(2, dtype=torch.int64, device=dev)
         if n_inside:
             out["n_inside"] = torch.empty((H, W), dtype=torch.int32, device=dev)
-        st = RasterStats(cnt.data_ptr() if stats else None, cnt.data_ptr() + 8 if stats else None,
+        st = RasterStats(cnt.data_ptr() if stats is True else None, cnt.data_ptr() + 8 if stats else None,
                          out["n_inside"].data_ptr() if n_inside else None)
     fn = load().vsr_raster_tiles if binned else load().vsr_raster_ex
     check(fn(m.h, sc.h, _dptr(out.get("id")), _dptr(out.get("depth")), _dptr(out.get("cov")),
