@@ -155,14 +155,19 @@ int64_t vsr_scene_size(vsr_scene s);
  * The merge of Sec. 1.3 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
  * to min(1, sum m^f), so the result does not depend on fragment order; it is
  * accumulated in 2^-24 fixed point and is bit-reproducible.
- * Scratch (tile bins) is held by the scene handle; the first call for a new
- * (map, scene) pair synchronises `stream` once to size it.  A scene must not
- * be rasterized on two streams at the same time. */
+ * Scratch (tile bins) is held by the scene handle.  It is sized with one
+ * synchronisation of `stream` the first time and whenever the map's tile
+ * count or the scene's T changes; otherwise no call synchronises: the bins
+ * grow ahead of need from the pair count of an earlier frame, and a frame
+ * that still outgrows them (e.g. after the camera moved) raises
+ * VSR_ERR_BIN_OVERFLOW in the device status (vsr_last_device_status) with
+ * that frame's outputs incomplete, the next call growing the bins.  A scene
+ * must not be rasterized on two streams at the same time. */
 vsr_status vsr_raster(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev, void* stream);
 
 /* The two halves of vsr_raster, for callers that reuse one binning:
- * vsr_bin builds the tile bins of (m, s) (count, scan, fill; the first call
- * for a new pair synchronises `stream` once to size them);
+ * vsr_bin builds the tile bins of (m, s) (count, scan, fill; sized as
+ * described for vsr_raster);
  * vsr_raster_tiles runs the tile coverage/depth kernel on the current bins
  * and returns VSR_ERR_INVALID_ARG if they were built for another map or an
  * older set-up of the scene. */
@@ -187,7 +192,7 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* dep
  * vsr_raster sizes the bins of a new map/scene pair).  The paper has no
  * counterpart; this is a service of the library.
  * The tile bins live in one fixed device array inside the library (about
- * 13.8 MB, held on every device that loads the library until the process
+ * 22 MB, held on every device that loads the library until the process
  * exits) instead of the scene's workspace: the call allocates nothing and
  * never synchronises.  Maps and scenes are made beforehand as usual.
  * Limits: at most 16384 tiles of 16x16 pixels (e.g. 2048 x 2048), at most
@@ -217,6 +222,36 @@ vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
  * vsr_raster. */
 vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
+
+/* ---- batched multi-view rendering -------------------------------------------
+ * A batch renders V views of one scene in one sequence of launches: the
+ * set-up of every (view, triangle) pair (Sec. 1.1, 1.1.2, 1.1.5 per view
+ * camera), the binning of every view over the concatenated tiles of all
+ * views, and one persistent raster launch in which CTAs take (view, tile)
+ * items from a shared atomic queue, so views of uneven size share the GPU
+ * without a tail per view.  Outputs per view are those of vsr_raster.
+ *
+ * vsr_batch_render: maps[V] (built with vsr_make_map*), tris_dev [T][3][3]
+ * (device, shared by all views), cams (host, V x 12 floats, one camera per
+ * view as in vsr_setup), id_dev / depth_dev / cov_dev (host arrays of V
+ * caller-owned device pointers, [H_v][W_v] each; the arrays themselves or
+ * any entry may be NULL).  The first call for a configuration (the same
+ * maps, map contents, scene buffer and T, output pointers) runs eagerly,
+ * synchronises `stream` once to size the bins, autotunes the persistent
+ * raster grid by timing 2, 4, 6 and 7 CTAs per SM on that frame, and
+ * captures the whole frame into a CUDA graph; later calls with the same
+ * configuration copy only the cameras (into pinned staging of the batch)
+ * and replay the graph on `stream`.  Device memory: V x T x 196 B of set-up
+ * records and bin caches plus the bins.  A batch must not render on two
+ * streams at once. */
+typedef struct vsr_batch_s* vsr_batch;
+vsr_status vsr_batch_create(vsr_batch* out);
+vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const float* tris_dev, int64_t T,
+                            const float* cams, uint32_t* const* id_dev, float* const* depth_dev,
+                            float* const* cov_dev, void* stream);
+/* The autotuned persistent raster grid (CTAs) and whether a graph is ready. */
+vsr_status vsr_batch_config(vsr_batch b, int* raster_grid, int* graphed);
+void vsr_batch_free(vsr_batch b);
 
 /* ---- status ---------------------------------------------------------------- */
 const char* vsr_status_str(vsr_status s);

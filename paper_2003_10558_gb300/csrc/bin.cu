@@ -184,17 +184,24 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
 
 // ---- per-triangle binning ---------------------------------------------------
 
+// One thread per triangle of one view: the view is v0, or views[blockIdx.y]
+// when views is not NULL (all views share T, ids and cap).
 template <bool FILL>
-__global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec, int T,
-                                                   const TileIndexHdr* __restrict__ hdr,
-                                                   const uint32_t* __restrict__ cell_start,
-                                                   const Cone* __restrict__ sorted, const Cone* __restrict__ big,
-                                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ extra,
-                                                   uint32_t* __restrict__ hits, const uint32_t* __restrict__ offsets,
+__global__ void __launch_bounds__(128) bin_kernel(BinView v0, const BinView* __restrict__ views, int T,
                                                    uint32_t* __restrict__ ids, uint32_t cap, int* status)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
+    const BinView v = views ? views[blockIdx.y] : v0;
+    const float4* __restrict__ rec = v.rec;
+    const TileIndexHdr* __restrict__ hdr = v.hdr;
+    const uint32_t* __restrict__ cell_start = v.cell_start;
+    const Cone* __restrict__ sorted = v.sorted;
+    const Cone* __restrict__ big = v.big;
+    uint32_t* __restrict__ counts = v.counts;
+    uint32_t* __restrict__ extra = v.extra;
+    uint32_t* __restrict__ hits = v.hits;
+    const uint32_t* __restrict__ offsets = v.offsets;
     const size_t TT = (size_t)T;
     uint32_t* my_hits = hits + (size_t)t * BIN_HIT_WORDS;
     uint32_t nhit = 0;
@@ -248,16 +255,20 @@ __global__ void __launch_bounds__(128) bin_kernel(const float4* __restrict__ rec
     const float cell = h.cell;
     const float amax = __uint_as_float(h.alpha_small_max), hmax = __uint_as_float(h.h_max);
 
+    // the cap enlarged once by the map's widest ramp (>= every tile's own):
+    // cos / sin of its radius beta, so each tile test is a few FMAs
+    const float cb = fmaxf(-1.0f, fminf(1.0f, cr - hmax * sr));
+    const float sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
     auto scan_range = [&](const Cone* __restrict__ list, uint32_t k0, uint32_t k1) {
         for (uint32_t k = k0; k < k1; ++k) {
             const Cone c = list[k];
-            if (cap_hits_cone(S, cr, sr, make_float3(c.c0.x, c.c0.y, c.c0.z), c.c0.w, c.c1.x, c.c1.y))
-                emit(__float_as_uint(c.c1.z));
+            // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
+            const float cg = fmaf(S.x, c.c0.x, fmaf(S.y, c.c0.y, S.z * c.c0.z));
+            if (cb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, cb, -c.c1.x * sb) - 2e-6f) emit(__float_as_uint(c.c1.z));
         }
     };
 
-    // search radius: enlarged cap (widest ramp of the map) + largest small tile
-    const float cb = fmaxf(-1.0f, fminf(1.0f, cr - hmax * sr));
+    // search radius: enlarged cap + largest small tile
     const float gamma = acosf(cb) + amax + 1e-4f;
     int r0 = 0, r1 = nlat - 1, c0i = 0, ncol = nlon;
     if (gamma < PI_F) {
@@ -360,8 +371,8 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
                             cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, counts,
-                                                       extra, hits, nullptr, nullptr, 0, nullptr);
+    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, hits, nullptr};
+    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, nullptr, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -371,8 +382,103 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
                            cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(rec, T, idx.hdr, idx.cell_start, idx.sorted, idx.big, counts,
-                                                      extra, const_cast<uint32_t*>(hits), offsets, ids, cap, status);
+    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, const_cast<uint32_t*>(hits),
+                    offsets};
+    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(v, nullptr, T, ids, cap, status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_bin_count_views(const BinView* views, int nviews, int T, cudaStream_t st)
+{
+    if (T == 0 || nviews == 0) return VSR_OK;
+    const BinView none{};
+    bin_kernel<false><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(none, views, T, nullptr, 0, nullptr);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_bin_fill_views(const BinView* views, int nviews, int T, uint32_t* ids, uint32_t cap, int* status,
+                                 cudaStream_t st)
+{
+    if (T == 0 || nviews == 0) return VSR_OK;
+    const BinView none{};
+    bin_kernel<true><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(none, views, T, ids, cap, status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+// ---- large exclusive scan (multi-CTA) ---------------------------------------
+// pass 1: per 4096-element block sums; pass 2: one CTA scans the block sums
+// (partials[nb] = total); pass 3: per block, local scan plus the block's base.
+
+__global__ void __launch_bounds__(1024) scan_block_sums(const uint32_t* __restrict__ counts,
+                                                         const uint32_t* __restrict__ extra, int n,
+                                                         uint32_t* __restrict__ partials)
+{
+    __shared__ uint32_t ws[32];
+    const int b = blockIdx.x * 4096 + 4 * threadIdx.x;
+    uint32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (b + q < n) v += counts[b + q] + (extra ? extra[b + q] : 0u);
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t w = ws[threadIdx.x];
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) partials[blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(1024) scan_blocks_apply(const uint32_t* __restrict__ counts,
+                                                           const uint32_t* __restrict__ extra, int n,
+                                                           const uint32_t* __restrict__ bases,
+                                                           uint32_t* __restrict__ offsets)
+{
+    __shared__ uint32_t warp_sums[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = blockIdx.x * 4096 + 4 * tid;
+    uint32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = b + q < n ? counts[b + q] + (extra ? extra[b + q] : 0u) : 0u;
+    const uint32_t local = v[0] + v[1] + v[2] + v[3];
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t run = bases[blockIdx.x] + x - local + (warp > 0 ? warp_sums[warp - 1] : 0u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (b + q < n) offsets[b + q] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) offsets[n] = bases[gridDim.x];
+}
+
+vsr_status launch_scan_large(const uint32_t* counts, const uint32_t* extra, int n, uint32_t* partials,
+                             uint32_t* offsets, cudaStream_t st)
+{
+    const int nb = (n + 4095) / 4096;
+    if (nb <= 1) return launch_scan(counts, extra, n, nullptr, offsets, st);
+    scan_block_sums<<<nb, 1024, 0, st>>>(counts, extra, n, partials);
+    // scan the nb block sums in place into partials[nb + 1 ...]: reuse the one-CTA scan
+    vsr_status s = launch_scan(partials, nullptr, nb, nullptr, partials + nb + 1, st);
+    if (s != VSR_OK) return s;
+    scan_blocks_apply<<<nb, 1024, 0, st>>>(counts, extra, n, partials + nb + 1, offsets);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

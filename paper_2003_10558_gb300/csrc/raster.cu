@@ -49,7 +49,7 @@ struct __align__(16) Stage {
     float4 s3[CHUNK];  // n2.hi xyz, a.n2
     float4 s4[CHUNK];  // n3.hi xyz, a.n3
     float4 s5[CHUNK];  // N-hat.hi xyz, a.N-hat
-    float4 s6[CHUNK];  // S-hat.lo xyz, triangle index (bits)
+    float4 s6[CHUNK];  // S-hat - a (tile axis) xyz, triangle index (bits)
 };
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -80,17 +80,25 @@ __device__ __forceinline__ float norm2_minus_one(float x, float y, float z)
     return __fadd_rn(__fadd_rn(s2.hi, -1.0f), tail);
 }
 
-__global__ void __launch_bounds__(RT, 8) raster_kernel(
-    const float4* __restrict__ map, int W, int H, const Cone* __restrict__ tiles, int tiles_x,
-    const float4* __restrict__ rec, int T, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ids,
-    uint32_t cap, uint32_t* __restrict__ out_id, float* __restrict__ out_depth, float* __restrict__ out_cov,
-    unsigned long long* __restrict__ n_alg, unsigned long long* __restrict__ n_exec, int32_t* __restrict__ n_inside,
-    int* __restrict__ status)
+// One 16x16 tile of one view.  Called by every thread of a CTA of RT
+// threads; `st` is the CTA's staging area (reusable across calls: every use
+// is fenced by the barriers of the chunk loop).
+template <bool STATS>
+__device__ __forceinline__ void raster_tile(const RasterView& view, int tile, Stage& st, bool count_alg,
+                                            uint32_t& cnt_alg, uint32_t& cnt_exec, int32_t* __restrict__ n_inside,
+                                            int* __restrict__ status)
 {
-    __shared__ Stage st;
-    __shared__ unsigned long long red[2][RT / 32];
+    const float4* __restrict__ map = view.map;
+    const int W = view.W, H = view.H, tiles_x = view.tiles_x, T = view.T;
+    const Cone* __restrict__ tiles = view.tiles;
+    const float4* __restrict__ rec = view.rec;
+    const uint32_t* __restrict__ offsets = view.offsets;
+    const uint32_t* __restrict__ ids = view.ids;
+    const uint32_t cap = view.cap;
+    uint32_t* __restrict__ out_id = view.out_id;
+    float* __restrict__ out_depth = view.out_depth;
+    float* __restrict__ out_cov = view.out_cov;
 
-    const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * TILE + (warp & 1) * 8 + (lane & 7);
@@ -164,7 +172,6 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
         }
     }
 
-    uint32_t cnt_alg = 0, cnt_exec = 0;
     const size_t TT = (size_t)T;
 
     for (uint32_t base = b0; base < b1; base += CHUNK) {
@@ -194,7 +201,12 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                 st.s3[threadIdx.x] = make_float4(n2.x, n2.y, n2.z, c2);
                 st.s4[threadIdx.x] = make_float4(n3.x, n3.y, n3.z, c3);
                 st.s5[threadIdx.x] = make_float4(pl.x, pl.y, pl.z, cN);
-                st.s6[threadIdx.x] = make_float4(l1.w, l2.w, l3.w, __uint_as_float(t));
+                // S-hat - a from the pair S-hat (exact differences, then one rounding)
+                const df dsx = df_add(two_sum(cp.x, -ax), df_make(l1.w));
+                const df dsy = df_add(two_sum(cp.y, -ay), df_make(l2.w));
+                const df dsz = df_add(two_sum(cp.z, -az), df_make(l3.w));
+                st.s6[threadIdx.x] = make_float4(__fadd_rn(dsx.hi, dsx.lo), __fadd_rn(dsy.hi, dsy.lo),
+                                                 __fadd_rn(dsz.hi, dsz.lo), __uint_as_float(t));
             }
         }
         __syncthreads();
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                 // by the cap alone)
                 const float lim = -(wh + wsin + (1.0f - wcos) + 1e-6f);
                 const float4 n1 = st.s2[jj], n2 = st.s3[jj], n3 = st.s4[jj];
-                keep = keep && (n_alg != nullptr || (fmaf(wax, n1.x, fmaf(way, n1.y, waz * n1.z)) > lim &&
+                keep = keep && (count_alg || (fmaf(wax, n1.x, fmaf(way, n1.y, waz * n1.z)) > lim &&
                        fmaf(wax, n2.x, fmaf(way, n2.y, waz * n2.z)) > lim &&
                        fmaf(wax, n3.x, fmaf(way, n3.y, waz * n3.z)) > lim));
             }
@@ -226,17 +238,19 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                 const float4 a = st.s0[j];
                 const float4 b = st.s1[j];
                 const float4 e = st.s6[j];
-                ++cnt_exec;
+                if (STATS) ++cnt_exec;
                 // miter distance, chord form
                 float g4[PPT];
                 bool p4[PPT], any4 = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    const float mx = (gx[p] - a.x) - e.x, my = (gy[p] - a.y) - e.y, mz = (gz[p] - a.z) - e.z;
+                    // G - S-hat = (G - a) - (S-hat - a): both differences are at most the tile
+                    // radius, so their rounding costs ~1e-9 rad where the miter matters
+                    const float mx = dgx[p] - e.x, my = dgy[p] - e.y, mz = dgz[p] - e.z;
                     const float q = fmaf(mx, mx, fmaf(my, my, mz * mz));
                     g4[p] = ((b.y - q) + eg[p]) * b.z;
                     p4[p] = pv[p] && g4[p] > -h[p];
-                    cnt_alg += p4[p];
+                    if (STATS) cnt_alg += p4[p];
                     any4 |= p4[p];
                 }
                 if (!__any_sync(0xffffffffu, any4)) continue;
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
                     in = in && f;
                     const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
                     key[p] = in && k < key[p] ? k : key[p];
-                    cnt_in[p] += in;
+                    if (STATS) cnt_in[p] += in;
                 }
             }
         }
@@ -288,9 +302,21 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
         if (out_id) out_id[o] = hit ? (uint32_t)(key[p] & 0xffffffffull) : 0xffffffffu;
         if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key[p] >> 32)) : INFINITY;
         if (out_cov) out_cov[o] = (float)acc[p] * (1.0f / 16777216.0f);
-        if (n_inside) n_inside[o] = cnt_in[p];
+        if (STATS && n_inside) n_inside[o] = cnt_in[p];
     }
-    if (n_alg || n_exec) {
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned long long* __restrict__ n_alg,
+                                                        unsigned long long* __restrict__ n_exec,
+                                                        int32_t* __restrict__ n_inside, int* __restrict__ status)
+{
+    __shared__ Stage st;
+    __shared__ unsigned long long red[2][RT / 32];
+    uint32_t cnt_alg = 0, cnt_exec = 0;
+    raster_tile<STATS>(view, blockIdx.x, st, n_alg != nullptr, cnt_alg, cnt_exec, n_inside, status);
+    if (STATS && (n_alg || n_exec)) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         // cnt_exec counts warp-level evaluations: one per (warp, triangle) for 64 pixels
         unsigned long long va = cnt_alg, ve = lane == 0 ? (unsigned long long)cnt_exec * (32ull * PPT) : 0ull;
         for (int o = 16; o; o >>= 1) {
@@ -314,6 +340,36 @@ __global__ void __launch_bounds__(RT, 8) raster_kernel(
     }
 }
 
+// Persistent multi-view raster: CTAs pull (view, tile) items from one atomic
+// queue until it runs dry, so views of uneven size share the GPU without a
+// tail per view.  Item i belongs to the last view v with tile_base[v] <= i.
+// No CTA waits on another; the loop ends when the counter passes `total`.
+__global__ void __launch_bounds__(RT, 7) raster_persistent_kernel(const RasterView* __restrict__ views,
+                                                                   const uint32_t* __restrict__ tile_base, int nviews,
+                                                                   uint32_t total, uint32_t* __restrict__ queue,
+                                                                   int* __restrict__ status)
+{
+    __shared__ Stage st;
+    __shared__ uint32_t s_item;
+    uint32_t ca = 0, ce = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = nviews - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_base[mid] <= item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        raster_tile<false>(views[lo], (int)(item - tile_base[lo]), st, false, ca, ce, nullptr, status);
+    }
+}
+
 }  // namespace
 
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
@@ -322,8 +378,22 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
                          int* status, cudaStream_t st)
 {
     const int tx = (W + TILE - 1) / TILE, ty = (H + TILE - 1) / TILE;
-    raster_kernel<<<tx * ty, RT, 0, st>>>(map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov,
-                                                 n_alg, n_exec, n_inside, status);
+    const RasterView v{map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov};
+    if (n_alg || n_exec || n_inside)
+        raster_kernel<true><<<tx * ty, RT, 0, st>>>(v, n_alg, n_exec, n_inside, status);
+    else
+        raster_kernel<false><<<tx * ty, RT, 0, st>>>(v, nullptr, nullptr, nullptr, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
+
+vsr_status launch_raster_persistent(const RasterView* views, const uint32_t* tile_base, int nviews, uint32_t total,
+                                    uint32_t* queue, int grid, int* status, cudaStream_t st)
+{
+    if (total == 0) return VSR_OK;
+    raster_persistent_kernel<<<grid, RT, 0, st>>>(views, tile_base, nviews, total, queue, status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+int raster_threads_per_cta() { return RT; }

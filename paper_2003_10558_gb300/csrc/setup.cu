@@ -61,11 +61,24 @@ __device__ __forceinline__ unsigned first_positive(const df3& n)
     return n.z.hi > 0.0f;
 }
 
-__global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tris, int T, Cam cam,
-                                                     float4* __restrict__ rec)
+// VIEWS: blockIdx.y is a view; its camera is read from cams_dev (12 floats)
+// and its records go to rec + view * REC_F * T.
+template <bool VIEWS>
+__global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tris, int T, Cam cam0,
+                                                     const float* __restrict__ cams_dev, float4* __restrict__ rec0)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
+    Cam cam = cam0;
+    float4* __restrict__ rec = rec0;
+    if (VIEWS) {
+        const float* c = cams_dev + 12 * blockIdx.y;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cam.O[q] = c[q];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) cam.M[q] = c[3 + q];
+        rec = rec0 + (size_t)blockIdx.y * REC_F * (size_t)T;
+    }
     float w[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) w[q] = tris[(size_t)t * 9 + q];
@@ -159,7 +172,17 @@ vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* r
     Cam c;
     for (int q = 0; q < 3; ++q) c.O[q] = cam[q];
     for (int q = 0; q < 9; ++q) c.M[q] = cam[3 + q];
-    setup_kernel<<<(T + 127) / 128, 128, 0, st>>>(tris, T, c, rec);
+    setup_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(tris, T, c, nullptr, rec);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_setup_views(const float* tris, int T, const float* cams_dev, int nviews, float4* rec,
+                              cudaStream_t st)
+{
+    if (T == 0 || nviews == 0) return VSR_OK;
+    Cam c = {};
+    setup_kernel<true><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(tris, T, c, cams_dev, rec);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -119,7 +119,7 @@ struct TileIndex {
 };
 // per-triangle hit cache between the count and fill passes of the binner:
 // word 0 = number of hits, then (tile, slot) for up to BIN_HIT_CACHE hits
-constexpr int BIN_HIT_CACHE = 4;
+constexpr int BIN_HIT_CACHE = 8;
 constexpr int BIN_HIT_WORDS = 1 + 2 * BIN_HIT_CACHE;
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
 // binning of one frame: counts and extra zeroed by the caller ->
@@ -131,6 +131,53 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
                            uint32_t* counts, uint32_t* extra, uint32_t* ids, uint32_t cap, int* status,
                            cudaStream_t st);
+// One view as the raster kernel sees it: its map, tile cones, set-up
+// records, bin offsets (indexed by the view's own tile number), bin ids and
+// outputs.
+struct RasterView {
+    const float4* map;
+    int W, H;
+    const Cone* tiles;
+    int tiles_x;
+    const float4* rec;
+    int T;
+    const uint32_t* offsets;
+    const uint32_t* ids;
+    uint32_t cap;
+    uint32_t* out_id;
+    float* out_depth;
+    float* out_cov;
+};
+
+// One view as the binner sees it (tile index of the view's map, the view's
+// set-up records, and its slices of the per-tile counters and offsets).
+struct BinView {
+    const TileIndexHdr* hdr;
+    const uint32_t* cell_start;
+    const Cone* sorted;
+    const Cone* big;
+    const float4* rec;
+    uint32_t* counts;
+    uint32_t* extra;
+    uint32_t* hits;
+    const uint32_t* offsets;
+};
+
+vsr_status launch_raster_persistent(const RasterView* views, const uint32_t* tile_base, int nviews, uint32_t total,
+                                    uint32_t* queue, int grid, int* status, cudaStream_t st);
+int raster_threads_per_cta();
+// views x T set-up with per-view cameras in device memory (Cam: O xyz, M 3x3)
+vsr_status launch_setup_views(const float* tris, int T, const float* cams_dev, int nviews, float4* rec,
+                              cudaStream_t st);
+// binning of nviews views at once (grid.y = view); ids / cap shared
+vsr_status launch_bin_count_views(const BinView* views, int nviews, int T, cudaStream_t st);
+vsr_status launch_bin_fill_views(const BinView* views, int nviews, int T, uint32_t* ids, uint32_t cap, int* status,
+                                 cudaStream_t st);
+// exclusive scan of counts (+ extra) for large n (multi-CTA); `partials`
+// needs 2 * ceil(n / 4096) + 2 words
+vsr_status launch_scan_large(const uint32_t* counts, const uint32_t* extra, int n, uint32_t* partials,
+                             uint32_t* offsets, cudaStream_t st);
+
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,

@@ -30,7 +30,8 @@ AOV_HORIZONTAL, AOV_DIAGONAL, AOV_VERTICAL, AOV_H4X3 = 0, 1, 2, 3
 EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
-           "vsr_scene_bin_pairs", "vsr_raster_noalloc",
+           "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_batch_create", "vsr_batch_render",
+           "vsr_batch_config", "vsr_batch_free",
            "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
 
 
@@ -85,6 +86,10 @@ def load(path: str = LIB_PATH):
             "vsr_raster_tiles": ([vp, vp, vp, vp, vp, P(RasterStats), vp], i32),
             "vsr_scene_bin_pairs": ([vp, vp, P(i64)], i32),
             "vsr_raster_noalloc": ([vp, vp, vp, vp, vp, vp, vp], i32),
+            "vsr_batch_create": ([P(vp)], i32),
+            "vsr_batch_render": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+            "vsr_batch_config": ([vp, P(i32), P(i32)], i32),
+            "vsr_batch_free": ([vp], None),
             "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_status_str": ([i32], ctypes.c_char_p),
             "vsr_last_device_status": ([], i32),
@@ -299,3 +304,51 @@ def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "dept
     check(load().vsr_render_host(m.h, sc.h, p(tris), T, c.ctypes.data_as(ctypes.c_void_p), p(out.get("id")),
                                  p(out.get("depth")), p(out.get("cov")), _stream_ptr(stream)), "vsr_render_host")
     return out
+
+
+class Batch:
+    """Batched multi-view rendering of one scene (vsr_batch_*): one
+    persistent raster launch over all views' tiles, replayed as a CUDA graph
+    while the configuration (maps, scene buffer, outputs) is unchanged."""
+
+    def __init__(self):
+        self.h = ctypes.c_void_p()
+        check(load().vsr_batch_create(ctypes.byref(self.h)), "vsr_batch_create")
+        self._keep = None
+
+    def render(self, maps, tris, cams, outs, stream=None):
+        """maps: list of Map; tris: CUDA float32 [T, 3, 3]; cams: [V, 12];
+        outs: list of dicts with CUDA tensors id / depth / cov per view."""
+        import torch
+        V = len(maps)
+        if not (tris.is_cuda and tris.dtype == torch.float32):
+            raise ValueError("triangles must be a CUDA float32 tensor [T, 3, 3]")
+        tris = tris.contiguous()
+        T = tris.numel() // 9
+        c = np.ascontiguousarray(np.asarray(cams, dtype=np.float32).reshape(V, 12))
+        mh = (ctypes.c_void_p * V)(*[m.h.value for m in maps])
+
+        def ptrs(key):
+            return (ctypes.c_void_p * V)(*[o[key].data_ptr() if o.get(key) is not None else None for o in outs])
+
+        ids, depths, covs = ptrs("id"), ptrs("depth"), ptrs("cov")
+        check(load().vsr_batch_render(self.h, V, mh, _dptr(tris) if T else None, T,
+                                      c.ctypes.data_as(ctypes.c_void_p), ids, depths, covs, _stream_ptr(stream)),
+              "vsr_batch_render")
+        self._keep = (tris, maps, outs)
+
+    def config(self):
+        g, r = ctypes.c_int(), ctypes.c_int()
+        check(load().vsr_batch_config(self.h, ctypes.byref(g), ctypes.byref(r)), "vsr_batch_config")
+        return {"raster_grid": g.value, "graphed": bool(r.value)}
+
+    def free(self):
+        if self.h:
+            load().vsr_batch_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""Batched multi-view rendering (one persistent raster launch over all views,
+CUDA-graph replay) against per-view vsr_raster calls and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_10558_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vsr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_10558_gb300 import build, vsr as V
+    build.build()
+    V.load()
+    return V
+
+
+def _views(n, seed):
+    rng = np.random.default_rng(seed)
+    sizes = [(96, 64), (160, 160), (200, 100), (33, 47), (128, 96), (64, 64)]
+    out = []
+    for v in range(n):
+        W, H = sizes[v % len(sizes)]
+        out.append(dict(W=W, H=H, k=float(rng.uniform(-1, 1)), l=float(rng.uniform(0.5, 1)),
+                        s=float(rng.uniform(0.5, 1)), omega=float(rng.uniform(90, 360)),
+                        cam=scenes.camera(rng.uniform(-1.5, 1.5, 3))))
+    return out
+
+
+def _outs(views, dev="cuda"):
+    return [{"id": torch.empty((v["H"], v["W"]), dtype=torch.int32, device=dev),
+             "depth": torch.empty((v["H"], v["W"]), dtype=torch.float32, device=dev),
+             "cov": torch.empty((v["H"], v["W"]), dtype=torch.float32, device=dev)} for v in views]
+
+
+def _np(o):
+    return {k: o[k].cpu().numpy().view(np.uint32) if k == "id" else o[k].cpu().numpy() for k in ("id", "depth", "cov")}
+
+
+def test_batch_equals_per_view_raster(vsr):
+    views = _views(6, seed=3)
+    tris_np = scenes.random_triangles(20000, 1.0, 30.0, 0.03, seed=8)
+    tris = torch.from_numpy(tris_np).cuda()
+    maps = [vsr.Map(v["W"], v["H"], v["k"], v["l"], v["s"], v["omega"]) for v in views]
+    b = vsr.Batch()
+    outs = _outs(views)
+    rng = np.random.default_rng(5)
+    for call in range(4):
+        if call == 3:  # move every camera: the graph replays with new cameras
+            for v in views:
+                v["cam"] = scenes.camera(rng.uniform(-1.5, 1.5, 3))
+        cams = np.stack([v["cam"] for v in views])
+        for o in outs:
+            o["id"].fill_(7)
+            o["cov"].fill_(-1)
+        b.render(maps, tris, cams, outs)
+        assert vsr.last_device_status() == 0
+        for v, m, o in zip(views, maps, outs):
+            ref = _np(vsr.raster(m, vsr.Scene(tris, v["cam"])))
+            got = _np(o)
+            for k in ("id", "depth", "cov"):
+                assert np.array_equal(got[k].view(np.uint32), ref[k].view(np.uint32)), (call, k)
+        if call >= 1:
+            assert b.config()["graphed"]
+    assert b.config()["raster_grid"] > 0
+
+
+def test_batch_view_against_oracle(vsr):
+    """Sampled pixels of one batched view, computed one by one by the oracle
+    on the same (oracle-made, FP32-rounded) map."""
+    from _util import compare
+    views = _views(3, seed=11)
+    tris_np = scenes.random_triangles(5000, 1.0, 20.0, 0.05, seed=12)
+    maps, m32s = [], []
+    for v in views:
+        m64, _ = oracle.make_map(v["W"], v["H"], v["k"], v["l"], v["s"], v["omega"])
+        m32 = m64.astype(np.float32)
+        m32s.append(m32)
+        maps.append(vsr.Map.from_tensor(torch.from_numpy(m32).cuda()))
+    b = vsr.Batch()
+    outs = _outs(views)
+    b.render(maps, torch.from_numpy(tris_np).cuda(), np.stack([v["cam"] for v in views]), outs)
+    assert vsr.last_device_status() == 0
+    rng = np.random.default_rng(1)
+    for v, m32, o in zip(views, m32s, outs):
+        pix = rng.integers(0, v["W"] * v["H"], 600)
+        rec = oracle.setup(tris_np, v["cam"])
+        exp = oracle.raster(m32, rec, pixels=pix)
+        compare(m32, rec, exp, _np(o), pixels=pix)
