@@ -224,33 +224,33 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
 
 /* ---- batched multi-view rendering -------------------------------------------
- * A batch renders V views of one scene in one sequence of launches: the
- * set-up of every (view, triangle) pair (Sec. 1.1, 1.1.2, 1.1.5 per view
- * camera), the binning of every view over the concatenated tiles of all
- * views, and one persistent raster launch in which CTAs take (view, tile)
- * items from a shared atomic queue, so views of uneven size share the GPU
- * without a tail per view.  Outputs per view are those of vsr_raster.
+ * A batch renders V views of one scene as one CUDA graph.  Each view is the
+ * chain of vsr_setup (with the view's camera, Sec. 1.1, 1.1.2, 1.1.5), vsr_bin
+ * and vsr_raster_tiles on a workspace of its own; the chains are spread over
+ * S parallel streams inside the graph, so every view keeps its working set
+ * in L2 while independent views overlap on the GPU, and no launch pays host
+ * overhead.  Outputs per view are those of vsr_raster.
  *
  * vsr_batch_render: maps[V] (built with vsr_make_map*), tris_dev [T][3][3]
  * (device, shared by all views), cams (host, V x 12 floats, one camera per
  * view as in vsr_setup), id_dev / depth_dev / cov_dev (host arrays of V
  * caller-owned device pointers, [H_v][W_v] each; the arrays themselves or
  * any entry may be NULL).  The first call for a configuration (the same
- * maps, map contents, scene buffer and T, output pointers) runs eagerly,
- * synchronises `stream` once to size the bins, autotunes the persistent
- * raster grid by timing 2, 4, 6 and 7 CTAs per SM on that frame, and
- * captures the whole frame into a CUDA graph; later calls with the same
- * configuration copy only the cameras (into pinned staging of the batch)
- * and replay the graph on `stream`.  Device memory: V x T x 196 B of set-up
- * records and bin caches plus the bins.  A batch must not render on two
- * streams at once. */
+ * maps, map contents, scene buffer and T, output pointers) renders the
+ * views eagerly, synchronises `stream` once to size every view's bins, then
+ * captures one graph for each S in {1, 2, 4, 8}, times their replays and
+ * keeps the fastest (the autotuner); later calls with the same configuration
+ * copy only the cameras (into pinned staging of the batch) and replay the
+ * graph on `stream`.  Device memory per view: T x 228 B of set-up records
+ * and bin caches plus its bins.  A batch must not render on two streams at
+ * once. */
 typedef struct vsr_batch_s* vsr_batch;
 vsr_status vsr_batch_create(vsr_batch* out);
 vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const float* tris_dev, int64_t T,
                             const float* cams, uint32_t* const* id_dev, float* const* depth_dev,
                             float* const* cov_dev, void* stream);
-/* The autotuned persistent raster grid (CTAs) and whether a graph is ready. */
-vsr_status vsr_batch_config(vsr_batch b, int* raster_grid, int* graphed);
+/* The autotuned number of parallel streams and whether a graph is ready. */
+vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed);
 void vsr_batch_free(vsr_batch b);
 
 /* ---- status ---------------------------------------------------------------- */

@@ -83,6 +83,8 @@ struct vsr_scene_s {
     bool total_pending = false;
     int last_ntiles = 0;
     uint64_t binned_map = 0, binned_scene = 0;  // generations the current bins belong to
+    RasterWork work = {};
+    uint32_t work_tiles = 0;
     // host-path buffers (vsr_render_host)
     float* tris_dev = nullptr;
     int64_t tris_alloc = 0;
@@ -391,6 +393,7 @@ void vsr_scene_free(vsr_scene sc)
     cudaFree(sc->offsets);
     cudaFree(sc->ids);
     cudaFree(sc->hits);
+    raster_work_free(&sc->work);
     cudaFree(sc->tris_dev);
     cudaFree(sc->out_dev);
     if (sc->total_event) {
@@ -478,6 +481,22 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
 {
     if (!m || !sc) return VSR_ERR_INVALID_ARG;
     if (sc->binned_map != m->gen || sc->binned_scene != sc->gen) return VSR_ERR_INVALID_ARG;
+    const uint32_t ntiles = (uint32_t)(m->tx * m->ty);
+    if (!stats || (!stats->n_alg_dev && !stats->n_exec_dev && !stats->n_inside_dev)) {
+        // timed path: work items, large bins split over several CTAs
+        if (ntiles > sc->work_tiles) {
+            raster_work_free(&sc->work);
+            sc->work_tiles = 0;
+            vsr_status s = raster_work_alloc(&sc->work, ntiles);
+            if (s != VSR_OK) return s;
+            sc->work_tiles = ntiles;
+        }
+        const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
+                           sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
+        return launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT, status_word(),
+                                   (cudaStream_t)stream);
+    }
+    // diagnostics: one CTA per tile, whole bins, counters
     return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
                          depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
                          stats ? (unsigned long long*)stats->n_exec_dev : nullptr,
@@ -643,149 +662,122 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
 // ---------------------------------------------------------------------------
 // Batched multi-view rendering (vsr_batch_*).
 //
-// V views of one scene in one sequence of launches: set-up of every
-// (view, triangle) pair, binning of every view at once over the
-// concatenated tiles of all views (multi-CTA scan), and one persistent
-// raster launch whose CTAs pull (view, tile) items from an atomic queue.
-// The first call for a configuration (views' maps, scene buffer, outputs)
-// runs eagerly: it sizes the bins (one synchronisation), autotunes the
-// persistent grid (CTAs per SM) by timing the candidates on the real
-// frame, and captures the whole sequence into a CUDA graph.  Later calls
-// with the same configuration only copy the cameras into pinned staging and
-// replay the graph.
+// V views of one scene as one CUDA graph: each view is a chain of the
+// single-view launches (set-up with the view's camera read from device
+// memory, bin count, scan, bin fill, raster work items) on its own
+// workspace, and the chains are spread over S parallel streams inside the
+// graph, so each view keeps its working set in L2 while independent views
+// overlap on the GPU and no launch pays host overhead.  The first call for a
+// configuration runs the views eagerly (sizing every view's bins with one
+// synchronisation), then captures one graph per candidate S in {1, 2, 4, 8},
+// times their replays and keeps the fastest (the autotuner).  Later calls
+// with the same configuration copy the cameras into pinned staging and
+// replay.
 namespace {
 
-struct BatchDesc {
-    size_t off_cams, off_base, off_bin, off_ras, bytes;
+constexpr int BATCH_STREAMS_MAX = 8;
+
+struct BatchView {
+    float4* rec = nullptr;
+    uint32_t* hits = nullptr;
+    uint32_t* counts = nullptr;  // counts | extra
+    uint32_t* offsets = nullptr;
+    uint32_t* partials = nullptr;
+    uint32_t* ids = nullptr;
+    uint32_t cap = 0;
+    int tiles = 0;
+    int64_t T = 0;
+    RasterWork work = {};
 };
 
-BatchDesc batch_layout(int V)
+void batch_view_free(BatchView& v)
 {
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    BatchDesc d;
-    d.off_cams = 0;
-    d.off_base = up(d.off_cams + sizeof(float) * 12 * (size_t)V);
-    d.off_bin = up(d.off_base + sizeof(uint32_t) * ((size_t)V + 1));
-    d.off_ras = up(d.off_bin + sizeof(BinView) * (size_t)V);
-    d.bytes = up(d.off_ras + sizeof(RasterView) * (size_t)V);
-    return d;
+    cudaFree(v.rec);
+    cudaFree(v.hits);
+    cudaFree(v.counts);
+    cudaFree(v.offsets);
+    cudaFree(v.partials);
+    cudaFree(v.ids);
+    raster_work_free(&v.work);
+    v = BatchView{};
 }
 
 }  // namespace
 
 struct vsr_batch_s {
-    cudaStream_t cap_stream = nullptr;
-    int V_alloc = 0;
-    int64_t T_alloc = 0;
-    float4* rec = nullptr;
-    uint32_t* hits = nullptr;
-    int tiles_alloc = 0;
-    uint32_t* counts = nullptr;    // counts | extra, 2 x tiles
-    uint32_t* offsets = nullptr;   // tiles + 1
-    uint32_t* partials = nullptr;  // multi-CTA scan scratch
-    uint32_t* ids = nullptr;
-    uint32_t cap = 0;
-    uint32_t* queue = nullptr;
-    void* desc_dev = nullptr;
-    void* desc_host = nullptr;  // pinned
-    size_t desc_bytes = 0;
-    cudaEvent_t desc_done = nullptr;
-    uint32_t* h_total = nullptr;  // pinned
-    std::vector<uint64_t> key;    // configuration of the captured graph / sized bins
+    cudaStream_t streams[BATCH_STREAMS_MAX] = {};
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS_MAX] = {};
+    cudaEvent_t cams_done = nullptr;
+    std::vector<BatchView> views;
+    float* cams_dev = nullptr;
+    float* cams_host = nullptr;  // pinned
+    int cams_alloc = 0;
+    uint32_t* h_total = nullptr;  // pinned, one per view
+    int totals_alloc = 0;
+    std::vector<uint64_t> key;
     cudaGraphExec_t exec = nullptr;
-    int grid = 0;
-    int sms = 0;
+    int nstreams = 0;
 };
 
 namespace {
 
-template <class Tp>
-void dfree(Tp*& p)
-{
-    cudaFree(p);
-    p = nullptr;
-}
-
-vsr_status batch_workspace(vsr_batch b, int V, int64_t T, int tiles)
+vsr_status batch_view_alloc(BatchView& v, int64_t T, int tiles)
 {
     vsr_status s;
-    if (V > b->V_alloc || T > b->T_alloc) {
-        dfree(b->rec);
-        dfree(b->hits);
-        b->V_alloc = 0;
-        b->T_alloc = 0;
-        if ((s = dalloc(&b->rec, (size_t)REC_F * (size_t)T * (size_t)V)) != VSR_OK) return s;
-        if ((s = dalloc(&b->hits, (size_t)BIN_HIT_WORDS * (size_t)T * (size_t)V)) != VSR_OK) return s;
-        b->V_alloc = V;
-        b->T_alloc = T;
+    if (T > v.T) {
+        cudaFree(v.rec);
+        cudaFree(v.hits);
+        v.rec = nullptr;
+        v.hits = nullptr;
+        v.T = 0;
+        if ((s = dalloc(&v.rec, (size_t)REC_F * (size_t)T)) != VSR_OK) return s;
+        if ((s = dalloc(&v.hits, (size_t)BIN_HIT_WORDS * (size_t)T)) != VSR_OK) return s;
+        v.T = T;
     }
-    if (tiles > b->tiles_alloc) {
-        dfree(b->counts);
-        dfree(b->offsets);
-        dfree(b->partials);
-        b->tiles_alloc = 0;
-        if ((s = dalloc(&b->counts, 2 * (size_t)tiles)) != VSR_OK) return s;
-        if ((s = dalloc(&b->offsets, (size_t)tiles + 1)) != VSR_OK) return s;
-        if ((s = dalloc(&b->partials, 2 * (size_t)((tiles + 4095) / 4096) + 2)) != VSR_OK) return s;
-        b->tiles_alloc = tiles;
-    }
-    BatchDesc d = batch_layout(V);
-    if (d.bytes > b->desc_bytes) {
-        if (b->desc_done) cudaEventSynchronize(b->desc_done);
-        cudaFree(b->desc_dev);
-        if (b->desc_host) cudaFreeHost(b->desc_host);
-        b->desc_dev = b->desc_host = nullptr;
-        b->desc_bytes = 0;
-        if (cudaMalloc(&b->desc_dev, d.bytes) != cudaSuccess || cudaMallocHost(&b->desc_host, d.bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return VSR_ERR_OOM;
-        }
-        b->desc_bytes = d.bytes;
+    if (tiles > v.tiles) {
+        cudaFree(v.counts);
+        cudaFree(v.offsets);
+        cudaFree(v.partials);
+        raster_work_free(&v.work);
+        v.counts = v.offsets = v.partials = nullptr;
+        v.tiles = 0;
+        if ((s = dalloc(&v.counts, 2 * (size_t)tiles)) != VSR_OK) return s;
+        if ((s = dalloc(&v.offsets, (size_t)tiles + 1)) != VSR_OK) return s;
+        if ((s = dalloc(&v.partials, 2 * (size_t)((tiles + 4095) / 4096) + 2)) != VSR_OK) return s;
+        if ((s = raster_work_alloc(&v.work, (uint32_t)tiles)) != VSR_OK) return s;
+        v.tiles = tiles;
     }
     return VSR_OK;
 }
 
-// the frame's launches after the descriptors are on the device
-vsr_status batch_launches(vsr_batch b, int V, int64_t T, int tiles, const float* tris, bool sized, int grid,
-                          cudaStream_t st)
+// set-up, count and scan of view v (before its bins are sized)
+vsr_status batch_view_front(vsr_batch b, int v, vsr_map m, const float* tris, int64_t T, cudaStream_t st)
 {
-    const BatchDesc d = batch_layout(V);
-    char* dd = (char*)b->desc_dev;
-    const float* cams = (const float*)(dd + d.off_cams);
-    const uint32_t* base = (const uint32_t*)(dd + d.off_base);
-    const BinView* bv = (const BinView*)(dd + d.off_bin);
-    const RasterView* rv = (const RasterView*)(dd + d.off_ras);
+    BatchView& bv = b->views[v];
+    const int tiles = m->tx * m->ty;
     vsr_status s;
-    if ((s = launch_setup_views(tris, (int)T, cams, V, b->rec, st)) != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemsetAsync(b->counts, 0, sizeof(uint32_t) * 2 * (size_t)b->tiles_alloc, st));
-    if ((s = launch_bin_count_views(bv, V, (int)T, st)) != VSR_OK) return s;
-    if ((s = launch_scan_large(b->counts, b->counts + b->tiles_alloc, tiles, b->partials, b->offsets, st)) != VSR_OK)
+    if ((s = launch_setup_views(tris, (int)T, b->cams_dev + 12 * v, 1, bv.rec, st)) != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaMemsetAsync(bv.counts, 0, sizeof(uint32_t) * 2 * (size_t)bv.tiles, st));
+    if ((s = launch_bin_count(bv.rec, (int)T, m->idx, bv.counts, bv.counts + bv.tiles, bv.hits, st)) != VSR_OK)
         return s;
-    if (!sized) return VSR_OK;
-    if ((s = launch_bin_fill_views(bv, V, (int)T, b->ids, b->cap, status_word(), st)) != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(uint32_t), st));
-    return launch_raster_persistent(rv, base, V, (uint32_t)tiles, b->queue, grid, status_word(), st);
+    return tiles <= 65536 ? launch_scan(bv.counts, bv.counts + bv.tiles, tiles, nullptr, bv.offsets, st)
+                          : launch_scan_large(bv.counts, bv.counts + bv.tiles, tiles, bv.partials, bv.offsets, st);
 }
 
-void batch_fill_desc(vsr_batch b, int V, const vsr_map* maps, int64_t T, const float* cams, uint32_t* const* id,
-                     float* const* depth, float* const* cov, const std::vector<uint32_t>& base)
+// fill and raster of view v
+vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, uint32_t* id, float* depth, float* cov,
+                           cudaStream_t st)
 {
-    const BatchDesc d = batch_layout(V);
-    char* hh = (char*)b->desc_host;
-    memcpy(hh + d.off_cams, cams, sizeof(float) * 12 * (size_t)V);
-    memcpy(hh + d.off_base, base.data(), sizeof(uint32_t) * ((size_t)V + 1));
-    BinView* bv = (BinView*)(hh + d.off_bin);
-    RasterView* rv = (RasterView*)(hh + d.off_ras);
-    for (int v = 0; v < V; ++v) {
-        const vsr_map m = maps[v];
-        const float4* rec = b->rec + (size_t)v * REC_F * (size_t)T;
-        bv[v] = BinView{m->idx.hdr, m->idx.cell_start, m->idx.sorted, m->idx.big, rec, b->counts + base[v],
-                        b->counts + b->tiles_alloc + base[v], b->hits + (size_t)v * BIN_HIT_WORDS * (size_t)T,
-                        b->offsets + base[v]};
-        rv[v] = RasterView{m->map,           m->p.W, m->p.H, m->tiles, m->tx, rec, (int)T, b->offsets + base[v],
-                           b->ids,           b->cap, id ? id[v] : nullptr, depth ? depth[v] : nullptr,
-                           cov ? cov[v] : nullptr};
-    }
+    BatchView& bv = b->views[v];
+    const int tiles = m->tx * m->ty;
+    vsr_status s;
+    if ((s = launch_bin_fill(bv.rec, (int)T, m->idx, bv.hits, bv.offsets, bv.counts, bv.counts + bv.tiles, bv.ids,
+                             bv.cap, status_word(), st)) != VSR_OK)
+        return s;
+    const RasterView rv{m->map, m->p.W, m->p.H, m->tiles, m->tx, bv.rec, (int)T, bv.offsets,
+                        bv.ids, bv.cap, id, depth, cov};
+    return launch_raster_items(rv, bv.offsets, (uint32_t)tiles, bv.cap, bv.work, SPLIT_MAX_DEFAULT, status_word(),
+                               st);
 }
 
 }  // namespace
@@ -798,13 +790,12 @@ vsr_status vsr_batch_create(vsr_batch* out)
     *out = nullptr;
     vsr_batch b = new (std::nothrow) vsr_batch_s;
     if (!b) return VSR_ERR_OOM;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->desc_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost((void**)&b->h_total, sizeof(uint32_t)) != cudaSuccess ||
-        dalloc(&b->queue, 1) != VSR_OK) {
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->cams_done, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < BATCH_STREAMS_MAX; ++i)
+        ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         vsr_batch_free(b);
         return VSR_ERR_CUDA;
@@ -816,20 +807,18 @@ vsr_status vsr_batch_create(vsr_batch* out)
 void vsr_batch_free(vsr_batch b)
 {
     if (!b) return;
-    if (b->desc_done) cudaEventSynchronize(b->desc_done);
+    if (b->cams_done) cudaEventSynchronize(b->cams_done);
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    cudaFree(b->rec);
-    cudaFree(b->hits);
-    cudaFree(b->counts);
-    cudaFree(b->offsets);
-    cudaFree(b->partials);
-    cudaFree(b->ids);
-    cudaFree(b->queue);
-    cudaFree(b->desc_dev);
-    if (b->desc_host) cudaFreeHost(b->desc_host);
+    for (auto& v : b->views) batch_view_free(v);
+    cudaFree(b->cams_dev);
+    if (b->cams_host) cudaFreeHost(b->cams_host);
     if (b->h_total) cudaFreeHost(b->h_total);
-    if (b->desc_done) cudaEventDestroy(b->desc_done);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int i = 0; i < BATCH_STREAMS_MAX; ++i) {
+        if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cams_done) cudaEventDestroy(b->cams_done);
     delete b;
 }
 
@@ -844,123 +833,153 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             if (!isfinite(cams[12 * v + q])) return VSR_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<uint32_t> base((size_t)nviews + 1, 0);
-    uint64_t tiles64 = 0;
-    for (int v = 0; v < nviews; ++v) {
-        base[v] = (uint32_t)tiles64;
-        tiles64 += (uint64_t)maps[v]->tx * maps[v]->ty;
-    }
-    if (tiles64 >= 0x7fffffffull) return VSR_ERR_INVALID_ARG;
-    const int tiles = (int)tiles64;
-    base[nviews] = (uint32_t)tiles;
+    auto out_ptr = [](auto* const* arr, int v) { return arr ? arr[v] : nullptr; };
 
-    // configuration key: everything the descriptors and the graph bake in
     std::vector<uint64_t> key = {(uint64_t)nviews, (uint64_t)T, (uint64_t)(uintptr_t)tris_dev};
     for (int v = 0; v < nviews; ++v) {
         key.push_back((uint64_t)(uintptr_t)maps[v]);
         key.push_back(maps[v]->gen);
-        key.push_back((uint64_t)(uintptr_t)(id_dev ? id_dev[v] : nullptr));
-        key.push_back((uint64_t)(uintptr_t)(depth_dev ? depth_dev[v] : nullptr));
-        key.push_back((uint64_t)(uintptr_t)(cov_dev ? cov_dev[v] : nullptr));
+        key.push_back((uint64_t)(uintptr_t)out_ptr(id_dev, v));
+        key.push_back((uint64_t)(uintptr_t)out_ptr(depth_dev, v));
+        key.push_back((uint64_t)(uintptr_t)out_ptr(cov_dev, v));
     }
-    const BatchDesc d = batch_layout(nviews);
+    const size_t cam_bytes = sizeof(float) * 12 * (size_t)nviews;
 
     if (b->exec && key == b->key) {
         // replay: new cameras only
-        VSR_CUDA_TRY(cudaEventSynchronize(b->desc_done));
-        memcpy((char*)b->desc_host + d.off_cams, cams, sizeof(float) * 12 * (size_t)nviews);
+        VSR_CUDA_TRY(cudaEventSynchronize(b->cams_done));
+        memcpy(b->cams_host, cams, cam_bytes);
         VSR_CUDA_TRY(cudaGraphLaunch(b->exec, st));
-        VSR_CUDA_TRY(cudaEventRecord(b->desc_done, st));
+        VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
         return VSR_OK;
     }
 
-    // new configuration: eager frame (sizing, autotuning), then capture
+    // new configuration
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
     b->key.clear();
-    vsr_status s = batch_workspace(b, nviews, T, tiles);
-    if (s != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaEventSynchronize(b->desc_done));
-    batch_fill_desc(b, nviews, maps, T, cams, id_dev, depth_dev, cov_dev, base);
-    VSR_CUDA_TRY(cudaMemcpyAsync(b->desc_dev, b->desc_host, d.bytes, cudaMemcpyHostToDevice, st));
-    if ((s = batch_launches(b, nviews, T, tiles, tris_dev, false, 0, st)) != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemcpyAsync(b->h_total, b->offsets + tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    VSR_CUDA_TRY(cudaStreamSynchronize(st));
-    const uint32_t total = *b->h_total;
-    if (total > b->cap || !b->ids) {
-        dfree(b->ids);
-        b->cap = 0;
-        uint64_t want = (uint64_t)total + total / 4 + 4096;
-        if (want > 0xffffffffull) want = 0xffffffffull;
-        if ((s = dalloc(&b->ids, (size_t)want)) != VSR_OK) return s;
-        b->cap = (uint32_t)want;
-        batch_fill_desc(b, nviews, maps, T, cams, id_dev, depth_dev, cov_dev, base);
-        VSR_CUDA_TRY(cudaMemcpyAsync(b->desc_dev, b->desc_host, d.bytes, cudaMemcpyHostToDevice, st));
+    VSR_CUDA_TRY(cudaEventSynchronize(b->cams_done));
+    vsr_status s;
+    if (nviews > b->cams_alloc) {
+        cudaFree(b->cams_dev);
+        if (b->cams_host) cudaFreeHost(b->cams_host);
+        if (b->h_total) cudaFreeHost(b->h_total);
+        b->cams_dev = nullptr;
+        b->cams_host = nullptr;
+        b->h_total = nullptr;
+        b->cams_alloc = 0;
+        if ((s = dalloc(&b->cams_dev, 12 * (size_t)nviews)) != VSR_OK) return s;
+        if (cudaMallocHost((void**)&b->cams_host, cam_bytes) != cudaSuccess ||
+            cudaMallocHost((void**)&b->h_total, sizeof(uint32_t) * (size_t)nviews) != cudaSuccess) {
+            cudaGetLastError();
+            return VSR_ERR_OOM;
+        }
+        b->cams_alloc = nviews;
     }
-    const BinView* bv = (const BinView*)((char*)b->desc_dev + d.off_bin);
-    const RasterView* rv = (const RasterView*)((char*)b->desc_dev + d.off_ras);
-    const uint32_t* dbase = (const uint32_t*)((char*)b->desc_dev + d.off_base);
-    if ((s = launch_bin_fill_views(bv, nviews, (int)T, b->ids, b->cap, status_word(), st)) != VSR_OK) return s;
+    if ((int)b->views.size() < nviews) b->views.resize(nviews);
+    for (int v = 0; v < nviews; ++v)
+        if ((s = batch_view_alloc(b->views[v], T, maps[v]->tx * maps[v]->ty)) != VSR_OK) return s;
+    memcpy(b->cams_host, cams, cam_bytes);
+    VSR_CUDA_TRY(cudaMemcpyAsync(b->cams_dev, b->cams_host, cam_bytes, cudaMemcpyHostToDevice, st));
 
-    // autotune the persistent grid on this frame (the raster pass is idempotent)
-    const int cand[4] = {2, 4, 6, 7};
+    // eager frame: fronts, one synchronisation to size every view's bins, backs
+    for (int v = 0; v < nviews; ++v) {
+        if ((s = batch_view_front(b, v, maps[v], tris_dev, T, st)) != VSR_OK) return s;
+        const int tiles = maps[v]->tx * maps[v]->ty;
+        VSR_CUDA_TRY(cudaMemcpyAsync(b->h_total + v, b->views[v].offsets + tiles, sizeof(uint32_t),
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    VSR_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int v = 0; v < nviews; ++v) {
+        BatchView& bv = b->views[v];
+        const uint32_t total = b->h_total[v];
+        if (total > bv.cap || !bv.ids) {
+            cudaFree(bv.ids);
+            bv.ids = nullptr;
+            bv.cap = 0;
+            uint64_t want = (uint64_t)total + total / 4 + 4096;
+            if (want > 0xffffffffull) want = 0xffffffffull;
+            if ((s = dalloc(&bv.ids, (size_t)want)) != VSR_OK) return s;
+            bv.cap = (uint32_t)want;
+        }
+    }
+    for (int v = 0; v < nviews; ++v)
+        if ((s = batch_view_back(b, v, maps[v], T, out_ptr(id_dev, v), out_ptr(depth_dev, v), out_ptr(cov_dev, v),
+                                 st)) != VSR_OK)
+            return s;
+    VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
+
+    // autotune: one graph per stream count, keep the fastest replay
+    const int cand[4] = {1, 2, 4, 8};
     float best = 1e30f;
-    int best_grid = b->sms * 7;
     cudaEvent_t e0, e1;
     VSR_CUDA_TRY(cudaEventCreate(&e0));
     VSR_CUDA_TRY(cudaEventCreate(&e1));
-    for (int rep = 0; rep < 2; ++rep)
-        for (int c : cand) {
-            const int grid = b->sms * c;
-            VSR_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(uint32_t), st));
-            VSR_CUDA_TRY(cudaEventRecord(e0, st));
-            if ((s = launch_raster_persistent(rv, dbase, nviews, (uint32_t)tiles, b->queue, grid, status_word(), st)) !=
-                VSR_OK)
-                return s;
-            VSR_CUDA_TRY(cudaEventRecord(e1, st));
-            VSR_CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            VSR_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep == 1 && ms < best) {  // the first round warms the caches
-                best = ms;
-                best_grid = grid;
-            }
+    for (int c : cand) {
+        const int S = c < nviews ? c : nviews;
+        cudaStream_t cs = b->streams[0];
+        cudaGraph_t g = nullptr;
+        VSR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        vsr_status cst = VSR_OK;
+        if (cudaMemcpyAsync(b->cams_dev, b->cams_host, cam_bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+            cudaEventRecord(b->fork, cs) != cudaSuccess)
+            cst = VSR_ERR_CUDA;
+        for (int i = 1; cst == VSR_OK && i < S; ++i)
+            if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) cst = VSR_ERR_CUDA;
+        for (int v = 0; cst == VSR_OK && v < nviews; ++v) {
+            cudaStream_t vs = b->streams[v % S];
+            cst = batch_view_front(b, v, maps[v], tris_dev, T, vs);
+            if (cst == VSR_OK)
+                cst = batch_view_back(b, v, maps[v], T, out_ptr(id_dev, v), out_ptr(depth_dev, v), out_ptr(cov_dev, v),
+                                      vs);
         }
+        for (int i = 1; cst == VSR_OK && i < S; ++i)
+            if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess)
+                cst = VSR_ERR_CUDA;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        if (cst != VSR_OK || ee != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cst != VSR_OK ? cst : VSR_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.0f;
+        bool timed = cudaGraphLaunch(ex, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
+        for (int r = 0; timed && r < 2; ++r) timed = cudaGraphLaunch(ex, st) == cudaSuccess;
+        timed = timed && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (timed && ms < best) {
+            best = ms;
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = ex;
+            b->nstreams = S;
+        } else {
+            cudaGraphExecDestroy(ex);
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->grid = best_grid;
-
-    // capture the frame (cameras copied from the pinned staging at replay)
-    cudaGraph_t g = nullptr;
-    VSR_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaMemcpyAsync((char*)b->desc_dev + d.off_cams, (char*)b->desc_host + d.off_cams,
-                                     sizeof(float) * 12 * (size_t)nviews, cudaMemcpyHostToDevice, b->cap_stream);
-    vsr_status cs = ce == cudaSuccess ? batch_launches(b, nviews, T, tiles, tris_dev, true, b->grid, b->cap_stream)
-                                      : VSR_ERR_CUDA;
-    cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &g);
-    if (cs != VSR_OK || ee != cudaSuccess || !g) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return cs != VSR_OK ? cs : VSR_ERR_CUDA;
-    }
-    ce = cudaGraphInstantiate(&b->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) {
-        b->exec = nullptr;
-        cudaGetLastError();
-        return VSR_ERR_CUDA;
-    }
+    if (!b->exec) return VSR_ERR_CUDA;
     b->key = key;
-    VSR_CUDA_TRY(cudaEventRecord(b->desc_done, st));
+    VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
     return VSR_OK;
 }
 
-vsr_status vsr_batch_config(vsr_batch b, int* raster_grid, int* graphed)
+vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed)
 {
     if (!b) return VSR_ERR_INVALID_ARG;
-    if (raster_grid) *raster_grid = b->grid;
+    if (streams) *streams = b->nstreams;
     if (graphed) *graphed = b->exec != nullptr;
     return VSR_OK;
 }

@@ -184,15 +184,13 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
 
 // ---- per-triangle binning ---------------------------------------------------
 
-// One thread per triangle of one view: the view is v0, or views[blockIdx.y]
-// when views is not NULL (all views share T, ids and cap).
+// One thread per triangle of the view v.
 template <bool FILL>
-__global__ void __launch_bounds__(128) bin_kernel(BinView v0, const BinView* __restrict__ views, int T,
-                                                   uint32_t* __restrict__ ids, uint32_t cap, int* status)
+__global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids, uint32_t cap,
+                                                   int* status)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    const BinView v = views ? views[blockIdx.y] : v0;
     const float4* __restrict__ rec = v.rec;
     const TileIndexHdr* __restrict__ hdr = v.hdr;
     const uint32_t* __restrict__ cell_start = v.cell_start;
@@ -372,7 +370,7 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
 {
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, hits, nullptr};
-    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, nullptr, T, nullptr, 0, nullptr);
+    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -384,26 +382,7 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, const_cast<uint32_t*>(hits),
                     offsets};
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(v, nullptr, T, ids, cap, status);
-    VSR_CUDA_TRY(cudaGetLastError());
-    return VSR_OK;
-}
-
-vsr_status launch_bin_count_views(const BinView* views, int nviews, int T, cudaStream_t st)
-{
-    if (T == 0 || nviews == 0) return VSR_OK;
-    const BinView none{};
-    bin_kernel<false><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(none, views, T, nullptr, 0, nullptr);
-    VSR_CUDA_TRY(cudaGetLastError());
-    return VSR_OK;
-}
-
-vsr_status launch_bin_fill_views(const BinView* views, int nviews, int T, uint32_t* ids, uint32_t cap, int* status,
-                                 cudaStream_t st)
-{
-    if (T == 0 || nviews == 0) return VSR_OK;
-    const BinView none{};
-    bin_kernel<true><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(none, views, T, ids, cap, status);
+    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

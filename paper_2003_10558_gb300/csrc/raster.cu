@@ -40,6 +40,7 @@ namespace {
 constexpr int RT = 128;          // threads per CTA (one 16x16 tile)
 constexpr int PPT = 2;           // pixels per thread: (x, y) and (x, y + 4) of the warp's 8x8 block
 constexpr int CHUNK = RT;        // triangles staged per pass
+constexpr int SPLIT_MAX = 4 * CHUNK;  // triangles per work item of a split tile
 static_assert(RT * PPT == TILE_PIX, "one CTA covers one tile");
 
 struct __align__(16) Stage {
@@ -83,10 +84,24 @@ __device__ __forceinline__ float norm2_minus_one(float x, float y, float z)
 // One 16x16 tile of one view.  Called by every thread of a CTA of RT
 // threads; `st` is the CTA's staging area (reusable across calls: every use
 // is fenced by the barriers of the chunk loop).
+// Split tiles: a tile whose bin is longer than SPLIT_MAX triangles is
+// processed as several work items of at most SPLIT_MAX triangles each.  The
+// items of one tile add their coverage (2^-24 fixed point) and take the
+// minimum of their visibility keys in the tile's accumulator slot with
+// atomics -- both are order-free, so the result is exactly that of one item
+// -- and the item that arrives last (atomic counter, nothing waits) writes
+// the outputs and clears the slot for the next frame.
+struct SplitAcc {
+    unsigned long long* acc;  // [slot][TILE_PIX], zero between frames (64 bits: many partials)
+    unsigned long long* key;  // [slot][TILE_PIX], ~0 between frames
+    uint32_t* done;           // [slot], zero between frames
+};
+
 template <bool STATS>
 __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, Stage& st, bool count_alg,
                                             uint32_t& cnt_alg, uint32_t& cnt_exec, int32_t* __restrict__ n_inside,
-                                            int* __restrict__ status)
+                                            int* __restrict__ status, int range_lo = 0, int range_hi = -1,
+                                            int split_slot = -1, int nsplit = 1, SplitAcc split = SplitAcc{})
 {
     const float4* __restrict__ map = view.map;
     const int W = view.W, H = view.H, tiles_x = view.tiles_x, T = view.T;
@@ -169,6 +184,11 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             if (threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
             b1 = cap;
             b0 = min(b0, cap);
+        }
+        if (range_hi >= 0) {  // one item of a split tile
+            const uint32_t lo = b0 + (uint32_t)range_lo, hi = b0 + (uint32_t)range_hi;
+            b0 = min(lo, b1);
+            b1 = min(hi, b1);
         }
     }
 
@@ -294,6 +314,31 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         }
     }
 
+    if (split_slot >= 0) {
+        // merge into the tile's slot; the last item to arrive writes it out
+        const int lp0 = (warp & 1) * 8 + (lane & 7) + TILE * ((warp >> 1) * 8 + (lane >> 3));
+        unsigned long long* __restrict__ sacc = split.acc + (size_t)split_slot * TILE_PIX;
+        unsigned long long* __restrict__ skey = split.key + (size_t)split_slot * TILE_PIX;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (acc[p]) atomicAdd(&sacc[lp0 + TILE * 4 * p], (unsigned long long)acc[p]);
+            if (key[p] != ~0ull) atomicMin(&skey[lp0 + TILE * 4 * p], key[p]);
+        }
+        __threadfence();
+        __syncthreads();
+        __shared__ int s_last;
+        if (threadIdx.x == 0) s_last = atomicAdd(&split.done[split_slot], 1u) == (unsigned)(nsplit - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            acc[p] = (uint32_t)min(atomicExch(&sacc[lp0 + TILE * 4 * p], 0ull), 16777216ull);
+            key[p] = atomicExch(&skey[lp0 + TILE * 4 * p], ~0ull);
+        }
+        if (threadIdx.x == 0) split.done[split_slot] = 0u;
+    }
+
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         if (!inimg[p]) continue;
@@ -340,34 +385,64 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
     }
 }
 
-// Persistent multi-view raster: CTAs pull (view, tile) items from one atomic
-// queue until it runs dry, so views of uneven size share the GPU without a
-// tail per view.  Item i belongs to the last view v with tile_base[v] <= i.
-// No CTA waits on another; the loop ends when the counter passes `total`.
-__global__ void __launch_bounds__(RT, 7) raster_persistent_kernel(const RasterView* __restrict__ views,
-                                                                   const uint32_t* __restrict__ tile_base, int nviews,
-                                                                   uint32_t total, uint32_t* __restrict__ queue,
-                                                                   int* __restrict__ status)
+// Raster over work items, one CTA each.  Items 0 .. n_tiles-1 are the tiles
+// themselves (the first item of a split tile); the further items of split
+// tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
+// return at once.
+__global__ void __launch_bounds__(RT, 7) raster_items_kernel(RasterView view, uint32_t n_tiles,
+                                                              const uint32_t* __restrict__ nsplit_of,
+                                                              const int32_t* __restrict__ split_slot,
+                                                              const uint2* __restrict__ extra,
+                                                              const uint32_t* __restrict__ n_extra, int split_max,
+                                                              SplitAcc split, int* __restrict__ status)
 {
     __shared__ Stage st;
-    __shared__ uint32_t s_item;
-    uint32_t ca = 0, ce = 0;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= total) break;
-        int lo = 0, hi = nviews - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tile_base[mid] <= item)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        raster_tile<false>(views[lo], (int)(item - tile_base[lo]), st, false, ca, ce, nullptr, status);
+    uint32_t u, k = 0;
+    if (blockIdx.x < n_tiles) {
+        u = blockIdx.x;
+    } else {
+        const uint32_t e = blockIdx.x - n_tiles;
+        if (e >= *n_extra) return;
+        const uint2 uk = extra[e];
+        if (uk.x == 0xffffffffu) return;
+        u = uk.x;
+        k = uk.y;
     }
+    const int nsplit = (int)nsplit_of[u];
+    uint32_t ca = 0, ce = 0;
+    if (nsplit == 1)
+        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status);
+    else
+        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max, (int)(k + 1) * split_max,
+                           split_slot[u], nsplit, split);
+}
+
+// Work items per tile: ceil(bin / split_max) when a split slot and room in
+// the extra list are free, else 1 (the tile runs in one CTA).
+__global__ void items_kernel(const uint32_t* __restrict__ offsets, uint32_t n_tiles, int split_max,
+                             uint32_t* __restrict__ nsplit_of, int32_t* __restrict__ split_slot,
+                             uint32_t* __restrict__ counters /* n_split, n_extra */, uint32_t split_cap,
+                             uint2* __restrict__ extra, uint32_t extra_cap)
+{
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_tiles) return;
+    const uint32_t c = offsets[u + 1] - offsets[u];
+    uint32_t n = 1;
+    int32_t slot = -1;
+    if (c > (uint32_t)split_max) {
+        const uint32_t want = (c + split_max - 1) / split_max;
+        const uint32_t sl = atomicAdd(&counters[0], 1u);
+        const uint32_t pos = atomicAdd(&counters[1], want - 1);
+        const bool ok = sl < split_cap && pos + (want - 1) <= extra_cap;
+        for (uint32_t q = 1; q < want && pos + q - 1 < extra_cap; ++q)
+            extra[pos + q - 1] = ok ? make_uint2(u, q) : make_uint2(0xffffffffu, 0u);
+        if (ok) {
+            n = want;
+            slot = (int32_t)sl;
+        }
+    }
+    nsplit_of[u] = n;
+    split_slot[u] = slot;
 }
 
 }  // namespace
@@ -387,13 +462,62 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
     return VSR_OK;
 }
 
-vsr_status launch_raster_persistent(const RasterView* views, const uint32_t* tile_base, int nviews, uint32_t total,
-                                    uint32_t* queue, int grid, int* status, cudaStream_t st)
+vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
+                               RasterWork w, int split_max, int* status, cudaStream_t st)
 {
-    if (total == 0) return VSR_OK;
-    raster_persistent_kernel<<<grid, RT, 0, st>>>(views, tile_base, nviews, total, queue, status);
+    if (n_tiles == 0) return VSR_OK;
+    split_max = split_max < CHUNK ? CHUNK : (split_max / CHUNK) * CHUNK;
+    // enough extra items for every pair of the bins, bounded by the list
+    const uint64_t bound = (uint64_t)cap / (uint64_t)split_max + 1;
+    const uint32_t extra_cap = bound < w.extra_cap ? (uint32_t)bound : w.extra_cap;
+    VSR_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), st));
+    items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, n_tiles, split_max, w.nsplit_of, w.split_slot,
+                                                        w.counters, w.split_cap, w.extra, extra_cap);
+    VSR_CUDA_TRY(cudaGetLastError());
+    raster_items_kernel<<<n_tiles + extra_cap, RT, 0, st>>>(view, n_tiles, w.nsplit_of, w.split_slot, w.extra,
+                                                            w.counters + 1, split_max, SplitAcc{w.acc, w.key, w.done},
+                                                            status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 int raster_threads_per_cta() { return RT; }
+
+vsr_status raster_work_alloc(RasterWork* w, uint32_t n_tiles)
+{
+    *w = RasterWork{};
+    const uint32_t cap = n_tiles < SPLIT_SLOTS ? n_tiles : SPLIT_SLOTS;
+    const uint32_t xcap = EXTRA_ITEMS;
+    if (cudaMalloc((void**)&w->nsplit_of, sizeof(uint32_t) * (n_tiles + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&w->split_slot, sizeof(int32_t) * (n_tiles + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&w->counters, sizeof(uint32_t) * 2) != cudaSuccess ||
+        cudaMalloc((void**)&w->extra, sizeof(uint2) * xcap) != cudaSuccess ||
+        cudaMalloc((void**)&w->acc, sizeof(unsigned long long) * TILE_PIX * ((size_t)cap + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&w->key, sizeof(unsigned long long) * TILE_PIX * ((size_t)cap + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&w->done, sizeof(uint32_t) * ((size_t)cap + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        raster_work_free(w);
+        return VSR_ERR_OOM;
+    }
+    w->split_cap = cap;
+    w->extra_cap = xcap;
+    if (cudaMemset(w->acc, 0, sizeof(unsigned long long) * TILE_PIX * ((size_t)cap + 1)) != cudaSuccess ||
+        cudaMemset(w->key, 0xff, sizeof(unsigned long long) * TILE_PIX * ((size_t)cap + 1)) != cudaSuccess ||
+        cudaMemset(w->done, 0, sizeof(uint32_t) * ((size_t)cap + 1)) != cudaSuccess) {
+        raster_work_free(w);
+        return VSR_ERR_CUDA;
+    }
+    return VSR_OK;
+}
+
+void raster_work_free(RasterWork* w)
+{
+    cudaFree(w->nsplit_of);
+    cudaFree(w->split_slot);
+    cudaFree(w->counters);
+    cudaFree(w->extra);
+    cudaFree(w->acc);
+    cudaFree(w->key);
+    cudaFree(w->done);
+    *w = RasterWork{};
+}

@@ -150,7 +150,7 @@ struct RasterView {
 };
 
 // One view as the binner sees it (tile index of the view's map, the view's
-// set-up records, and its slices of the per-tile counters and offsets).
+// set-up records, its per-tile counters and offsets, its hit cache).
 struct BinView {
     const TileIndexHdr* hdr;
     const uint32_t* cell_start;
@@ -163,16 +163,36 @@ struct BinView {
     const uint32_t* offsets;
 };
 
-vsr_status launch_raster_persistent(const RasterView* views, const uint32_t* tile_base, int nviews, uint32_t total,
-                                    uint32_t* queue, int grid, int* status, cudaStream_t st);
+// Work items of the raster: a tile whose bin is longer than split_max
+// triangles is processed by several CTAs whose results merge order-free
+// (see SplitAcc in raster.cu).
+constexpr uint32_t SPLIT_SLOTS = 4096;    // split tiles per launch (others run unsplit)
+constexpr uint32_t EXTRA_ITEMS = 1u << 16;  // extra items per launch
+constexpr int SPLIT_MAX_DEFAULT = 512;    // triangles per item of a split tile
+struct RasterWork {
+    uint32_t* nsplit_of;      // n_tiles: items of each tile
+    int32_t* split_slot;      // n_tiles: accumulator slot of a split tile, -1 if not split
+    uint32_t* counters;       // 2: split tiles, extra items
+    uint2* extra;             // extra_cap: (tile, k) of the further items
+    uint32_t split_cap, extra_cap;
+    unsigned long long* acc;  // split_cap x TILE_PIX, zero between frames
+    unsigned long long* key;  // split_cap x TILE_PIX, all ones between frames
+    uint32_t* done;           // split_cap, zero between frames
+};
+// items + raster over all tiles of a view; offsets: its bin offsets
+// (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items)
+vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
+                               RasterWork w, int split_max, int* status, cudaStream_t st);
+// allocate / free a RasterWork for up to n_tiles tiles (accumulators
+// initialised)
+vsr_status raster_work_alloc(RasterWork* w, uint32_t n_tiles);
+void raster_work_free(RasterWork* w);
 int raster_threads_per_cta();
-// views x T set-up with per-view cameras in device memory (Cam: O xyz, M 3x3)
+// set-up of nviews views (grid.y = view) with the cameras in device memory
+// (12 floats each: O xyz, M 3x3 row-major); view v's records at
+// rec + v * REC_F * T
 vsr_status launch_setup_views(const float* tris, int T, const float* cams_dev, int nviews, float4* rec,
                               cudaStream_t st);
-// binning of nviews views at once (grid.y = view); ids / cap shared
-vsr_status launch_bin_count_views(const BinView* views, int nviews, int T, cudaStream_t st);
-vsr_status launch_bin_fill_views(const BinView* views, int nviews, int T, uint32_t* ids, uint32_t cap, int* status,
-                                 cudaStream_t st);
 // exclusive scan of counts (+ extra) for large n (multi-CTA); `partials`
 // needs 2 * ceil(n / 4096) + 2 words
 vsr_status launch_scan_large(const uint32_t* counts, const uint32_t* extra, int n, uint32_t* partials,

@@ -307,9 +307,9 @@ def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "dept
 
 
 class Batch:
-    """Batched multi-view rendering of one scene (vsr_batch_*): one
-    persistent raster launch over all views' tiles, replayed as a CUDA graph
-    while the configuration (maps, scene buffer, outputs) is unchanged."""
+    """Batched multi-view rendering of one scene (vsr_batch_*): one CUDA
+    graph of per-view chains over parallel streams, replayed while the
+    configuration (maps, scene buffer, outputs) is unchanged."""
 
     def __init__(self):
         self.h = ctypes.c_void_p()
@@ -340,7 +340,7 @@ class Batch:
     def config(self):
         g, r = ctypes.c_int(), ctypes.c_int()
         check(load().vsr_batch_config(self.h, ctypes.byref(g), ctypes.byref(r)), "vsr_batch_config")
-        return {"raster_grid": g.value, "graphed": bool(r.value)}
+        return {"streams": g.value, "graphed": bool(r.value)}
 
     def free(self):
         if self.h:

@@ -1,5 +1,5 @@
-"""Batched multi-view rendering (one persistent raster launch over all views,
-CUDA-graph replay) against per-view vsr_raster calls and the oracle."""
+"""Batched multi-view rendering (one CUDA graph of per-view chains over
+parallel streams) against per-view vsr_raster calls and the oracle."""
 import numpy as np
 import pytest
 
@@ -67,7 +67,7 @@ def test_batch_equals_per_view_raster(vsr):
                 assert np.array_equal(got[k].view(np.uint32), ref[k].view(np.uint32)), (call, k)
         if call >= 1:
             assert b.config()["graphed"]
-    assert b.config()["raster_grid"] > 0
+    assert b.config()["streams"] in (1, 2, 4, 6)
 
 
 def test_batch_view_against_oracle(vsr):
