@@ -253,6 +253,65 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
 vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed);
 void vsr_batch_free(vsr_batch b);
 
+/* ---- serving ------------------------------------------------------------------
+ * A rendering server with continuous batching.  A worker thread owns `slots`
+ * CUDA streams; submitted requests wait in a FIFO queue and are admitted into
+ * free slots as soon as a slot and device memory allow, while earlier
+ * requests still run, so their launches overlap on the GPU.  Each request is
+ * rendered exactly as vsr_raster renders it alone (its map, its camera's
+ * set-up, its bins), on a workspace of its slot.  Maps come from an LRU cache
+ * keyed by the exact lens parameters and size; entries in use are never
+ * evicted.  Device memory of cached maps and slot workspaces is held under
+ * `budget_bytes`: a request needing more evicts idle maps, waits while other
+ * requests run, and fails with VSR_ERR_BUDGET if it cannot fit alone.  A
+ * request whose bins outgrew their capacity is rendered again with grown
+ * bins (counted in `reruns`; the server's workspaces report to status words
+ * of their own, so vsr_last_device_status does not see them).  Completion is polled on the host; no device
+ * code waits.  Timestamps are seconds of one steady clock (vsr_serve_now). */
+typedef struct vsr_server_s* vsr_server;
+typedef struct {
+    int64_t budget_bytes; /* device memory for maps and workspaces */
+    int slots;            /* requests in flight at once (one stream each), 1..32 */
+    int max_maps;         /* map-cache entries, 0 = limited by the budget only */
+} vsr_serve_cfg;
+typedef struct {
+    int scene;            /* index from vsr_serve_add_scene */
+    vsr_map_params lens;  /* the request's map (W, H included) */
+    float cam[12];        /* camera as in vsr_setup */
+    uint32_t* id_dev;     /* caller-owned device outputs [lens.H][lens.W]; */
+    float* depth_dev;     /* any may be NULL; must stay valid until the */
+    float* cov_dev;       /* request is done */
+} vsr_request;
+typedef struct {
+    vsr_status status;    /* VSR_OK, VSR_ERR_CANCELLED, VSR_ERR_BUDGET, ... */
+    int done;             /* 1 once final (then the ticket is released) */
+    int map_cache_hit;
+    double t_submit, t_start, t_done;
+} vsr_result;
+typedef struct {
+    int64_t submitted, completed, failed, cancelled;
+    int64_t map_hits, map_misses, map_evictions, reruns;
+    int64_t bytes_in_use, maps_cached, queued;
+} vsr_serve_stats;
+
+vsr_status vsr_serve_create(const vsr_serve_cfg* cfg, vsr_server* out);
+/* Register resident triangles (device [T][3][3], caller-owned, kept alive by
+ * the caller while the server lives); returns its scene index. */
+vsr_status vsr_serve_add_scene(vsr_server s, const float* tris_dev, int64_t T, int* scene);
+/* Queue a request (non-blocking).  VSR_ERR_INVALID_ARG for bad parameters
+ * or scene, VSR_ERR_BUDGET if its map alone exceeds the budget. */
+vsr_status vsr_serve_submit(vsr_server s, const vsr_request* r, uint64_t* ticket);
+/* Non-blocking: out->done = 0 while pending. */
+vsr_status vsr_serve_poll(vsr_server s, uint64_t ticket, vsr_result* out);
+/* Blocks until the request is final. */
+vsr_status vsr_serve_wait(vsr_server s, uint64_t ticket, vsr_result* out);
+/* Cancels a request still in the queue (VSR_ERR_INVALID_ARG once running). */
+vsr_status vsr_serve_cancel(vsr_server s, uint64_t ticket);
+vsr_status vsr_serve_stats_get(vsr_server s, vsr_serve_stats* out);
+double vsr_serve_now(void);
+/* Finishes the queued and running requests, then frees everything. */
+vsr_status vsr_serve_destroy(vsr_server s);
+
 /* ---- status ---------------------------------------------------------------- */
 const char* vsr_status_str(vsr_status s);
 /* Synchronises the device, returns and clears the device-side status word

@@ -10,7 +10,7 @@
 #include <vector>
 #include <mutex>
 
-#include "vsr_internal.cuh"
+#include "handles.cuh"
 
 namespace {
 
@@ -18,8 +18,8 @@ std::atomic<uint64_t> g_gen{1};
 std::mutex g_status_mu;
 int* g_status[256] = {};
 
-// The device-side status word of the current device (allocated and zeroed
-// on first use).
+}  // namespace
+
 int* status_word()
 {
     int dev = 0;
@@ -39,58 +39,6 @@ int* status_word()
     }
     return g_status[dev];
 }
-
-template <class Tp>
-vsr_status dalloc(Tp** p, size_t n)
-{
-    *p = nullptr;
-    if (n == 0) n = 1;
-    if (cudaMalloc((void**)p, n * sizeof(Tp)) != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return VSR_ERR_OOM;
-    }
-    return VSR_OK;
-}
-
-}  // namespace
-
-struct vsr_map_s {
-    vsr_map_params p;  // effective parameters
-    float4* map = nullptr;
-    Cone* tiles = nullptr;
-    TileIndex idx = {};
-    int tx = 0, ty = 0;
-    uint64_t gen = 0;
-};
-
-struct vsr_scene_s {
-    int64_t T = 0;
-    int64_t T_alloc = 0;
-    float4* rec = nullptr;
-    uint64_t gen = 0;
-    // bin workspace
-    int ws_tiles = 0;
-    uint32_t* counts = nullptr;
-    uint32_t* offsets = nullptr;
-    uint32_t* ids = nullptr;
-    uint32_t cap = 0;
-    uint32_t* hits = nullptr;  // per-triangle hit cache, BIN_HIT_WORDS x T_alloc
-    int64_t hits_T = 0;
-    uint64_t sized_shape = 0;          // (tiles, T) the bins were last sized for
-    uint32_t* h_total = nullptr;       // pinned: pair total of a recent binning
-    cudaEvent_t total_event = nullptr;  // completion of that copy
-    bool total_pending = false;
-    int last_ntiles = 0;
-    uint64_t binned_map = 0, binned_scene = 0;  // generations the current bins belong to
-    RasterWork work = {};
-    uint32_t work_tiles = 0;
-    // host-path buffers (vsr_render_host)
-    float* tris_dev = nullptr;
-    int64_t tris_alloc = 0;
-    void* out_dev = nullptr;  // id | depth | cov staging, 12 B per pixel
-    size_t out_alloc = 0;
-};
 
 namespace {
 
@@ -469,7 +417,7 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->sized_shape = shape;
     }
     if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->hits, sc->offsets, counts, extra, sc->ids, sc->cap,
-                             status_word(), st)) != VSR_OK)
+                             scene_status(sc), st)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
@@ -493,14 +441,14 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
         }
         const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
                            sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
-        return launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT, status_word(),
+        return launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT, scene_status(sc),
                                    (cudaStream_t)stream);
     }
     // diagnostics: one CTA per tile, whole bins, counters
     return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
                          depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
                          stats ? (unsigned long long*)stats->n_exec_dev : nullptr,
-                         stats ? stats->n_inside_dev : nullptr, status_word(), (cudaStream_t)stream);
+                         stats ? stats->n_inside_dev : nullptr, scene_status(sc), (cudaStream_t)stream);
 }
 
 vsr_status vsr_raster_ex(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,

@@ -1,0 +1,67 @@
+// handles.cuh -- the library's handle structures and host helpers, shared
+// by the host files of the library (api.cu, serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vsr_internal.cuh"
+
+// The device-side status word of the current device (allocated and zeroed
+// on first use).
+int* status_word();
+
+template <class Tp>
+inline vsr_status dalloc(Tp** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc((void**)p, n * sizeof(Tp)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return VSR_ERR_OOM;
+    }
+    return VSR_OK;
+}
+
+struct vsr_map_s {
+    vsr_map_params p;  // effective parameters
+    float4* map = nullptr;
+    Cone* tiles = nullptr;
+    TileIndex idx = {};
+    int tx = 0, ty = 0;
+    uint64_t gen = 0;
+};
+
+struct vsr_scene_s {
+    int64_t T = 0;
+    int64_t T_alloc = 0;
+    float4* rec = nullptr;
+    uint64_t gen = 0;
+    // bin workspace
+    int ws_tiles = 0;
+    uint32_t* counts = nullptr;
+    uint32_t* offsets = nullptr;
+    uint32_t* ids = nullptr;
+    uint32_t cap = 0;
+    uint32_t* hits = nullptr;  // per-triangle hit cache, BIN_HIT_WORDS x T_alloc
+    int64_t hits_T = 0;
+    uint64_t sized_shape = 0;           // (tiles, T) the bins were last sized for
+    uint32_t* h_total = nullptr;        // pinned: pair total of a recent binning
+    cudaEvent_t total_event = nullptr;  // completion of that copy
+    bool total_pending = false;
+    int last_ntiles = 0;
+    uint64_t binned_map = 0, binned_scene = 0;  // generations the current bins belong to
+    RasterWork work = {};
+    uint32_t work_tiles = 0;
+    // host-path buffers (vsr_render_host)
+    float* tris_dev = nullptr;
+    int64_t tris_alloc = 0;
+    void* out_dev = nullptr;  // id | depth | cov staging, 12 B per pixel
+    size_t out_alloc = 0;
+    // device status word of this scene's kernels: NULL = the per-device word
+    // of vsr_last_device_status; the server gives its workspaces their own
+    int* status = nullptr;
+};
+
+inline int* scene_status(const vsr_scene_s* s) { return s->status ? s->status : status_word(); }

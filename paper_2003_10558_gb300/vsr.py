@@ -31,7 +31,9 @@ EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_up
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
            "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_batch_create", "vsr_batch_render",
-           "vsr_batch_config", "vsr_batch_free",
+           "vsr_batch_config", "vsr_batch_free", "vsr_serve_create", "vsr_serve_add_scene", "vsr_serve_submit",
+           "vsr_serve_poll", "vsr_serve_wait", "vsr_serve_cancel", "vsr_serve_stats_get", "vsr_serve_now",
+           "vsr_serve_destroy",
            "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
 
 
@@ -44,6 +46,26 @@ class VsrError(RuntimeError):
 class MapParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_float), ("l", ctypes.c_float), ("s", ctypes.c_float), ("omega_deg", ctypes.c_float),
                 ("W", ctypes.c_int), ("H", ctypes.c_int), ("aov", ctypes.c_int), ("strict_limits", ctypes.c_int)]
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int), ("max_maps", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int), ("lens", MapParams), ("cam", ctypes.c_float * 12),
+                ("id_dev", ctypes.c_void_p), ("depth_dev", ctypes.c_void_p), ("cov_dev", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("done", ctypes.c_int), ("map_cache_hit", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "cancelled", "map_hits",
+                                              "map_misses", "map_evictions", "reruns", "bytes_in_use",
+                                              "maps_cached", "queued")]
 
 
 class RasterStats(ctypes.Structure):
@@ -90,6 +112,15 @@ def load(path: str = LIB_PATH):
             "vsr_batch_render": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_batch_config": ([vp, P(i32), P(i32)], i32),
             "vsr_batch_free": ([vp], None),
+            "vsr_serve_create": ([P(ServeCfg), P(vp)], i32),
+            "vsr_serve_add_scene": ([vp, vp, i64, P(i32)], i32),
+            "vsr_serve_submit": ([vp, P(Request), P(ctypes.c_uint64)], i32),
+            "vsr_serve_poll": ([vp, ctypes.c_uint64, P(Result)], i32),
+            "vsr_serve_wait": ([vp, ctypes.c_uint64, P(Result)], i32),
+            "vsr_serve_cancel": ([vp, ctypes.c_uint64], i32),
+            "vsr_serve_stats_get": ([vp, P(ServeStats)], i32),
+            "vsr_serve_now": ([], ctypes.c_double),
+            "vsr_serve_destroy": ([vp], i32),
             "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_status_str": ([i32], ctypes.c_char_p),
             "vsr_last_device_status": ([], i32),
@@ -350,5 +381,81 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Rendering server with continuous batching (vsr_serve_*)."""
+
+    def __init__(self, budget_bytes=40 << 30, slots=8, max_maps=0):
+        self.h = ctypes.c_void_p()
+        cfg = ServeCfg(int(budget_bytes), int(slots), int(max_maps))
+        check(load().vsr_serve_create(ctypes.byref(cfg), ctypes.byref(self.h)), "vsr_serve_create")
+        self._scenes = []
+
+    def add_scene(self, tris):
+        """Resident triangles: a CUDA float32 tensor [T, 3, 3] kept alive here."""
+        tris = tris.contiguous()
+        self._scenes.append(tris)
+        idx = ctypes.c_int()
+        T = tris.numel() // 9
+        check(load().vsr_serve_add_scene(self.h, _dptr(tris) if T else None, T, ctypes.byref(idx)),
+              "vsr_serve_add_scene")
+        return idx.value
+
+    @staticmethod
+    def now():
+        return load().vsr_serve_now()
+
+    def submit(self, scene, lens, cam, out):
+        """lens: dict(W, H, k, l, s, omega[, aov, strict]); out: dict of
+        CUDA tensors id / depth / cov (kept alive by the caller until done).
+        Returns the ticket."""
+        r = Request()
+        r.scene = scene
+        r.lens = MapParams(lens["k"], lens["l"], lens["s"], lens["omega"], lens["W"], lens["H"],
+                           lens.get("aov", 0), int(lens.get("strict", False)))
+        c = _cam_array(cam)
+        for q in range(12):
+            r.cam[q] = float(c[q])
+        r.id_dev = out["id"].data_ptr() if out.get("id") is not None else None
+        r.depth_dev = out["depth"].data_ptr() if out.get("depth") is not None else None
+        r.cov_dev = out["cov"].data_ptr() if out.get("cov") is not None else None
+        t = ctypes.c_uint64()
+        check(load().vsr_serve_submit(self.h, ctypes.byref(r), ctypes.byref(t)), "vsr_serve_submit")
+        return t.value
+
+    @staticmethod
+    def _res(res):
+        return {"status": res.status, "done": bool(res.done), "map_cache_hit": bool(res.map_cache_hit),
+                "t_submit": res.t_submit, "t_start": res.t_start, "t_done": res.t_done}
+
+    def poll(self, ticket):
+        res = Result()
+        check(load().vsr_serve_poll(self.h, ticket, ctypes.byref(res)), "vsr_serve_poll")
+        return self._res(res)
+
+    def wait(self, ticket):
+        res = Result()
+        check(load().vsr_serve_wait(self.h, ticket, ctypes.byref(res)), "vsr_serve_wait")
+        return self._res(res)
+
+    def cancel(self, ticket):
+        return load().vsr_serve_cancel(self.h, ticket) == VSR_OK
+
+    def stats(self):
+        st = ServeStats()
+        check(load().vsr_serve_stats_get(self.h, ctypes.byref(st)), "vsr_serve_stats_get")
+        return {n: getattr(st, n) for n, _ in ServeStats._fields_}
+
+    def close(self):
+        if self.h:
+            load().vsr_serve_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
