@@ -52,10 +52,13 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200000, help="pixels of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
                     help="single: the 1080p single-view frame (default); batched: 64 mixed views of a "
                          "1M-triangle scene, batched launch vs per-view plain launches")
     ap.add_argument("--views", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per lens stream")
+    ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     return ap.parse_args()
 
 
@@ -434,9 +437,100 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank, world, local):
+    """Poisson arrivals over 4 resident scenes of {100k, 300k, 600k, 1M}
+    triangles (the batched workload's generator, seeds 30-33), views drawn
+    from the batched workload's distribution, 40 GB budget.  Two lens
+    streams: every request a fresh lens draw (map cache ~always misses), and
+    lenses drawn from a pool of 256 (the cache hits).  Latency = result
+    ready minus arrival; the client owns 96 output buffer sets and waits
+    for a set's previous request before reusing it (that wait counts in the
+    latency)."""
+    import torch
+    from paper_2003_10558_gb300 import vsr as V
+    from paper_2003_10558_gb300 import build as B
+    from paper_2003_10558_gb300 import scenes
+
+    torch.cuda.set_device(local)
+    B.build()
+    V.load()
+    dev = torch.device("cuda", local)
+    sizes = [100_000, 300_000, 600_000, 1_000_000]
+    srv = V.Server(budget_bytes=40 << 30, slots=args.slots)
+    scene_t = [torch.from_numpy(scenes.random_triangles(n, 1.0, 60.0, 0.0096, 30 + i)).to(dev)
+               for i, n in enumerate(sizes)]
+    sids = [srv.add_scene(t) for t in scene_t]
+    Wm, Hm = 2048, 1080
+    nbuf = 96
+    bufs = [{"id": torch.empty(Wm * Hm, dtype=torch.int32, device=dev),
+             "depth": torch.empty(Wm * Hm, dtype=torch.float32, device=dev),
+             "cov": torch.empty(Wm * Hm, dtype=torch.float32, device=dev)} for _ in range(nbuf)]
+    rng = np.random.default_rng(3 + 17 * rank)
+
+    def draw_lens(r):
+        W, H = scenes.VIEW_SIZES[r.integers(len(scenes.VIEW_SIZES))]
+        return dict(W=int(W), H=int(H), k=float(r.uniform(-1, 1)), l=float(r.uniform(0.5, 1)),
+                    s=float(r.uniform(0.5, 1)), omega=float(r.uniform(90, 360)))
+
+    pool = [draw_lens(rng) for _ in range(256)]
+
+    def run_stream(pooled):
+        n = int(args.rate * args.duration)
+        arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n))
+        pending = [None] * nbuf
+        done = []
+        t0 = V.Server.now() + 0.05
+        for i in range(n):
+            lens = pool[rng.integers(len(pool))] if pooled else draw_lens(rng)
+            d = rng.normal(size=3)
+            cam = scenes.camera(5.0 * rng.uniform() ** (1 / 3) * d / np.linalg.norm(d))
+            b = i % nbuf
+            if pending[b] is not None:
+                done.append((pending[b][1], srv.wait(pending[b][0])))
+            arr = t0 + arrivals[i]
+            while V.Server.now() < arr:
+                pass
+            npx = lens["W"] * lens["H"]
+            out = {k: bufs[b][k][:npx] for k in ("id", "depth", "cov")}
+            pending[b] = (srv.submit(sids[int(rng.integers(4))], lens, cam, out), arr)
+        for p in pending:
+            if p is not None:
+                done.append((p[1], srv.wait(p[0])))
+        lat = np.array([r["t_done"] - arr for arr, r in done])
+        ok = all(r["status"] == 0 for _, r in done)
+        span = max(r["t_done"] for _, r in done) - t0
+        hits = np.mean([r["map_cache_hit"] for _, r in done])
+        return {"requests": n, "all_ok": ok, "frames_per_s": n / span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                "p99_ms": 1000 * float(np.percentile(lat, 99)), "map_hit_rate": float(hits),
+                "offered_rate": args.rate, "seconds": span}
+
+    fresh = run_stream(False)
+    pooled = run_stream(True)
+    st = srv.stats()
+    srv.close()
+    if rank != 0:
+        return
+    line = {"metric": "serving frames/s and p50/p99 latency", "value": pooled["frames_per_s"], "unit": "frames/s",
+            "higher_is_better": True, "n_gpus": world, "dtype": "f32", "data": "synthetic (seeded scene generator)",
+            "pooled_lenses": pooled, "fresh_lenses": fresh,
+            "server": {"slots": args.slots, "budget_bytes": 40 << 30, "reruns": st["reruns"],
+                       "map_evictions": st["map_evictions"], "bytes_in_use": st["bytes_in_use"]},
+            "config": {"workload": "Poisson arrivals, 4 resident scenes (100k-1M triangles), mixed views",
+                       "rate": args.rate, "duration_s": args.duration, "scenes": sizes}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "serving":
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU arm; "
+                                  "the oracle is timed on the single-view workload"}))
+            return
+        run_serving(args, rank, world, local)
+        return
     if args.workload == "batched":
         if args.impl == "reference":
             if rank == 0:
