@@ -70,6 +70,14 @@ def _load():
             lib.orc_setup.argtypes = [i64, vp, vp, vp]
             lib.orc_raster.argtypes = [i32, i32, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
             lib.orc_raster.restype = i64
+            lib.orc_shade.argtypes = [i32, i32, vp, i64, vp, vp, i64, vp, vp, i32]
+            lib.orc_shade.restype = i32
+            lib.orc_setup64.argtypes = [i64, vp, vp, vp]
+            lib.orc_map_tangent.argtypes = [i32, i32, vp, i32, i32, vp]
+            lib.orc_map_tangent.restype = i32
+            lib.orc_shade_grad.argtypes = [i32, i32, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_shade_grad.restype = i32
+            lib.orc_setup_grad.argtypes = [i64, vp, vp, vp, vp, vp]
             assert lib.orc_record_size() == REC
             _lib = lib
             del P
@@ -177,4 +185,138 @@ def raster(map_, rec, pixels=None, nthreads=0, extras=False):
         for key in list(out):
             if isinstance(out[key], np.ndarray):
                 out[key] = out[key].reshape(H, W)
+    return out
+
+
+def shade(map_, rec, colors, pixels=None, nthreads=0):
+    """Shaded image (front-to-back merge of c_t |N-hat_t . G| over the
+    fragments): [H, W] for pixels=None, else one value per listed pixel."""
+    H, W = map_.shape[:2]
+    m = np.ascontiguousarray(map_, dtype=np.float64)
+    rec = np.ascontiguousarray(rec, dtype=np.float64)
+    col = np.ascontiguousarray(colors, dtype=np.float64)
+    if pixels is None:
+        npix, pix = W * H, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64).ravel()
+        npix = pix.size
+    img = np.zeros(npix)
+    if _load().orc_shade(W, H, _ptr(m), rec.shape[0], _ptr(rec), _ptr(col), npix, _ptr(pix), _ptr(img), nthreads):
+        raise ValueError("orc_shade: bad sizes")
+    return img.reshape(H, W) if pixels is None else img
+
+
+IDENTITY_CAM = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=np.float64)
+
+
+def setup64(tris, cam=None):
+    """Set-up records from float64 world triangles [T, 3, 3] and camera."""
+    tris = np.ascontiguousarray(tris, dtype=np.float64).reshape(-1, 9)
+    cam = IDENTITY_CAM if cam is None else np.ascontiguousarray(cam, dtype=np.float64)
+    rec = np.zeros((tris.shape[0], REC))
+    _load().orc_setup64(tris.shape[0], _ptr(tris), _ptr(cam), _ptr(rec))
+    return rec
+
+
+def map_tangent(W, H, params, which, aov=0):
+    """d(map)/d(param) [H, W, 4] for which in 0..3 = k, l, s, Omega (degrees),
+    at the effective parameters `params` (complex step)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros((H, W, 4))
+    if _load().orc_map_tangent(W, H, _ptr(p), aov, which, _ptr(out)):
+        raise ValueError("orc_map_tangent failed")
+    return out
+
+
+def shade_grad(map_, rec, colors, dimage, pixels=None, dcov=None, ddepth=None):
+    """Adjoint of the shaded image (plus coverage / depth) -> (drec [T, REC],
+    dcolors [T], dmap [npix, 4] = d/d(G, delta))."""
+    H, W = map_.shape[:2]
+    m = np.ascontiguousarray(map_, dtype=np.float64)
+    rec = np.ascontiguousarray(rec, dtype=np.float64)
+    col = np.ascontiguousarray(colors, dtype=np.float64)
+    if pixels is None:
+        npix, pix = W * H, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64).ravel()
+        npix = pix.size
+
+    def vec(a):
+        return None if a is None else np.ascontiguousarray(a, dtype=np.float64).ravel()
+
+    dI, dC, dD = vec(dimage), vec(dcov), vec(ddepth)
+    T = rec.shape[0]
+    drec = np.zeros((T, REC))
+    dcol = np.zeros(T)
+    dmap = np.zeros((npix, 4))
+    if _load().orc_shade_grad(W, H, _ptr(m), T, _ptr(rec), _ptr(col), npix, _ptr(pix), _ptr(dI), _ptr(dC),
+                              _ptr(dD), _ptr(drec), _ptr(dcol), _ptr(dmap)):
+        raise ValueError("orc_shade_grad: bad sizes")
+    return drec, dcol, dmap
+
+
+def setup_grad(tris, rec, drec, cam=None):
+    """World-vertex gradients [T, 3, 3] from record gradients."""
+    tris = np.ascontiguousarray(tris, dtype=np.float64).reshape(-1, 9)
+    cam = IDENTITY_CAM if cam is None else np.ascontiguousarray(cam, dtype=np.float64)
+    out = np.zeros((tris.shape[0], 9))
+    _load().orc_setup_grad(tris.shape[0], _ptr(tris), _ptr(cam), _ptr(np.ascontiguousarray(rec)),
+                           _ptr(np.ascontiguousarray(drec)), _ptr(out))
+    return out.reshape(-1, 3, 3)
+
+
+def render_grad(map_, params, tris, colors, dimage, pixels=None, dcov=None, ddepth=None, cam=None, aov=0,
+                tangents=None):
+    """The oracle's analytic gradient of sum(dimage * I + dcov * cov +
+    ddepth * depth) over the listed pixels: returns dict with dtris [T, 3, 3],
+    dcolors [T] and dlens [4] = d/d(k, l, s, Omega in degrees).
+
+    map_ is the map the image is computed on (FP64, or an FP32 map promoted);
+    params its effective parameters, for the map tangents."""
+    H, W = map_.shape[:2]
+    rec = setup64(tris, cam)
+    drec, dcol, dmap = shade_grad(map_, rec, colors, dimage, pixels, dcov, ddepth)
+    dtris = setup_grad(tris, rec, drec, cam)
+    if tangents is None:
+        tangents = [map_tangent(W, H, params, j, aov) for j in range(4)]
+    dlens = np.zeros(4)
+    for j in range(4):
+        tj = tangents[j].reshape(-1, 4)
+        if pixels is not None:
+            tj = tj[np.asarray(pixels, dtype=np.int64).ravel()]
+        dlens[j] = float(np.sum(tj * dmap))
+    return {"dtris": dtris, "dcolors": dcol, "dlens": dlens, "dmap": dmap, "drec": drec}
+
+
+def shade_fd(verts, colors, lens, pixels, W, H, h=1e-6, which=("k", "l", "s", "omega"), vert_idx=(),
+             weights=None, cam=None, aov=0):
+    """FP64 central differences of sum(weights * I) over `pixels` (test
+    infrastructure for the gradient checks): d/dk, d/dl, d/ds, d/dOmega of the
+    map (rebuilt at +-h) and d/d(vertex coordinate) for (t, v, c) in vert_idx,
+    the vertices taken in float64 so that +-h is represented exactly."""
+    verts = np.asarray(verts, dtype=np.float64)
+    w = None if weights is None else np.asarray(weights, dtype=np.float64).ravel()
+
+    def total(lens_, verts_):
+        m, _ = make_map(W, H, lens_["k"], lens_["l"], lens_["s"], lens_["omega"], aov=aov)
+        img = shade(m, setup64(verts_, cam), colors, pixels)
+        return float(np.sum(img if w is None else img * w))
+
+    out = {}
+    for name in which:
+        lp, lm = dict(lens), dict(lens)
+        lp[name] += h
+        lm[name] -= h
+        out[name] = (total(lp, verts) - total(lm, verts)) / (2 * h)
+    if vert_idx:
+        m0, _ = make_map(W, H, lens["k"], lens["l"], lens["s"], lens["omega"], aov=aov)
+        for (t, v, c) in vert_idx:
+            vp, vm = verts.copy(), verts.copy()
+            vp[t, v, c] += h
+            vm[t, v, c] -= h
+            fp = shade(m0, setup64(vp, cam), colors, pixels)
+            fm = shade(m0, setup64(vm, cam), colors, pixels)
+            if w is not None:
+                fp, fm = fp * w, fm * w
+            out[(t, v, c)] = float(np.sum(fp) - np.sum(fm)) / (2 * h)
     return out

@@ -24,6 +24,12 @@
  *            bstep for the centre test, ray-plane depth r = (A.N)/(G.N), and
  *            the front-to-back mask merge of Sec. 1.3 (hidden surface
  *            occlusion).
+ *   shade    the same merge applied to a shade pass c_t |N-hat . G| (the
+ *            differentiable workload's image, Sec. 1.3 and Sec. 1.1.5).
+ *   gradient the analytic adjoint of that image (and of coverage and depth)
+ *            through the merge, gpstep / min, the plane distances, the
+ *            set-up and the map; the map's lens tangents by complex step.
+ *            Pinned by central differences of the functions above.
  *
  * The only shortcut is that the miter-plane test of gbpxstep is evaluated
  * before the three edge-plane tests: a pair that fails it is not a fragment
@@ -381,9 +387,11 @@ int orc_map(int W, int H, const double* p, int aov, double* out, int nthreads)
  * Culled (valid = 0): a vertex at the eye, A'.(B' x C') == 0, or a cap whose
  * sin(rho) rounds to zero (a triangle far below a pixel).
  */
-static int vertex_less(const float* P, const float* Q)
+/* Canonical vertex order: lexicographic order of the bit patterns of the
+ * world coordinates (FP32 patterns for FP32 input; the FP64 patterns of
+ * FP32 values promoted to double order the same way). */
+static int vertex_less_f(const float* P, const float* Q)
 {
-    /* lexicographic order of the FP32 bit patterns of (x, y, z) */
     for (int c = 0; c < 3; ++c) {
         uint32_t a, b;
         memcpy(&a, &P[c], 4);
@@ -393,11 +401,21 @@ static int vertex_less(const float* P, const float* Q)
     return 0;
 }
 
-static void edge_normal(const float* Pw, const float* Qw, const double* Pc, const double* Qc, double sigma,
-                        double* n)
+static int vertex_less_d(const double* P, const double* Q)
+{
+    for (int c = 0; c < 3; ++c) {
+        uint64_t a, b;
+        memcpy(&a, &P[c], 8);
+        memcpy(&b, &Q[c], 8);
+        if (a != b) return a < b;
+    }
+    return 0;
+}
+
+static void edge_normal(int swap, const double* Pc, const double* Qc, double sigma, double* n)
 {
     double x[3];
-    if (vertex_less(Qw, Pw)) {
+    if (swap) {
         /* canonical order is (Q, P): n = -(Q' x P') */
         cross3(Qc, Pc, x);
         x[0] = -x[0];
@@ -410,6 +428,71 @@ static void edge_normal(const float* Pw, const float* Qw, const double* Pc, cons
     for (int c = 0; c < 3; ++c) n[c] = sigma * x[c] / len;
 }
 
+/* One triangle: w = world vertices A, B, C (double); swap[e] = 1 when edge
+ * e = AB, BC, CA lists its vertices against the canonical order. */
+static void setup_one(const double* w, const int* swap, const double* O, const double* M, double* r)
+{
+    memset(r, 0, sizeof(double) * ORC_REC);
+    double V[3][3];
+    int at_eye = 0;
+    for (int q = 0; q < 3; ++q) {
+        double d[3] = {w[3 * q] - O[0], w[3 * q + 1] - O[1], w[3 * q + 2] - O[2]};
+        for (int c = 0; c < 3; ++c) V[q][c] = M[3 * c] * d[0] + M[3 * c + 1] * d[1] + M[3 * c + 2] * d[2];
+        if (V[q][0] == 0.0 && V[q][1] == 0.0 && V[q][2] == 0.0) at_eye = 1;
+    }
+    double bxc[3];
+    cross3(V[1], V[2], bxc);
+    double det = dot3(V[0], bxc);
+    if (at_eye || det == 0.0 || !isfinite(det)) return; /* culled */
+    double sigma = det > 0.0 ? 1.0 : -1.0;
+    edge_normal(swap[0], V[0], V[1], sigma, r + REC_N1);
+    edge_normal(swap[1], V[1], V[2], sigma, r + REC_N2);
+    edge_normal(swap[2], V[2], V[0], sigma, r + REC_N3);
+
+    /* miter: smallest circle over the projected vertices */
+    double U[3][3];
+    for (int q = 0; q < 3; ++q) {
+        double len = sqrt(dot3(V[q], V[q]));
+        for (int c = 0; c < 3; ++c) U[q][c] = V[q][c] / len;
+    }
+    double e_a[3], e_b[3], e_c[3];
+    for (int c = 0; c < 3; ++c) {
+        e_a[c] = U[1][c] - U[2][c];
+        e_b[c] = U[2][c] - U[0][c];
+        e_c[c] = U[0][c] - U[1][c];
+    }
+    double a2 = dot3(e_a, e_a), b2 = dot3(e_b, e_b), c2 = dot3(e_c, e_c);
+    double Os = a2 * (b2 + c2 - a2), Ot = b2 * (c2 + a2 - b2), Op = c2 * (a2 + b2 - c2);
+    double S[3];
+    for (int c = 0; c < 3; ++c) {
+        if (Os <= 0.0)
+            S[c] = 0.5 * (U[1][c] + U[2][c]);
+        else if (Ot <= 0.0)
+            S[c] = 0.5 * (U[2][c] + U[0][c]);
+        else if (Op <= 0.0)
+            S[c] = 0.5 * (U[0][c] + U[1][c]);
+        else
+            S[c] = (Os * U[0][c] + Ot * U[1][c] + Op * U[2][c]) / (Os + Ot + Op);
+    }
+    double slen = sqrt(dot3(S, S));
+    double sr = sqrt((1.0 - slen) * (1.0 + slen)); /* sin(rho), reading R17 */
+    if (!(slen > 0.0) || !(sr > 0.0)) return; /* degenerate: det == 0, or a point-sized cap */
+    for (int c = 0; c < 3; ++c) r[REC_S + c] = S[c] / slen;
+    r[REC_C] = slen;
+    r[REC_SR] = sr;
+
+    /* plane for depth */
+    double ab[3], cb[3];
+    for (int c = 0; c < 3; ++c) {
+        ab[c] = V[0][c] - V[1][c];
+        cb[c] = V[2][c] - V[1][c];
+    }
+    cross3(ab, cb, r + REC_N);
+    r[REC_D] = dot3(V[0], r + REC_N);
+    r[REC_VALID] = 1.0;
+    r[REC_SIGMA] = sigma;
+}
+
 void orc_setup(int64_t T, const float* tris, const float* cam, double* rec)
 {
     const double O[3] = {cam[0], cam[1], cam[2]};
@@ -417,66 +500,24 @@ void orc_setup(int64_t T, const float* tris, const float* cam, double* rec)
     for (int q = 0; q < 9; ++q) M[q] = cam[3 + q];
     for (int64_t t = 0; t < T; ++t) {
         const float* w = tris + 9 * t;
-        double* r = rec + ORC_REC * t;
-        memset(r, 0, sizeof(double) * ORC_REC);
-        double V[3][3];
-        int at_eye = 0;
-        for (int q = 0; q < 3; ++q) {
-            double d[3] = {(double)w[3 * q] - O[0], (double)w[3 * q + 1] - O[1], (double)w[3 * q + 2] - O[2]};
-            for (int c = 0; c < 3; ++c) V[q][c] = M[3 * c] * d[0] + M[3 * c + 1] * d[1] + M[3 * c + 2] * d[2];
-            if (V[q][0] == 0.0 && V[q][1] == 0.0 && V[q][2] == 0.0) at_eye = 1;
-        }
-        double bxc[3];
-        cross3(V[1], V[2], bxc);
-        double det = dot3(V[0], bxc);
-        if (at_eye || det == 0.0 || !isfinite(det)) continue; /* culled */
-        double sigma = det > 0.0 ? 1.0 : -1.0;
-        edge_normal(w + 0, w + 3, V[0], V[1], sigma, r + REC_N1);
-        edge_normal(w + 3, w + 6, V[1], V[2], sigma, r + REC_N2);
-        edge_normal(w + 6, w + 0, V[2], V[0], sigma, r + REC_N3);
+        double wd[9];
+        for (int q = 0; q < 9; ++q) wd[q] = w[q];
+        int swap[3] = {vertex_less_f(w + 3, w + 0), vertex_less_f(w + 6, w + 3), vertex_less_f(w + 0, w + 6)};
+        setup_one(wd, swap, O, M, rec + ORC_REC * t);
+    }
+}
 
-        /* miter: smallest circle over the projected vertices */
-        double U[3][3];
-        for (int q = 0; q < 3; ++q) {
-            double len = sqrt(dot3(V[q], V[q]));
-            for (int c = 0; c < 3; ++c) U[q][c] = V[q][c] / len;
-        }
-        double e_a[3], e_b[3], e_c[3];
-        for (int c = 0; c < 3; ++c) {
-            e_a[c] = U[1][c] - U[2][c];
-            e_b[c] = U[2][c] - U[0][c];
-            e_c[c] = U[0][c] - U[1][c];
-        }
-        double a2 = dot3(e_a, e_a), b2 = dot3(e_b, e_b), c2 = dot3(e_c, e_c);
-        double Os = a2 * (b2 + c2 - a2), Ot = b2 * (c2 + a2 - b2), Op = c2 * (a2 + b2 - c2);
-        double S[3];
-        for (int c = 0; c < 3; ++c) {
-            if (Os <= 0.0)
-                S[c] = 0.5 * (U[1][c] + U[2][c]);
-            else if (Ot <= 0.0)
-                S[c] = 0.5 * (U[2][c] + U[0][c]);
-            else if (Op <= 0.0)
-                S[c] = 0.5 * (U[0][c] + U[1][c]);
-            else
-                S[c] = (Os * U[0][c] + Ot * U[1][c] + Op * U[2][c]) / (Os + Ot + Op);
-        }
-        double slen = sqrt(dot3(S, S));
-        double sr = sqrt((1.0 - slen) * (1.0 + slen)); /* sin(rho), reading R17 */
-        if (!(slen > 0.0) || !(sr > 0.0)) continue; /* degenerate: det == 0, or a point-sized cap */
-        for (int c = 0; c < 3; ++c) r[REC_S + c] = S[c] / slen;
-        r[REC_C] = slen;
-        r[REC_SR] = sr;
-
-        /* plane for depth */
-        double ab[3], cb[3];
-        for (int c = 0; c < 3; ++c) {
-            ab[c] = V[0][c] - V[1][c];
-            cb[c] = V[2][c] - V[1][c];
-        }
-        cross3(ab, cb, r + REC_N);
-        r[REC_D] = dot3(V[0], r + REC_N);
-        r[REC_VALID] = 1.0;
-        r[REC_SIGMA] = sigma;
+/* The same set-up from double-precision world vertices and camera (used to
+ * differentiate by central differences with steps far below an FP32 ulp). */
+void orc_setup64(int64_t T, const double* tris, const double* cam, double* rec)
+{
+    const double O[3] = {cam[0], cam[1], cam[2]};
+    double M[9];
+    for (int q = 0; q < 9; ++q) M[q] = cam[3 + q];
+    for (int64_t t = 0; t < T; ++t) {
+        const double* w = tris + 9 * t;
+        int swap[3] = {vertex_less_d(w + 3, w + 0), vertex_less_d(w + 6, w + 3), vertex_less_d(w + 0, w + 6)};
+        setup_one(w, swap, O, M, rec + ORC_REC * t);
     }
 }
 
@@ -642,4 +683,523 @@ int64_t orc_raster(int W, int H, const double* map, int64_t T, const double* rec
     J.n_alg = 0;
     run_threads(ncores(nthreads), raster_worker, &J);
     return J.n_alg;
+}
+
+/* ------------------------------------------------------------------------
+ * Shaded image (the differentiable workload): per pixel the front-to-back
+ * merge of Sec. 1.3 applied to a shade pass, as the paper applies it to its
+ * depth, UV and normal passes:
+ *   m^fc = min(m^f, 1 - m^b);  I = I + m^fc * shade_f;  m^b = m^b + m^fc
+ * over the fragments in ascending (r, t), with shade_f = c_t |N-hat_t . G|
+ * (a Lambert-like term of the triangle's unit plane normal).  Fragments and
+ * m^f as in orc_raster.  image: npix values.
+ */
+typedef struct {
+    double r, m, shade;
+    uint32_t t;
+} sfrag;
+
+static int sfrag_cmp(const void* a, const void* b)
+{
+    const sfrag* x = (const sfrag*)a;
+    const sfrag* y = (const sfrag*)b;
+    if (x->r < y->r) return -1;
+    if (x->r > y->r) return 1;
+    return x->t < y->t ? -1 : (x->t > y->t ? 1 : 0);
+}
+
+typedef struct {
+    int W, H;
+    const double* map;
+    int64_t T;
+    const double* rec;
+    const double* colors;
+    int64_t npix;
+    const int64_t* pix;
+    double* image;
+    int64_t next;
+} shade_job;
+
+static void* shade_worker(void* arg)
+{
+    shade_job* J = (shade_job*)arg;
+    size_t cap = 64;
+    sfrag* F = (sfrag*)malloc(cap * sizeof(sfrag));
+    for (;;) {
+        int64_t q0 = __atomic_fetch_add(&J->next, 64, __ATOMIC_RELAXED);
+        if (q0 >= J->npix) break;
+        int64_t q1 = q0 + 64 < J->npix ? q0 + 64 : J->npix;
+        for (int64_t q = q0; q < q1; ++q) {
+            int64_t p = J->pix ? J->pix[q] : q;
+            const double* G = J->map + 4 * p;
+            double delta = G[3];
+            size_t nf = 0;
+            if (delta > 0.0) {
+                double lim = -0.5 / delta;
+                for (int64_t t = 0; t < J->T; ++t) {
+                    const double* r = J->rec + ORC_REC * t;
+                    if (r[REC_VALID] == 0.0) continue;
+                    double g4 = (dot3(G, r + REC_S) - r[REC_C]) / r[REC_SR];
+                    if (!(g4 > lim)) continue;
+                    double g1 = dot3(G, r + REC_N1), g2 = dot3(G, r + REC_N2), g3 = dot3(G, r + REC_N3);
+                    if (!(g1 > lim && g2 > lim && g3 > lim)) continue;
+                    double GN = dot3(G, r + REC_N);
+                    double rr = r[REC_D] / GN;
+                    if (!(rr > 0.0) || !isfinite(rr)) continue;
+                    double m = 1.0;
+                    double gs[4] = {g1, g2, g3, g4};
+                    for (int i = 0; i < 4; ++i) {
+                        double st = clampd(delta * gs[i] + 0.5, 0.0, 1.0);
+                        if (st < m) m = st;
+                    }
+                    if (nf == cap) {
+                        cap *= 2;
+                        F = (sfrag*)realloc(F, cap * sizeof(sfrag));
+                    }
+                    double nlen = sqrt(dot3(r + REC_N, r + REC_N));
+                    F[nf].r = rr;
+                    F[nf].m = m;
+                    F[nf].shade = J->colors[t] * fabs(GN / nlen);
+                    F[nf].t = (uint32_t)t;
+                    ++nf;
+                }
+            }
+            qsort(F, nf, sizeof(sfrag), sfrag_cmp);
+            double mb = 0.0, img = 0.0;
+            for (size_t f = 0; f < nf; ++f) {
+                double mfc = F[f].m < 1.0 - mb ? F[f].m : 1.0 - mb;
+                img += mfc * F[f].shade;
+                mb += mfc;
+            }
+            J->image[q] = img;
+        }
+    }
+    free(F);
+    return NULL;
+}
+
+int orc_shade(int W, int H, const double* map, int64_t T, const double* rec, const double* colors, int64_t npix,
+              const int64_t* pix, double* image, int nthreads)
+{
+    if (W <= 0 || H <= 0 || T < 0 || npix < 0) return -1;
+    if (!pix && npix != (int64_t)W * H) return -1;
+    shade_job J = {W, H, map, T, rec, colors, npix, pix, image, 0};
+    run_threads(ncores(nthreads), shade_worker, &J);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Derivatives of the map with respect to the lens parameters
+ * (k, l, s, Omega in degrees), by the complex-step method (Squire and
+ * Trapp 1998): the map function is analytic in each parameter, so with the
+ * parameter p_j + i h, h = 1e-30, Im v / h is dv/dp_j to the last bit, with
+ * no subtractive cancellation.  delta = 1/fw with fw = max_c (|d_i v_c| +
+ * |d_j v_c|) (reading R8) is differentiated by the chain rule at the
+ * maximising component (the first one, as in orc_map) and the signs of its
+ * differences.  out[(j*W + i)*4 + 0..3] = (dv_x, dv_y, dv_z, d delta)/dp_j;
+ * zero on invalid pixels.  which: 0 k, 1 l, 2 s, 3 Omega.
+ */
+#include <complex.h>
+
+static int map_dir_cs(double x, double y, const double* p, int which, double* v, double* dv)
+{
+    const double h = 1e-30;
+    double complex k = p[0], l = p[1], s = p[2], om = p[3];
+    if (which == 0) k += I * h;
+    if (which == 1) l += I * h;
+    if (which == 2) s += I * h;
+    if (which == 3) om += I * h;
+    double complex half = om * ORC_PI / 360.0;
+    double complex R = csqrt(x * x + l * y * y);
+    double complex theta, sor;
+    int Rzero = x == 0.0 && y == 0.0;
+    if (p[0] > 0.0) {
+        double complex tk = ctan(k * half);
+        theta = catan(tk * R) / k;
+        sor = Rzero ? tk / k : csin(theta) / R;
+    } else if (p[0] == 0.0) {
+        theta = half * R;
+        sor = Rzero ? half : csin(theta) / R;
+    } else {
+        double complex sk = csin(k * half);
+        double complex arg = sk * R;
+        if (creal(arg) > 1.0 || creal(arg) < -1.0) {
+            v[0] = v[1] = v[2] = dv[0] = dv[1] = dv[2] = 0.0;
+            return 0;
+        }
+        theta = casin(arg) / k;
+        sor = Rzero ? sk / k : csin(theta) / R;
+    }
+    double complex w[3] = {x * sor, y * sor / (l * (1.0 - s) + s), ccos(theta)};
+    double complex n = csqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    for (int c = 0; c < 3; ++c) {
+        double complex q = w[c] / n;
+        v[c] = creal(q);
+        dv[c] = cimag(q) / h;
+    }
+    return 1;
+}
+
+int orc_map_tangent(int W, int H, const double* p, int aov, int which, double* out)
+{
+    if (W <= 0 || H <= 0 || which < 0 || which > 3) return -1;
+    const int GW = W + 2;
+    const size_t gn = (size_t)GW * (size_t)(H + 2);
+    double* g = (double*)malloc(gn * 6 * sizeof(double));
+    int* ok = (int*)malloc(gn * sizeof(int));
+    if (!g || !ok) {
+        free(g);
+        free(ok);
+        return -2;
+    }
+    const double aspect = (double)W / (double)H;
+    for (int gj = 0; gj < H + 2; ++gj)
+        for (int gi = 0; gi < GW; ++gi) {
+            size_t q = (size_t)gj * GW + gi;
+            double xy[2];
+            orc_view_coord((gi - 0.5) / W, (gj - 0.5) / H, aspect, aov, xy);
+            ok[q] = map_dir_cs(xy[0], xy[1], p, which, g + 6 * q, g + 6 * q + 3);
+        }
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            double* o = out + ((size_t)j * W + i) * 4;
+            size_t c0 = (size_t)(j + 1) * GW + (i + 1);
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+            if (!ok[c0]) continue;
+            size_t cl = c0 - 1, cr = c0 + 1, cu = c0 - GW, cd = c0 + GW;
+            double fw = 0.0, dfw = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                /* value (0) and tangent (3) of the two differences */
+                double di[2], dj[2];
+                for (int part = 0; part < 2; ++part) {
+                    int off = part ? 3 : 0;
+                    double vc = g[6 * c0 + off + c];
+                    if (ok[cl] && ok[cr])
+                        di[part] = (g[6 * cr + off + c] - g[6 * cl + off + c]) * 0.5;
+                    else if (ok[cr])
+                        di[part] = g[6 * cr + off + c] - vc;
+                    else if (ok[cl])
+                        di[part] = vc - g[6 * cl + off + c];
+                    else
+                        di[part] = 0.0;
+                    if (ok[cu] && ok[cd])
+                        dj[part] = (g[6 * cd + off + c] - g[6 * cu + off + c]) * 0.5;
+                    else if (ok[cd])
+                        dj[part] = g[6 * cd + off + c] - vc;
+                    else if (ok[cu])
+                        dj[part] = vc - g[6 * cu + off + c];
+                    else
+                        dj[part] = 0.0;
+                }
+                double f = fabs(di[0]) + fabs(dj[0]);
+                if (f > fw) {
+                    fw = f;
+                    double si = di[0] > 0.0 ? 1.0 : (di[0] < 0.0 ? -1.0 : 0.0);
+                    double sj = dj[0] > 0.0 ? 1.0 : (dj[0] < 0.0 ? -1.0 : 0.0);
+                    dfw = si * di[1] + sj * dj[1];
+                }
+            }
+            if (!(fw > 0.0)) continue;
+            for (int c = 0; c < 3; ++c) o[c] = g[6 * c0 + 3 + c];
+            o[3] = -dfw / (fw * fw);
+        }
+    free(g);
+    free(ok);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the shaded image (and of the coverage and depth outputs) with
+ * respect to the set-up records, the colours and the map, per pixel in the
+ * merge order of orc_shade.  With upstream gradients dI, dcov, ddepth of a
+ * pixel and its fragments f = 0, 1, ... in ascending (r, t):
+ *
+ *   the merge m^fc = min(m^f, 1 - m^b), m^b += m^fc takes m^fc = m^f until
+ *   the first fragment f* with m^f > 1 - m^b, which takes 1 - m^b and
+ *   leaves m^b = 1 (every later fragment then adds nothing).  Hence
+ *     dI/d shade_f = m^fc_f,
+ *     dI/d m^f_f   = shade_f - shade_f*  for f < f* (shade_f alone when no
+ *                    fragment saturates the pixel), 0 from f* on,
+ *     dcov/d m^f_f = 1 for every f when no fragment saturates, else 0;
+ *   m^f = min_i clamp(delta g_i + 1/2, 0, 1) passes its gradient to the
+ *   first minimising distance i* when its clamp is not saturated:
+ *     d g_i* = delta dm, d delta = g_i* dm;
+ *   g_1..3 = G.n_i, g_4 = (G.S-hat - c)/sin(rho), sin(rho) = sqrt(1 - c^2);
+ *   shade = col |G.N|/|N|;  depth r = d/(G.N) of the nearest centre-inside
+ *   fragment.
+ *
+ * drec[t*ORC_REC + ...] receives d/d(n_1, n_2, n_3, S-hat, c, N, d) at the
+ * record offsets (REC_N1 .. REC_D); dcolors[t]; dmap[q*4 + 0..3] =
+ * d/d(G, delta) of listed pixel q.  Single-threaded over pixels (the
+ * accumulation into drec is then in a fixed order).
+ */
+int orc_shade_grad(int W, int H, const double* map, int64_t T, const double* rec, const double* colors,
+                   int64_t npix, const int64_t* pix, const double* dimage, const double* dcov, const double* ddepth,
+                   double* drec, double* dcolors, double* dmap)
+{
+    if (W <= 0 || H <= 0 || T < 0 || npix < 0) return -1;
+    if (!pix && npix != (int64_t)W * H) return -1;
+    memset(drec, 0, sizeof(double) * ORC_REC * (size_t)T);
+    memset(dcolors, 0, sizeof(double) * (size_t)T);
+    size_t cap = 64;
+    sfrag* F = (sfrag*)malloc(cap * sizeof(sfrag));
+    for (int64_t q = 0; q < npix; ++q) {
+        int64_t p = pix ? pix[q] : q;
+        const double* G = map + 4 * p;
+        const double delta = G[3];
+        double* dG = dmap + 4 * q;
+        dG[0] = dG[1] = dG[2] = dG[3] = 0.0;
+        if (!(delta > 0.0)) continue;
+        const double lim = -0.5 / delta;
+        size_t nf = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            const double* r = rec + ORC_REC * t;
+            if (r[REC_VALID] == 0.0) continue;
+            double g4 = (dot3(G, r + REC_S) - r[REC_C]) / r[REC_SR];
+            if (!(g4 > lim)) continue;
+            double g1 = dot3(G, r + REC_N1), g2 = dot3(G, r + REC_N2), g3 = dot3(G, r + REC_N3);
+            if (!(g1 > lim && g2 > lim && g3 > lim)) continue;
+            double GN = dot3(G, r + REC_N);
+            double rr = r[REC_D] / GN;
+            if (!(rr > 0.0) || !isfinite(rr)) continue;
+            double m = 1.0;
+            double gs[4] = {g1, g2, g3, g4};
+            for (int i = 0; i < 4; ++i) {
+                double st = clampd(delta * gs[i] + 0.5, 0.0, 1.0);
+                if (st < m) m = st;
+            }
+            if (nf == cap) {
+                cap *= 2;
+                F = (sfrag*)realloc(F, cap * sizeof(sfrag));
+            }
+            double nlen = sqrt(dot3(r + REC_N, r + REC_N));
+            F[nf].r = rr;
+            F[nf].m = m;
+            F[nf].shade = colors[t] * fabs(GN / nlen);
+            F[nf].t = (uint32_t)t;
+            ++nf;
+        }
+        qsort(F, nf, sizeof(sfrag), sfrag_cmp);
+        const double dI = dimage ? dimage[q] : 0.0;
+        const double dC = dcov ? dcov[q] : 0.0;
+        const double dD = ddepth ? ddepth[q] : 0.0;
+        /* the saturating fragment f*, if any */
+        size_t fstar = nf;
+        double mb = 0.0;
+        for (size_t f = 0; f < nf; ++f) {
+            if (F[f].m > 1.0 - mb) {
+                fstar = f;
+                break;
+            }
+            mb += F[f].m;
+        }
+        const double beta = fstar < nf ? -dI * F[fstar].shade : dC;
+        mb = 0.0;
+        const size_t last = fstar < nf ? fstar + 1 : nf;
+        for (size_t f = 0; f < last; ++f) {
+            const int64_t t = F[f].t;
+            const double* r = rec + ORC_REC * t;
+            double* dr = drec + ORC_REC * t;
+            double dm, dshade;
+            if (f == fstar) {
+                dm = 0.0;
+                dshade = dI * (1.0 - mb);
+            } else {
+                dm = dI * F[f].shade + beta;
+                dshade = dI * F[f].m;
+                mb += F[f].m;
+            }
+            /* m^f: the first minimising distance, if its clamp is open */
+            if (dm != 0.0) {
+                double gs[4] = {dot3(G, r + REC_N1), dot3(G, r + REC_N2), dot3(G, r + REC_N3),
+                                (dot3(G, r + REC_S) - r[REC_C]) / r[REC_SR]};
+                double m = 1.0;
+                int istar = -1;
+                for (int i = 0; i < 4; ++i) {
+                    double st = clampd(delta * gs[i] + 0.5, 0.0, 1.0);
+                    if (st < m) {
+                        m = st;
+                        istar = i;
+                    }
+                }
+                double arg = istar >= 0 ? delta * gs[istar] + 0.5 : 1.0;
+                if (istar >= 0 && arg > 0.0 && arg < 1.0) {
+                    const double dg = dm * delta;
+                    dG[3] += dm * gs[istar];
+                    if (istar < 3) {
+                        const int off = REC_N1 + 3 * istar;
+                        for (int c = 0; c < 3; ++c) {
+                            dr[off + c] += dg * G[c];
+                            dG[c] += dg * r[off + c];
+                        }
+                    } else {
+                        const double sr = r[REC_SR], cc = r[REC_C];
+                        for (int c = 0; c < 3; ++c) {
+                            dr[REC_S + c] += dg * G[c] / sr;
+                            dG[c] += dg * r[REC_S + c] / sr;
+                        }
+                        dr[REC_C] += dg * (-1.0 / sr + gs[3] * cc / (sr * sr));
+                    }
+                }
+            }
+            /* shade = col |G.N| / |N| */
+            if (dshade != 0.0) {
+                const double nlen = sqrt(dot3(r + REC_N, r + REC_N));
+                const double u = dot3(G, r + REC_N) / nlen;
+                dcolors[t] += dshade * fabs(u);
+                const double du = dshade * colors[t] * (u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0));
+                for (int c = 0; c < 3; ++c) {
+                    dG[c] += du * r[REC_N + c] / nlen;
+                    dr[REC_N + c] += du * (G[c] - u * r[REC_N + c] / nlen) / nlen;
+                }
+            }
+        }
+        /* depth of the nearest centre-inside fragment */
+        if (dD != 0.0) {
+            for (size_t f = 0; f < nf; ++f) {
+                const double* r = rec + ORC_REC * F[f].t;
+                if (!(tie_inside(dot3(G, r + REC_N1), r + REC_N1) && tie_inside(dot3(G, r + REC_N2), r + REC_N2) &&
+                      tie_inside(dot3(G, r + REC_N3), r + REC_N3)))
+                    continue;
+                double* dr = drec + ORC_REC * F[f].t;
+                const double GN = dot3(G, r + REC_N);
+                dr[REC_D] += dD / GN;
+                const double dGN = -dD * F[f].r / GN;
+                for (int c = 0; c < 3; ++c) {
+                    dG[c] += dGN * r[REC_N + c];
+                    dr[REC_N + c] += dGN * G[c];
+                }
+                break;
+            }
+        }
+    }
+    free(F);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the set-up (orc_setup64's arithmetic, in reverse): record
+ * gradients drec (layout of orc_shade_grad) -> world-vertex gradients
+ * dtris[t*9 + 3*v + c].
+ *   n_e = sigma x/|x|, x = P' x Q'    =>  dx = sigma (dn - x^ (x^.dn))/|x|,
+ *                                          dP' += Q' x dx, dQ' += dx x P'
+ *   S-hat = S/|S|, c = |S|             =>  dS = (dS^ - S^ (S^.dS^))/|S| + S^ dc
+ *   S = (U_a + U_b)/2 or (Os U0 + Ot U1 + Op U2)/(Os + Ot + Op) with the
+ *   squared chords a2, b2, c2 of the unit vertices U = V/|V|
+ *   N = (A' - B') x (C' - B'), d = A'.N
+ *   X' = M (X - O)                     =>  dX = M^T dX'
+ */
+void orc_setup_grad(int64_t T, const double* tris, const double* cam, const double* rec, const double* drec,
+                    double* dtris)
+{
+    const double O[3] = {cam[0], cam[1], cam[2]};
+    const double* M = cam + 3;
+    for (int64_t t = 0; t < T; ++t) {
+        const double* w = tris + 9 * t;
+        const double* r = rec + ORC_REC * t;
+        const double* dr = drec + ORC_REC * t;
+        double* dw = dtris + 9 * t;
+        for (int q = 0; q < 9; ++q) dw[q] = 0.0;
+        if (r[REC_VALID] == 0.0) continue;
+        double V[3][3], dV[3][3] = {{0}};
+        for (int q = 0; q < 3; ++q) {
+            double d[3] = {w[3 * q] - O[0], w[3 * q + 1] - O[1], w[3 * q + 2] - O[2]};
+            for (int c = 0; c < 3; ++c) V[q][c] = M[3 * c] * d[0] + M[3 * c + 1] * d[1] + M[3 * c + 2] * d[2];
+        }
+        const double sigma = r[REC_SIGMA];
+        /* edge normals */
+        for (int e = 0; e < 3; ++e) {
+            const int P = e, Q = (e + 1) % 3;
+            double x[3];
+            cross3(V[P], V[Q], x);
+            const double len = sqrt(dot3(x, x));
+            const double* dn = dr + REC_N1 + 3 * e;
+            double xh[3] = {x[0] / len, x[1] / len, x[2] / len};
+            const double pr = dot3(xh, dn);
+            double dx[3], a[3], b[3];
+            for (int c = 0; c < 3; ++c) dx[c] = sigma * (dn[c] - xh[c] * pr) / len;
+            cross3(V[Q], dx, a);
+            cross3(dx, V[P], b);
+            for (int c = 0; c < 3; ++c) {
+                dV[P][c] += a[c];
+                dV[Q][c] += b[c];
+            }
+        }
+        /* miter */
+        double U[3][3], Ulen[3];
+        for (int q = 0; q < 3; ++q) {
+            Ulen[q] = sqrt(dot3(V[q], V[q]));
+            for (int c = 0; c < 3; ++c) U[q][c] = V[q][c] / Ulen[q];
+        }
+        double e_a[3], e_b[3], e_c[3];
+        for (int c = 0; c < 3; ++c) {
+            e_a[c] = U[1][c] - U[2][c];
+            e_b[c] = U[2][c] - U[0][c];
+            e_c[c] = U[0][c] - U[1][c];
+        }
+        const double a2 = dot3(e_a, e_a), b2 = dot3(e_b, e_b), c2 = dot3(e_c, e_c);
+        const double Os = a2 * (b2 + c2 - a2), Ot = b2 * (c2 + a2 - b2), Op = c2 * (a2 + b2 - c2);
+        const double* Sh = r + REC_S;
+        const double slen = r[REC_C];
+        double S[3], dS[3], dU[3][3] = {{0}};
+        for (int c = 0; c < 3; ++c) S[c] = Sh[c] * slen;
+        const double prS = dot3(Sh, dr + REC_S);
+        for (int c = 0; c < 3; ++c) dS[c] = (dr[REC_S + c] - Sh[c] * prS) / slen + Sh[c] * dr[REC_C];
+        if (Os <= 0.0 || Ot <= 0.0 || Op <= 0.0) {
+            const int a = Os <= 0.0 ? 1 : (Ot <= 0.0 ? 2 : 0);
+            const int b = Os <= 0.0 ? 2 : (Ot <= 0.0 ? 0 : 1);
+            for (int c = 0; c < 3; ++c) {
+                dU[a][c] += 0.5 * dS[c];
+                dU[b][c] += 0.5 * dS[c];
+            }
+        } else {
+            const double sum = Os + Ot + Op;
+            const double Oq[3] = {Os, Ot, Op};
+            double dO[3];
+            for (int q = 0; q < 3; ++q) {
+                double u[3] = {U[q][0] - S[0], U[q][1] - S[1], U[q][2] - S[2]};
+                dO[q] = dot3(dS, u) / sum;
+                for (int c = 0; c < 3; ++c) dU[q][c] += Oq[q] / sum * dS[c];
+            }
+            const double da2 = dO[0] * (b2 + c2 - 2.0 * a2) + dO[1] * b2 + dO[2] * c2;
+            const double db2 = dO[0] * a2 + dO[1] * (c2 + a2 - 2.0 * b2) + dO[2] * c2;
+            const double dc2 = dO[0] * a2 + dO[1] * b2 + dO[2] * (a2 + b2 - 2.0 * c2);
+            for (int c = 0; c < 3; ++c) {
+                dU[1][c] += 2.0 * da2 * e_a[c];
+                dU[2][c] -= 2.0 * da2 * e_a[c];
+                dU[2][c] += 2.0 * db2 * e_b[c];
+                dU[0][c] -= 2.0 * db2 * e_b[c];
+                dU[0][c] += 2.0 * dc2 * e_c[c];
+                dU[1][c] -= 2.0 * dc2 * e_c[c];
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            const double pr = dot3(U[q], dU[q]);
+            for (int c = 0; c < 3; ++c) dV[q][c] += (dU[q][c] - U[q][c] * pr) / Ulen[q];
+        }
+        /* plane and depth offset */
+        double ab[3], cb[3], N[3];
+        for (int c = 0; c < 3; ++c) {
+            ab[c] = V[0][c] - V[1][c];
+            cb[c] = V[2][c] - V[1][c];
+        }
+        cross3(ab, cb, N);
+        double dN[3];
+        for (int c = 0; c < 3; ++c) {
+            dN[c] = dr[REC_N + c] + dr[REC_D] * V[0][c];
+            dV[0][c] += dr[REC_D] * N[c];
+        }
+        double de1[3], de2[3];
+        cross3(cb, dN, de1);
+        cross3(dN, ab, de2);
+        for (int c = 0; c < 3; ++c) {
+            dV[0][c] += de1[c];
+            dV[2][c] += de2[c];
+            dV[1][c] -= de1[c] + de2[c];
+        }
+        /* world */
+        for (int q = 0; q < 3; ++q)
+            for (int c = 0; c < 3; ++c)
+                dw[3 * q + c] = M[c] * dV[q][0] + M[3 + c] * dV[q][1] + M[6 + c] * dV[q][2];
+    }
 }

@@ -135,3 +135,24 @@ def batched_views(n_views=64, seed=2):
 def batched_scene(seed=2, n=1_000_000):
     """Shared scene of the batched workload: rho ~ U[1, 60], edge ~0.01 rad."""
     return random_triangles(n, 1.0, 60.0, 0.0096, seed)
+
+
+# Differentiation workload: 1024 x 1024, 10,000 triangles of the tiny-scene
+# generator with rho ~ U[1, 10] and jitter 0.05 rad (depth complexity about
+# one over the sphere), colours c_t ~ U[0.2, 1]; the target lens is
+# (k, l, s) = (0.2, 0.7, 0.9), the fit starts from (0.6, 1, 1) with vertex
+# noise N(0, 0.01^2) per coordinate.  Omega = 180 deg, horizontal AOV.
+GRAD_TARGET = {"k": 0.2, "l": 0.7, "s": 0.9, "omega": 180.0}
+GRAD_START = {"k": 0.6, "l": 1.0, "s": 1.0, "omega": 180.0}
+
+
+def grad_scene(seed=4, n=10_000, W=1024, H=1024):
+    """Returns (target lens, start lens, true tris, noisy tris, colours, W, H);
+    triangles float32 [n, 3, 3], colours float32 [n]."""
+    tris = random_triangles(n, 1.0, 10.0, 0.05, seed)
+    rng = np.random.default_rng(seed + 1000)
+    colors = rng.uniform(0.2, 1.0, n).astype(np.float32)
+    noisy = (tris.astype(np.float64) + rng.normal(0.0, 0.01, tris.shape)).astype(np.float32)
+    target = dict(GRAD_TARGET, W=W, H=H)
+    start = dict(GRAD_START, W=W, H=H)
+    return target, start, tris, noisy, colors, W, H
