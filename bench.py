@@ -39,8 +39,8 @@ UNIT = "tests/s"
 OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
 LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
 # kernels of libvsr.so per step: map, tile index, set-up, bin count, bin scan,
-# bin fill, raster
-LAUNCHES_PER_STEP = 7
+# bin fill, work items, raster
+LAUNCHES_PER_STEP = 8
 
 
 def parse():
@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200000, help="pixels of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "grad"],
                     help="single: the 1080p single-view frame (default); batched: 64 mixed views of a "
                          "1M-triangle scene, batched launch vs per-view plain launches")
     ap.add_argument("--views", type=int, default=64)
@@ -343,7 +343,7 @@ def run_vsr(args, rank, world, local):
         "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32)",
                      "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "raster_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
+                     "kernel": "raster_items_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
                      f"{LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} sm_max_mhz)"},
         "clocks": clk.summary(),
         "gpu_launches": LAUNCHES_PER_STEP * K,
@@ -520,6 +520,81 @@ def run_serving(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_grad(args, rank, world, local):
+    """The differentiation workload: 1024x1024 map at the fit's start lens
+    (k=0.6, l=1, s=1, Omega=180), 10,000 seeded triangles with vertex noise,
+    per-triangle colours.  One step is one forward and backward of the shaded
+    image: map (a1) and set-up (a2) for the current lens and vertices, binning
+    (a3), fragment lists with the sorted front-to-back merge (a4 + a5), then
+    the adjoint to vertices, colours and (k, l, s, Omega) with a fixed
+    upstream dL/dI.  Reports differentiable frames/s and the stage times."""
+    import torch
+    import torch.distributed as dist
+    from paper_2003_10558_gb300 import vsr as V
+    from paper_2003_10558_gb300 import build as B
+    from paper_2003_10558_gb300 import scenes, replicas
+
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    B.build()
+    V.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    target, start, tris_t, noisy, colors, W, H = scenes.grad_scene()
+    tris = torch.from_numpy(noisy).to(dev)
+    col = torch.from_numpy(colors).to(dev)
+    r = V.ShadedRenderer(W, H)
+    up = torch.from_numpy(np.random.default_rng(5).normal(size=(H, W)).astype(np.float32)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    T = tris.shape[0]
+
+    def step(evs=None):
+        r.set_lens(start["k"], start["l"], start["s"], start["omega"])
+        r.scene.update(tris, r.cam)
+        if evs:
+            evs[0].record(stream)
+        out = V.raster_shaded(r.map, r.scene, r.frags, col)
+        if evs:
+            evs[1].record(stream)
+        V.raster_backward(r.map, r.scene, r.frags, tris, col, out["id"], dimage=up)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    assert V.last_device_status() == 0
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    stage = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev0[k].record(stream)
+            step(stage[k])
+        torch.cuda.synchronize()
+    assert V.last_device_status() == 0
+    step_ms = [a.elapsed_time(s_[2]) for a, s_ in zip(ev0, stage)]
+    frames, tot_s = replicas.combine(K, sum(step_ms) / 1000.0)
+    if rank != 0:
+        return
+    line = {"metric": "differentiable frames/s (forward + backward)", "value": frames / tot_s, "unit": "frames/s",
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / K * world,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scene generator)",
+            "stage_ms": {"map+setup": statistics.mean(a.elapsed_time(s_[0]) for a, s_ in zip(ev0, stage)),
+                         "forward": statistics.mean(s_[0].elapsed_time(s_[1]) for s_ in stage),
+                         "backward": statistics.mean(s_[1].elapsed_time(s_[2]) for s_ in stage)},
+            "config": {"workload": "differentiation 1024x1024, k=0.6 l=1 s=1 Omega=180, 10k triangles",
+                       "W": W, "H": H, "T": int(T), "l2": "flushed before every step (256 MB write, outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -530,6 +605,14 @@ def main():
                                   "the oracle is timed on the single-view workload"}))
             return
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "grad":
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the differentiation workload has no CPU arm; "
+                                  "the oracle is timed on the single-view workload"}))
+            return
+        run_grad(args, rank, world, local)
         return
     if args.workload == "batched":
         if args.impl == "reference":

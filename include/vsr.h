@@ -41,7 +41,7 @@ typedef enum {
     VSR_ERR_OOM = -2,          /* device or host allocation failed */
     VSR_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     VSR_ERR_BIN_OVERFLOW = -4, /* a tile bin exceeded its capacity (device-side) */
-    VSR_ERR_FRAG_OVERFLOW = -5,/* reserved: the merge is order-free and keeps no fragment list */
+    VSR_ERR_FRAG_OVERFLOW = -5,/* differentiable path: fragment lists of another frame (device status) */
     VSR_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
     VSR_ERR_BUDGET = -7,       /* a request does not fit the memory budget */
     VSR_ERR_CANCELLED = -8
@@ -311,6 +311,61 @@ vsr_status vsr_serve_stats_get(vsr_server s, vsr_serve_stats* out);
 double vsr_serve_now(void);
 /* Finishes the queued and running requests, then frees everything. */
 vsr_status vsr_serve_destroy(vsr_server s);
+
+/* ---- differentiable rendering ----------------------------------------------
+ * A shaded image and its hand-written adjoint.  The image is the
+ * front-to-back mask merge of Sec. 1.3 applied to a shade pass
+ *   I = sum over the fragments of a pixel in ascending (r, t) of
+ *       m^fc shade,  m^fc = min(m^f, 1 - m^b),  m^b += m^fc,
+ *   shade_t = c_t |N-hat_t . G|   (N-hat the hard normal of Sec. 1.1.5),
+ * with the fragments, m^f (gpstep on the four plane distances, Sec. 1.1.1
+ * and 1.1.2) and depth of vsr_raster.  The merge depends on the order, so
+ * the forward keeps every fragment of every pixel in a fragment-list handle
+ * that the backward reads.
+ *
+ * vsr_frags: library-owned fragment lists and backward workspace; grows to
+ * the largest frame it has seen.  One frame at a time: a forward replaces
+ * the lists of the previous one. */
+typedef struct vsr_frags_s* vsr_frags;
+vsr_status vsr_frags_create(vsr_frags* out);
+void vsr_frags_free(vsr_frags f);
+
+/* vsr_raster_shaded: bins (as vsr_raster), counts the fragments of every
+ * pixel, sizes the lists (one synchronisation of `stream` per call: the
+ * fragment total is read back), fills, sorts and merges them.
+ * colors_dev: device [T] colour c_t per triangle (NULL: all 1).
+ * Outputs (caller-owned device [H][W], any may be NULL): image_dev (I),
+ * cov_dev (final m^b of the merge: the coverage of vsr_raster within
+ * rounding), id_dev and depth_dev (as vsr_raster).  At most 2^32 - 1
+ * fragments per frame.  Errors: VSR_ERR_INVALID_ARG, VSR_ERR_OOM,
+ * VSR_ERR_CUDA; device-side VSR_ERR_BIN_OVERFLOW / VSR_ERR_FRAG_OVERFLOW in
+ * the status word. */
+vsr_status vsr_raster_shaded(vsr_map m, vsr_scene s, const float* colors_dev, vsr_frags f, float* image_dev,
+                             float* cov_dev, uint32_t* id_dev, float* depth_dev, void* stream);
+
+/* vsr_raster_backward: the adjoint of the last vsr_raster_shaded of (m, s)
+ * into f.  Upstream gradients (device [H][W], NULL = 0): dimage_dev = dL/dI,
+ * dcov_dev = dL/dcov, ddepth_dev = dL/ddepth (through r = (A'.N)/(G.N) of
+ * the visible triangle, Sec. 1.1.5; the visibility switch itself has no
+ * gradient).  id_dev: that forward's id output (needed with ddepth_dev).
+ * tris_dev: the world triangles [T][3][3] of the scene's current set-up
+ * (the camera is the scene's).  Outputs (device, overwritten, NULL to
+ * skip): dtris_dev [T][3][3] = dL/d(world vertices), dcolors_dev [T] =
+ * dL/dc_t, dlens_dev (double [4]) = dL/d(k, l, s, Omega in degrees) of the
+ * map at its effective parameters (after the limits; a map made by
+ * vsr_map_from_device has no lens: VSR_ERR_INVALID_ARG).
+ * The adjoint follows the forward exactly: the merge (saturation at the
+ * first fragment with m^f > 1 - m^b), gpstep / min (the gradient goes to
+ * the minimising plane distance while its clamp is open), the plane
+ * distances g_1..3 = G.n_i and g_4 = (G.S-hat - cos rho)/sin rho, the
+ * set-up (edge normals, smallest circle, plane, camera transform) and the
+ * map (2D->3D transform and global delta).  Per-triangle sums use float
+ * atomics (their order, hence the last bits, varies between runs).
+ * VSR_ERR_INVALID_ARG if f holds no forward of this map and set-up. */
+vsr_status vsr_raster_backward(vsr_map m, vsr_scene s, const float* tris_dev, const float* colors_dev, vsr_frags f,
+                               const uint32_t* id_dev, const float* dimage_dev, const float* dcov_dev,
+                               const float* ddepth_dev, float* dtris_dev, float* dcolors_dev, double* dlens_dev,
+                               void* stream);
 
 /* ---- status ---------------------------------------------------------------- */
 const char* vsr_status_str(vsr_status s);

@@ -119,6 +119,7 @@ vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const flo
         sc->T_alloc = T;
     }
     sc->T = T;
+    for (int q = 0; q < 12; ++q) sc->cam[q] = cam[q];
     // the record layout is field-major with stride T: keep it dense
     vsr_status s = launch_setup(tris_dev, (int)T, cam, sc->rec, st);
     sc->gen = g_gen.fetch_add(1);

@@ -35,6 +35,7 @@ struct vsr_map_s {
 
 struct vsr_scene_s {
     int64_t T = 0;
+    float cam[12] = {};  // camera of the current set-up
     int64_t T_alloc = 0;
     float4* rec = nullptr;
     uint64_t gen = 0;

@@ -219,10 +219,11 @@ __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict
 
 }  // namespace
 
-vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      cudaStream_t st)
+namespace {
+
+// per-map scalars, formed once in double precision and rounded to float
+MapP make_params(int W, int H, int aov, float k, float l, float s, float omega_deg)
 {
-    // per-map scalars, formed once in double precision and rounded to float
     MapP p;
     double half = (double)omega_deg * M_PI / 360.0;
     p.k = k;
@@ -233,14 +234,21 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
     p.sk = (float)sin((double)k * half);
     p.half = (float)half;
     p.inv_ls = (float)(1.0 / ((double)l * (1.0 - (double)s) + (double)s));
-    double a = (double)W / (double)H;
     switch (aov) {
     case VSR_AOV_DIAGONAL: p.sc = (float)(1.0 / sqrt((double)W * W + (double)H * H)); break;
     case VSR_AOV_VERTICAL: p.sc = (float)(1.0 / H); break;
     case VSR_AOV_H4X3: p.sc = (float)(0.75 / H); break;
     default: p.sc = (float)(1.0 / W); break;
     }
-    (void)a;
+    return p;
+}
+
+}  // namespace
+
+vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
+                      cudaStream_t st)
+{
+    const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
     map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, p, map, tiles);
     VSR_CUDA_TRY(cudaGetLastError());
@@ -255,3 +263,211 @@ vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaSt
     return VSR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Map adjoint: the lens gradient dL/d(k, l, s, Omega in degrees) from the
+// per-pixel gradients (dG, d delta) of the map, by forward-mode tangents of
+// the map function (the chain rule through the 2D->3D transform of Sec. 2)
+// and of the global delta (reading of fwidth as central differences,
+// Sec. 1.1.1), contracted per pixel and reduced per CTA; a one-CTA pass sums
+// the CTA partials in double precision in a fixed order.
+//
+//   R = sqrt(x^2 + l y^2)                      dR/dl = y^2/(2R)
+//   k > 0: theta = atan(tan(a) R)/k, a = k Omega/2
+//   k = 0: theta = (Omega/2) R                 (flat in k: both branches agree
+//                                               to second order at k = 0)
+//   k < 0: theta = asin(sin(a) R)/k
+//   w = (x sin(theta)/R, y sin(theta)/R / (l(1-s)+s), cos(theta)), v = w/|w|
+//   delta = 1/fw, fw = max_c (|d_i v_c| + |d_j v_c|): the derivative of the
+//   maximising component (first maximum) with the signs of its differences.
+// The gradient is the one of the map at its effective parameters (after the
+// parameter limits).
+namespace {
+
+struct TanP {
+    MapP p;
+    float s;
+    float ck;  // cos(k Omega/2)
+};
+
+constexpr float DEG_HALF = 0.00872664625997164788f;  // d(Omega/2 in rad)/d(Omega in deg) = pi/360
+
+// tangents dv[q] = dv/dparam_q (q = k, l, s, Omega) at pixel centre (i, j);
+// false where the map is undefined
+__device__ __forceinline__ bool map_tangent(int i, int j, int W, int H, const TanP& tp, float3& v, float3 dv[4])
+{
+    const MapP& p = tp.p;
+    if (!map_fn(i, j, W, H, p, v)) return false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dv[q] = make_float3(0.0f, 0.0f, 0.0f);
+    const float x = (float)(2 * i + 1 - W) * p.sc;
+    const float y = (float)(2 * j + 1 - H) * p.sc;
+    const float R = sqrtf(fmaf(x, x, p.l * y * y));
+    if (!(R > 0.0f)) return true;  // the optical axis: v = (0, 0, 1) for every lens
+    const float dR[4] = {0.0f, y * y / (2.0f * R), 0.0f, 0.0f};
+    float th, dth[4];
+    if (p.kind > 0) {
+        const float u = p.tk * R;
+        th = atanf(u) * p.inv_k;
+        const float sec2 = fmaf(p.tk, p.tk, 1.0f);
+        const float dtk[4] = {sec2 * p.half, 0.0f, 0.0f, sec2 * p.k * DEG_HALF};
+        const float w = p.inv_k / fmaf(u, u, 1.0f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dth[q] = fmaf(dtk[q], R, p.tk * dR[q]) * w;
+        dth[0] -= th * p.inv_k;
+    } else if (p.kind == 0) {
+        th = p.half * R;
+        dth[0] = 0.0f;
+        dth[1] = p.half * dR[1];
+        dth[2] = 0.0f;
+        dth[3] = DEG_HALF * R;
+    } else {
+        const float u = p.sk * R;
+        th = asinf(u) * p.inv_k;
+        const float dsk[4] = {tp.ck * p.half, 0.0f, 0.0f, tp.ck * p.k * DEG_HALF};
+        const float w = p.inv_k * rsqrtf(fmaxf(fmaf(-u, u, 1.0f), 1e-30f));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dth[q] = fmaf(dsk[q], R, p.sk * dR[q]) * w;
+        dth[0] -= th * p.inv_k;
+    }
+    float st, ct;
+    sincosf(th, &st, &ct);
+    const float sor = st / R;
+    const float il = p.inv_ls;
+    const float dil[4] = {0.0f, -il * il * (1.0f - tp.s), -il * il * (1.0f - p.l), 0.0f};
+    const float wx = x * sor, wy = y * sor * il, wz = ct;
+    const float n = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    const float inv = 1.0f / n;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float dsor = (ct * dth[q] - sor * dR[q]) / R;
+        const float dwx = x * dsor;
+        const float dwy = y * fmaf(dsor, il, sor * dil[q]);
+        const float dwz = -st * dth[q];
+        const float pr = (wx * dwx + wy * dwy + wz * dwz) * inv * inv;
+        dv[q] = make_float3((dwx - wx * pr) * inv, (dwy - wy * pr) * inv, (dwz - wz * pr) * inv);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(MAP_THREADS) map_backward_kernel(int W, int H, TanP tp,
+                                                                    const float4* __restrict__ dmap,
+                                                                    float* __restrict__ partials)
+{
+    __shared__ float3 sv[HW * HW];
+    __shared__ float3 sd[4][HW * HW];
+    __shared__ unsigned char sok[HW * HW];
+    __shared__ float red[4][MAP_THREADS / 32];
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
+    if (threadIdx.x < HW * HW) {
+        const int q = threadIdx.x, qi = q % HW, qj = q / HW;
+        float3 v = make_float3(0.0f, 0.0f, 0.0f), dv[4];
+        const bool ok = map_tangent(i0 + qi, j0 + qj, W, H, tp, v, dv);
+        sv[q] = v;
+        sok[q] = ok;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sd[k][q] = ok ? dv[k] : make_float3(0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (threadIdx.x < TILE_PIX) {
+        const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
+        const int i = tx * TILE + li, j = ty * TILE + lj;
+        const int c = (lj + 1) * HW + (li + 1);
+        if (i < W && j < H && sok[c]) {
+            const float4 dm = dmap[(size_t)j * W + i];
+            const int L = c - 1, Rr = c + 1, U = c - HW, D = c + HW;
+            // the map kernel's fwidth, with the maximising component's tangent
+            float fw = 0.0f, dfw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                auto get = [&](const float3& a) { return comp == 0 ? a.x : (comp == 1 ? a.y : a.z); };
+                int ia = c, ib = c, ja = c, jb = c;  // di = (v[ia] - v[ib]) * fi, dj likewise
+                float fi = 0.0f, fj = 0.0f;
+                if (sok[L] && sok[Rr]) { ia = Rr; ib = L; fi = 0.5f; }
+                else if (sok[Rr]) { ia = Rr; fi = 1.0f; }
+                else if (sok[L]) { ib = L; fi = 1.0f; }
+                if (sok[U] && sok[D]) { ja = D; jb = U; fj = 0.5f; }
+                else if (sok[D]) { ja = D; fj = 1.0f; }
+                else if (sok[U]) { jb = U; fj = 1.0f; }
+                const float di = fi == 0.0f ? 0.0f : (fi == 0.5f ? (get(sv[ia]) - get(sv[ib])) * 0.5f
+                                                                 : get(sv[ia]) - get(sv[ib]));
+                const float dj = fj == 0.0f ? 0.0f : (fj == 0.5f ? (get(sv[ja]) - get(sv[jb])) * 0.5f
+                                                                 : get(sv[ja]) - get(sv[jb]));
+                const float f = fabsf(di) + fabsf(dj);
+                if (f > fw) {
+                    fw = f;
+                    const float si = di > 0.0f ? fi : (di < 0.0f ? -fi : 0.0f);
+                    const float sj = dj > 0.0f ? fj : (dj < 0.0f ? -fj : 0.0f);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        dfw[k] = si * (get(sd[k][ia]) - get(sd[k][ib])) + sj * (get(sd[k][ja]) - get(sd[k][jb]));
+                }
+            }
+            if (fw > 0.0f) {
+                const float dd = -dm.w / (fw * fw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float3 t = sd[k][c];
+                    acc[k] = fmaf(dm.x, t.x, fmaf(dm.y, t.y, fmaf(dm.z, t.z, dd * dfw[k])));
+                }
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float a = acc[k];
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) red[k][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float a = 0.0f;
+        for (int w = 0; w < MAP_THREADS / 32; ++w) a += red[threadIdx.x][w];
+        partials[(size_t)(ty * gridDim.x + tx) * 4 + threadIdx.x] = a;
+    }
+}
+
+__global__ void __launch_bounds__(256) lens_reduce_kernel(const float* __restrict__ partials, int nblocks,
+                                                          double* __restrict__ dlens)
+{
+    __shared__ double red[4][256];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += 256)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] += (double)partials[(size_t)b * 4 + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) dlens[threadIdx.x] = red[threadIdx.x][0];
+}
+
+}  // namespace
+
+size_t map_backward_partials(int W, int H)
+{
+    return (size_t)((W + TILE - 1) / TILE) * (size_t)((H + TILE - 1) / TILE) * 4;
+}
+
+vsr_status launch_map_backward(int W, int H, int aov, float k, float l, float s, float omega_deg,
+                               const float4* dmap, float* partials, double* dlens, cudaStream_t st)
+{
+    TanP tp;
+    tp.p = make_params(W, H, aov, k, l, s, omega_deg);
+    tp.s = s;
+    tp.ck = (float)cos((double)k * (double)omega_deg * M_PI / 360.0);
+    dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
+    map_backward_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, tp, dmap, partials);
+    VSR_CUDA_TRY(cudaGetLastError());
+    lens_reduce_kernel<<<1, 256, 0, st>>>(partials, (int)(grid.x * grid.y), dlens);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}

@@ -32,54 +32,16 @@
 // Work culling: the triangles of a chunk are first tested lane-parallel
 // (lane j <-> triangle j) against each warp's own 8x8-pixel view cone; the
 // surviving ones are then evaluated for all 64 pixels.
-#include "df.cuh"
-#include "vsr_internal.cuh"
+#include "stage.cuh"
 
 namespace {
 
 constexpr int RT = 128;          // threads per CTA (one 16x16 tile)
 constexpr int PPT = 2;           // pixels per thread: (x, y) and (x, y + 4) of the warp's 8x8 block
 constexpr int CHUNK = RT;        // triangles staged per pass
+static_assert(CHUNK == STAGE_CHUNK, "one staging slot per thread");
 constexpr int SPLIT_MAX = 4 * CHUNK;  // triangles per work item of a split tile
 static_assert(RT * PPT == TILE_PIX, "one CTA covers one tile");
-
-struct __align__(16) Stage {
-    float4 s0[CHUNK];  // S-hat.hi xyz, tie flags (bits)
-    float4 s1[CHUNK];  // sin rho, 2(1 - cos rho), 1/(2 sin rho), A'.N-hat
-    float4 s2[CHUNK];  // n1.hi xyz, a.n1
-    float4 s3[CHUNK];  // n2.hi xyz, a.n2
-    float4 s4[CHUNK];  // n3.hi xyz, a.n3
-    float4 s5[CHUNK];  // N-hat.hi xyz, a.N-hat
-    float4 s6[CHUNK];  // S-hat - a (tile axis) xyz, triangle index (bits)
-};
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_min(float v)
-{
-    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v)
-{
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// |G|^2 - 1, error-free (TwoProd / TwoSum): the chord form of the miter
-// distance equals (G.S-hat - cos rho)/sin rho for any G only with this term,
-// and FP32 map directions are unit to ~1e-7, not exactly.
-__device__ __forceinline__ float norm2_minus_one(float x, float y, float z)
-{
-    const df px2 = two_prod(x, x), py2 = two_prod(y, y), pz2 = two_prod(z, z);
-    const df s1 = two_sum(px2.hi, py2.hi);
-    const df s2 = two_sum(s1.hi, pz2.hi);
-    const float tail = __fadd_rn(__fadd_rn(__fadd_rn(px2.lo, py2.lo), __fadd_rn(pz2.lo, s1.lo)), s2.lo);
-    return __fadd_rn(__fadd_rn(s2.hi, -1.0f), tail);
-}
 
 // One 16x16 tile of one view.  Called by every thread of a CTA of RT
 // threads; `st` is the CTA's staging area (reusable across calls: every use
@@ -203,30 +165,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 // never produced by a completed binning: a stale or overflowed
                 // bin must not index outside the records
                 raise_status(status, VSR_ERR_BIN_OVERFLOW);
-                st.s6[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(0xffffffffu));
+                st.s6[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(STAGE_EMPTY));
             } else {
-                const float4 cp = rec[RF_CAP * TT + t];
-                const float4 cp2 = rec[RF_CAP2 * TT + t];
-                const float4 n1 = rec[RF_N1 * TT + t], n2 = rec[RF_N2 * TT + t], n3 = rec[RF_N3 * TT + t];
-                const float4 pl = rec[RF_PL * TT + t];
-                const float4 l1 = rec[RF_N1L * TT + t], l2 = rec[RF_N2L * TT + t], l3 = rec[RF_N3L * TT + t];
-                const float4 ll = rec[RF_PLL * TT + t];
-                const float c1 = dot_f_df(ax, ay, az, {{n1.x, l1.x}, {n1.y, l1.y}, {n1.z, l1.z}});
-                const float c2 = dot_f_df(ax, ay, az, {{n2.x, l2.x}, {n2.y, l2.y}, {n2.z, l2.z}});
-                const float c3 = dot_f_df(ax, ay, az, {{n3.x, l3.x}, {n3.y, l3.y}, {n3.z, l3.z}});
-                const float cN = dot_f_df(ax, ay, az, {{pl.x, ll.x}, {pl.y, ll.y}, {pl.z, ll.z}});
-                st.s0[threadIdx.x] = make_float4(cp.x, cp.y, cp.z, n1.w);
-                st.s1[threadIdx.x] = make_float4(cp2.x, cp2.y, cp2.z, pl.w);
-                st.s2[threadIdx.x] = make_float4(n1.x, n1.y, n1.z, c1);
-                st.s3[threadIdx.x] = make_float4(n2.x, n2.y, n2.z, c2);
-                st.s4[threadIdx.x] = make_float4(n3.x, n3.y, n3.z, c3);
-                st.s5[threadIdx.x] = make_float4(pl.x, pl.y, pl.z, cN);
-                // S-hat - a from the pair S-hat (exact differences, then one rounding)
-                const df dsx = df_add(two_sum(cp.x, -ax), df_make(l1.w));
-                const df dsy = df_add(two_sum(cp.y, -ay), df_make(l2.w));
-                const df dsz = df_add(two_sum(cp.z, -az), df_make(l3.w));
-                st.s6[threadIdx.x] = make_float4(__fadd_rn(dsx.hi, dsx.lo), __fadd_rn(dsy.hi, dsy.lo),
-                                                 __fadd_rn(dsz.hi, dsz.lo), __uint_as_float(t));
+                stage_triangle(rec, TT, t, ax, ay, az, st, threadIdx.x);
             }
         }
         __syncthreads();
@@ -235,7 +176,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             // lane-parallel cull of 32 triangles against this warp's cone
             bool keep = false;
             const int jj = gbase + lane;
-            if (jj < n && __float_as_uint(st.s6[jj].w) != 0xffffffffu) {
+            if (jj < n && __float_as_uint(st.s6[jj].w) != STAGE_EMPTY) {
                 const float4 a = st.s0[jj];
                 const float4 b = st.s1[jj];
                 keep = cap_hits_cone(make_float3(a.x, a.y, a.z), 1.0f - 0.5f * b.y, b.x, make_float3(wax, way, waz),
@@ -266,9 +207,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 for (int p = 0; p < PPT; ++p) {
                     // G - S-hat = (G - a) - (S-hat - a): both differences are at most the tile
                     // radius, so their rounding costs ~1e-9 rad where the miter matters
-                    const float mx = dgx[p] - e.x, my = dgy[p] - e.y, mz = dgz[p] - e.z;
-                    const float q = fmaf(mx, mx, fmaf(my, my, mz * mz));
-                    g4[p] = ((b.y - q) + eg[p]) * b.z;
+                    g4[p] = miter_distance(dgx[p], dgy[p], dgz[p], e, b, eg[p]);
                     p4[p] = pv[p] && g4[p] > -h[p];
                     if (STATS) cnt_alg += p4[p];
                     any4 |= p4[p];
@@ -279,9 +218,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 bool frag[PPT], anyf = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    g1[p] = fmaf(dgx[p], n1.x, fmaf(dgy[p], n1.y, fmaf(dgz[p], n1.z, n1.w)));
-                    g2[p] = fmaf(dgx[p], n2.x, fmaf(dgy[p], n2.y, fmaf(dgz[p], n2.z, n2.w)));
-                    g3[p] = fmaf(dgx[p], n3.x, fmaf(dgy[p], n3.y, fmaf(dgz[p], n3.z, n3.w)));
+                    g1[p] = plane_distance(dgx[p], dgy[p], dgz[p], n1);
+                    g2[p] = plane_distance(dgx[p], dgy[p], dgz[p], n2);
+                    g3[p] = plane_distance(dgx[p], dgy[p], dgz[p], n3);
                     gm[p] = fminf(fminf(g1[p], g2[p]), fminf(g3[p], g4[p]));
                     frag[p] = p4[p] && gm[p] > -h[p];
                     anyf |= frag[p];
@@ -293,19 +232,13 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     // predicated: every lane computes, non-fragments add nothing
-                    const float D = fmaf(dgx[p], pl.x, fmaf(dgy[p], pl.y, fmaf(dgz[p], pl.z, pl.w)));
+                    const float D = plane_distance(dgx[p], dgy[p], dgz[p], pl);
                     const float r = __fdividef(b.w, D);
                     const bool f = frag[p] && r > 0.0f && r < INFINITY;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
                     acc[p] = min(acc[p] + (f ? __float2uint_rn(m * 16777216.0f) : 0u), 16777216u);
                     // centre-inside: all three edge distances >= 0, exact zeros by the tie rule
-                    const float g3m = fminf(fminf(g1[p], g2[p]), g3[p]);
-                    bool in = g3m > 0.0f;
-                    if (g3m == 0.0f)
-                        in = (g1[p] > 0.0f || (g1[p] == 0.0f && (ties & 1u))) &&
-                             (g2[p] > 0.0f || (g2[p] == 0.0f && (ties & 2u))) &&
-                             (g3[p] > 0.0f || (g3[p] == 0.0f && (ties & 4u)));
-                    in = in && f;
+                    const bool in = f && centre_inside(g1[p], g2[p], g3[p], ties);
                     const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
                     key[p] = in && k < key[p] ? k : key[p];
                     if (STATS) cnt_in[p] += in;

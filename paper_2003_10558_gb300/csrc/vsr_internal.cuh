@@ -202,3 +202,45 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
                          int* status, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Differentiable path (grad.cu, map.cu).
+// Gradient of the set-up records, field-major [GF_COUNT][T] float4:
+enum {
+    GF_N1 = 0,   // d/d n_AB (xyz), 0
+    GF_N2 = 1,   // d/d n_BC
+    GF_N3 = 2,   // d/d n_CA
+    GF_CAP = 3,  // d/d S-hat (xyz), d/d cos rho
+    GF_PL = 4,   // d/d N-hat (xyz), d/d colour
+    GF_D = 5,    // d/d (A'.N-hat), 0, 0, 0
+    GF_COUNT = 6
+};
+struct FragArgs {
+    const float4* map;
+    int W, H;
+    const Cone* tiles;
+    const float4* rec;
+    int T;
+    const uint32_t* offsets;  // tile bins
+    const uint32_t* ids;
+    uint32_t cap;
+    const float* colors;      // per triangle, NULL = 1
+    uint32_t* counts;         // W*H fragments per pixel (count pass)
+    const uint32_t* foff;     // W*H + 1 exclusive scan of counts
+    float4* frags;            // fragment records (r, t, m^f, shade)
+    uint32_t fcap;
+    float* image;
+    float* cov;
+    uint32_t* out_id;
+    float* out_depth;
+    int* status;
+};
+vsr_status launch_frag_count(const FragArgs& a, cudaStream_t st);
+vsr_status launch_frag_fill(const FragArgs& a, cudaStream_t st);
+vsr_status launch_frag_backward(const FragArgs& a, const uint32_t* id, const float* dimage, const float* dcov,
+                                const float* ddepth, float4* grad, float4* dmap, cudaStream_t st);
+vsr_status launch_setup_backward(const float* tris, int T, const float cam[12], const float4* rec, const float4* grad,
+                                 float* dtris, float* dcolors, cudaStream_t st);
+size_t map_backward_partials(int W, int H);
+vsr_status launch_map_backward(int W, int H, int aov, float k, float l, float s, float omega_deg,
+                               const float4* dmap, float* partials, double* dlens, cudaStream_t st);

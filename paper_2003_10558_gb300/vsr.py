@@ -34,6 +34,7 @@ EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_up
            "vsr_batch_config", "vsr_batch_free", "vsr_serve_create", "vsr_serve_add_scene", "vsr_serve_submit",
            "vsr_serve_poll", "vsr_serve_wait", "vsr_serve_cancel", "vsr_serve_stats_get", "vsr_serve_now",
            "vsr_serve_destroy",
+           "vsr_frags_create", "vsr_frags_free", "vsr_raster_shaded", "vsr_raster_backward",
            "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
 
 
@@ -122,6 +123,10 @@ def load(path: str = LIB_PATH):
             "vsr_serve_now": ([], ctypes.c_double),
             "vsr_serve_destroy": ([vp], i32),
             "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+            "vsr_frags_create": ([P(vp)], i32),
+            "vsr_frags_free": ([vp], None),
+            "vsr_raster_shaded": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+            "vsr_raster_backward": ([vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
             "vsr_status_str": ([i32], ctypes.c_char_p),
             "vsr_last_device_status": ([], i32),
             "vsr_version": ([], ctypes.c_char_p),
@@ -459,3 +464,158 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Differentiable rendering: the shaded image I = front-to-back merge of
+# c_t |N-hat_t . G| and its hand-written adjoint (vsr_raster_shaded /
+# vsr_raster_backward).
+
+class Frags:
+    """Fragment lists of the last shaded forward and the backward workspace."""
+
+    def __init__(self):
+        self.h = ctypes.c_void_p()
+        check(load().vsr_frags_create(ctypes.byref(self.h)), "vsr_frags_create")
+
+    def free(self):
+        if self.h:
+            load().vsr_frags_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def raster_shaded(m: Map, sc: Scene, frags: Frags, colors=None, out=None, stream=None):
+    """Shaded forward: dict of CUDA tensors image, cov, depth [H, W] float32
+    and id (int32 view of uint32).  colors: CUDA float32 [T] or None (all 1)."""
+    import torch
+    H, W = m.shape
+    dev = torch.device("cuda")
+    if out is None:
+        out = {"image": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "cov": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "id": torch.empty((H, W), dtype=torch.int32, device=dev)}
+    if colors is not None:
+        if not (colors.is_cuda and colors.dtype == torch.float32 and colors.numel() == sc.T):
+            raise ValueError("colors must be a CUDA float32 tensor with one value per triangle")
+        colors = colors.contiguous()
+    check(load().vsr_raster_shaded(m.h, sc.h, _dptr(colors), frags.h, _dptr(out.get("image")), _dptr(out.get("cov")),
+                                   _dptr(out.get("id")), _dptr(out.get("depth")), _stream_ptr(stream)),
+          "vsr_raster_shaded")
+    return out
+
+
+def raster_backward(m: Map, sc: Scene, frags: Frags, tris, colors=None, id=None, dimage=None, dcov=None,
+                    ddepth=None, want=("tris", "colors", "lens"), stream=None):
+    """Adjoint of the last raster_shaded of (m, sc) into frags: returns dict
+    with dtris [T, 3, 3], dcolors [T] (float32 CUDA) and dlens (float64 CUDA
+    [4] = d/d(k, l, s, Omega in degrees)), as requested by `want`."""
+    import torch
+    T = sc.T
+    dev = torch.device("cuda")
+
+    def c(t):
+        return None if t is None else t.contiguous()
+
+    dimage, dcov, ddepth, colors, tris = c(dimage), c(dcov), c(ddepth), c(colors), c(tris)
+    out = {}
+    if "tris" in want:
+        out["dtris"] = torch.empty((T, 3, 3), dtype=torch.float32, device=dev)
+    if "colors" in want:
+        out["dcolors"] = torch.empty((T,), dtype=torch.float32, device=dev)
+    if "lens" in want:
+        out["dlens"] = torch.empty((4,), dtype=torch.float64, device=dev)
+    check(load().vsr_raster_backward(m.h, sc.h, _dptr(tris), _dptr(colors), frags.h, _dptr(id), _dptr(dimage),
+                                     _dptr(dcov), _dptr(ddepth), _dptr(out.get("dtris")), _dptr(out.get("dcolors")),
+                                     _dptr(out.get("dlens")), _stream_ptr(stream)), "vsr_raster_backward")
+    return out
+
+
+class ShadedRenderer:
+    """Device state of differentiable rendering at one resolution: the map
+    (regenerated for each lens), the scene set-up and the fragment lists."""
+
+    def __init__(self, W, H, aov=AOV_HORIZONTAL, cam=None):
+        self.W, self.H, self.aov = int(W), int(H), int(aov)
+        self.cam = [0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1] if cam is None else list(np.asarray(cam).ravel())
+        self.map = None
+        self.scene = Scene()
+        self.frags = Frags()
+        self.generation = 0  # forwards run so far; a backward must belong to the latest
+
+    def set_lens(self, k, l, s, omega_deg, stream=None):
+        if self.map is None:
+            self.map = Map(self.W, self.H, k, l, s, omega_deg, self.aov, stream=stream)
+        else:
+            self.map.update(self.W, self.H, k, l, s, omega_deg, self.aov, stream=stream)
+        p = self.map.params()
+        return (p["k"], p["l"], p["s"], p["omega_deg"])
+
+
+def _autograd_function():
+    import torch
+
+    class RenderShaded(torch.autograd.Function):
+        """(tris [T,3,3] f32 CUDA, colors [T] f32 CUDA, lens [4] f64 (k, l, s,
+        Omega deg), renderer) -> (image, cov, depth, id).  Backward through
+        vsr_raster_backward; a lens parameter clamped by the limits gets a
+        zero gradient."""
+
+        @staticmethod
+        def forward(ctx, tris, colors, lens, renderer):
+            lv = [float(x) for x in lens.detach().cpu().double()]
+            eff = renderer.set_lens(*lv)
+            tris_c = tris.detach().contiguous()
+            col_c = colors.detach().contiguous()
+            renderer.scene.update(tris_c, renderer.cam)
+            out = raster_shaded(renderer.map, renderer.scene, renderer.frags, col_c)
+            renderer.generation += 1
+            ctx.generation = renderer.generation
+            ctx.renderer = renderer
+            ctx.open = [abs(e - v) <= 1e-6 * max(1.0, abs(v)) for e, v in zip(eff, lv)]
+            ctx.lens_meta = (lens.dtype, lens.device)
+            ctx.save_for_backward(tris_c, col_c, out["id"])
+            ctx.mark_non_differentiable(out["id"])
+            return out["image"], out["cov"], out["depth"], out["id"]
+
+        @staticmethod
+        def backward(ctx, dimage, dcov, ddepth, did):
+            tris, colors, ids = ctx.saved_tensors
+            r = ctx.renderer
+            if ctx.generation != r.generation:
+                raise VsrError(-1, "backward of a shaded render whose renderer has run another forward since")
+            want = []
+            if ctx.needs_input_grad[0]:
+                want.append("tris")
+            if ctx.needs_input_grad[1]:
+                want.append("colors")
+            if ctx.needs_input_grad[2]:
+                want.append("lens")
+            g = raster_backward(r.map, r.scene, r.frags, tris, colors, ids, dimage, dcov, ddepth, want=tuple(want))
+            dl = None
+            if "dlens" in g:
+                dl = g["dlens"].to(device=ctx.lens_meta[1], dtype=ctx.lens_meta[0])
+                dl = dl * torch.tensor([1.0 if o else 0.0 for o in ctx.open], dtype=dl.dtype, device=dl.device)
+            return g.get("dtris"), g.get("dcolors"), dl, None
+
+    return RenderShaded
+
+
+_render_fn = None
+
+
+def render_shaded(tris, colors, lens, renderer: ShadedRenderer):
+    """Differentiable render: (image, cov, depth, id) with gradients to tris,
+    colors and lens (a float64 tensor [4] = k, l, s, Omega in degrees).
+    One frame per renderer at a time: run backward before the renderer's
+    next forward (a stale backward raises VsrError)."""
+    global _render_fn
+    if _render_fn is None:
+        _render_fn = _autograd_function()
+    return _render_fn.apply(tris, colors, lens, renderer)
