@@ -75,8 +75,9 @@ def workload():
     return lens, tris, cam
 
 
-RASTER_SOURCES = ("paper_2003_10558_gb300/csrc/raster.cu", "paper_2003_10558_gb300/csrc/df.cuh",
-                  "paper_2003_10558_gb300/csrc/vsr_internal.cuh")
+RASTER_SOURCES = ("paper_2003_10558_gb300/csrc/raster.cu", "paper_2003_10558_gb300/csrc/stage.cuh",
+                  "paper_2003_10558_gb300/csrc/df.cuh", "paper_2003_10558_gb300/csrc/vsr_internal.cuh")
+RASTER_PROFILE = "raster_items_kernel_1080p_single_view.md"
 
 
 def raster_traffic():
@@ -85,7 +86,7 @@ def raster_traffic():
     import hashlib
     import re
     try:
-        with open(os.path.join(ROOT, "profiles", "raster_kernel_1080p_single_view.md")) as f:
+        with open(os.path.join(ROOT, "profiles", RASTER_PROFILE)) as f:
             txt = f.read()
         h = hashlib.sha256()
         for p in RASTER_SOURCES:

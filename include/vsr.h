@@ -9,7 +9,7 @@
  * great-circle planes OAB, OBC, OCA (Sec. 1.1) plus the miter cap of its
  * smallest enclosing circle (Sec. 1.1.2), coverage uses the analytic
  * global-delta step (Sec. 1.1.1), depth is the ray-plane distance (Sec.
- * 1.1.5) and fragments merge front to back (Sec. 1.3).
+ * 1.1.4) and fragments merge front to back (Sec. 1.4).
  *
  * Conventions shared by every entry point:
  *   - All device pointers are CUDA global-memory pointers on the current
@@ -95,7 +95,7 @@ vsr_status vsr_make_map_ex(const vsr_map_params* p, void* stream, vsr_map* out);
  * array in DEVICE memory (copied; the caller keeps ownership).  Directions
  * must be unit length where delta > 0; delta <= 0 marks an invalid pixel.
  * Tile cones are computed from the data.  Lets a user rasterize into a map
- * made elsewhere (the paper's "perspective pixel-shader pass", Sec. 1.1.6). */
+ * made elsewhere (the paper's "perspective pixel-shader pass", Sec. 1.1.5). */
 vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream, vsr_map* out);
 
 /* Regenerate an existing map in place for new parameters (reallocates
@@ -114,7 +114,7 @@ vsr_status vsr_map_download(vsr_map m, float* host_xyzd);
 void vsr_map_free(vsr_map m);
 
 /* ---- triangle set-up --------------------------------------------------------
- * vsr_setup: per-triangle set-up (Sec. 1.1, 1.1.2, 1.1.5) of T world-space
+ * vsr_setup: per-triangle set-up (Sec. 1.1, 1.1.2, 1.1.4) of T world-space
  * triangles `tris_dev` (device, FP32, [T][3 vertices][xyz]) seen by the
  * camera `cam` (host, 12 floats: eye O xyz, then the 3x3 world->camera
  * rotation M row-major; X' = M (X - O)).  Computes in FP32-pair arithmetic
@@ -140,7 +140,7 @@ int64_t vsr_scene_size(vsr_scene s);
 
 /* ---- rasterization ---------------------------------------------------------
  * vsr_raster: rasterize the scene into the map (Sec. 1.1.2 eq.
- * "rasterization", Sec. 1.1.1 gpstep/gbpxstep, Sec. 1.1.5 depth, Sec. 1.3
+ * "rasterization", Sec. 1.1.1 gpstep/gbpxstep, Sec. 1.1.4 depth, Sec. 1.4
  * merge).  For pixel direction G with global delta delta and triangle t:
  *   g_1..3 = G.n_i, g_4 = miter distance (G.S-hat - cos rho)/sin rho,
  *   fragment iff every g_i > -1/(2 delta) and depth r = (A'.N)/(G.N) > 0,
@@ -152,7 +152,7 @@ int64_t vsr_scene_size(vsr_scene s);
  *         0xFFFFFFFF if none;
  *   depth float: its r, +inf if none;
  *   cov   float: the front-to-back merged mask m^b = min(1, sum of m^f).
- * The merge of Sec. 1.3 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
+ * The merge of Sec. 1.4 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
  * to min(1, sum m^f), so the result does not depend on fragment order; it is
  * accumulated in 2^-24 fixed point and is bit-reproducible.
  * Scratch (tile bins) is held by the scene handle.  It is sized with one
@@ -225,7 +225,7 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64
 
 /* ---- batched multi-view rendering -------------------------------------------
  * A batch renders V views of one scene as one CUDA graph.  Each view is the
- * chain of vsr_setup (with the view's camera, Sec. 1.1, 1.1.2, 1.1.5), vsr_bin
+ * chain of vsr_setup (with the view's camera, Sec. 1.1, 1.1.2, 1.1.4), vsr_bin
  * and vsr_raster_tiles on a workspace of its own; the chains are spread over
  * S parallel streams inside the graph, so every view keeps its working set
  * in L2 while independent views overlap on the GPU, and no launch pays host
@@ -241,9 +241,15 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64
  * captures one graph for each S in {1, 2, 4, 8}, times their replays and
  * keeps the fastest (the autotuner); later calls with the same configuration
  * copy only the cameras (into pinned staging of the batch) and replay the
- * graph on `stream`.  Device memory per view: T x 228 B of set-up records
- * and bin caches plus its bins.  A batch must not render on two streams at
- * once. */
+ * graph on `stream`.  Each call waits for the previous frame of the batch to
+ * finish; a replay leaves every view's (tile, triangle) pair total in pinned
+ * memory, and a call that finds a view within 1/8 of its bin capacity
+ * re-sizes the bins and captures again (as for a new configuration).  A
+ * frame whose cameras outgrow the bins before that raises
+ * VSR_ERR_BIN_OVERFLOW in the device status with its outputs incomplete; the
+ * next call grows the bins.  Device memory per view: T x 228 B of set-up
+ * records and bin caches plus its bins.  A batch must not render on two
+ * streams at once. */
 typedef struct vsr_batch_s* vsr_batch;
 vsr_status vsr_batch_create(vsr_batch* out);
 vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const float* tris_dev, int64_t T,
@@ -314,10 +320,10 @@ vsr_status vsr_serve_destroy(vsr_server s);
 
 /* ---- differentiable rendering ----------------------------------------------
  * A shaded image and its hand-written adjoint.  The image is the
- * front-to-back mask merge of Sec. 1.3 applied to a shade pass
+ * front-to-back mask merge of Sec. 1.4 applied to a shade pass
  *   I = sum over the fragments of a pixel in ascending (r, t) of
  *       m^fc shade,  m^fc = min(m^f, 1 - m^b),  m^b += m^fc,
- *   shade_t = c_t |N-hat_t . G|   (N-hat the hard normal of Sec. 1.1.5),
+ *   shade_t = c_t |N-hat_t . G|   (N-hat the hard normal of Sec. 1.1.4),
  * with the fragments, m^f (gpstep on the four plane distances, Sec. 1.1.1
  * and 1.1.2) and depth of vsr_raster.  The merge depends on the order, so
  * the forward keeps every fragment of every pixel in a fragment-list handle
@@ -346,7 +352,7 @@ vsr_status vsr_raster_shaded(vsr_map m, vsr_scene s, const float* colors_dev, vs
 /* vsr_raster_backward: the adjoint of the last vsr_raster_shaded of (m, s)
  * into f.  Upstream gradients (device [H][W], NULL = 0): dimage_dev = dL/dI,
  * dcov_dev = dL/dcov, ddepth_dev = dL/ddepth (through r = (A'.N)/(G.N) of
- * the visible triangle, Sec. 1.1.5; the visibility switch itself has no
+ * the visible triangle, Sec. 1.1.4; the visibility switch itself has no
  * gradient).  id_dev: that forward's id output (needed with ddepth_dev).
  * tris_dev: the world triangles [T][3][3] of the scene's current set-up
  * (the camera is the scene's).  Outputs (device, overwritten, NULL to

@@ -8,8 +8,8 @@ The arithmetic lives in ``vsr_oracle.c`` (plain C, double precision, brute
 force over every pixel x triangle pair).  Each function there cites the part
 of the paper it follows: the Universal perspective 2D->3D map and its limits
 (Sec. 2), the global delta (Sec. 1.1.1), the edge-plane normals (Sec. 1.1), the
-miter / smallest circle (Sec. 1.1.2), the ray-plane depth (Sec. 1.1.5) and the
-front-to-back mask merge (Sec. 1.3).
+miter / smallest circle (Sec. 1.1.2), the ray-plane depth (Sec. 1.1.4) and the
+front-to-back mask merge (Sec. 1.4).
 
 Every function of this oracle is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force and textbook routines; none is marked

@@ -18,14 +18,14 @@
  *            fwidth of the map.
  *   setup    edge-plane normals ||A x B||, ||B x C||, ||C x A|| (Sec. 1.1),
  *            the miter / smallest-circle vector S (Sec. 1.1.2), the hard
- *            normal N and plane offset d = A.N (Sec. 1.1.5, depth equation).
+ *            normal N and plane offset d = A.N (Sec. 1.1.4, depth equation).
  *   raster   the four plane distances of the rasterization equation
  *            (Sec. 1.1.2, eq. "rasterization"), gpstep / gbpxstep (Sec. 1.1.1),
  *            bstep for the centre test, ray-plane depth r = (A.N)/(G.N), and
- *            the front-to-back mask merge of Sec. 1.3 (hidden surface
+ *            the front-to-back mask merge of Sec. 1.4 (hidden surface
  *            occlusion).
  *   shade    the same merge applied to a shade pass c_t |N-hat . G| (the
- *            differentiable workload's image, Sec. 1.3 and Sec. 1.1.5).
+ *            differentiable workload's image, Sec. 1.4 and Sec. 1.1.4).
  *   gradient the analytic adjoint of that image (and of coverage and depth)
  *            through the merge, gpstep / min, the plane distances, the
  *            set-up and the map; the map's lens tangents by complex step.
@@ -382,7 +382,7 @@ int orc_map(int W, int H, const double* p, int aov, double* out, int nthreads)
  *   O_p <= 0, else (O_s A + O_t B + O_p C)/(O_s+O_t+O_p);
  *   stored as S-hat, |S| = cos(rho) and sin(rho) = sqrt(1 - |S|^2).
  *
- * Plane (Sec. 1.1.5): N = (A'-B') x (C'-B'), d = A'.N.
+ * Plane (Sec. 1.1.4): N = (A'-B') x (C'-B'), d = A'.N.
  *
  * Culled (valid = 0): a vertex at the eye, A'.(B' x C') == 0, or a cap whose
  * sin(rho) rounds to zero (a triangle far below a pixel).
@@ -532,7 +532,7 @@ void orc_setup64(int64_t T, const double* tris, const double* cam, double* rec)
  *   r         = d / (G . N)                               (depth)
  *   centre-inside iff bstep on g_1..3 with the tie rule R11
  * Fragments are merged front to back in ascending (r, t)  (reading R15):
- *   m^fc = min(m^f, 1 - m^b);  m^b = m^b + m^fc          (Sec. 1.3)
+ *   m^fc = min(m^f, 1 - m^b);  m^b = m^b + m^fc          (Sec. 1.4)
  * cov = final m^b; id, depth = the first centre-inside fragment.
  */
 typedef struct {
@@ -687,7 +687,7 @@ int64_t orc_raster(int W, int H, const double* map, int64_t T, const double* rec
 
 /* ------------------------------------------------------------------------
  * Shaded image (the differentiable workload): per pixel the front-to-back
- * merge of Sec. 1.3 applied to a shade pass, as the paper applies it to its
+ * merge of Sec. 1.4 applied to a shade pass, as the paper applies it to its
  * depth, UV and normal passes:
  *   m^fc = min(m^f, 1 - m^b);  I = I + m^fc * shade_f;  m^b = m^b + m^fc
  * over the fragments in ascending (r, t), with shade_f = c_t |N-hat_t . G|

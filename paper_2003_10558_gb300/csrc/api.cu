@@ -795,12 +795,22 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     const size_t cam_bytes = sizeof(float) * 12 * (size_t)nviews;
 
     if (b->exec && key == b->key) {
-        // replay: new cameras only
+        // replay: new cameras only.  The previous replay (complete once its
+        // event has) left each view's pair total in pinned memory: a view
+        // within 1/8 of its bin capacity rebuilds the configuration with
+        // larger bins before this frame instead of overflowing in a later one.
         VSR_CUDA_TRY(cudaEventSynchronize(b->cams_done));
-        memcpy(b->cams_host, cams, cam_bytes);
-        VSR_CUDA_TRY(cudaGraphLaunch(b->exec, st));
-        VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
-        return VSR_OK;
+        bool grow = false;
+        for (int v = 0; v < nviews && !grow; ++v) {
+            const uint64_t last = b->h_total[v];
+            grow = last + last / 8 > b->views[v].cap;
+        }
+        if (!grow) {
+            memcpy(b->cams_host, cams, cam_bytes);
+            VSR_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+            VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
+            return VSR_OK;
+        }
     }
 
     // new configuration
@@ -844,7 +854,7 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     for (int v = 0; v < nviews; ++v) {
         BatchView& bv = b->views[v];
         const uint32_t total = b->h_total[v];
-        if (total > bv.cap || !bv.ids) {
+        if (total + total / 8 > bv.cap || !bv.ids) {
             cudaFree(bv.ids);
             bv.ids = nullptr;
             bv.cap = 0;
@@ -880,6 +890,10 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
         for (int v = 0; cst == VSR_OK && v < nviews; ++v) {
             cudaStream_t vs = b->streams[v % S];
             cst = batch_view_front(b, v, maps[v], tris_dev, T, vs);
+            const int tiles = maps[v]->tx * maps[v]->ty;
+            if (cst == VSR_OK && cudaMemcpyAsync(b->h_total + v, b->views[v].offsets + tiles, sizeof(uint32_t),
+                                                 cudaMemcpyDeviceToHost, vs) != cudaSuccess)
+                cst = VSR_ERR_CUDA;
             if (cst == VSR_OK)
                 cst = batch_view_back(b, v, maps[v], T, out_ptr(id_dev, v), out_ptr(depth_dev, v), out_ptr(cov_dev, v),
                                       vs);

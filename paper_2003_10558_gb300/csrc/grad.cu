@@ -2,8 +2,8 @@
 // front-to-back merge of a shade pass, and its hand-written adjoint.
 //
 // Forward (vsr_raster_shaded).  The image is the paper's front-to-back mask
-// merge (Sec. 1.3) applied to a shade pass, shade_t = c_t |N-hat_t . G|
-// (the hard normal of Sec. 1.1.5):
+// merge (Sec. 1.4) applied to a shade pass, shade_t = c_t |N-hat_t . G|
+// (the hard normal of Sec. 1.1.4):
 //   over the fragments of a pixel in ascending (r, t):
 //     m^fc = min(m^f, 1 - m^b);  I += m^fc shade;  m^b += m^fc
 // Unlike coverage, the image depends on the order, so every fragment is

@@ -14,9 +14,9 @@
 //            which keeps its accuracy for caps far below a pixel
 // then   fragment   iff min g_i > -1/(2 delta) and r > 0   (gbpxstep)
 //        m^f        = clamp(delta min g_i + 1/2, 0, 1)       (gpstep)
-//        r          = (A'.N-hat)/(G.N-hat)                    (Sec. 1.1.5)
+//        r          = (A'.N-hat)/(G.N-hat)                    (Sec. 1.1.4)
 //        centre-inside iff g_1..3 >= 0 (tie rule via the normal's sign)
-// and merges front to back (Sec. 1.3).  The merge
+// and merges front to back (Sec. 1.4).  The merge
 //   m^fc = min(m^f, 1 - m^b),  m^b = m^b + m^fc
 // equals m^b = min(1, sum m^f) by induction, independent of the order, so
 // each pixel keeps a saturating 2^-24 fixed-point sum and the 64-bit key

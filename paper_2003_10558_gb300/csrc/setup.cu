@@ -15,7 +15,7 @@
 //     S = midpoint of the side opposite the first non-positive O, else the
 //     circumcentre (O_s A + O_t B + O_p C)/(O_s + O_t + O_p);
 //     kept as S-hat, cos rho = |S|, sin rho, 2(1 - cos rho), 1/(2 sin rho).
-//   plane: N = (A'-B') x (C'-B') (Sec. 1.1.5), kept as N-hat and A'.N-hat.
+//   plane: N = (A'-B') x (C'-B') (Sec. 1.1.4), kept as N-hat and A'.N-hat.
 // Culled: a vertex at the eye, A'.(B' x C') = 0, or sin rho = 0.
 //
 // Everything is FP32 arithmetic; the pairs (Dekker / Knuth error-free

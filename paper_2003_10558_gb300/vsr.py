@@ -21,6 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvsr.so")
 
 VSR_OK = 0
+VSR_ERR_INVALID_ARG, VSR_ERR_OOM, VSR_ERR_CUDA, VSR_ERR_BIN_OVERFLOW = -1, -2, -3, -4
+VSR_ERR_FRAG_OVERFLOW, VSR_ERR_TIMEOUT, VSR_ERR_BUDGET, VSR_ERR_CANCELLED = -5, -6, -7, -8
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "tile bin overflow",
           -5: "fragment list overflow", -6: "device wait timed out", -7: "memory budget exceeded", -8: "cancelled"}
 NO_ID = 0xFFFFFFFF

@@ -92,3 +92,29 @@ def test_batch_view_against_oracle(vsr):
         rec = oracle.setup(tris_np, v["cam"])
         exp = oracle.raster(m32, rec, pixels=pix)
         compare(m32, rec, exp, _np(o), pixels=pix)
+
+
+def test_batch_grows_bins_when_cameras_move(vsr):
+    # pinhole views that first look away from the scene (empty bins), then
+    # from inside it: the first frame with the new cameras may outgrow the
+    # bins (reported in the device status), the next call re-sizes them and
+    # renders exactly what per-view vsr_raster renders
+    views = [dict(W=128, H=96, k=1.0, l=1.0, s=1.0, omega=90.0) for _ in range(3)]
+    tris = torch.from_numpy(scenes.random_triangles(20000, 1.0, 30.0, 0.03, seed=8)).cuda()
+    maps = [vsr.Map(v["W"], v["H"], v["k"], v["l"], v["s"], v["omega"]) for v in views]
+    b = vsr.Batch()
+    outs = _outs(views)
+    far = np.stack([scenes.camera((0.0, 0.0, 200.0 + i)) for i in range(3)])
+    near = np.stack([scenes.camera((0.2 * i, 0.0, 0.0)) for i in range(3)])
+    b.render(maps, tris, far, outs)
+    b.render(maps, tris, far, outs)
+    assert vsr.last_device_status() == 0
+    b.render(maps, tris, near, outs)
+    assert vsr.last_device_status() in (0, vsr.VSR_ERR_BIN_OVERFLOW)
+    b.render(maps, tris, near, outs)
+    assert vsr.last_device_status() == 0
+    for cam, m, o in zip(near, maps, outs):
+        ref = _np(vsr.raster(m, vsr.Scene(tris, cam)))
+        got = _np(o)
+        for k in ("id", "depth", "cov"):
+            assert np.array_equal(got[k].view(np.uint32), ref[k].view(np.uint32)), k

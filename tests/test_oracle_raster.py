@@ -1,4 +1,4 @@
-"""Pins of the oracle's rasterizer: the front-to-back merge (Sec. 1.3), the
+"""Pins of the oracle's rasterizer: the front-to-back merge (Sec. 1.4), the
 edge ramp (gpstep, Sec. 1.1.1) on hand-built stacks, visibility against a
 textbook 2D edge-function rasterizer (Pineda) for the pinhole map, exact
 watertightness of a closed mesh, the covered solid angle against the Van

@@ -1,6 +1,6 @@
 """Pins of the oracle's triangle set-up: edge-plane normals (Sec. 1.1), the
 miter smallest circle (Sec. 1.1.2) against a brute-force smallest enclosing
-cap, the plane depth (Sec. 1.1.5) against a closed form, and culling."""
+cap, the plane depth (Sec. 1.1.4) against a closed form, and culling."""
 import itertools
 
 import numpy as np
