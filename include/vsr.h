@@ -154,7 +154,7 @@ int64_t vsr_scene_size(vsr_scene s);
  *   cov   float: the front-to-back merged mask m^b = min(1, sum of m^f).
  * The merge of Sec. 1.4 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
  * to min(1, sum m^f), so the result does not depend on fragment order; it is
- * accumulated in 2^-24 fixed point and is bit-reproducible.
+ * accumulated in 2^-22 fixed point and is bit-reproducible.
  * Scratch (tile bins) is held by the scene handle.  It is sized with one
  * synchronisation of `stream` the first time and whenever the map's tile
  * count or the scene's T changes; otherwise no call synchronises: the bins
@@ -192,13 +192,13 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* dep
  * vsr_raster sizes the bins of a new map/scene pair).  The paper has no
  * counterpart; this is a service of the library.
  * The tile bins live in one fixed device array inside the library (about
- * 22 MB, held on every device that loads the library until the process
+ * 4.3 MB, held on every device that loads the library until the process
  * exits) instead of the scene's workspace: the call allocates nothing and
  * never synchronises.  Maps and scenes are made beforehand as usual.
- * Limits: at most 16384 tiles of 16x16 pixels (e.g. 2048 x 2048), at most
- * 262144 triangles (else VSR_ERR_INVALID_ARG), at most 2^20 (tile, triangle)
- * pairs (known only on the device: exceeding it writes VSR_ERR_BIN_OVERFLOW
- * to the status and leaves the outputs incomplete).
+ * Limits: at most 16384 tiles of 16x16 pixels (e.g. 2048 x 2048; else
+ * VSR_ERR_INVALID_ARG), at most 2^20 (tile, triangle) pairs (known only on
+ * the device: exceeding it writes VSR_ERR_BIN_OVERFLOW to the status and
+ * leaves the outputs incomplete).
  * status_dev: optional caller-owned device int32 that receives VSR_OK or the
  * device-side error of this call (cleared by the call).  With NULL the
  * status goes to a word of the library's array.

@@ -71,6 +71,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.cell_start, (size_t)IDX_CELLS_MAX + 1)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
     return VSR_OK;
 }
 
@@ -83,6 +84,7 @@ void map_release(vsr_map m)
     cudaFree(m->idx.cell_start);
     cudaFree(m->idx.sorted);
     cudaFree(m->idx.big);
+    cudaFree(m->idx.geom);
     m->map = nullptr;
     m->tiles = nullptr;
     m->idx = TileIndex{};
@@ -101,7 +103,8 @@ vsr_status check_params(const vsr_map_params* p)
 
 vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
-    vsr_status s = launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles, st);
+    vsr_status s = launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles,
+                              m->idx.geom, st);
     if (s != VSR_OK) return s;
     s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     m->gen = g_gen.fetch_add(1);
@@ -126,6 +129,26 @@ vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const flo
     return s;
 }
 
+// bin ids and the count pass's pair list, both of `want` entries (frees the
+// old ones, which waits for the launches still using them)
+vsr_status bins_realloc(vsr_scene sc, uint32_t want)
+{
+    cudaFree(sc->ids);
+    cudaFree(sc->pairs);
+    sc->ids = nullptr;
+    sc->pairs = nullptr;
+    sc->cap = 0;
+    vsr_status s;
+    if ((s = dalloc(&sc->ids, (size_t)want)) != VSR_OK) return s;
+    if ((s = dalloc(&sc->pairs, (size_t)want)) != VSR_OK) {
+        cudaFree(sc->ids);
+        sc->ids = nullptr;
+        return s;
+    }
+    sc->cap = want;
+    return VSR_OK;
+}
+
 vsr_status ensure_ws(vsr_scene sc, int ntiles)
 {
     if (ntiles <= sc->ws_tiles) return VSR_OK;
@@ -134,7 +157,7 @@ vsr_status ensure_ws(vsr_scene sc, int ntiles)
     sc->counts = sc->offsets = nullptr;
     sc->ws_tiles = 0;
     vsr_status s;
-    if ((s = dalloc(&sc->counts, 2 * (size_t)ntiles)) != VSR_OK) return s;  // counts | extra
+    if ((s = dalloc(&sc->counts, (size_t)ntiles + 1)) != VSR_OK) return s;  // counts | pair cursor
     if ((s = dalloc(&sc->offsets, (size_t)ntiles + 1)) != VSR_OK) return s;
     sc->ws_tiles = ntiles;
     sc->sized_shape = 0;
@@ -237,7 +260,7 @@ vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream
     if (s == VSR_OK && cudaMemcpyAsync(m->map, xyzd_dev, sizeof(float4) * (size_t)W * H, cudaMemcpyDeviceToDevice,
                                        st) != cudaSuccess)
         s = VSR_ERR_CUDA;
-    if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, st);
+    if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, m->idx.geom, st);
     if (s == VSR_OK) s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     if (s != VSR_OK) {
         map_release(m);
@@ -341,7 +364,7 @@ void vsr_scene_free(vsr_scene sc)
     cudaFree(sc->counts);
     cudaFree(sc->offsets);
     cudaFree(sc->ids);
-    cudaFree(sc->hits);
+    cudaFree(sc->pairs);
     raster_work_free(&sc->work);
     cudaFree(sc->tris_dev);
     cudaFree(sc->out_dev);
@@ -365,14 +388,6 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     const int T = (int)sc->T;
     sc->last_ntiles = ntiles;
     uint32_t* counts = sc->counts;
-    uint32_t* extra = sc->counts + sc->ws_tiles;
-    if (sc->T > sc->hits_T) {
-        cudaFree(sc->hits);
-        sc->hits = nullptr;
-        sc->hits_T = 0;
-        if ((s = dalloc(&sc->hits, (size_t)BIN_HIT_WORDS * (size_t)sc->T)) != VSR_OK) return s;
-        sc->hits_T = sc->T;
-    }
     // Bin capacity.  Sized synchronously the first time and whenever the
     // number of tiles or triangles changes; otherwise the pair total of the
     // previous binning (copied to pinned memory, read only once its event has
@@ -386,17 +401,15 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         if (last + last / 8 > sc->cap) {
             uint64_t want = last + last / 4 + 4096;
             if (want > 0xffffffffull) want = 0xffffffffull;
-            uint32_t* ids = nullptr;
-            if ((s = dalloc(&ids, (size_t)want)) != VSR_OK) return s;
-            cudaFree(sc->ids);  // waits for the launches that still read the old bins
-            sc->ids = ids;
-            sc->cap = (uint32_t)want;
+            if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
         }
     }
-    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    VSR_CUDA_TRY(cudaMemsetAsync(extra, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, extra, sc->hits, st)) != VSR_OK) return s;
-    if ((s = launch_scan(counts, extra, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
+    uint32_t* cursor = counts + ntiles;
+    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ((size_t)ntiles + 1), st));
+    uint2* pairs = sc->pairs;
+    const uint32_t pair_cap = sc->cap;
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st)) != VSR_OK) return s;
+    if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
     if (!sc->total_pending) {
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         VSR_CUDA_TRY(cudaEventRecord(sc->total_event, st));
@@ -407,17 +420,14 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->total_pending = false;
         const uint32_t total = *sc->h_total;
         if (total > sc->cap || sc->cap == 0) {
-            cudaFree(sc->ids);
-            sc->ids = nullptr;
-            sc->cap = 0;
             uint64_t want = (uint64_t)total + total / 4 + 4096;
             if (want > 0xffffffffull) want = 0xffffffffull;
-            if ((s = dalloc(&sc->ids, (size_t)want)) != VSR_OK) return s;
-            sc->cap = (uint32_t)want;
+            if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
+            pairs = nullptr;  // this frame's pair list went with the old buffer: search again
         }
         sc->sized_shape = shape;
     }
-    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->hits, sc->offsets, counts, extra, sc->ids, sc->cap,
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->offsets, counts, cursor, pairs, pair_cap, sc->ids, sc->cap,
                              scene_status(sc), st)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;
@@ -531,22 +541,18 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
 // are prepared beforehand; the call itself allocates nothing and never
 // synchronises.
 //
-// Limits: map of at most NA_TILES_MAX 16x16 tiles (e.g. 2048 x 2048), scene
-// of at most NA_T_MAX triangles, at most NA_PAIRS_MAX (tile, triangle) bin
-// pairs.  The array takes about 22 MB on every device that loads the
-// library, until the process exits.
+// Limits: map of at most NA_TILES_MAX 16x16 tiles (e.g. 2048 x 2048), at
+// most NA_PAIRS_MAX (tile, triangle) bin pairs.  The array takes about
+// 4.3 MB on every device that loads the library, until the process exits.
 namespace {
 
 constexpr uint32_t NA_TILES_MAX = 16384;
-constexpr uint32_t NA_T_MAX = 262144;
 constexpr uint32_t NA_PAIRS_MAX = 1u << 20;
 constexpr size_t NA_STATUS_WORDS = 64;  // word 0: status when the caller passes none
 constexpr size_t NA_COUNTS = NA_STATUS_WORDS;
-constexpr size_t NA_EXTRA = NA_COUNTS + NA_TILES_MAX;
-constexpr size_t NA_OFFSETS = NA_EXTRA + NA_TILES_MAX;
+constexpr size_t NA_OFFSETS = NA_COUNTS + NA_TILES_MAX;
 constexpr size_t NA_IDS = NA_OFFSETS + NA_TILES_MAX + 64;
-constexpr size_t NA_HITS = NA_IDS + NA_PAIRS_MAX;
-constexpr size_t NA_WORDS = NA_HITS + (size_t)BIN_HIT_WORDS * NA_T_MAX;
+constexpr size_t NA_WORDS = NA_IDS + NA_PAIRS_MAX;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 
@@ -582,7 +588,7 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
 {
     if (!m || !sc) return VSR_ERR_INVALID_ARG;
     const int ntiles = m->tx * m->ty;
-    if ((uint32_t)ntiles > NA_TILES_MAX || sc->T < 0 || (uint64_t)sc->T > NA_T_MAX) return VSR_ERR_INVALID_ARG;
+    if ((uint32_t)ntiles > NA_TILES_MAX || sc->T < 0) return VSR_ERR_INVALID_ARG;
     vsr_status err = VSR_OK;
     uint32_t* base = noalloc_scratch(&err);
     if (!base) return err;
@@ -590,19 +596,17 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
     const int T = (int)sc->T;
     int* status = status_dev ? (int*)status_dev : (int*)base;
     uint32_t* counts = base + NA_COUNTS;
-    uint32_t* extra = base + NA_EXTRA;
     uint32_t* offsets = base + NA_OFFSETS;
     uint32_t* ids = base + NA_IDS;
-    uint32_t* hits = base + NA_HITS;
     vsr_status s;
     // the array keeps the previous call's contents: clear what starts at zero
     VSR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    VSR_CUDA_TRY(cudaMemsetAsync(extra, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, extra, hits, st)) != VSR_OK) return s;
-    if ((s = launch_scan(counts, extra, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
-    if ((s = launch_bin_fill(sc->rec, T, m->idx, hits, offsets, counts, extra, ids, NA_PAIRS_MAX, status, st)) !=
-        VSR_OK)
+    // no pair list: the fill searches again
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, nullptr, nullptr, 0, st)) != VSR_OK) return s;
+    if ((s = launch_scan(counts, nullptr, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
+    if ((s = launch_bin_fill(sc->rec, T, m->idx, offsets, counts, nullptr, nullptr, 0, ids, NA_PAIRS_MAX, status,
+                             st)) != VSR_OK)
         return s;
     return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, T, offsets, ids, NA_PAIRS_MAX, id_dev, depth_dev,
                          cov_dev, nullptr, nullptr, nullptr, status, st);
@@ -628,11 +632,11 @@ constexpr int BATCH_STREAMS_MAX = 8;
 
 struct BatchView {
     float4* rec = nullptr;
-    uint32_t* hits = nullptr;
-    uint32_t* counts = nullptr;  // counts | extra
+    uint32_t* counts = nullptr;
     uint32_t* offsets = nullptr;
     uint32_t* partials = nullptr;
     uint32_t* ids = nullptr;
+    uint2* pairs = nullptr;  // the count pass's hits, cap entries
     uint32_t cap = 0;
     int tiles = 0;
     int64_t T = 0;
@@ -642,11 +646,11 @@ struct BatchView {
 void batch_view_free(BatchView& v)
 {
     cudaFree(v.rec);
-    cudaFree(v.hits);
     cudaFree(v.counts);
     cudaFree(v.offsets);
     cudaFree(v.partials);
     cudaFree(v.ids);
+    cudaFree(v.pairs);
     raster_work_free(&v.work);
     v = BatchView{};
 }
@@ -675,12 +679,9 @@ vsr_status batch_view_alloc(BatchView& v, int64_t T, int tiles)
     vsr_status s;
     if (T > v.T) {
         cudaFree(v.rec);
-        cudaFree(v.hits);
         v.rec = nullptr;
-        v.hits = nullptr;
         v.T = 0;
         if ((s = dalloc(&v.rec, (size_t)REC_F * (size_t)T)) != VSR_OK) return s;
-        if ((s = dalloc(&v.hits, (size_t)BIN_HIT_WORDS * (size_t)T)) != VSR_OK) return s;
         v.T = T;
     }
     if (tiles > v.tiles) {
@@ -690,7 +691,7 @@ vsr_status batch_view_alloc(BatchView& v, int64_t T, int tiles)
         raster_work_free(&v.work);
         v.counts = v.offsets = v.partials = nullptr;
         v.tiles = 0;
-        if ((s = dalloc(&v.counts, 2 * (size_t)tiles)) != VSR_OK) return s;
+        if ((s = dalloc(&v.counts, (size_t)tiles + 1)) != VSR_OK) return s;  // counts | pair cursor
         if ((s = dalloc(&v.offsets, (size_t)tiles + 1)) != VSR_OK) return s;
         if ((s = dalloc(&v.partials, 2 * (size_t)((tiles + 4095) / 4096) + 2)) != VSR_OK) return s;
         if ((s = raster_work_alloc(&v.work, (uint32_t)tiles)) != VSR_OK) return s;
@@ -699,29 +700,34 @@ vsr_status batch_view_alloc(BatchView& v, int64_t T, int tiles)
     return VSR_OK;
 }
 
-// set-up, count and scan of view v (before its bins are sized)
-vsr_status batch_view_front(vsr_batch b, int v, vsr_map m, const float* tris, int64_t T, cudaStream_t st)
+// set-up, count and scan of view v (before its bins are sized); with
+// use_pairs the count records its hits for the fill (not while the bins may
+// still be re-sized)
+vsr_status batch_view_front(vsr_batch b, int v, vsr_map m, const float* tris, int64_t T, bool use_pairs,
+                            cudaStream_t st)
 {
     BatchView& bv = b->views[v];
     const int tiles = m->tx * m->ty;
     vsr_status s;
     if ((s = launch_setup_views(tris, (int)T, b->cams_dev + 12 * v, 1, bv.rec, st)) != VSR_OK) return s;
-    VSR_CUDA_TRY(cudaMemsetAsync(bv.counts, 0, sizeof(uint32_t) * 2 * (size_t)bv.tiles, st));
-    if ((s = launch_bin_count(bv.rec, (int)T, m->idx, bv.counts, bv.counts + bv.tiles, bv.hits, st)) != VSR_OK)
+    VSR_CUDA_TRY(cudaMemsetAsync(bv.counts, 0, sizeof(uint32_t) * ((size_t)tiles + 1), st));
+    if ((s = launch_bin_count(bv.rec, (int)T, m->idx, bv.counts, bv.counts + tiles, use_pairs ? bv.pairs : nullptr,
+                              use_pairs ? bv.cap : 0u, st)) != VSR_OK)
         return s;
-    return tiles <= 65536 ? launch_scan(bv.counts, bv.counts + bv.tiles, tiles, nullptr, bv.offsets, st)
-                          : launch_scan_large(bv.counts, bv.counts + bv.tiles, tiles, bv.partials, bv.offsets, st);
+    return tiles <= 65536 ? launch_scan(bv.counts, nullptr, tiles, nullptr, bv.offsets, st)
+                          : launch_scan_large(bv.counts, nullptr, tiles, bv.partials, bv.offsets, st);
 }
 
 // fill and raster of view v
-vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, uint32_t* id, float* depth, float* cov,
-                           cudaStream_t st)
+vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pairs, uint32_t* id, float* depth,
+                           float* cov, cudaStream_t st)
 {
     BatchView& bv = b->views[v];
     const int tiles = m->tx * m->ty;
     vsr_status s;
-    if ((s = launch_bin_fill(bv.rec, (int)T, m->idx, bv.hits, bv.offsets, bv.counts, bv.counts + bv.tiles, bv.ids,
-                             bv.cap, status_word(), st)) != VSR_OK)
+    if ((s = launch_bin_fill(bv.rec, (int)T, m->idx, bv.offsets, bv.counts, bv.counts + tiles,
+                             use_pairs ? bv.pairs : nullptr, use_pairs ? bv.cap : 0u, bv.ids, bv.cap, status_word(),
+                             st)) != VSR_OK)
         return s;
     const RasterView rv{m->map, m->p.W, m->p.H, m->tiles, m->tx, bv.rec, (int)T, bv.offsets,
                         bv.ids, bv.cap, id, depth, cov};
@@ -845,7 +851,7 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
 
     // eager frame: fronts, one synchronisation to size every view's bins, backs
     for (int v = 0; v < nviews; ++v) {
-        if ((s = batch_view_front(b, v, maps[v], tris_dev, T, st)) != VSR_OK) return s;
+        if ((s = batch_view_front(b, v, maps[v], tris_dev, T, false, st)) != VSR_OK) return s;
         const int tiles = maps[v]->tx * maps[v]->ty;
         VSR_CUDA_TRY(cudaMemcpyAsync(b->h_total + v, b->views[v].offsets + tiles, sizeof(uint32_t),
                                      cudaMemcpyDeviceToHost, st));
@@ -856,17 +862,20 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
         const uint32_t total = b->h_total[v];
         if (total + total / 8 > bv.cap || !bv.ids) {
             cudaFree(bv.ids);
+            cudaFree(bv.pairs);
             bv.ids = nullptr;
+            bv.pairs = nullptr;
             bv.cap = 0;
             uint64_t want = (uint64_t)total + total / 4 + 4096;
             if (want > 0xffffffffull) want = 0xffffffffull;
             if ((s = dalloc(&bv.ids, (size_t)want)) != VSR_OK) return s;
+            if ((s = dalloc(&bv.pairs, (size_t)want)) != VSR_OK) return s;
             bv.cap = (uint32_t)want;
         }
     }
     for (int v = 0; v < nviews; ++v)
-        if ((s = batch_view_back(b, v, maps[v], T, out_ptr(id_dev, v), out_ptr(depth_dev, v), out_ptr(cov_dev, v),
-                                 st)) != VSR_OK)
+        if ((s = batch_view_back(b, v, maps[v], T, false, out_ptr(id_dev, v), out_ptr(depth_dev, v),
+                                 out_ptr(cov_dev, v), st)) != VSR_OK)
             return s;
     VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
 
@@ -889,14 +898,14 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) cst = VSR_ERR_CUDA;
         for (int v = 0; cst == VSR_OK && v < nviews; ++v) {
             cudaStream_t vs = b->streams[v % S];
-            cst = batch_view_front(b, v, maps[v], tris_dev, T, vs);
+            cst = batch_view_front(b, v, maps[v], tris_dev, T, true, vs);
             const int tiles = maps[v]->tx * maps[v]->ty;
             if (cst == VSR_OK && cudaMemcpyAsync(b->h_total + v, b->views[v].offsets + tiles, sizeof(uint32_t),
                                                  cudaMemcpyDeviceToHost, vs) != cudaSuccess)
                 cst = VSR_ERR_CUDA;
             if (cst == VSR_OK)
-                cst = batch_view_back(b, v, maps[v], T, out_ptr(id_dev, v), out_ptr(depth_dev, v), out_ptr(cov_dev, v),
-                                      vs);
+                cst = batch_view_back(b, v, maps[v], T, true, out_ptr(id_dev, v), out_ptr(depth_dev, v),
+                                      out_ptr(cov_dev, v), vs);
         }
         for (int i = 1; cst == VSR_OK && i < S; ++i)
             if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||

@@ -14,10 +14,12 @@
 // the cap centre are visited, so the work per triangle is a few dozen cone
 // tests whatever the map's size, and no tile is found twice.
 //
-// Per frame: count (one thread per triangle, atomic per-tile counters) ->
-// exclusive scan -> fill (atomic per-tile cursors).  The order of ids inside
-// a bin is not fixed; the raster kernel's result does not depend on it.
+// Per frame: count (atomic per-tile counters) -> exclusive scan -> fill
+// (atomic per-tile cursors).  The order of ids inside a bin is not fixed;
+// the raster kernel's result does not depend on it.
 #include <math.h>
+
+#include <atomic>
 
 #include "vsr_internal.cuh"
 
@@ -34,8 +36,6 @@ __device__ __forceinline__ int hist_bin(float a)
 
 __device__ __forceinline__ float hist_upper(int b) { return exp2f((float)(b + 1) / 3.0f - 17.0f); }
 
-__device__ __forceinline__ float cone_half_angle(const Cone& c) { return acosf(fmaxf(-1.0f, fminf(1.0f, c.c0.w))); }
-
 __device__ __forceinline__ int cell_row(float lat, const TileIndexHdr& h)
 {
     return min(h.nlat - 1, max(0, (int)floorf((lat + 0.5f * PI_F) / h.cell)));
@@ -48,22 +48,19 @@ __device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
     return c < 0 ? c + h.nlon : c;
 }
 
-__device__ __forceinline__ int home_cell(float3 a, const TileIndexHdr& h)
-{
-    float lat = asinf(fmaxf(-1.0f, fminf(1.0f, a.y)));
-    float lon = atan2f(a.x, a.z);
-    return cell_row(lat, h) * h.nlon + cell_col(lon, h);
-}
-
 // ---- tile index -------------------------------------------------------------
 //
 // One CTA of IDX_THREADS threads builds the whole index: the histogram of
 // tile half-angles and the grid plan, the per-cell counts (in shared
 // memory), their exclusive scan, and the cell-sorted cone copies.  A tile
 // index holds one entry per tile, so a single CTA keeps every phase a few
-// loads per thread and saves the launch gaps of separate kernels.
+// loads per thread and saves the launch gaps of separate kernels.  The map
+// kernels have already computed each tile's half-angle and axis latitude /
+// longitude (TileIndex::geom); every pass issues IDX_BATCH loads per thread
+// before using any, so a pass costs about one memory latency.
 
 constexpr int IDX_THREADS = 1024;
+constexpr int IDX_BATCH = 8;
 
 __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
 {
@@ -73,7 +70,13 @@ __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
     return e;
 }
 
-__global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __restrict__ tiles, int ntiles,
+__device__ __forceinline__ int home_cell_geom(const float4& g, const TileIndexHdr& h)
+{
+    return cell_row(g.y, h) * h.nlon + cell_col(g.z, h);
+}
+
+__global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __restrict__ tiles,
+                                                                 const float4* __restrict__ geom, int ntiles,
                                                                  TileIndexHdr* __restrict__ hdr,
                                                                  uint32_t* __restrict__ cell_start,
                                                                  Cone* __restrict__ sorted, Cone* __restrict__ big)
@@ -84,19 +87,41 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
     __shared__ TileIndexHdr s_h;
     __shared__ uint32_t s_warp[IDX_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float4 none = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
 
     for (int q = tid; q < IDX_CELLS_MAX; q += IDX_THREADS) s_cell[q] = 0u;
     if (tid < IDX_HIST) s_hist[tid] = 0u;
     if (tid == 0) s_nvalid = s_hmax = s_amax = s_nbig = 0u;
     __syncthreads();
 
-    // histogram of half-angles, widest ramp
-    for (int i = tid; i < ntiles; i += IDX_THREADS) {
-        const Cone c = tiles[i];
-        if (c.c1.z == 0.0f) continue;
-        atomicAdd(&s_hist[hist_bin(cone_half_angle(c))], 1u);
-        atomicAdd(&s_nvalid, 1u);
-        atomicMax(&s_hmax, __float_as_uint(c.c1.y));  // non-negative floats order as their bits
+    // histogram of half-angles, widest ramp; lanes with the same bin add
+    // once (__match_any_sync), the counters once per warp
+    unsigned my_valid = 0u, my_hmax = 0u;
+    for (int base0 = 0; base0 < ntiles; base0 += IDX_THREADS * IDX_BATCH) {
+        const int base = base0 + tid;
+        float4 g[IDX_BATCH];
+#pragma unroll
+        for (int q = 0; q < IDX_BATCH; ++q) {
+            const int i = base + q * IDX_THREADS;
+            g[q] = i < ntiles ? geom[i] : none;
+        }
+#pragma unroll
+        for (int q = 0; q < IDX_BATCH; ++q) {
+            const bool ok = g[q].w >= 0.0f;
+            const int bin = ok ? hist_bin(g[q].x) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(peers));
+            my_valid += ok;
+            if (ok) my_hmax = max(my_hmax, __float_as_uint(g[q].w));  // non-negative floats order as their bits
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        my_valid += __shfl_xor_sync(0xffffffffu, my_valid, o);
+        my_hmax = max(my_hmax, __shfl_xor_sync(0xffffffffu, my_hmax, o));
+    }
+    if (lane == 0) {
+        atomicAdd(&s_nvalid, my_valid);
+        atomicMax(&s_hmax, my_hmax);
     }
     __syncthreads();
 
@@ -121,17 +146,28 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
     const TileIndexHdr h = s_h;
 
     // per-cell counts of the small tiles; big tiles to their own list
-    for (int i = tid; i < ntiles; i += IDX_THREADS) {
-        const Cone c = tiles[i];
-        if (c.c1.z == 0.0f) continue;
-        const float a = cone_half_angle(c);
-        if (a > h.alpha_cut) {
-            big[atomicAdd(&s_nbig, 1u)] = index_entry(c, i);
-        } else {
-            atomicAdd(&s_cell[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u);
-            atomicMax(&s_amax, __float_as_uint(a));
+    unsigned my_amax = 0u;
+    for (int base = tid; base < ntiles; base += IDX_THREADS * IDX_BATCH) {
+        float4 g[IDX_BATCH];
+#pragma unroll
+        for (int q = 0; q < IDX_BATCH; ++q) {
+            const int i = base + q * IDX_THREADS;
+            g[q] = i < ntiles ? geom[i] : none;
+        }
+#pragma unroll
+        for (int q = 0; q < IDX_BATCH; ++q) {
+            if (g[q].w < 0.0f) continue;
+            const int i = base + q * IDX_THREADS;
+            if (g[q].x > h.alpha_cut) {
+                big[atomicAdd(&s_nbig, 1u)] = index_entry(tiles[i], i);
+            } else {
+                atomicAdd(&s_cell[home_cell_geom(g[q], h)], 1u);
+                my_amax = max(my_amax, __float_as_uint(g[q].x));
+            }
         }
     }
+    for (int o = 16; o; o >>= 1) my_amax = max(my_amax, __shfl_xor_sync(0xffffffffu, my_amax, o));
+    if (lane == 0) atomicMax(&s_amax, my_amax);
     __syncthreads();
 
     // exclusive scan of the cell counts (contiguous segment per thread)
@@ -166,10 +202,22 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
     __syncthreads();
 
     // cell-sorted copies of the small tiles' cones
-    for (int i = tid; i < ntiles; i += IDX_THREADS) {
-        const Cone c = tiles[i];
-        if (c.c1.z == 0.0f || cone_half_angle(c) > h.alpha_cut) continue;
-        sorted[atomicAdd(&s_cell[home_cell(make_float3(c.c0.x, c.c0.y, c.c0.z), h)], 1u)] = index_entry(c, i);
+    constexpr int CB = IDX_BATCH / 2;  // cones are 8 words: half the batch keeps them in registers
+    for (int base = tid; base < ntiles; base += IDX_THREADS * CB) {
+        float4 g[CB];
+        Cone c[CB];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+            const int i = base + q * IDX_THREADS;
+            g[q] = i < ntiles ? geom[i] : none;
+            if (i < ntiles) c[q] = tiles[i];
+        }
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+            if (g[q].w < 0.0f || g[q].x > h.alpha_cut) continue;
+            const int i = base + q * IDX_THREADS;
+            sorted[atomicAdd(&s_cell[home_cell_geom(g[q], h)], 1u)] = index_entry(c[q], i);
+        }
     }
     if (tid == 0) {
         TileIndexHdr o = h;
@@ -183,118 +231,203 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
 }
 
 // ---- per-triangle binning ---------------------------------------------------
+//
+// The candidate tiles of a triangle are the cones of its search window: the
+// index rows r0..r1 around the cap centre, each a contiguous range of the
+// cell-sorted cones (two ranges where the window wraps across longitude
+// +-pi), plus the big tiles.  One warp bins 32 triangles.  Phase 1, one lane
+// per triangle: the cap enlarged by the widest ramp and the window.  Phase
+// 2: the windows' (triangle, row range) pairs -- the big list cut into
+// chunks of BIN_BIG_CHUNK cones counts as further pairs -- are concatenated
+// in lane order and handed out one pair per lane per round, so the
+// dependent loads of the search run on all lanes at once instead of one
+// lane walking its whole window; each lane tests its range four cones at a
+// time.
+//
+// count: counts[tile] += 1 per hit (no value returned, so nothing waits),
+// and the hit is recorded as (tile, triangle) in the pair list -- staged per
+// warp in shared memory and appended with one atomic per warp and round.
+// fill: a map over the pair list that takes slot counts[tile] - 1 by atomic
+// decrement (one pair per thread, so the atomics' latency overlaps) and
+// writes ids[offsets[tile] + slot] = triangle.  When the list would overflow
+// (the first binning of a new shape, whose capacity is not known yet, or a
+// caller without a list) the fill searches again instead, with the same
+// decrement.  The counts return to zero either way; the order of ids inside
+// a bin is not fixed and the raster kernels' results do not depend on it.
 
-// One thread per triangle of the view v.
+constexpr int BIN_BIG_CHUNK = 16;
+constexpr int BIN_STAGE = 128;  // hits staged per warp and round
+
+// FILL: false = count + record, true = fill by searching again
 template <bool FILL>
 __global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids, uint32_t cap,
                                                    int* status)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const float4* __restrict__ rec = v.rec;
-    const TileIndexHdr* __restrict__ hdr = v.hdr;
-    const uint32_t* __restrict__ cell_start = v.cell_start;
-    const Cone* __restrict__ sorted = v.sorted;
-    const Cone* __restrict__ big = v.big;
-    uint32_t* __restrict__ counts = v.counts;
-    uint32_t* __restrict__ extra = v.extra;
-    uint32_t* __restrict__ hits = v.hits;
-    const uint32_t* __restrict__ offsets = v.offsets;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (FILL && v.pairs && *v.cursor <= v.pair_cap) return;  // the pair list is complete: bin_pairs_kernel fills
     const size_t TT = (size_t)T;
-    uint32_t* my_hits = hits + (size_t)t * BIN_HIT_WORDS;
-    uint32_t nhit = 0;
+    const TileIndexHdr* __restrict__ hp = v.hdr;
+    const int nlat = hp->nlat, nlon = hp->nlon;
+    const float cell = hp->cell;
+    const float amax = __uint_as_float(hp->alpha_small_max), hmax = __uint_as_float(hp->h_max);
+    const uint32_t nbig = hp->n_big;
+    const int bigpairs = (int)((nbig + BIN_BIG_CHUNK - 1) / BIN_BIG_CHUNK);
+    __shared__ uint2 s_hit[4][BIN_STAGE];
+    __shared__ uint32_t s_nhit[4];
+    if (!FILL && lane == 0) s_nhit[warp] = 0u;
+    __syncwarp();
 
-    auto put = [&](uint32_t tile, uint32_t pos) {
-        if (pos < cap && pos < offsets[tile + 1])
-            ids[pos] = (uint32_t)t;
+    // phase 1: this lane's triangle
+    float sx = 0.0f, sy = 0.0f, sz = 1.0f, cb = 1.0f, sb = 0.0f;
+    int r0 = 0, c0i = 0, ncol = 0, segs = 1, rowpairs = 0, npairs = 0;
+    if (t < T) {
+        const float4 q0 = v.rec[RF_CAP * TT + t];
+        const float4 q1 = v.rec[RF_CAP2 * TT + t];
+        if (q1.w != 0.0f) {
+            sx = q0.x;
+            sy = q0.y;
+            sz = q0.z;
+            // the cap enlarged once by the map's widest ramp (>= every tile's
+            // own): cos / sin of its radius beta, so each tile test is a few FMAs
+            cb = fmaxf(-1.0f, fminf(1.0f, q0.w - hmax * q1.x));
+            sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
+            // search radius: enlarged cap + largest small tile
+            const float gamma = acosf(cb) + amax + 1e-4f;
+            int r1 = nlat - 1;
+            ncol = nlon;
+            if (gamma < PI_F) {
+                const float lat = asinf(fmaxf(-1.0f, fminf(1.0f, sy)));
+                const float lon = atan2f(sx, sz);
+                r0 = cell_row(lat - gamma, *hp);
+                r1 = cell_row(lat + gamma, *hp);
+                if (fabsf(lat) + gamma < 0.5f * PI_F - 1e-3f) {
+                    // longitude half-width of a cap that holds no pole
+                    const float dl = asinf(fminf(1.0f, sinf(gamma) / cosf(lat))) + 1e-4f;
+                    c0i = (int)floorf((lon - dl + PI_F) / cell);
+                    const int c1i = (int)floorf((lon + dl + PI_F) / cell);
+                    ncol = min(nlon, c1i - c0i + 1);
+                    c0i %= nlon;
+                    if (c0i < 0) c0i += nlon;
+                }
+            }
+            segs = c0i + ncol <= nlon ? 1 : 2;
+            rowpairs = (r1 - r0 + 1) * segs;
+            npairs = rowpairs + bigpairs;
+        }
+    }
+    int incl = npairs;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int off = incl - npairs;
+
+    // phase 2: one (triangle, range) pair per lane and round
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        int q = 0;  // the last lane whose pairs start at or before p
+        for (int st = 16; st > 0; st >>= 1) {
+            const int oc = __shfl_sync(FULL, off, q + st);
+            if (oc <= p) q += st;
+        }
+        const int u = p - __shfl_sync(FULL, off, q);
+        const float tx = __shfl_sync(FULL, sx, q), ty = __shfl_sync(FULL, sy, q), tz = __shfl_sync(FULL, sz, q);
+        const float tcb = __shfl_sync(FULL, cb, q), tsb = __shfl_sync(FULL, sb, q);
+        const int tr0 = __shfl_sync(FULL, r0, q), tc0 = __shfl_sync(FULL, c0i, q);
+        const int tncol = __shfl_sync(FULL, ncol, q), tsegs = __shfl_sync(FULL, segs, q);
+        const int trows = __shfl_sync(FULL, rowpairs, q);
+        const uint32_t tt = (uint32_t)__shfl_sync(FULL, t, q);
+        uint32_t a = 0, b = 0;
+        const Cone* __restrict__ list = v.sorted;
+        if (p < total) {
+            if (u < trows) {
+                const int row = tr0 + u / tsegs, seg = u - (u / tsegs) * tsegs;
+                const uint32_t* __restrict__ rs = v.cell_start + (size_t)row * nlon;
+                if (tsegs == 1) {
+                    a = rs[tc0];
+                    b = rs[tc0 + tncol];
+                } else if (seg == 0) {  // the window wraps across longitude +-pi
+                    a = rs[tc0];
+                    b = rs[nlon];
+                } else {
+                    a = rs[0];
+                    b = rs[tc0 + tncol - nlon];
+                }
+            } else {
+                a = (uint32_t)(u - trows) * BIN_BIG_CHUNK;
+                b = min(nbig, a + BIN_BIG_CHUNK);
+                list = v.big;
+            }
+        }
+        for (uint32_t k0 = a; k0 < b; k0 += 4) {
+            Cone c[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k0 + e < b) c[e] = list[k0 + e];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (k0 + e >= b) break;
+                // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
+                const float cg = fmaf(tx, c[e].c0.x, fmaf(ty, c[e].c0.y, tz * c[e].c0.z));
+                if (!(tcb + c[e].c0.w <= 2e-6f || cg >= fmaf(c[e].c0.w, tcb, -c[e].c1.x * tsb) - 2e-6f)) continue;
+                const uint32_t tile = __float_as_uint(c[e].c1.z);
+                if (!FILL) {
+                    atomicAdd(&v.counts[tile], 1u);
+                    if (v.pairs) {
+                        const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
+                        if (j < BIN_STAGE) {
+                            s_hit[warp][j] = make_uint2(tile, tt);
+                        } else {  // a round with more hits than the stage holds: straight to the list
+                            const uint32_t g = atomicAdd(v.cursor, 1u);
+                            if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
+                        }
+                    }
+                } else {
+                    const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
+                    if (pos < cap && pos < v.offsets[tile + 1])
+                        ids[pos] = tt;
+                    else
+                        raise_status(status, VSR_ERR_BIN_OVERFLOW);
+                }
+            }
+        }
+        if (!FILL && v.pairs) {
+            // append this round's staged hits to the pair list
+            __syncwarp();
+            const uint32_t n = min(s_nhit[warp], (uint32_t)BIN_STAGE);
+            uint32_t g0 = 0;
+            if (lane == 0 && n) g0 = atomicAdd(v.cursor, n);
+            g0 = __shfl_sync(FULL, g0, 0);
+            for (uint32_t j = lane; j < n; j += 32)
+                if (g0 + j < v.pair_cap) v.pairs[g0 + j] = s_hit[warp][j];
+            __syncwarp();
+            if (lane == 0) s_nhit[warp] = 0u;
+            __syncwarp();
+        }
+    }
+}
+
+// The fill as a map over the pair list of the count pass (when it is
+// complete): slot = --counts[tile], ids[offsets[tile] + slot] = triangle.
+__global__ void __launch_bounds__(256) bin_pairs_kernel(const uint2* __restrict__ pairs,
+                                                         const uint32_t* __restrict__ cursor, uint32_t pair_cap,
+                                                         const uint32_t* __restrict__ offsets,
+                                                         uint32_t* __restrict__ counts, uint32_t* __restrict__ ids,
+                                                         uint32_t cap, int* status)
+{
+    const uint32_t n = *cursor;
+    if (n > pair_cap) return;  // incomplete: the search-based fill runs instead
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint2 e = pairs[p];
+        const uint32_t pos = offsets[e.x] + atomicSub(&counts[e.x], 1u) - 1u;
+        if (pos < cap && pos < offsets[e.x + 1])
+            ids[pos] = e.y;
         else
             raise_status(status, VSR_ERR_BIN_OVERFLOW);
-    };
-
-    if (FILL) {
-        // the count pass recorded (tile, slot) for up to BIN_HIT_CACHE hits
-        const uint32_t n = my_hits[0];
-        const uint32_t nc = min(n, (uint32_t)BIN_HIT_CACHE);
-        for (uint32_t q = 0; q < nc; ++q) {
-            const uint32_t tile = my_hits[1 + 2 * q];
-            put(tile, offsets[tile] + my_hits[2 + 2 * q]);
-        }
-        if (n <= BIN_HIT_CACHE) return;
     }
-
-    // count: the first BIN_HIT_CACHE hits take a slot in `counts`, the rest
-    // are counted in `extra`.  fill (only for triangles with more hits):
-    // search again, skip the cached hits, place the others after the slotted
-    // ones of their tile.
-    auto emit = [&](uint32_t tile) {
-        if (!FILL) {
-            if (nhit < BIN_HIT_CACHE) {
-                my_hits[1 + 2 * nhit] = tile;
-                my_hits[2 + 2 * nhit] = atomicAdd(&counts[tile], 1u);
-            } else {
-                atomicAdd(&extra[tile], 1u);
-            }
-        } else if (nhit >= BIN_HIT_CACHE) {
-            put(tile, offsets[tile] + counts[tile] + atomicSub(&extra[tile], 1u) - 1u);
-        }
-        ++nhit;
-    };
-
-    const float4 c0 = rec[RF_CAP * TT + t];
-    const float4 c1 = rec[RF_CAP2 * TT + t];
-    if (c1.w == 0.0f) {  // culled
-        if (!FILL) my_hits[0] = 0;
-        return;
-    }
-    const float3 S = make_float3(c0.x, c0.y, c0.z);
-    const float cr = c0.w, sr = c1.x;
-    const TileIndexHdr& h = *hdr;
-    const int nlat = h.nlat, nlon = h.nlon;
-    const float cell = h.cell;
-    const float amax = __uint_as_float(h.alpha_small_max), hmax = __uint_as_float(h.h_max);
-
-    // the cap enlarged once by the map's widest ramp (>= every tile's own):
-    // cos / sin of its radius beta, so each tile test is a few FMAs
-    const float cb = fmaxf(-1.0f, fminf(1.0f, cr - hmax * sr));
-    const float sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
-    auto scan_range = [&](const Cone* __restrict__ list, uint32_t k0, uint32_t k1) {
-        for (uint32_t k = k0; k < k1; ++k) {
-            const Cone c = list[k];
-            // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
-            const float cg = fmaf(S.x, c.c0.x, fmaf(S.y, c.c0.y, S.z * c.c0.z));
-            if (cb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, cb, -c.c1.x * sb) - 2e-6f) emit(__float_as_uint(c.c1.z));
-        }
-    };
-
-    // search radius: enlarged cap + largest small tile
-    const float gamma = acosf(cb) + amax + 1e-4f;
-    int r0 = 0, r1 = nlat - 1, c0i = 0, ncol = nlon;
-    if (gamma < PI_F) {
-        const float lat = asinf(fmaxf(-1.0f, fminf(1.0f, S.y)));
-        const float lon = atan2f(S.x, S.z);
-        r0 = cell_row(lat - gamma, h);
-        r1 = cell_row(lat + gamma, h);
-        if (fabsf(lat) + gamma < 0.5f * PI_F - 1e-3f) {
-            // longitude half-width of a cap that holds no pole
-            const float dl = asinf(fminf(1.0f, sinf(gamma) / cosf(lat))) + 1e-4f;
-            c0i = (int)floorf((lon - dl + PI_F) / cell);
-            const int c1i = (int)floorf((lon + dl + PI_F) / cell);
-            ncol = min(nlon, c1i - c0i + 1);
-            c0i %= nlon;
-            if (c0i < 0) c0i += nlon;
-        }
-    }
-    for (int r = r0; r <= r1; ++r) {
-        const uint32_t* row = cell_start + r * nlon;
-        if (c0i + ncol <= nlon) {
-            scan_range(sorted, row[c0i], row[c0i + ncol]);
-        } else {  // the window wraps across longitude +-pi
-            scan_range(sorted, row[c0i], row[nlon]);
-            scan_range(sorted, row[0], row[c0i + ncol - nlon]);
-        }
-    }
-    scan_range(big, 0, h.n_big);
-    if (!FILL) my_hits[0] = nhit;
 }
 
 // Exclusive scan of n counts (+ extra, when not NULL) into offsets[0..n] by
@@ -359,29 +492,44 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
     const size_t smem = sizeof(uint32_t) * IDX_CELLS_MAX;  // 128 KB of per-cell counts
-    VSR_CUDA_TRY(cudaFuncSetAttribute(idx_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    idx_build_kernel<<<1, IDX_THREADS, smem, st>>>(tiles, ntiles, idx.hdr, idx.cell_start, idx.sorted, idx.big);
+    // the shared-memory opt-in is a property of the kernel on a device: set
+    // once per device, not per map (a driver call on the launch path)
+    static std::atomic<bool> s_attr_set[256];
+    int dev = 0;
+    VSR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256 || !s_attr_set[dev].load(std::memory_order_acquire)) {
+        VSR_CUDA_TRY(cudaFuncSetAttribute(idx_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev >= 0 && dev < 256) s_attr_set[dev].store(true, std::memory_order_release);
+    }
+    idx_build_kernel<<<1, IDX_THREADS, smem, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.sorted,
+                                                   idx.big);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* extra, uint32_t* hits,
-                            cudaStream_t st)
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
+                            uint2* pairs, uint32_t pair_cap, cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, hits, nullptr};
+    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, nullptr, pairs, pair_cap, cursor};
     bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
-                           uint32_t* counts, uint32_t* extra, uint32_t* ids, uint32_t cap, int* status,
-                           cudaStream_t st)
+vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
+                           const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
+                           int* status, cudaStream_t st)
 {
     if (T == 0) return VSR_OK;
-    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, extra, const_cast<uint32_t*>(hits),
-                    offsets};
+    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, offsets, const_cast<uint2*>(pairs),
+                    pair_cap, const_cast<uint32_t*>(cursor)};
+    if (pairs) {
+        constexpr int BIN_PAIR_BLOCKS = 152 * 8;
+        bin_pairs_kernel<<<BIN_PAIR_BLOCKS, 256, 0, st>>>(pairs, cursor, pair_cap, offsets, counts, ids, cap,
+                                                          status);
+        VSR_CUDA_TRY(cudaGetLastError());
+    }
     bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;

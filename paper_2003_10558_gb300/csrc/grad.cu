@@ -194,14 +194,15 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
                 }
                 if (!__any_sync(0xffffffffu, any4)) continue;
                 const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
-                float g1[PPT], g2[PPT], g3[PPT], gm[PPT];
+                float g1[PPT], g2[PPT], g3[PPT], g3m[PPT], gm[PPT];
                 bool frag[PPT], anyf = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     g1[p] = plane_distance(dgx[p], dgy[p], dgz[p], n1);
                     g2[p] = plane_distance(dgx[p], dgy[p], dgz[p], n2);
                     g3[p] = plane_distance(dgx[p], dgy[p], dgz[p], n3);
-                    gm[p] = fminf(fminf(g1[p], g2[p]), fminf(g3[p], g4[p]));
+                    g3m[p] = fminf(fminf(g1[p], g2[p]), g3[p]);
+                    gm[p] = fminf(g3m[p], g4[p]);
                     frag[p] = p4[p] && gm[p] > -h[p];
                     anyf |= frag[p];
                 }
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
                             v.frags[fbase[p] + cnt[p]] =
                                 make_float4(r, __uint_as_float(t), m, scol[j] * fabsf(D));
                         const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | t;
-                        if (centre_inside(g1[p], g2[p], g3[p], ties) && k < key[p]) key[p] = k;
+                        if (centre_inside(g1[p], g2[p], g3[p], g3m[p], ties) && k < key[p]) key[p] = k;
                     }
                     ++cnt[p];
                 }

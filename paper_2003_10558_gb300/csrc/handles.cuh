@@ -44,9 +44,8 @@ struct vsr_scene_s {
     uint32_t* counts = nullptr;
     uint32_t* offsets = nullptr;
     uint32_t* ids = nullptr;
+    uint2* pairs = nullptr;  // (tile, triangle) of every hit of the count pass, cap entries
     uint32_t cap = 0;
-    uint32_t* hits = nullptr;  // per-triangle hit cache, BIN_HIT_WORDS x T_alloc
-    int64_t hits_T = 0;
     uint64_t sized_shape = 0;           // (tiles, T) the bins were last sized for
     uint32_t* h_total = nullptr;        // pinned: pair total of a recent binning
     cudaEvent_t total_event = nullptr;  // completion of that copy

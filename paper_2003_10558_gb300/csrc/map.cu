@@ -58,7 +58,7 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
 
 // Block-wide reduction of the tile cone from per-thread (valid, G, h).
 // Every thread of the block calls it; blockDim.x is a multiple of 32, <= 512.
-__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
+__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom)
 {
     __shared__ float red[4][16];
     const int nwarps = blockDim.x >> 5;
@@ -124,6 +124,10 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out)
         float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
         out->c0 = make_float4(ax, ay, az, ca);
         out->c1 = make_float4(sa, hh, n, 0.0f);
+        // the tile's half-angle and the latitude / longitude of its axis, for
+        // the tile index (the same functions the index would apply)
+        *geom = make_float4(acosf(fmaxf(-1.0f, fminf(1.0f, ca))), asinf(fmaxf(-1.0f, fminf(1.0f, ay))),
+                            atan2f(ax, az), n > 0.0f ? hh : -1.0f);
     }
 }
 
@@ -131,7 +135,7 @@ constexpr int HW = TILE + 2;
 constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation per thread
 
 __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, float4* __restrict__ map,
-                                                           Cone* __restrict__ tiles)
+                                                           Cone* __restrict__ tiles, float4* __restrict__ geom)
 {
     __shared__ float3 sv[HW * HW];
     __shared__ unsigned char sok[HW * HW];
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, 
     __syncthreads();
     if (threadIdx.x >= TILE_PIX) {
         // the halo-only threads take part in the cone reduction's barriers
-        reduce_cone(false, make_float3(0.0f, 0.0f, 0.0f), 0.0f, &tiles[ty * gridDim.x + tx]);
+        reduce_cone(false, make_float3(0.0f, 0.0f, 0.0f), 0.0f, &tiles[ty * gridDim.x + tx], &geom[ty * gridDim.x + tx]);
         return;
     }
     const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
@@ -194,12 +198,12 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, 
         }
         map[(size_t)j * W + i] = o;
     }
-    reduce_cone(valid, G, h, &tiles[ty * gridDim.x + tx]);
+    reduce_cone(valid, G, h, &tiles[ty * gridDim.x + tx], &geom[ty * gridDim.x + tx]);
 }
 
 // Cones of a map supplied by the caller.
 __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict__ map, int W, int H,
-                                                         Cone* __restrict__ tiles)
+                                                         Cone* __restrict__ tiles, float4* __restrict__ geom)
 {
     const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
     const int i = blockIdx.x * TILE + li, j = blockIdx.y * TILE + lj;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict
             h = 0.5f / o.w;
         }
     }
-    reduce_cone(valid, G, h, &tiles[blockIdx.y * gridDim.x + blockIdx.x]);
+    reduce_cone(valid, G, h, &tiles[blockIdx.y * gridDim.x + blockIdx.x], &geom[blockIdx.y * gridDim.x + blockIdx.x]);
 }
 
 }  // namespace
@@ -246,19 +250,19 @@ MapP make_params(int W, int H, int aov, float k, float l, float s, float omega_d
 }  // namespace
 
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      cudaStream_t st)
+                      float4* geom, cudaStream_t st)
 {
     const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, p, map, tiles);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, p, map, tiles, geom);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaStream_t st)
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st)
 {
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    cone_kernel<<<grid, TILE_PIX, 0, st>>>(map, W, H, tiles);
+    cone_kernel<<<grid, TILE_PIX, 0, st>>>(map, W, H, tiles, geom);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -19,7 +19,7 @@
 // and merges front to back (Sec. 1.4).  The merge
 //   m^fc = min(m^f, 1 - m^b),  m^b = m^b + m^fc
 // equals m^b = min(1, sum m^f) by induction, independent of the order, so
-// each pixel keeps a saturating 2^-24 fixed-point sum and the 64-bit key
+// each pixel keeps a saturating 2^-22 fixed-point sum and the 64-bit key
 // (bits(r) << 32 | t) of its nearest centre-inside triangle.
 //
 // Accuracy in FP32: every distance is re-centred on the tile's cone axis a,
@@ -48,7 +48,7 @@ static_assert(RT * PPT == TILE_PIX, "one CTA covers one tile");
 // is fenced by the barriers of the chunk loop).
 // Split tiles: a tile whose bin is longer than SPLIT_MAX triangles is
 // processed as several work items of at most SPLIT_MAX triangles each.  The
-// items of one tile add their coverage (2^-24 fixed point) and take the
+// items of one tile add their coverage (2^-22 fixed point) and take the
 // minimum of their visibility keys in the tile's accumulator slot with
 // atomics -- both are order-free, so the result is exactly that of one item
 // -- and the item that arrives last (atomic counter, nothing waits) writes
@@ -84,7 +84,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
     const Cone tc = tiles[tile];
     const float ax = tc.c0.x, ay = tc.c0.y, az = tc.c0.z;
 
-    float gx[PPT], gy[PPT], gz[PPT], dgx[PPT], dgy[PPT], dgz[PPT], delta[PPT], h[PPT], eg[PPT];
+    float gx[PPT], gy[PPT], gz[PPT], dgx[PPT], dgy[PPT], dgz[PPT], delta[PPT], h[PPT], lim[PPT], eg[PPT];
     bool pv[PPT], inimg[PPT];
     uint32_t acc[PPT];
     unsigned long long key[PPT];
@@ -101,6 +101,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         gz[p] = g.z;
         delta[p] = g.w;
         h[p] = pv[p] ? 0.5f / g.w : 0.0f;
+        lim[p] = pv[p] ? -h[p] : INFINITY;  // fragment iff min distance > lim
         eg[p] = pv[p] ? norm2_minus_one(g.x, g.y, g.z) : 0.0f;
         dgx[p] = g.x - ax;
         dgy[p] = g.y - ay;
@@ -158,6 +159,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
 
     for (uint32_t base = b0; base < b1; base += CHUNK) {
         const int n = (int)min((uint32_t)CHUNK, b1 - base);
+        // saturate once per chunk: at most CHUNK terms of <= COV_ONE each were added since
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) acc[p] = min(acc[p], COV_ONE);
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t t = ids[base + threadIdx.x];
@@ -202,27 +206,24 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 if (STATS) ++cnt_exec;
                 // miter distance, chord form
                 float g4[PPT];
-                bool p4[PPT], any4 = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     // G - S-hat = (G - a) - (S-hat - a): both differences are at most the tile
                     // radius, so their rounding costs ~1e-9 rad where the miter matters
                     g4[p] = miter_distance(dgx[p], dgy[p], dgz[p], e, b, eg[p]);
-                    p4[p] = pv[p] && g4[p] > -h[p];
-                    if (STATS) cnt_alg += p4[p];
-                    any4 |= p4[p];
+                    if (STATS) cnt_alg += g4[p] > lim[p];
                 }
-                if (!__any_sync(0xffffffffu, any4)) continue;
                 const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
-                float g1[PPT], g2[PPT], g3[PPT], gm[PPT];
+                float g1[PPT], g2[PPT], g3[PPT], g3m[PPT], gm[PPT];
                 bool frag[PPT], anyf = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     g1[p] = plane_distance(dgx[p], dgy[p], dgz[p], n1);
                     g2[p] = plane_distance(dgx[p], dgy[p], dgz[p], n2);
                     g3[p] = plane_distance(dgx[p], dgy[p], dgz[p], n3);
-                    gm[p] = fminf(fminf(g1[p], g2[p]), fminf(g3[p], g4[p]));
-                    frag[p] = p4[p] && gm[p] > -h[p];
+                    g3m[p] = fminf(fminf(g1[p], g2[p]), g3[p]);
+                    gm[p] = fminf(g3m[p], g4[p]);
+                    frag[p] = gm[p] > lim[p];  // gbpxstep on all four distances; never on invalid pixels
                     anyf |= frag[p];
                 }
                 if (!__any_sync(0xffffffffu, anyf)) continue;
@@ -236,9 +237,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                     const float r = __fdividef(b.w, D);
                     const bool f = frag[p] && r > 0.0f && r < INFINITY;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
-                    acc[p] = min(acc[p] + (f ? __float2uint_rn(m * 16777216.0f) : 0u), 16777216u);
+                    acc[p] += f ? cov_fixed(m) : 0u;
                     // centre-inside: all three edge distances >= 0, exact zeros by the tie rule
-                    const bool in = f && centre_inside(g1[p], g2[p], g3[p], ties);
+                    const bool in = f && centre_inside(g1[p], g2[p], g3[p], g3m[p], ties);
                     const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
                     key[p] = in && k < key[p] ? k : key[p];
                     if (STATS) cnt_in[p] += in;
@@ -246,6 +247,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             }
         }
     }
+
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) acc[p] = min(acc[p], COV_ONE);
 
     if (split_slot >= 0) {
         // merge into the tile's slot; the last item to arrive writes it out
@@ -266,7 +270,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         __threadfence();
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            acc[p] = (uint32_t)min(atomicExch(&sacc[lp0 + TILE * 4 * p], 0ull), 16777216ull);
+            acc[p] = (uint32_t)min(atomicExch(&sacc[lp0 + TILE * 4 * p], 0ull), (unsigned long long)COV_ONE);
             key[p] = atomicExch(&skey[lp0 + TILE * 4 * p], ~0ull);
         }
         if (threadIdx.x == 0) split.done[split_slot] = 0u;
@@ -279,7 +283,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         const bool hit = key[p] != ~0ull;
         if (out_id) out_id[o] = hit ? (uint32_t)(key[p] & 0xffffffffull) : 0xffffffffu;
         if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key[p] >> 32)) : INFINITY;
-        if (out_cov) out_cov[o] = (float)acc[p] * (1.0f / 16777216.0f);
+        if (out_cov) out_cov[o] = (float)acc[p] * (1.0f / (float)COV_ONE);
         if (STATS && n_inside) n_inside[o] = cnt_in[p];
     }
 }
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
 // themselves (the first item of a split tile); the further items of split
 // tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
 // return at once.
-__global__ void __launch_bounds__(RT, 7) raster_items_kernel(RasterView view, uint32_t n_tiles,
+__global__ void __launch_bounds__(RT, 8) raster_items_kernel(RasterView view, uint32_t n_tiles,
                                                               const uint32_t* __restrict__ nsplit_of,
                                                               const int32_t* __restrict__ split_slot,
                                                               const uint2* __restrict__ extra,

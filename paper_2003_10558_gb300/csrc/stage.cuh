@@ -83,10 +83,22 @@ __device__ __forceinline__ float plane_distance(float dgx, float dgy, float dgz,
     return fmaf(dgx, n.x, fmaf(dgy, n.y, fmaf(dgz, n.z, n.w)));
 }
 
-// Centre-inside test (bstep on g_1..3, exact zeros by the tie rule).
-__device__ __forceinline__ bool centre_inside(float g1, float g2, float g3, unsigned ties)
+// Coverage in 2^-22 fixed point.  m in [0, 1]: fma(m, 2^22, 2^23) lies in
+// [2^23, 2^24), where the float spacing is 1, so its single rounding leaves
+// round-to-nearest(m 2^22) in the low mantissa bits.  Sums of these terms
+// saturate at COV_ONE (coverage 1): min(a + b, C) composes over any grouping
+// of non-negative terms, so the result does not depend on how the terms were
+// split between CTAs.
+constexpr uint32_t COV_ONE = 1u << 22;
+__device__ __forceinline__ uint32_t cov_fixed(float m)
 {
-    const float g3m = fminf(fminf(g1, g2), g3);
+    return __float_as_uint(fmaf(m, 4194304.0f, 8388608.0f)) - 0x4B000000u;
+}
+
+// Centre-inside test (bstep on g_1..3, exact zeros by the tie rule);
+// g3m = min(g1, g2, g3).
+__device__ __forceinline__ bool centre_inside(float g1, float g2, float g3, float g3m, unsigned ties)
+{
     bool in = g3m > 0.0f;
     if (g3m == 0.0f)
         in = (g1 > 0.0f || (g1 == 0.0f && (ties & 1u))) && (g2 > 0.0f || (g2 == 0.0f && (ties & 2u))) &&

@@ -103,8 +103,8 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
 
 // Kernel launchers (defined in the .cu files, called by the host library).
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      cudaStream_t st);
-vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, cudaStream_t st);
+                      float4* geom, cudaStream_t st);
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
@@ -116,21 +116,22 @@ struct TileIndex {
     uint32_t* cell_start;  // IDX_CELLS_MAX + 1
     Cone* sorted;          // ntiles
     Cone* big;             // ntiles
+    float4* geom;          // ntiles: (alpha, latitude, longitude of the axis, h), h = -1 if the tile is empty;
+                           // written with the cones by the map kernels
 };
-// per-triangle hit cache between the count and fill passes of the binner:
-// word 0 = number of hits, then (tile, slot) for up to BIN_HIT_CACHE hits
-constexpr int BIN_HIT_CACHE = 8;
-constexpr int BIN_HIT_WORDS = 1 + 2 * BIN_HIT_CACHE;
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
-// binning of one frame: counts and extra zeroed by the caller ->
-// launch_bin_count -> launch_scan(counts, extra) -> launch_bin_fill
-vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* extra, uint32_t* hits,
-                            cudaStream_t st);
+// binning of one frame: counts and cursor zeroed by the caller ->
+// launch_bin_count (records (tile, triangle) into pairs[0, pair_cap)
+// and counts them in *cursor; pairs may be NULL) -> launch_scan(counts,
+// NULL) -> launch_bin_fill (a map over the pairs when *cursor <= pair_cap,
+// else a second search; pass the count pass's pairs / pair_cap, or NULL)
+vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
+                            uint2* pairs, uint32_t pair_cap, cudaStream_t st);
 vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
                        cudaStream_t st);
-vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* hits, const uint32_t* offsets,
-                           uint32_t* counts, uint32_t* extra, uint32_t* ids, uint32_t cap, int* status,
-                           cudaStream_t st);
+vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
+                           const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
+                           int* status, cudaStream_t st);
 // One view as the raster kernel sees it: its map, tile cones, set-up
 // records, bin offsets (indexed by the view's own tile number), bin ids and
 // outputs.
@@ -150,7 +151,7 @@ struct RasterView {
 };
 
 // One view as the binner sees it (tile index of the view's map, the view's
-// set-up records, its per-tile counters and offsets, its hit cache).
+// set-up records, its per-tile counters and offsets).
 struct BinView {
     const TileIndexHdr* hdr;
     const uint32_t* cell_start;
@@ -158,9 +159,10 @@ struct BinView {
     const Cone* big;
     const float4* rec;
     uint32_t* counts;
-    uint32_t* extra;
-    uint32_t* hits;
     const uint32_t* offsets;
+    uint2* pairs;       // (tile, triangle) of every hit, or NULL
+    uint32_t pair_cap;
+    uint32_t* cursor;   // hits recorded (may exceed pair_cap: the list is then incomplete)
 };
 
 // Work items of the raster: a tile whose bin is longer than split_max

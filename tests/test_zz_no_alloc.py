@@ -82,14 +82,29 @@ def test_noalloc_matches_raster_twice(vsr, workload):
         assert np.isinf(d[~hit]).all()
 
 
-def test_noalloc_rejects_oversized_scene(vsr):
-    m = vsr.Map(64, 64, 0.0, 1.0, 1.0, 180.0)
-    big = torch.from_numpy(scenes.random_triangles(262145, 1.0, 10.0, 0.01, seed=3)).cuda()
-    sc = vsr.Scene(big)
-    outs = _outputs(64, 64)
-    status = torch.zeros((1,), dtype=torch.int32, device="cuda")
-    assert _noalloc(vsr, m, sc, outs, status) == -1
+def test_noalloc_limits(vsr):
+    # more tiles than the array holds: refused on the host
     big_map = vsr.Map(4096, 2048, 0.0, 1.0, 1.0, 180.0)
     small = vsr.Scene(torch.from_numpy(scenes.random_triangles(10, 1.0, 10.0, 0.1, seed=4)).cuda())
+    status = torch.zeros((1,), dtype=torch.int32, device="cuda")
     outs = _outputs(2048, 4096)
     assert _noalloc(vsr, big_map, small, outs, status) == -1
+    # more (tile, triangle) pairs than the array holds: known only on the
+    # device, reported in the status word, no access outside the array
+    m = vsr.Map(64, 64, 0.0, 1.0, 1.0, 180.0)
+    many = vsr.Scene(torch.from_numpy(scenes.random_triangles(600000, 1.0, 10.0, 0.3, seed=3)).cuda())
+    outs = _outputs(64, 64)
+    status.fill_(0)
+    assert _noalloc(vsr, m, many, outs, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == vsr.VSR_ERR_BIN_OVERFLOW
+    # the array is usable again right after
+    lens, tris, _cam = scenes.tiny_scene()
+    tm = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    ts = vsr.Scene(torch.from_numpy(tris).cuda())
+    ref = vsr.raster(tm, ts)
+    outs = _outputs(lens["H"], lens["W"])
+    assert _noalloc(vsr, tm, ts, outs, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(outs[0].cpu().numpy(), ref["id"].cpu().numpy())
