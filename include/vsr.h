@@ -98,6 +98,54 @@ vsr_status vsr_make_map_ex(const vsr_map_params* p, void* stream, vsr_map* out);
  * made elsewhere (the paper's "perspective pixel-shader pass", Sec. 1.1.5). */
 vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream, vsr_map* out);
 
+/* Maps of other projections (Sec. 2.2) and lens distortion (Sec. 2.3).
+ * The rasterizer takes any direction map, so these feed the same raster,
+ * binning and differentiable path.  Pixel centres, AOV types and the
+ * global delta as for vsr_make_map; the delta uses neighbours on the same
+ * chart only (one-sided at a cube map's face borders).
+ *   VSR_MAP_UNIVERSAL    param = (k, l, s, omega_deg), limits applied
+ *   VSR_MAP_RECTILINEAR  param = (omega_deg): G = normalize(x, y, cot(Omega/2))
+ *                        (Sec. 2.2.1; omega < 180)
+ *   VSR_MAP_PANORAMA     param = (omega_h_deg, height): with
+ *                        f' = (Omega_h (f_s - 1/2), height (f_t - 1/2)),
+ *                        G = normalize(sin f'_x, f'_y, cos f'_x) (Sec. 2.2.2)
+ *   VSR_MAP_DOME         param = (compression_deg, tilt_deg, offset): with
+ *                        f' = (2 f_s - 1, 1 - 2 f_t), R = |f'|,
+ *                        theta = R (compression + 90 deg),
+ *                        G = normalize(f'_x sin(theta)/R, cos(theta),
+ *                        f'_y sin(theta)/R + offset) tilted about x; pixels
+ *                        with R > 1 are invalid (Sec. 2.2.3)
+ *   VSR_MAP_EQUIRECT     no param: f' = pi (2 f_s - 1, f_t),
+ *                        G = (sin f'_x sin f'_y, -cos f'_y, cos f'_x sin f'_y)
+ *                        (Sec. 2.2.4)
+ *   VSR_MAP_CUBE         no param: W = 6 H for square faces; face
+ *                        floor(6 f_s) rotates normalize(fract(6 f_s) - 1/2,
+ *                        f_t - 1/2, 1/2) to look along +x, -x, -z, +z, +y,
+ *                        -y (Sec. 2.2.7; face 3, absent from the paper's
+ *                        case list, is the front face along +z)
+ * distortion = (k1, k2, p1, p2, q1, q2), Brown-Conrady on the view
+ * coordinates of the Universal and rectilinear kinds (Sec. 2.3):
+ * r2 = x^2 + y^2, (x, y) <- (x, y)(1 + k1 r2 + k2 r2^2) + (x, y)(p1 x + p2 y)
+ * + (q1, q2) r2; zeros leave the map unchanged.
+ * vsr_raster_backward's lens gradient exists only for undistorted
+ * Universal maps. */
+typedef enum {
+    VSR_MAP_UNIVERSAL = 0,
+    VSR_MAP_RECTILINEAR = 1,
+    VSR_MAP_PANORAMA = 2,
+    VSR_MAP_DOME = 3,
+    VSR_MAP_EQUIRECT = 4,
+    VSR_MAP_CUBE = 5
+} vsr_map_kind;
+typedef struct {
+    int kind;  /* vsr_map_kind */
+    int W, H;
+    int aov;   /* vsr_aov: Universal and rectilinear */
+    float param[4];
+    float distortion[6];
+} vsr_map_spec;
+vsr_status vsr_make_map_spec(const vsr_map_spec* spec, void* stream, vsr_map* out);
+
 /* Regenerate an existing map in place for new parameters (reallocates
  * only when W or H change).  Same semantics as vsr_make_map_ex. */
 vsr_status vsr_map_update(vsr_map m, const vsr_map_params* p, void* stream);
@@ -359,7 +407,8 @@ vsr_status vsr_raster_shaded(vsr_map m, vsr_scene s, const float* colors_dev, vs
  * skip): dtris_dev [T][3][3] = dL/d(world vertices), dcolors_dev [T] =
  * dL/dc_t, dlens_dev (double [4]) = dL/d(k, l, s, Omega in degrees) of the
  * map at its effective parameters (after the limits; a map made by
- * vsr_map_from_device has no lens: VSR_ERR_INVALID_ARG).
+ * vsr_map_from_device, a distorted map or another kind of vsr_make_map_spec
+ * has none: VSR_ERR_INVALID_ARG).
  * The adjoint follows the forward exactly: the merge (saturation at the
  * first fragment with m^f > 1 - m^b), gpstep / min (the gradient goes to
  * the minimising plane distance while its clamp is open), the plane

@@ -78,6 +78,9 @@ def _load():
             lib.orc_shade_grad.argtypes = [i32, i32, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_shade_grad.restype = i32
             lib.orc_setup_grad.argtypes = [i64, vp, vp, vp, vp, vp]
+            lib.orc_map_spec.argtypes = [i32, i32, i32, vp, vp, i32, vp]
+            lib.orc_map_spec.restype = i32
+            lib.orc_map_spec_dirs.argtypes = [i64, vp, vp, i32, i32, i32, vp, vp, i32, vp, vp]
             assert lib.orc_record_size() == REC
             _lib = lib
             del P
@@ -320,3 +323,36 @@ def shade_fd(verts, colors, lens, pixels, W, H, h=1e-6, which=("k", "l", "s", "o
                 fp, fm = fp * w, fm * w
             out[(t, v, c)] = float(np.sum(fp) - np.sum(fm)) / (2 * h)
     return out
+
+
+MAP_UNIVERSAL, MAP_RECTILINEAR, MAP_PANORAMA, MAP_DOME, MAP_EQUIRECT, MAP_CUBE = range(6)
+
+
+def make_map_spec(W, H, kind, param=(), dist=(0, 0, 0, 0, 0, 0), aov=0):
+    """FP64 map [H, W, 4] of another projection (Sec. 2.2) or of the
+    Universal / rectilinear model with Brown-Conrady distortion (Sec. 2.3).
+    param: kind-specific (see orc_map_spec); for the Universal kind the
+    effective parameters (k, l, s, Omega_deg) after limits."""
+    p = np.zeros(4)
+    p[:len(param)] = np.asarray(param, dtype=np.float64)
+    d = np.zeros(6)
+    d[:len(dist)] = np.asarray(dist, dtype=np.float64)
+    out = np.zeros((H, W, 4))
+    if _load().orc_map_spec(W, H, kind, _ptr(p), _ptr(d), aov, _ptr(out)):
+        raise ValueError("orc_map_spec: bad arguments")
+    return out
+
+
+def map_spec_dirs(fs, ft, W, H, kind, param=(), dist=(0, 0, 0, 0, 0, 0), aov=0):
+    """The map function of make_map_spec at texture coordinates (fs, ft):
+    (directions [n, 3], valid [n])."""
+    fs = np.ascontiguousarray(fs, dtype=np.float64).ravel()
+    ft = np.ascontiguousarray(ft, dtype=np.float64).ravel()
+    p = np.zeros(4)
+    p[:len(param)] = np.asarray(param, dtype=np.float64)
+    d = np.zeros(6)
+    d[:len(dist)] = np.asarray(dist, dtype=np.float64)
+    v = np.zeros((fs.size, 3))
+    ok = np.zeros(fs.size, dtype=np.int32)
+    _load().orc_map_spec_dirs(fs.size, _ptr(fs), _ptr(ft), W, H, kind, _ptr(p), _ptr(d), aov, _ptr(v), _ptr(ok))
+    return v, ok.astype(bool)

@@ -1203,3 +1203,183 @@ void orc_setup_grad(int64_t T, const double* tris, const double* cam, const doub
                 dw[3 * q + c] = M[c] * dV[q][0] + M[3 + c] * dV[q][1] + M[6 + c] * dV[q][2];
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Perspective maps of other projections (Sec. 2.2) and the lens distortion
+ * of view coordinates (Sec. 2.3), evaluated like orc_map: the direction of
+ * every pixel centre, the global delta from central differences of the map
+ * function at the neighbouring centres (reading R8), here restricted to
+ * neighbours of the same chart (the cube map's faces), invalid pixels
+ * (0,0,0,0).
+ *
+ * kind 0 Universal (param k, l, s, Omega_deg after limits) with the
+ *        Brown-Conrady distortion dist[6] = (k1, k2, p1, p2, q1, q2) of its
+ *        view coordinates (x, y) in the map's AOV normalisation:
+ *        r2 = x^2 + y^2, (x, y) <- (x, y)(1 + k1 r2 + k2 r2^2)
+ *                                 + (x, y)(p1 x + p2 y) + (q1, q2) r2
+ * kind 1 rectilinear (param Omega_deg): normalize(x, y, cot(Omega/2)),
+ *        the same distortion applies
+ * kind 2 curved panorama (param Omega_h_deg, height): with
+ *        f' = (Omega_h (f_s - 1/2), height (f_t - 1/2)),
+ *        v = normalize(sin f'_x, f'_y, cos f'_x)
+ * kind 3 full dome (param compression_deg, tilt_deg, offset):
+ *        f' = (2 f_s - 1, 1 - 2 f_t), R = |f'|, theta = R (compression + pi/2),
+ *        v = normalize(f'_x sin(theta)/R, cos(theta), f'_y sin(theta)/R + offset)
+ *        rotated by the tilt about x; pixels with R > 1 are outside the dome
+ * kind 4 equirectangular: f' = pi (2 f_s - 1, f_t),
+ *        v = (sin f'_x sin f'_y, -cos f'_y, cos f'_x sin f'_y)
+ * kind 5 cube map (W = 6 H): face i = floor(6 f_s), local
+ *        u = normalize(fract(6 f_s) - 1/2, f_t - 1/2, 1/2), v = M_i u with
+ *        the rows of M_i as printed for faces 0, 1, 2, 4, 5 and M_3 = I
+ *        (reading: the printed case list has no face 3; the other five look
+ *        along +x, -x, -z, +y, -y, so face 3 is the front face along +z)
+ */
+static int map_spec_dir(double fs, double ft, int W, int H, int kind, const double* prm, const double* dist,
+                        int aov, double* v, int* chart)
+{
+    *chart = 0;
+    const double aspect = (double)W / (double)H;
+    if (kind == 0 || kind == 1) {
+        double xy[2];
+        orc_view_coord(fs, ft, aspect, aov, xy);
+        double x = xy[0], y = xy[1];
+        const double r2 = x * x + y * y;
+        const double rad = 1.0 + dist[0] * r2 + dist[1] * r2 * r2;
+        const double pr = dist[2] * x + dist[3] * y;
+        const double xd = x * rad + x * pr + dist[4] * r2;
+        const double yd = y * rad + y * pr + dist[5] * r2;
+        if (kind == 0) return orc_map_dir(xd, yd, prm, v);
+        double w[3] = {xd, yd, 1.0 / tan(prm[0] * ORC_PI / 360.0)};
+        double n = sqrt(dot3(w, w));
+        for (int c = 0; c < 3; ++c) v[c] = w[c] / n;
+        return 1;
+    }
+    if (kind == 2) {
+        const double fx = prm[0] * ORC_PI / 180.0 * (fs - 0.5), fy = prm[1] * (ft - 0.5);
+        double w[3] = {sin(fx), fy, cos(fx)};
+        double n = sqrt(dot3(w, w));
+        for (int c = 0; c < 3; ++c) v[c] = w[c] / n;
+        return 1;
+    }
+    if (kind == 3) {
+        const double fx = 2.0 * fs - 1.0, fy = 1.0 - 2.0 * ft;
+        const double R = sqrt(fx * fx + fy * fy);
+        if (R > 1.0) {
+            v[0] = v[1] = v[2] = 0.0;
+            return 0;
+        }
+        const double theta = R * (prm[0] * ORC_PI / 180.0 + 0.5 * ORC_PI);
+        const double sor = R > 0.0 ? sin(theta) / R : prm[0] * ORC_PI / 180.0 + 0.5 * ORC_PI;
+        double w[3] = {fx * sor, cos(theta), fy * sor + prm[2]};
+        double n = sqrt(dot3(w, w));
+        for (int c = 0; c < 3; ++c) w[c] /= n;
+        const double ct = cos(prm[1] * ORC_PI / 180.0), st = sin(prm[1] * ORC_PI / 180.0);
+        /* row vector times the tilt matrix [[1,0,0],[0,c,-s],[0,s,c]] */
+        v[0] = w[0];
+        v[1] = w[1] * ct + w[2] * st;
+        v[2] = -w[1] * st + w[2] * ct;
+        return 1;
+    }
+    if (kind == 4) {
+        const double fx = ORC_PI * (2.0 * fs - 1.0), fy = ORC_PI * ft;
+        v[0] = sin(fx) * sin(fy);
+        v[1] = -cos(fy);
+        v[2] = cos(fx) * sin(fy);
+        return 1;
+    }
+    /* kind 5: cube */
+    const double s6 = 6.0 * fs;
+    const int face = (int)floor(s6);
+    *chart = face;
+    if (face < 0 || face > 5) {  /* beyond the strip (halo pixels): no chart */
+        v[0] = v[1] = v[2] = 0.0;
+        return 0;
+    }
+    double u[3] = {s6 - face - 0.5, ft - 0.5, 0.5};
+    double n = sqrt(dot3(u, u));
+    for (int c = 0; c < 3; ++c) u[c] /= n;
+    /* rows of M_i: world = M_i u */
+    static const double M[6][9] = {
+        {0, 0, 1, -1, 0, 0, 0, -1, 0},   /* [ Z, -X, -Y] */
+        {0, 0, -1, 1, 0, 0, 0, -1, 0},   /* [-Z,  X, -Y] */
+        {1, 0, 0, 0, -1, 0, 0, 0, -1},   /* [ X, -Y, -Z] */
+        {1, 0, 0, 0, 1, 0, 0, 0, 1},     /* [ X,  Y,  Z] (reading) */
+        {1, 0, 0, 0, 0, 1, 0, -1, 0},    /* [ X,  Z, -Y] */
+        {-1, 0, 0, 0, 0, -1, 0, -1, 0},  /* [-X, -Z, -Y] */
+    };
+    for (int r = 0; r < 3; ++r) v[r] = M[face][3 * r] * u[0] + M[face][3 * r + 1] * u[1] + M[face][3 * r + 2] * u[2];
+    return 1;
+}
+
+int orc_map_spec(int W, int H, int kind, const double* prm, const double* dist, int aov, double* out)
+{
+    if (W <= 0 || H <= 0 || kind < 0 || kind > 5) return -1;
+    const int GW = W + 2;
+    const size_t gn = (size_t)GW * (size_t)(H + 2);
+    double* g = (double*)malloc(gn * 3 * sizeof(double));
+    int* ok = (int*)malloc(gn * sizeof(int));
+    int* ch = (int*)malloc(gn * sizeof(int));
+    if (!g || !ok || !ch) {
+        free(g);
+        free(ok);
+        free(ch);
+        return -2;
+    }
+    for (int gj = 0; gj < H + 2; ++gj)
+        for (int gi = 0; gi < GW; ++gi) {
+            const size_t q = (size_t)gj * GW + gi;
+            ok[q] = map_spec_dir((gi - 0.5) / W, (gj - 0.5) / H, W, H, kind, prm, dist, aov, g + 3 * q, &ch[q]);
+        }
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            double* o = out + ((size_t)j * W + i) * 4;
+            const size_t c0 = (size_t)(j + 1) * GW + (i + 1);
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+            if (!ok[c0]) continue;
+            /* a neighbour counts only when valid and on the same chart */
+            const size_t nb[4] = {c0 - 1, c0 + 1, c0 - GW, c0 + GW};
+            int use[4];
+            for (int q = 0; q < 4; ++q) use[q] = ok[nb[q]] && ch[nb[q]] == ch[c0];
+            double fw = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double vc = g[3 * c0 + c];
+                double di, dj;
+                if (use[0] && use[1])
+                    di = (g[3 * nb[1] + c] - g[3 * nb[0] + c]) * 0.5;
+                else if (use[1])
+                    di = g[3 * nb[1] + c] - vc;
+                else if (use[0])
+                    di = vc - g[3 * nb[0] + c];
+                else
+                    di = 0.0;
+                if (use[2] && use[3])
+                    dj = (g[3 * nb[3] + c] - g[3 * nb[2] + c]) * 0.5;
+                else if (use[3])
+                    dj = g[3 * nb[3] + c] - vc;
+                else if (use[2])
+                    dj = vc - g[3 * nb[2] + c];
+                else
+                    dj = 0.0;
+                const double f = fabs(di) + fabs(dj);
+                if (f > fw) fw = f;
+            }
+            if (!(fw > 0.0)) continue;
+            for (int c = 0; c < 3; ++c) o[c] = g[3 * c0 + c];
+            o[3] = 1.0 / fw;
+        }
+    free(g);
+    free(ok);
+    free(ch);
+    return 0;
+}
+
+/* The map function of orc_map_spec at arbitrary texture coordinates (for
+ * the solid-angle pins).  v: n x 3, valid: n. */
+void orc_map_spec_dirs(int64_t n, const double* fs, const double* ft, int W, int H, int kind, const double* prm,
+                       const double* dist, int aov, double* v, int32_t* valid)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        int chart;
+        valid[q] = map_spec_dir(fs[q], ft[q], W, H, kind, prm, dist, aov, v + 3 * q, &chart);
+    }
+}

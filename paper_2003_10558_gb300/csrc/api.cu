@@ -101,10 +101,28 @@ vsr_status check_params(const vsr_map_params* p)
     return VSR_OK;
 }
 
+// the spec of a plain Universal map with m->p's (effective) parameters
+void set_universal_spec(vsr_map m)
+{
+    m->spec = vsr_map_spec{};
+    m->spec.kind = VSR_MAP_UNIVERSAL;
+    m->spec.W = m->p.W;
+    m->spec.H = m->p.H;
+    m->spec.aov = m->p.aov;
+    m->spec.param[0] = m->p.k;
+    m->spec.param[1] = m->p.l;
+    m->spec.param[2] = m->p.s;
+    m->spec.param[3] = m->p.omega_deg;
+    m->lens_grad = true;
+}
+
 vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
-    vsr_status s = launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles,
-                              m->idx.geom, st);
+    bool plain = m->spec.kind == VSR_MAP_UNIVERSAL;
+    for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
+    vsr_status s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map,
+                                      m->tiles, m->idx.geom, st)
+                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, st);
     if (s != VSR_OK) return s;
     s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     m->gen = g_gen.fetch_add(1);
@@ -207,6 +225,7 @@ vsr_status vsr_make_map_ex(const vsr_map_params* p, void* stream, vsr_map* out)
     if (!m) return VSR_ERR_OOM;
     m->p = *p;
     apply_limits(&m->p);
+    set_universal_spec(m);
     if ((s = map_alloc(m, p->W, p->H)) != VSR_OK || (s = map_generate(m, (cudaStream_t)stream)) != VSR_OK) {
         map_release(m);
         delete m;
@@ -230,6 +249,54 @@ vsr_status vsr_make_map(float k, float l, float s, float omega_deg, int W, int H
     return vsr_make_map_ex(&p, stream, out);
 }
 
+vsr_status vsr_make_map_spec(const vsr_map_spec* sp, void* stream, vsr_map* out)
+{
+    if (!out) return VSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!sp || !size_ok(sp->W, sp->H) || sp->kind < VSR_MAP_UNIVERSAL || sp->kind > VSR_MAP_CUBE || sp->aov < 0 ||
+        sp->aov > 3)
+        return VSR_ERR_INVALID_ARG;
+    for (int q = 0; q < 4; ++q)
+        if (!isfinite(sp->param[q])) return VSR_ERR_INVALID_ARG;
+    bool undistorted = true;
+    for (int q = 0; q < 6; ++q) {
+        if (!isfinite(sp->distortion[q])) return VSR_ERR_INVALID_ARG;
+        undistorted = undistorted && sp->distortion[q] == 0.0f;
+    }
+    if (sp->kind == VSR_MAP_RECTILINEAR && !(sp->param[0] > 0.0f && sp->param[0] < 180.0f)) return VSR_ERR_INVALID_ARG;
+    if (sp->kind == VSR_MAP_PANORAMA && !(sp->param[0] > 0.0f && sp->param[1] >= 0.0f)) return VSR_ERR_INVALID_ARG;
+    vsr_map m = new (std::nothrow) vsr_map_s;
+    if (!m) return VSR_ERR_OOM;
+    memset(&m->p, 0, sizeof(m->p));
+    m->p.W = sp->W;
+    m->p.H = sp->H;
+    m->p.aov = sp->aov;
+    m->spec = *sp;
+    if (sp->kind == VSR_MAP_UNIVERSAL) {
+        m->p.k = sp->param[0];
+        m->p.l = sp->param[1];
+        m->p.s = sp->param[2];
+        m->p.omega_deg = sp->param[3];
+        apply_limits(&m->p);
+        m->spec.param[0] = m->p.k;
+        m->spec.param[1] = m->p.l;
+        m->spec.param[2] = m->p.s;
+        m->spec.param[3] = m->p.omega_deg;
+        m->lens_grad = undistorted;
+    } else {
+        m->p.k = m->p.l = m->p.s = m->p.omega_deg = NAN;
+        m->lens_grad = false;
+    }
+    vsr_status s;
+    if ((s = map_alloc(m, sp->W, sp->H)) != VSR_OK || (s = map_generate(m, (cudaStream_t)stream)) != VSR_OK) {
+        map_release(m);
+        delete m;
+        return s;
+    }
+    *out = m;
+    return VSR_OK;
+}
+
 vsr_status vsr_map_update(vsr_map m, const vsr_map_params* p, void* stream)
 {
     if (!m) return VSR_ERR_INVALID_ARG;
@@ -241,6 +308,7 @@ vsr_status vsr_map_update(vsr_map m, const vsr_map_params* p, void* stream)
     }
     m->p = *p;
     apply_limits(&m->p);
+    set_universal_spec(m);
     return map_generate(m, (cudaStream_t)stream);
 }
 
@@ -255,6 +323,7 @@ vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream
     m->p.W = W;
     m->p.H = H;
     m->p.k = m->p.l = m->p.s = m->p.omega_deg = NAN;
+    m->lens_grad = false;
     vsr_status s = map_alloc(m, W, H);
     cudaStream_t st = (cudaStream_t)stream;
     if (s == VSR_OK && cudaMemcpyAsync(m->map, xyzd_dev, sizeof(float4) * (size_t)W * H, cudaMemcpyDeviceToDevice,

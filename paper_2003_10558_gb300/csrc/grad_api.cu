@@ -156,8 +156,7 @@ vsr_status vsr_raster_backward(vsr_map m, vsr_scene sc, const float* tris_dev, c
         return VSR_ERR_INVALID_ARG;
     if (ddepth_dev && !id_dev) return VSR_ERR_INVALID_ARG;
     if (dtris_dev && sc->T > 0 && !tris_dev) return VSR_ERR_INVALID_ARG;
-    if (dlens_dev && !(isfinite(m->p.k) && isfinite(m->p.l) && isfinite(m->p.s) && isfinite(m->p.omega_deg)))
-        return VSR_ERR_INVALID_ARG;
+    if (dlens_dev && !m->lens_grad) return VSR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t T = sc->T;
     vsr_status s;

@@ -24,11 +24,9 @@ struct MapP {
     int kind;      // 1: k > 0, 0: k == 0, -1: k < 0
 };
 
-// Map function at pixel centre (i, j) (may lie outside the picture).
-__device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p, float3& v)
+// Universal perspective direction of view coordinates (x, y).
+__device__ __forceinline__ bool universal_dir(float x, float y, const MapP& p, float3& v)
 {
-    float x = (float)(2 * i + 1 - W) * p.sc;
-    float y = (float)(2 * j + 1 - H) * p.sc;
     float R = sqrtf(fmaf(x, x, p.l * y * y));
     float th;
     float lim;  // lim_{R -> 0} sin(theta)/R
@@ -54,6 +52,14 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
     inv = inv * fmaf(-0.5f * n2 * inv, inv, 1.5f);
     v = make_float3(wx * inv, wy * inv, wz * inv);
     return true;
+}
+
+// Map function at pixel centre (i, j) (may lie outside the picture).
+__device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p, float3& v)
+{
+    const float x = (float)(2 * i + 1 - W) * p.sc;
+    const float y = (float)(2 * j + 1 - H) * p.sc;
+    return universal_dir(x, y, p, v);
 }
 
 // Block-wide reduction of the tile cone from per-thread (valid, G, h).
@@ -134,7 +140,14 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
 constexpr int HW = TILE + 2;
 constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation per thread
 
-__global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, float4* __restrict__ map,
+// One 16x16 tile of a map: the map function F at every pixel centre of the
+// tile and its one-pixel halo (F(i, j, v) returns 0 where the map is
+// undefined, else 1 + the pixel's chart -- the face of a cube map, 0 for
+// single-chart maps), the global delta from central differences over
+// neighbours of the same chart (one-sided next to an unusable neighbour),
+// the map row and the tile cone.
+template <class F>
+__global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, float4* __restrict__ map,
                                                            Cone* __restrict__ tiles, float4* __restrict__ geom)
 {
     __shared__ float3 sv[HW * HW];
@@ -144,9 +157,9 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, 
     if (threadIdx.x < HW * HW) {
         const int q = threadIdx.x, qi = q % HW, qj = q / HW;
         float3 v = make_float3(0.0f, 0.0f, 0.0f);
-        bool ok = map_fn(i0 + qi, j0 + qj, W, H, p, v);
+        const int ok = fn(i0 + qi, j0 + qj, W, H, v);
         sv[q] = v;
-        sok[q] = ok;
+        sok[q] = (unsigned char)ok;
     }
     __syncthreads();
     if (threadIdx.x >= TILE_PIX) {
@@ -162,28 +175,30 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, 
     float h = 0.0f;
     if (i < W && j < H) {
         float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (sok[c]) {
+        const unsigned char cc = sok[c];
+        if (cc) {
             const float3 vc = sv[c];
             const int L = c - 1, Rr = c + 1, U = c - HW, D = c + HW;
+            const bool uL = sok[L] == cc, uR = sok[Rr] == cc, uU = sok[U] == cc, uD = sok[D] == cc;
             float fw = 0.0f;
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
                 auto get = [&](int q) { return comp == 0 ? sv[q].x : (comp == 1 ? sv[q].y : sv[q].z); };
                 float vcc = comp == 0 ? vc.x : (comp == 1 ? vc.y : vc.z);
                 float di, dj;
-                if (sok[L] && sok[Rr])
+                if (uL && uR)
                     di = (get(Rr) - get(L)) * 0.5f;
-                else if (sok[Rr])
+                else if (uR)
                     di = get(Rr) - vcc;
-                else if (sok[L])
+                else if (uL)
                     di = vcc - get(L);
                 else
                     di = 0.0f;
-                if (sok[U] && sok[D])
+                if (uU && uD)
                     dj = (get(D) - get(U)) * 0.5f;
-                else if (sok[D])
+                else if (uD)
                     dj = get(D) - vcc;
-                else if (sok[U])
+                else if (uU)
                     dj = vcc - get(U);
                 else
                     dj = 0.0f;
@@ -200,6 +215,87 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, MapP p, 
     }
     reduce_cone(valid, G, h, &tiles[ty * gridDim.x + tx], &geom[ty * gridDim.x + tx]);
 }
+
+// The Universal perspective map function.
+struct UniversalFn {
+    MapP p;
+    __device__ __forceinline__ int operator()(int i, int j, int W, int H, float3& v) const
+    {
+        return map_fn(i, j, W, H, p, v) ? 1 : 0;
+    }
+};
+
+__device__ __forceinline__ float3 normalized(float x, float y, float z)
+{
+    const float n2 = fmaf(x, x, fmaf(y, y, z * z));
+    float inv = rsqrtf(n2);
+    inv = inv * fmaf(-0.5f * n2 * inv, inv, 1.5f);  // one Newton step: |v| = 1 to ~1 ulp
+    return make_float3(x * inv, y * inv, z * inv);
+}
+
+// The other projections of Sec. 2.2 and the Brown-Conrady distortion of the
+// view coordinates (Sec. 2.3), see vsr_map_spec.
+struct SpecFn {
+    int kind;
+    MapP p;          // Universal lens; p.sc = view-coordinate scale of the AOV type
+    float cot_half;  // rectilinear: cot(Omega/2)
+    float d[6];      // k1, k2, p1, p2, q1, q2
+    float a[4];      // panorama: Omega_h (rad), height; dome: compression + pi/2 (rad), cos tilt, sin tilt, offset
+
+    __device__ __forceinline__ int operator()(int i, int j, int W, int H, float3& v) const
+    {
+        if (kind == VSR_MAP_UNIVERSAL || kind == VSR_MAP_RECTILINEAR) {
+            const float x = (float)(2 * i + 1 - W) * p.sc, y = (float)(2 * j + 1 - H) * p.sc;
+            const float r2 = fmaf(x, x, y * y);
+            const float rad = fmaf(d[1] * r2, r2, fmaf(d[0], r2, 1.0f));
+            const float pr = fmaf(d[2], x, d[3] * y);
+            const float xd = fmaf(x, rad, fmaf(x, pr, d[4] * r2));
+            const float yd = fmaf(y, rad, fmaf(y, pr, d[5] * r2));
+            if (kind == VSR_MAP_UNIVERSAL) return universal_dir(xd, yd, p, v) ? 1 : 0;
+            v = normalized(xd, yd, cot_half);
+            return 1;
+        }
+        const float fs = ((float)i + 0.5f) / (float)W, ft = ((float)j + 0.5f) / (float)H;
+        if (kind == VSR_MAP_PANORAMA) {
+            float sx, cx;
+            sincosf(a[0] * (fs - 0.5f), &sx, &cx);
+            v = normalized(sx, a[1] * (ft - 0.5f), cx);
+            return 1;
+        }
+        if (kind == VSR_MAP_DOME) {
+            const float fx = 2.0f * fs - 1.0f, fy = 1.0f - 2.0f * ft;
+            const float R = sqrtf(fmaf(fx, fx, fy * fy));
+            if (R > 1.0f) return 0;
+            float st, ct;
+            sincosf(R * a[0], &st, &ct);
+            const float sor = R > 0.0f ? st / R : a[0];
+            const float3 w = normalized(fx * sor, ct, fmaf(fy, sor, a[3]));
+            v = make_float3(w.x, fmaf(w.y, a[1], w.z * a[2]), fmaf(-w.y, a[2], w.z * a[1]));
+            return 1;
+        }
+        if (kind == VSR_MAP_EQUIRECT) {
+            float sx, cx, sy, cy;
+            sincospif(2.0f * fs - 1.0f, &sx, &cx);
+            sincospif(ft, &sy, &cy);
+            v = make_float3(sx * sy, -cy, cx * sy);
+            return 1;
+        }
+        // cube: face = floor(6 f_s), rows of the face rotation (world = M u)
+        const float s6 = 6.0f * fs;
+        const int face = (int)floorf(s6);
+        if (face < 0 || face > 5) return 0;  // beyond the strip
+        const float3 u = normalized(s6 - (float)face - 0.5f, ft - 0.5f, 0.5f);
+        switch (face) {
+        case 0: v = make_float3(u.z, -u.x, -u.y); break;   // [ Z, -X, -Y]
+        case 1: v = make_float3(-u.z, u.x, -u.y); break;   // [-Z,  X, -Y]
+        case 2: v = make_float3(u.x, -u.y, -u.z); break;   // [ X, -Y, -Z]
+        case 3: v = u; break;                               // [ X,  Y,  Z]: the front face
+        case 4: v = make_float3(u.x, u.z, -u.y); break;    // [ X,  Z, -Y]
+        default: v = make_float3(-u.x, -u.z, -u.y); break; // [-X, -Z, -Y]
+        }
+        return 1 + face;
+    }
+};
 
 // Cones of a map supplied by the caller.
 __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict__ map, int W, int H,
@@ -254,7 +350,30 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
 {
     const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, p, map, tiles, geom);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, float4* geom, cudaStream_t st)
+{
+    SpecFn f;
+    f.kind = sp.kind;
+    f.p = make_params(sp.W, sp.H, sp.aov, sp.param[0], sp.param[1], sp.param[2], sp.param[3]);
+    f.cot_half = (float)(1.0 / tan((double)sp.param[0] * M_PI / 360.0));
+    for (int q = 0; q < 6; ++q) f.d[q] = sp.distortion[q];
+    for (int q = 0; q < 4; ++q) f.a[q] = 0.0f;
+    if (sp.kind == VSR_MAP_PANORAMA) {
+        f.a[0] = (float)((double)sp.param[0] * M_PI / 180.0);
+        f.a[1] = sp.param[1];
+    } else if (sp.kind == VSR_MAP_DOME) {
+        f.a[0] = (float)((double)sp.param[0] * M_PI / 180.0 + 0.5 * M_PI);
+        f.a[1] = (float)cos((double)sp.param[1] * M_PI / 180.0);
+        f.a[2] = (float)sin((double)sp.param[1] * M_PI / 180.0);
+        f.a[3] = sp.param[2];
+    }
+    dim3 grid((sp.W + TILE - 1) / TILE, (sp.H + TILE - 1) / TILE);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -105,6 +105,8 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
                       float4* geom, cudaStream_t st);
 vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st);
+// a map of any vsr_map_kind (param after limits for the Universal kind)
+vsr_status launch_map_spec(const vsr_map_spec& spec, float4* map, Cone* tiles, float4* geom, cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).

@@ -27,9 +27,10 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA error"
           -5: "fragment list overflow", -6: "device wait timed out", -7: "memory budget exceeded", -8: "cancelled"}
 NO_ID = 0xFFFFFFFF
 AOV_HORIZONTAL, AOV_DIAGONAL, AOV_VERTICAL, AOV_H4X3 = 0, 1, 2, 3
+MAP_UNIVERSAL, MAP_RECTILINEAR, MAP_PANORAMA, MAP_DOME, MAP_EQUIRECT, MAP_CUBE = range(6)
 
 # every symbol include/vsr.h declares
-EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
+EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
            "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_batch_create", "vsr_batch_render",
@@ -49,6 +50,11 @@ class VsrError(RuntimeError):
 class MapParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_float), ("l", ctypes.c_float), ("s", ctypes.c_float), ("omega_deg", ctypes.c_float),
                 ("W", ctypes.c_int), ("H", ctypes.c_int), ("aov", ctypes.c_int), ("strict_limits", ctypes.c_int)]
+
+
+class MapSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("W", ctypes.c_int), ("H", ctypes.c_int), ("aov", ctypes.c_int),
+                ("param", ctypes.c_float * 4), ("distortion", ctypes.c_float * 6)]
 
 
 class ServeCfg(ctypes.Structure):
@@ -94,6 +100,7 @@ def load(path: str = LIB_PATH):
         sig = {
             "vsr_make_map": ([f32, f32, f32, f32, i32, i32, vp, P(vp)], i32),
             "vsr_make_map_ex": ([P(MapParams), vp, P(vp)], i32),
+            "vsr_make_map_spec": ([P(MapSpec), vp, P(vp)], i32),
             "vsr_map_from_device": ([vp, i32, i32, vp, P(vp)], i32),
             "vsr_map_update": ([vp, P(MapParams), vp], i32),
             "vsr_map_params_effective": ([vp, P(MapParams)], i32),
@@ -182,6 +189,21 @@ class Map:
             p = MapParams(k, l, s, omega_deg, W, H, aov, int(strict))
             check(L.vsr_make_map_ex(ctypes.byref(p), _stream_ptr(stream), ctypes.byref(self.h)), "vsr_make_map_ex")
         self._keep = None
+
+    @classmethod
+    def from_spec(cls, kind, W, H, param=(), distortion=(), aov=AOV_HORIZONTAL, stream=None):
+        """A map of another projection (MAP_RECTILINEAR, MAP_PANORAMA,
+        MAP_DOME, MAP_EQUIRECT, MAP_CUBE) or a Universal / rectilinear map
+        with Brown-Conrady distortion (k1, k2, p1, p2, q1, q2)."""
+        sp = MapSpec()
+        sp.kind, sp.W, sp.H, sp.aov = int(kind), int(W), int(H), int(aov)
+        for q, x in enumerate(param):
+            sp.param[q] = float(x)
+        for q, x in enumerate(distortion):
+            sp.distortion[q] = float(x)
+        h = ctypes.c_void_p()
+        check(load().vsr_make_map_spec(ctypes.byref(sp), _stream_ptr(stream), ctypes.byref(h)), "vsr_make_map_spec")
+        return cls(W, H, 0, 0, 0, 0, _handle=h)
 
     @classmethod
     def from_tensor(cls, xyzd, stream=None):
