@@ -143,8 +143,16 @@ typedef struct {
     int aov;   /* vsr_aov: Universal and rectilinear */
     float param[4];
     float distortion[6];
+    int flags; /* VSR_MAP_DERIVATIVES: keep (d_i G, d_j G) for vsr_raster_pstep */
 } vsr_map_spec;
+#define VSR_MAP_DERIVATIVES 1
 vsr_status vsr_make_map_spec(const vsr_map_spec* spec, void* stream, vsr_map* out);
+
+/* (d_i G, d_j G) of a map made with VSR_MAP_DERIVATIVES, synchronous copy
+ * into host memory: W*H*8 floats, (d_i G xyz, 0, d_j G xyz, 0) per pixel --
+ * the central (one-sided next to an unusable neighbour) differences of the
+ * map function that the global delta is formed from. */
+vsr_status vsr_map_download_derivatives(vsr_map m, float* host);
 
 /* Regenerate an existing map in place for new parameters (reallocates
  * only when W or H change).  Same semantics as vsr_make_map_ex. */
@@ -212,6 +220,17 @@ int64_t vsr_scene_size(vsr_scene s);
  * that frame's outputs incomplete, the next call growing the bins.  A scene
  * must not be rasterized on two streams at the same time. */
 vsr_status vsr_raster(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev, void* stream);
+
+/* vsr_raster_pstep: vsr_raster with the per-fragment pixel step of Sec.
+ * 1.1.1 instead of the global delta: every plane distance g ramps over its
+ * own fwidth w = |d_i g| + |d_j g|, d g = n . d G for the edges and
+ * (S-hat . d G)/sin(rho) for the miter, from the map's differences:
+ *   fragment iff every g > -w/2 (bpxstep), m^f = min clamp(g/w + 1/2, 0, 1).
+ * The map must be made with VSR_MAP_DERIVATIVES (else VSR_ERR_INVALID_ARG).
+ * Bins the scene for the wider caps of this step (bins that vsr_raster_tiles
+ * may reuse).  Outputs as vsr_raster. */
+vsr_status vsr_raster_pstep(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            void* stream);
 
 /* The two halves of vsr_raster, for callers that reuse one binning:
  * vsr_bin builds the tile bins of (m, s) (count, scan, fill; sized as

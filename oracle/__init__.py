@@ -78,7 +78,9 @@ def _load():
             lib.orc_shade_grad.argtypes = [i32, i32, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_shade_grad.restype = i32
             lib.orc_setup_grad.argtypes = [i64, vp, vp, vp, vp, vp]
-            lib.orc_map_spec.argtypes = [i32, i32, i32, vp, vp, i32, vp]
+            lib.orc_map_spec.argtypes = [i32, i32, i32, vp, vp, i32, vp, vp]
+            lib.orc_raster_pstep.argtypes = [i32, i32, vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]
+            lib.orc_raster_pstep.restype = i64
             lib.orc_map_spec.restype = i32
             lib.orc_map_spec_dirs.argtypes = [i64, vp, vp, i32, i32, i32, vp, vp, i32, vp, vp]
             assert lib.orc_record_size() == REC
@@ -328,18 +330,52 @@ def shade_fd(verts, colors, lens, pixels, W, H, h=1e-6, which=("k", "l", "s", "o
 MAP_UNIVERSAL, MAP_RECTILINEAR, MAP_PANORAMA, MAP_DOME, MAP_EQUIRECT, MAP_CUBE = range(6)
 
 
-def make_map_spec(W, H, kind, param=(), dist=(0, 0, 0, 0, 0, 0), aov=0):
+def make_map_spec(W, H, kind, param=(), dist=(0, 0, 0, 0, 0, 0), aov=0, derivs=False):
     """FP64 map [H, W, 4] of another projection (Sec. 2.2) or of the
     Universal / rectilinear model with Brown-Conrady distortion (Sec. 2.3).
     param: kind-specific (see orc_map_spec); for the Universal kind the
-    effective parameters (k, l, s, Omega_deg) after limits."""
+    effective parameters (k, l, s, Omega_deg) after limits.  With
+    derivs=True also returns the differences (d_i G, d_j G) [H, W, 6] the
+    global delta is formed from (for pstep)."""
     p = np.zeros(4)
     p[:len(param)] = np.asarray(param, dtype=np.float64)
     d = np.zeros(6)
     d[:len(dist)] = np.asarray(dist, dtype=np.float64)
     out = np.zeros((H, W, 4))
-    if _load().orc_map_spec(W, H, kind, _ptr(p), _ptr(d), aov, _ptr(out)):
+    dv = np.zeros((H, W, 6)) if derivs else None
+    if _load().orc_map_spec(W, H, kind, _ptr(p), _ptr(d), aov, _ptr(out), _ptr(dv)):
         raise ValueError("orc_map_spec: bad arguments")
+    return (out, dv) if derivs else out
+
+
+def raster_pstep(map_, dmap, rec, pixels=None, nthreads=0, extras=False):
+    """Brute-force raster with the per-fragment pixel step: like raster()
+    with dmap [H, W, 6] = (d_i G, d_j G) per pixel."""
+    H, W = map_.shape[:2]
+    m = np.ascontiguousarray(map_, dtype=np.float64)
+    dm = np.ascontiguousarray(dmap, dtype=np.float64)
+    rec = np.ascontiguousarray(rec, dtype=np.float64)
+    if pixels is None:
+        npix, pix = W * H, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64).ravel()
+        npix = pix.size
+    out = {"id": np.zeros(npix, dtype=np.uint32), "depth": np.zeros(npix), "cov": np.zeros(npix)}
+    sm = ni = nf = None
+    if extras:
+        sm = out["sum_mf"] = np.zeros(npix)
+        ni = out["n_inside"] = np.zeros(npix, dtype=np.int32)
+        nf = out["n_frag"] = np.zeros(npix, dtype=np.int32)
+    n_alg = _load().orc_raster_pstep(W, H, _ptr(m), _ptr(dm), rec.shape[0], _ptr(rec), npix, _ptr(pix),
+                                     _ptr(out["id"]), _ptr(out["depth"]), _ptr(out["cov"]), _ptr(sm), _ptr(ni),
+                                     _ptr(nf), nthreads)
+    if n_alg < 0:
+        raise ValueError("orc_raster_pstep: bad sizes")
+    out["n_alg"] = int(n_alg)
+    if pixels is None:
+        for key in list(out):
+            if isinstance(out[key], np.ndarray):
+                out[key] = out[key].reshape(H, W)
     return out
 
 

@@ -565,6 +565,7 @@ static int tie_inside(double g, const double* n)
 typedef struct {
     int W, H;
     const double* map;
+    const double* dmap; /* per-pixel (d_i G, d_j G) for pstep, NULL for gpstep */
     int64_t T;
     const double* rec;
     int64_t npix;
@@ -597,20 +598,38 @@ static void* raster_worker(void* arg)
             size_t nf = 0;
             if (delta > 0.0) {
                 double lim = -0.5 / delta;
+                const double* dI = J->dmap ? J->dmap + 6 * p : NULL;
+                const double* dJ = J->dmap ? J->dmap + 6 * p + 3 : NULL;
                 for (int64_t t = 0; t < J->T; ++t) {
                     const double* r = J->rec + ORC_REC * t;
                     if (r[REC_VALID] == 0.0) continue;
                     double g4 = (dot3(G, r + REC_S) - r[REC_C]) / r[REC_SR];
-                    if (!(g4 > lim)) continue;
+                    /* pstep (Sec. 1.1.1): the ramp of each distance is its own
+                     * fwidth, |d_i g| + |d_j g| with d g = n . d G (reading R29) */
+                    double w4 = 0.0, w[3] = {0.0, 0.0, 0.0};
+                    if (dI) {
+                        w4 = (fabs(dot3(r + REC_S, dI)) + fabs(dot3(r + REC_S, dJ))) / r[REC_SR];
+                        for (int e = 0; e < 3; ++e)
+                            w[e] = fabs(dot3(r + REC_N1 + 3 * e, dI)) + fabs(dot3(r + REC_N1 + 3 * e, dJ));
+                        if (!(g4 > -0.5 * w4)) continue;
+                    } else if (!(g4 > lim)) {
+                        continue;
+                    }
                     ++n_alg; /* G inside the enlarged cap: one algorithmic test */
                     double g1 = dot3(G, r + REC_N1), g2 = dot3(G, r + REC_N2), g3 = dot3(G, r + REC_N3);
-                    if (!(g1 > lim && g2 > lim && g3 > lim)) continue;
+                    if (dI) {
+                        if (!(g1 > -0.5 * w[0] && g2 > -0.5 * w[1] && g3 > -0.5 * w[2])) continue;
+                    } else if (!(g1 > lim && g2 > lim && g3 > lim)) {
+                        continue;
+                    }
                     double rr = r[REC_D] / dot3(G, r + REC_N);
                     if (!(rr > 0.0) || !isfinite(rr)) continue;
                     double m = 1.0;
                     double gs[4] = {g1, g2, g3, g4};
+                    double ws[4] = {w[0], w[1], w[2], w4};
                     for (int i = 0; i < 4; ++i) {
-                        double st = clampd(delta * gs[i] + 0.5, 0.0, 1.0);
+                        double st = dI ? clampd(gs[i] / fmax(ws[i], 1e-300) + 0.5, 0.0, 1.0)
+                                       : clampd(delta * gs[i] + 0.5, 0.0, 1.0);
                         if (st < m) m = st;
                     }
                     if (nf == cap) {
@@ -669,6 +688,41 @@ int64_t orc_raster(int W, int H, const double* map, int64_t T, const double* rec
     J.W = W;
     J.H = H;
     J.map = map;
+    J.dmap = NULL;
+    J.T = T;
+    J.rec = rec;
+    J.npix = npix;
+    J.pix = pix;
+    J.id = id;
+    J.depth = depth;
+    J.cov = cov;
+    J.sum_mf = sum_mf;
+    J.n_inside = n_inside;
+    J.n_frag = n_frag;
+    J.next = 0;
+    J.n_alg = 0;
+    run_threads(ncores(nthreads), raster_worker, &J);
+    return J.n_alg;
+}
+
+/* The same rasterization with the per-fragment pixel step (pstep, Sec.
+ * 1.1.1) instead of the global delta: m^f = min_i clamp(g_i / w_i + 1/2,
+ * 0, 1), fragment iff every g_i > -w_i / 2, with w_i = |d_i g_i| + |d_j g_i|
+ * the fwidth of each distance, d g = n . d G for the edge planes and
+ * (S-hat . d G) / sin(rho) for the miter (reading R29).  dmap: H*W*6
+ * doubles, (d_i G, d_j G) per pixel (orc_map_derivs).  map's 4th channel
+ * only marks valid pixels (delta > 0). */
+int64_t orc_raster_pstep(int W, int H, const double* map, const double* dmap, int64_t T, const double* rec,
+                         int64_t npix, const int64_t* pix, uint32_t* id, double* depth, double* cov, double* sum_mf,
+                         int32_t* n_inside, int32_t* n_frag, int nthreads)
+{
+    if (W <= 0 || H <= 0 || T < 0 || npix < 0 || !dmap) return -1;
+    if (!pix && npix != (int64_t)W * H) return -1;
+    raster_job J;
+    J.W = W;
+    J.H = H;
+    J.map = map;
+    J.dmap = dmap;
     J.T = T;
     J.rec = rec;
     J.npix = npix;
@@ -1311,7 +1365,7 @@ static int map_spec_dir(double fs, double ft, int W, int H, int kind, const doub
     return 1;
 }
 
-int orc_map_spec(int W, int H, int kind, const double* prm, const double* dist, int aov, double* out)
+int orc_map_spec(int W, int H, int kind, const double* prm, const double* dist, int aov, double* out, double* deriv)
 {
     if (W <= 0 || H <= 0 || kind < 0 || kind > 5) return -1;
     const int GW = W + 2;
@@ -1340,7 +1394,7 @@ int orc_map_spec(int W, int H, int kind, const double* prm, const double* dist, 
             const size_t nb[4] = {c0 - 1, c0 + 1, c0 - GW, c0 + GW};
             int use[4];
             for (int q = 0; q < 4; ++q) use[q] = ok[nb[q]] && ch[nb[q]] == ch[c0];
-            double fw = 0.0;
+            double fw = 0.0, dv[6];
             for (int c = 0; c < 3; ++c) {
                 const double vc = g[3 * c0 + c];
                 double di, dj;
@@ -1362,10 +1416,14 @@ int orc_map_spec(int W, int H, int kind, const double* prm, const double* dist, 
                     dj = 0.0;
                 const double f = fabs(di) + fabs(dj);
                 if (f > fw) fw = f;
+                dv[c] = di;
+                dv[3 + c] = dj;
             }
             if (!(fw > 0.0)) continue;
             for (int c = 0; c < 3; ++c) o[c] = g[3 * c0 + c];
             o[3] = 1.0 / fw;
+            if (deriv)
+                for (int c = 0; c < 6; ++c) deriv[((size_t)j * W + i) * 6 + c] = dv[c];
         }
     free(g);
     free(ok);

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvsr.so")
-SOURCES = ["api.cu", "map.cu", "setup.cu", "bin.cu", "raster.cu", "serve.cu", "grad.cu", "grad_api.cu"]
+SOURCES = ["api.cu", "map.cu", "setup.cu", "bin.cu", "raster.cu", "serve.cu", "grad.cu", "grad_api.cu", "pstep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -72,6 +72,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
+    if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }
 
@@ -85,6 +86,8 @@ void map_release(vsr_map m)
     cudaFree(m->idx.sorted);
     cudaFree(m->idx.big);
     cudaFree(m->idx.geom);
+    cudaFree(m->deriv);
+    m->deriv = nullptr;
     m->map = nullptr;
     m->tiles = nullptr;
     m->idx = TileIndex{};
@@ -104,7 +107,9 @@ vsr_status check_params(const vsr_map_params* p)
 // the spec of a plain Universal map with m->p's (effective) parameters
 void set_universal_spec(vsr_map m)
 {
+    const int flags = m->spec.flags;
     m->spec = vsr_map_spec{};
+    m->spec.flags = flags;
     m->spec.kind = VSR_MAP_UNIVERSAL;
     m->spec.W = m->p.W;
     m->spec.H = m->p.H;
@@ -118,11 +123,11 @@ void set_universal_spec(vsr_map m)
 
 vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
-    bool plain = m->spec.kind == VSR_MAP_UNIVERSAL;
+    bool plain = m->spec.kind == VSR_MAP_UNIVERSAL && !m->deriv;
     for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
     vsr_status s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map,
                                       m->tiles, m->idx.geom, st)
-                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, st);
+                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, st);
     if (s != VSR_OK) return s;
     s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
     m->gen = g_gen.fetch_add(1);
@@ -264,6 +269,7 @@ vsr_status vsr_make_map_spec(const vsr_map_spec* sp, void* stream, vsr_map* out)
         undistorted = undistorted && sp->distortion[q] == 0.0f;
     }
     if (sp->kind == VSR_MAP_RECTILINEAR && !(sp->param[0] > 0.0f && sp->param[0] < 180.0f)) return VSR_ERR_INVALID_ARG;
+    if (sp->flags & ~VSR_MAP_DERIVATIVES) return VSR_ERR_INVALID_ARG;
     if (sp->kind == VSR_MAP_PANORAMA && !(sp->param[0] > 0.0f && sp->param[1] >= 0.0f)) return VSR_ERR_INVALID_ARG;
     vsr_map m = new (std::nothrow) vsr_map_s;
     if (!m) return VSR_ERR_OOM;
@@ -366,6 +372,16 @@ vsr_status vsr_map_download(vsr_map m, float* host_xyzd)
     return VSR_OK;
 }
 
+vsr_status vsr_map_download_derivatives(vsr_map m, float* host)
+{
+    if (!m || !host || !m->deriv) return VSR_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return VSR_ERR_CUDA;
+    if (cudaMemcpy(host, m->deriv, 2 * sizeof(float4) * (size_t)m->p.W * m->p.H, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return VSR_ERR_CUDA;
+    return VSR_OK;
+}
+
 void vsr_map_free(vsr_map m)
 {
     if (!m) return;
@@ -447,10 +463,29 @@ void vsr_scene_free(vsr_scene sc)
 
 int64_t vsr_scene_size(vsr_scene sc) { return sc ? sc->T : -1; }
 
+static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st);
+
 vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
 {
     if (!m || !sc) return VSR_ERR_INVALID_ARG;
+    return bin_scene(m, sc, 0, (cudaStream_t)stream);
+}
+
+vsr_status vsr_raster_pstep(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev, void* stream)
+{
+    if (!m || !sc || !m->deriv) return VSR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    vsr_status s = bin_scene(m, sc, 1, st);
+    if (s != VSR_OK) return s;
+    const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
+                       sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
+    return launch_raster_pstep(v, m->deriv, scene_status(sc), st);
+}
+
+}  // extern "C"
+
+static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
+{
     const int ntiles = m->tx * m->ty;
     vsr_status s = ensure_ws(sc, ntiles);
     if (s != VSR_OK) return s;
@@ -462,7 +497,8 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     // previous binning (copied to pinned memory, read only once its event has
     // completed, never waited for) grows the capacity ahead of need, and the
     // fill kernel reports any overflow in the status word.
-    const uint64_t shape = ((uint64_t)ntiles << 32) ^ (uint64_t)sc->T;
+    // the bins' sizes depend on the map, the scene and the step's cap width
+    const uint64_t shape = ((uint64_t)ntiles << 32) ^ (uint64_t)sc->T ^ ((uint64_t)(pstep != 0) << 63);
     const bool resize = sc->cap == 0 || sc->sized_shape != shape;
     if (!resize && sc->total_pending && cudaEventQuery(sc->total_event) == cudaSuccess) {
         sc->total_pending = false;
@@ -477,7 +513,7 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
     VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ((size_t)ntiles + 1), st));
     uint2* pairs = sc->pairs;
     const uint32_t pair_cap = sc->cap;
-    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st)) != VSR_OK) return s;
+    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st, pstep)) != VSR_OK) return s;
     if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
     if (!sc->total_pending) {
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -497,12 +533,14 @@ vsr_status vsr_bin(vsr_map m, vsr_scene sc, void* stream)
         sc->sized_shape = shape;
     }
     if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->offsets, counts, cursor, pairs, pair_cap, sc->ids, sc->cap,
-                             scene_status(sc), st)) != VSR_OK)
+                             scene_status(sc), st, pstep)) != VSR_OK)
         return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
     return VSR_OK;
 }
+
+extern "C" {
 
 vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
                             const vsr_raster_stats* stats, void* stream)

@@ -291,8 +291,14 @@ __global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __
             sz = q0.z;
             // the cap enlarged once by the map's widest ramp (>= every tile's
             // own): cos / sin of its radius beta, so each tile test is a few FMAs
-            cb = fmaxf(-1.0f, fminf(1.0f, q0.w - hmax * q1.x));
-            sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
+            if (v.pstep) {
+                const float2 c = pstep_cap(q0.w, q1.x, hmax);
+                cb = c.x;
+                sb = c.y;
+            } else {
+                cb = fmaxf(-1.0f, fminf(1.0f, q0.w - hmax * q1.x));
+                sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
+            }
             // search radius: enlarged cap + largest small tile
             const float gamma = acosf(cb) + amax + 1e-4f;
             int r1 = nlat - 1;
@@ -508,10 +514,10 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
 }
 
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
-                            uint2* pairs, uint32_t pair_cap, cudaStream_t st)
+                            uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep)
 {
     if (T == 0) return VSR_OK;
-    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, nullptr, pairs, pair_cap, cursor};
+    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, nullptr, pairs, pair_cap, cursor, pstep};
     bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
@@ -519,11 +525,11 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
 
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
                            const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
-                           int* status, cudaStream_t st)
+                           int* status, cudaStream_t st, int pstep)
 {
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, offsets, const_cast<uint2*>(pairs),
-                    pair_cap, const_cast<uint32_t*>(cursor)};
+                    pair_cap, const_cast<uint32_t*>(cursor), pstep};
     if (pairs) {
         constexpr int BIN_PAIR_BLOCKS = 152 * 8;
         bin_pairs_kernel<<<BIN_PAIR_BLOCKS, 256, 0, st>>>(pairs, cursor, pair_cap, offsets, counts, ids, cap,

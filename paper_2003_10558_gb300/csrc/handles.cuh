@@ -28,6 +28,7 @@ struct vsr_map_s {
     vsr_map_params p;  // effective parameters
     vsr_map_spec spec = {};  // the projection (kind VSR_MAP_UNIVERSAL with no distortion for vsr_make_map*)
     bool lens_grad = true;   // the lens gradient of vsr_raster_backward applies (undistorted Universal)
+    float4* deriv = nullptr; // 2 float4 per pixel with VSR_MAP_DERIVATIVES
     float4* map = nullptr;
     Cone* tiles = nullptr;
     TileIndex idx = {};

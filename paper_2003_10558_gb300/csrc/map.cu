@@ -146,9 +146,13 @@ constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation 
 // single-chart maps), the global delta from central differences over
 // neighbours of the same chart (one-sided next to an unusable neighbour),
 // the map row and the tile cone.
+// deriv (optional): the differences (d_i G, d_j G) the delta is formed
+// from, 2 float4 per pixel, for the per-fragment pixel step; the tile
+// cones then carry the widest ramp of either step.
 template <class F>
 __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, float4* __restrict__ map,
-                                                           Cone* __restrict__ tiles, float4* __restrict__ geom)
+                                                           Cone* __restrict__ tiles, float4* __restrict__ geom,
+                                                           float4* __restrict__ deriv = nullptr)
 {
     __shared__ float3 sv[HW * HW];
     __shared__ unsigned char sok[HW * HW];
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, fl
             const int L = c - 1, Rr = c + 1, U = c - HW, D = c + HW;
             const bool uL = sok[L] == cc, uR = sok[Rr] == cc, uU = sok[U] == cc, uD = sok[D] == cc;
             float fw = 0.0f;
+            float dv[6];
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
                 auto get = [&](int q) { return comp == 0 ? sv[q].x : (comp == 1 ? sv[q].y : sv[q].z); };
@@ -203,12 +208,25 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, fl
                 else
                     dj = 0.0f;
                 fw = fmaxf(fw, fabsf(di) + fabsf(dj));
+                dv[comp] = di;
+                dv[3 + comp] = dj;
             }
             if (fw > 0.0f) {
                 o = make_float4(vc.x, vc.y, vc.z, __frcp_rn(fw));
                 valid = true;
                 G = vc;
                 h = 0.5f / o.w;  // exactly the raster kernel's ramp half-width
+                if (deriv) {
+                    // pstep ramp half-width bound for any unit normal n:
+                    // (|n.d_i G| + |n.d_j G|)/2 <= (|d_i G| + |d_j G|)/2
+                    const float ni = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
+                    const float nj = sqrtf(fmaf(dv[3], dv[3], fmaf(dv[4], dv[4], dv[5] * dv[5])));
+                    h = fmaxf(h, 0.5f * (ni + nj) * 1.000001f);
+                }
+            }
+            if (deriv) {
+                deriv[2 * ((size_t)j * W + i)] = valid ? make_float4(dv[0], dv[1], dv[2], 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                deriv[2 * ((size_t)j * W + i) + 1] = valid ? make_float4(dv[3], dv[4], dv[5], 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
         map[(size_t)j * W + i] = o;
@@ -355,7 +373,8 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
     return VSR_OK;
 }
 
-vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, float4* geom, cudaStream_t st)
+vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, float4* geom, float4* deriv,
+                           cudaStream_t st)
 {
     SpecFn f;
     f.kind = sp.kind;
@@ -373,7 +392,7 @@ vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, flo
         f.a[3] = sp.param[2];
     }
     dim3 grid((sp.W + TILE - 1) / TILE, (sp.H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

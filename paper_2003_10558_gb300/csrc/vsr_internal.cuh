@@ -105,8 +105,10 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
                       float4* geom, cudaStream_t st);
 vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st);
-// a map of any vsr_map_kind (param after limits for the Universal kind)
-vsr_status launch_map_spec(const vsr_map_spec& spec, float4* map, Cone* tiles, float4* geom, cudaStream_t st);
+// a map of any vsr_map_kind (param after limits for the Universal kind);
+// deriv (optional): 2 float4 per pixel, (d_i G, d_j G) for the pixel step
+vsr_status launch_map_spec(const vsr_map_spec& spec, float4* map, Cone* tiles, float4* geom, float4* deriv,
+                           cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
@@ -128,12 +130,12 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
 // NULL) -> launch_bin_fill (a map over the pairs when *cursor <= pair_cap,
 // else a second search; pass the count pass's pairs / pair_cap, or NULL)
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
-                            uint2* pairs, uint32_t pair_cap, cudaStream_t st);
+                            uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep = 0);
 vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
                        cudaStream_t st);
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
                            const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
-                           int* status, cudaStream_t st);
+                           int* status, cudaStream_t st, int pstep = 0);
 // One view as the raster kernel sees it: its map, tile cones, set-up
 // records, bin offsets (indexed by the view's own tile number), bin ids and
 // outputs.
@@ -165,7 +167,26 @@ struct BinView {
     uint2* pairs;       // (tile, triangle) of every hit, or NULL
     uint32_t pair_cap;
     uint32_t* cursor;   // hits recorded (may exceed pair_cap: the list is then incomplete)
+    int pstep;          // bins for the per-fragment pixel step (wider caps, see pstep_cap)
 };
+
+// The cap that holds every fragment of the per-fragment pixel step
+// (pstep.cu): its miter test G.S - cos rho > -(|S.d_i G| + |S.d_j G|)/2 is
+// not scaled by sin rho like the global step's, and |S.d G| <= sin(theta)
+// |d G| at angle theta from S, so with h >= the widest ramp half-width
+// (|d_i G| + |d_j G|)/2 every fragment lies within the angle rho + 4h of S.
+// Returns (cos, sin) of that radius.
+__device__ __forceinline__ float2 pstep_cap(float cos_rho, float sin_rho, float h)
+{
+    const float e = 4.0f * h;
+    if (e >= 3.14159265f) return make_float2(-1.0f, 0.0f);
+    float se, ce;
+    sincosf(e, &se, &ce);
+    const float c = fmaf(cos_rho, ce, -sin_rho * se);
+    const float s = fmaf(sin_rho, ce, cos_rho * se);
+    // past the antipode the cap is the whole sphere
+    return (s < 0.0f && c < 0.0f) ? make_float2(-1.0f, 0.0f) : make_float2(c, fmaxf(s, 0.0f));
+}
 
 // Work items of the raster: a tile whose bin is longer than split_max
 // triangles is processed by several CTAs whose results merge order-free
@@ -248,3 +269,7 @@ vsr_status launch_setup_backward(const float* tris, int T, const float cam[12], 
 size_t map_backward_partials(int W, int H);
 vsr_status launch_map_backward(int W, int H, int aov, float k, float l, float s, float omega_deg,
                                const float4* dmap, float* partials, double* dlens, cudaStream_t st);
+
+// rasterization with the per-fragment pixel step (pstep.cu): one CTA per
+// tile over whole bins; deriv: 2 float4 per pixel from launch_map_spec
+vsr_status launch_raster_pstep(const RasterView& view, const float4* deriv, int* status, cudaStream_t st);

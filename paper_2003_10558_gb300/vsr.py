@@ -30,7 +30,8 @@ AOV_HORIZONTAL, AOV_DIAGONAL, AOV_VERTICAL, AOV_H4X3 = 0, 1, 2, 3
 MAP_UNIVERSAL, MAP_RECTILINEAR, MAP_PANORAMA, MAP_DOME, MAP_EQUIRECT, MAP_CUBE = range(6)
 
 # every symbol include/vsr.h declares
-EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
+EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_download_derivatives", "vsr_raster_pstep",
+           "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
            "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_batch_create", "vsr_batch_render",
@@ -54,7 +55,10 @@ class MapParams(ctypes.Structure):
 
 class MapSpec(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("W", ctypes.c_int), ("H", ctypes.c_int), ("aov", ctypes.c_int),
-                ("param", ctypes.c_float * 4), ("distortion", ctypes.c_float * 6)]
+                ("param", ctypes.c_float * 4), ("distortion", ctypes.c_float * 6), ("flags", ctypes.c_int)]
+
+
+MAP_DERIVATIVES = 1
 
 
 class ServeCfg(ctypes.Structure):
@@ -101,6 +105,8 @@ def load(path: str = LIB_PATH):
             "vsr_make_map": ([f32, f32, f32, f32, i32, i32, vp, P(vp)], i32),
             "vsr_make_map_ex": ([P(MapParams), vp, P(vp)], i32),
             "vsr_make_map_spec": ([P(MapSpec), vp, P(vp)], i32),
+            "vsr_map_download_derivatives": ([vp, vp], i32),
+            "vsr_raster_pstep": ([vp, vp, vp, vp, vp, vp], i32),
             "vsr_map_from_device": ([vp, i32, i32, vp, P(vp)], i32),
             "vsr_map_update": ([vp, P(MapParams), vp], i32),
             "vsr_map_params_effective": ([vp, P(MapParams)], i32),
@@ -191,12 +197,14 @@ class Map:
         self._keep = None
 
     @classmethod
-    def from_spec(cls, kind, W, H, param=(), distortion=(), aov=AOV_HORIZONTAL, stream=None):
+    def from_spec(cls, kind, W, H, param=(), distortion=(), aov=AOV_HORIZONTAL, derivatives=False, stream=None):
         """A map of another projection (MAP_RECTILINEAR, MAP_PANORAMA,
         MAP_DOME, MAP_EQUIRECT, MAP_CUBE) or a Universal / rectilinear map
-        with Brown-Conrady distortion (k1, k2, p1, p2, q1, q2)."""
+        with Brown-Conrady distortion (k1, k2, p1, p2, q1, q2).
+        derivatives=True keeps the map's differences for raster(pstep=True)."""
         sp = MapSpec()
         sp.kind, sp.W, sp.H, sp.aov = int(kind), int(W), int(H), int(aov)
+        sp.flags = MAP_DERIVATIVES if derivatives else 0
         for q, x in enumerate(param):
             sp.param[q] = float(x)
         for q, x in enumerate(distortion):
@@ -240,6 +248,14 @@ class Map:
         out = np.empty((H, W, 4), dtype=np.float32)
         check(load().vsr_map_download(self.h, out.ctypes.data_as(ctypes.c_void_p)), "vsr_map_download")
         return out
+
+    def download_derivatives(self):
+        """(d_i G, d_j G) [H, W, 6] of a map made with derivatives=True."""
+        H, W = self.shape
+        out = np.empty((H, W, 8), dtype=np.float32)
+        check(load().vsr_map_download_derivatives(self.h, out.ctypes.data_as(ctypes.c_void_p)),
+              "vsr_map_download_derivatives")
+        return np.concatenate([out[..., 0:3], out[..., 4:7]], axis=-1)
 
     def tensor(self):
         """A torch copy of the map, [H, W, 4] float32 on the device."""
@@ -306,6 +322,21 @@ class Scene:
 def bin(m: Map, sc: Scene, stream=None):
     """Build the tile bins of (m, sc) (vsr_bin)."""
     check(load().vsr_bin(m.h, sc.h, _stream_ptr(stream)), "vsr_bin")
+
+
+def raster_pstep(m: Map, sc: Scene, out=None, stream=None):
+    """Rasterize with the per-fragment pixel step (vsr_raster_pstep); the map
+    needs derivatives.  Returns id (int32 view of uint32), depth, cov."""
+    import torch
+    H, W = m.shape
+    dev = torch.device("cuda")
+    if out is None:
+        out = {"id": torch.empty((H, W), dtype=torch.int32, device=dev),
+               "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
+    check(load().vsr_raster_pstep(m.h, sc.h, _dptr(out.get("id")), _dptr(out.get("depth")), _dptr(out.get("cov")),
+                                  _stream_ptr(stream)), "vsr_raster_pstep")
+    return out
 
 
 def raster(m: Map, sc: Scene, out=None, stats=False, n_inside=False, stream=None, binned=False):
