@@ -40,8 +40,9 @@ UNIT = "tests/s"
 OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
 LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
 # kernels of libvsr.so per step: map, tile index, set-up, bin count, bin scan,
-# bin fill, work items, raster
-LAUNCHES_PER_STEP = 8
+# bin pair fill, bin search fill (returns at once when the pair list is
+# complete), work items, raster
+LAUNCHES_PER_STEP = 9
 
 
 def parse():
@@ -307,6 +308,21 @@ def run_vsr(args, rank, world, local):
         b.record(stream)
         torch.cuda.synchronize()
         stage_ms[name + " alone"] = a.elapsed_time(b)
+    # the per-fragment pixel step on the same frame (binning for its wider
+    # caps + raster), a quality variant: mean of K calls
+    pm = V.Map.from_spec(V.MAP_UNIVERSAL, W, H, (lens["k"], lens["l"], lens["s"], lens["omega"]), derivatives=True)
+    ps_sc = V.Scene(tris, cam)
+    V.raster_pstep(pm, ps_sc, out=out)
+    torch.cuda.synchronize()
+    a, b = evt(), evt()
+    a.record(stream)
+    for _ in range(K):
+        V.raster_pstep(pm, ps_sc, out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    assert V.last_device_status() == 0
+    pstep_ms = a.elapsed_time(b) / K
+    del pm, ps_sc
     # replicas: tests summed over ranks, time of the slowest rank
     total_units, tot_s = replicas.combine(n_alg * K, sum(step_ms) / 1000.0)
     ms_per_step = 1000.0 * tot_s / K
@@ -359,6 +375,7 @@ def run_vsr(args, rank, world, local):
         "raster_kernel_ms": statistics.mean(rast_ms),
         "stage_ms": stage_ms,
         "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
+        "variants": {"pstep_bin_and_raster_ms": pstep_ms},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32)",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "raster_items_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
