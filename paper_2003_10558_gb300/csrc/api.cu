@@ -72,6 +72,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
+    if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }
@@ -86,6 +87,7 @@ void map_release(vsr_map m)
     cudaFree(m->idx.sorted);
     cudaFree(m->idx.big);
     cudaFree(m->idx.geom);
+    cudaFree(m->idx.cell_count);
     cudaFree(m->deriv);
     m->deriv = nullptr;
     m->map = nullptr;

@@ -19,7 +19,6 @@
 // the raster kernel's result does not depend on it.
 #include <math.h>
 
-#include <atomic>
 
 #include "vsr_internal.cuh"
 
@@ -50,17 +49,16 @@ __device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
 
 // ---- tile index -------------------------------------------------------------
 //
-// One CTA of IDX_THREADS threads builds the whole index: the histogram of
-// tile half-angles and the grid plan, the per-cell counts (in shared
-// memory), their exclusive scan, and the cell-sorted cone copies.  A tile
-// index holds one entry per tile, so a single CTA keeps every phase a few
-// loads per thread and saves the launch gaps of separate kernels.  The map
-// kernels have already computed each tile's half-angle and axis latitude /
-// longitude (TileIndex::geom); every pass issues IDX_BATCH loads per thread
-// before using any, so a pass costs about one memory latency.
+// Built from the per-tile geometry the map kernels write (TileIndex::geom:
+// half-angle, axis latitude / longitude, ramp half-width) in four grid-wide
+// steps: the histogram of half-angles (idx_hist_kernel), the grid plan and
+// the per-cell counts (idx_count_kernel, which computes the plan from the
+// histogram in every CTA), the exclusive scan of the cell counts, and the
+// cell-sorted copies of the small tiles' cones (idx_copy_kernel, which takes
+// its slot by decrementing the cell count).  Every step spreads the tiles
+// over the whole GPU; the plan itself is a 64-bin walk.
 
-constexpr int IDX_THREADS = 1024;
-constexpr int IDX_BATCH = 8;
+constexpr int IDX_THREADS = 256;
 
 __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
 {
@@ -75,159 +73,107 @@ __device__ __forceinline__ int home_cell_geom(const float4& g, const TileIndexHd
     return cell_row(g.y, h) * h.nlon + cell_col(g.z, h);
 }
 
-__global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __restrict__ tiles,
+// hdr zeroed by the caller
+__global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const float4* __restrict__ geom, int ntiles,
+                                                                TileIndexHdr* __restrict__ hdr)
+{
+    __shared__ unsigned s_hist[IDX_HIST];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < IDX_HIST) s_hist[tid] = 0u;
+    __syncthreads();
+    const int i = blockIdx.x * IDX_THREADS + tid;
+    const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    const bool ok = g.w >= 0.0f;
+    const int bin = ok ? hist_bin(g.x) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(peers));
+    unsigned nv = ok, hm = ok ? __float_as_uint(g.w) : 0u;  // non-negative floats order as their bits
+    for (int o = 16; o; o >>= 1) {
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    }
+    if (lane == 0 && nv) {
+        atomicAdd(&hdr->n_valid, nv);
+        atomicMax(&hdr->h_max, hm);
+    }
+    __syncthreads();
+    if (tid < IDX_HIST && s_hist[tid]) atomicAdd(&hdr->hist[tid], s_hist[tid]);
+}
+
+// the grid plan: cell size from the 99th percentile of the half-angles
+__device__ void index_plan(const TileIndexHdr* hdr, TileIndexHdr& h)
+{
+    const unsigned nvalid = hdr->n_valid;
+    const unsigned target = (unsigned)ceilf(0.99f * (float)nvalid);
+    unsigned run = 0;
+    int b = 0;
+    for (; b < IDX_HIST; ++b) {
+        run += hdr->hist[b];
+        if (run >= target) break;
+    }
+    const float cut = hist_upper(min(b, IDX_HIST - 1));
+    const float cell = fminf(PI_F / 8.0f, fmaxf(PI_F / IDX_NLAT_MAX, cut));
+    const int nlat = min(IDX_NLAT_MAX, (int)ceilf(PI_F / cell));
+    h.nlat = nlat;
+    h.nlon = 2 * nlat;
+    h.ncell = 2 * nlat * nlat;
+    h.cell = PI_F / nlat;
+    h.alpha_cut = cut;
+}
+
+// cell_count (IDX_CELLS_MAX) zeroed by the caller
+__global__ void __launch_bounds__(IDX_THREADS) idx_count_kernel(const Cone* __restrict__ tiles,
                                                                  const float4* __restrict__ geom, int ntiles,
                                                                  TileIndexHdr* __restrict__ hdr,
-                                                                 uint32_t* __restrict__ cell_start,
-                                                                 Cone* __restrict__ sorted, Cone* __restrict__ big)
+                                                                 uint32_t* __restrict__ cell_count,
+                                                                 Cone* __restrict__ big)
 {
-    extern __shared__ uint32_t s_cell[];  // IDX_CELLS_MAX counts, then cursors
-    __shared__ unsigned s_hist[IDX_HIST];
-    __shared__ unsigned s_nvalid, s_hmax, s_amax, s_nbig;
     __shared__ TileIndexHdr s_h;
-    __shared__ uint32_t s_warp[IDX_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float4 none = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-
-    for (int q = tid; q < IDX_CELLS_MAX; q += IDX_THREADS) s_cell[q] = 0u;
-    if (tid < IDX_HIST) s_hist[tid] = 0u;
-    if (tid == 0) s_nvalid = s_hmax = s_amax = s_nbig = 0u;
-    __syncthreads();
-
-    // histogram of half-angles, widest ramp; lanes with the same bin add
-    // once (__match_any_sync), the counters once per warp
-    unsigned my_valid = 0u, my_hmax = 0u;
-    for (int base0 = 0; base0 < ntiles; base0 += IDX_THREADS * IDX_BATCH) {
-        const int base = base0 + tid;
-        float4 g[IDX_BATCH];
-#pragma unroll
-        for (int q = 0; q < IDX_BATCH; ++q) {
-            const int i = base + q * IDX_THREADS;
-            g[q] = i < ntiles ? geom[i] : none;
-        }
-#pragma unroll
-        for (int q = 0; q < IDX_BATCH; ++q) {
-            const bool ok = g[q].w >= 0.0f;
-            const int bin = ok ? hist_bin(g[q].x) : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
-            if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(peers));
-            my_valid += ok;
-            if (ok) my_hmax = max(my_hmax, __float_as_uint(g[q].w));  // non-negative floats order as their bits
-        }
-    }
-    for (int o = 16; o; o >>= 1) {
-        my_valid += __shfl_xor_sync(0xffffffffu, my_valid, o);
-        my_hmax = max(my_hmax, __shfl_xor_sync(0xffffffffu, my_hmax, o));
-    }
-    if (lane == 0) {
-        atomicAdd(&s_nvalid, my_valid);
-        atomicMax(&s_hmax, my_hmax);
-    }
-    __syncthreads();
-
-    // grid size and small / big threshold from the 99th percentile
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
-        unsigned target = (unsigned)ceilf(0.99f * (float)s_nvalid), run = 0;
-        int b = 0;
-        for (; b < IDX_HIST; ++b) {
-            run += s_hist[b];
-            if (run >= target) break;
+        index_plan(hdr, s_h);
+        if (blockIdx.x == 0) {
+            hdr->nlat = s_h.nlat;
+            hdr->nlon = s_h.nlon;
+            hdr->ncell = s_h.ncell;
+            hdr->cell = s_h.cell;
+            hdr->alpha_cut = s_h.alpha_cut;
         }
-        const float cut = hist_upper(min(b, IDX_HIST - 1));
-        const float cell = fminf(PI_F / 8.0f, fmaxf(PI_F / IDX_NLAT_MAX, cut));
-        const int nlat = min(IDX_NLAT_MAX, (int)ceilf(PI_F / cell));
-        s_h.nlat = nlat;
-        s_h.nlon = 2 * nlat;
-        s_h.ncell = 2 * nlat * nlat;
-        s_h.cell = PI_F / nlat;
-        s_h.alpha_cut = cut;
     }
     __syncthreads();
-    const TileIndexHdr h = s_h;
-
-    // per-cell counts of the small tiles; big tiles to their own list
-    unsigned my_amax = 0u;
-    for (int base = tid; base < ntiles; base += IDX_THREADS * IDX_BATCH) {
-        float4 g[IDX_BATCH];
-#pragma unroll
-        for (int q = 0; q < IDX_BATCH; ++q) {
-            const int i = base + q * IDX_THREADS;
-            g[q] = i < ntiles ? geom[i] : none;
-        }
-#pragma unroll
-        for (int q = 0; q < IDX_BATCH; ++q) {
-            if (g[q].w < 0.0f) continue;
-            const int i = base + q * IDX_THREADS;
-            if (g[q].x > h.alpha_cut) {
-                big[atomicAdd(&s_nbig, 1u)] = index_entry(tiles[i], i);
+    const int i = blockIdx.x * IDX_THREADS + tid;
+    unsigned am = 0u;
+    if (i < ntiles) {
+        const float4 g = geom[i];
+        if (g.w >= 0.0f) {
+            if (g.x > s_h.alpha_cut) {
+                big[atomicAdd(&hdr->n_big, 1u)] = index_entry(tiles[i], i);
             } else {
-                atomicAdd(&s_cell[home_cell_geom(g[q], h)], 1u);
-                my_amax = max(my_amax, __float_as_uint(g[q].x));
+                atomicAdd(&cell_count[home_cell_geom(g, s_h)], 1u);
+                am = __float_as_uint(g.x);
             }
         }
     }
-    for (int o = 16; o; o >>= 1) my_amax = max(my_amax, __shfl_xor_sync(0xffffffffu, my_amax, o));
-    if (lane == 0) atomicMax(&s_amax, my_amax);
-    __syncthreads();
+    for (int o = 16; o; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if (lane == 0 && am) atomicMax(&hdr->alpha_small_max, am);
+}
 
-    // exclusive scan of the cell counts (contiguous segment per thread)
-    const int per = (h.ncell + IDX_THREADS - 1) / IDX_THREADS;
-    const int b0 = min(h.ncell, tid * per), b1 = min(h.ncell, b0 + per);
-    uint32_t local = 0;
-    for (int q = b0; q < b1; ++q) local += s_cell[q];
-    uint32_t x = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
+__global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __restrict__ tiles,
+                                                                const float4* __restrict__ geom, int ntiles,
+                                                                const TileIndexHdr* __restrict__ hdr,
+                                                                const uint32_t* __restrict__ cell_start,
+                                                                uint32_t* __restrict__ cell_count,
+                                                                Cone* __restrict__ sorted)
+{
+    __shared__ TileIndexHdr s_h;
+    if (threadIdx.x == 0) s_h = *hdr;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t v = s_warp[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        s_warp[lane] = v;
-    }
-    __syncthreads();
-    uint32_t run = x - local + (warp > 0 ? s_warp[warp - 1] : 0u);
-    for (int q = b0; q < b1; ++q) {
-        const uint32_t cnt = s_cell[q];
-        cell_start[q] = run;
-        s_cell[q] = run;  // becomes the fill cursor
-        run += cnt;
-    }
-    if (tid == IDX_THREADS - 1) cell_start[h.ncell] = s_warp[31];
-    __syncthreads();
-
-    // cell-sorted copies of the small tiles' cones
-    constexpr int CB = IDX_BATCH / 2;  // cones are 8 words: half the batch keeps them in registers
-    for (int base = tid; base < ntiles; base += IDX_THREADS * CB) {
-        float4 g[CB];
-        Cone c[CB];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) {
-            const int i = base + q * IDX_THREADS;
-            g[q] = i < ntiles ? geom[i] : none;
-            if (i < ntiles) c[q] = tiles[i];
-        }
-#pragma unroll
-        for (int q = 0; q < CB; ++q) {
-            if (g[q].w < 0.0f || g[q].x > h.alpha_cut) continue;
-            const int i = base + q * IDX_THREADS;
-            sorted[atomicAdd(&s_cell[home_cell_geom(g[q], h)], 1u)] = index_entry(c[q], i);
-        }
-    }
-    if (tid == 0) {
-        TileIndexHdr o = h;
-        o.alpha_small_max = s_amax;
-        o.h_max = s_hmax;
-        o.n_big = s_nbig;
-        o.n_valid = s_nvalid;
-        for (int q = 0; q < IDX_HIST; ++q) o.hist[q] = s_hist[q];
-        *hdr = o;
-    }
+    const int i = blockIdx.x * IDX_THREADS + threadIdx.x;
+    if (i >= ntiles) return;
+    const float4 g = geom[i];
+    if (g.w < 0.0f || g.x > s_h.alpha_cut) return;
+    const int c = home_cell_geom(g, s_h);
+    sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
 }
 
 // ---- per-triangle binning ---------------------------------------------------
@@ -256,7 +202,7 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_build_kernel(const Cone* __re
 // a bin is not fixed and the raster kernels' results do not depend on it.
 
 constexpr int BIN_BIG_CHUNK = 16;
-constexpr int BIN_STAGE = 128;  // hits staged per warp and round
+constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full)
 
 // FILL: false = count + record, true = fill by searching again
 template <bool FILL>
@@ -401,17 +347,20 @@ __global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __
             }
         }
         if (!FILL && v.pairs) {
-            // append this round's staged hits to the pair list
+            // append the staged hits to the pair list once the stage is half
+            // full (a round adds about one hit per lane), and at the end
             __syncwarp();
             const uint32_t n = min(s_nhit[warp], (uint32_t)BIN_STAGE);
-            uint32_t g0 = 0;
-            if (lane == 0 && n) g0 = atomicAdd(v.cursor, n);
-            g0 = __shfl_sync(FULL, g0, 0);
-            for (uint32_t j = lane; j < n; j += 32)
-                if (g0 + j < v.pair_cap) v.pairs[g0 + j] = s_hit[warp][j];
-            __syncwarp();
-            if (lane == 0) s_nhit[warp] = 0u;
-            __syncwarp();
+            if (n >= BIN_STAGE / 2 || base + 32 >= total) {
+                uint32_t g0 = 0;
+                if (lane == 0 && n) g0 = atomicAdd(v.cursor, n);
+                g0 = __shfl_sync(FULL, g0, 0);
+                for (uint32_t j = lane; j < n; j += 32)
+                    if (g0 + j < v.pair_cap) v.pairs[g0 + j] = s_hit[warp][j];
+                __syncwarp();
+                if (lane == 0) s_nhit[warp] = 0u;
+                __syncwarp();
+            }
         }
     }
 }
@@ -497,19 +446,22 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
-    const size_t smem = sizeof(uint32_t) * IDX_CELLS_MAX;  // 128 KB of per-cell counts
-    // the shared-memory opt-in is a property of the kernel on a device: set
-    // once per device, not per map (a driver call on the launch path)
-    static std::atomic<bool> s_attr_set[256];
-    int dev = 0;
-    VSR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256 || !s_attr_set[dev].load(std::memory_order_acquire)) {
-        VSR_CUDA_TRY(cudaFuncSetAttribute(idx_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 256) s_attr_set[dev].store(true, std::memory_order_release);
+    const int nb = (ntiles + IDX_THREADS - 1) / IDX_THREADS;
+    VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
+    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
+    if (ntiles > 0) {
+        idx_hist_kernel<<<nb, IDX_THREADS, 0, st>>>(idx.geom, ntiles, idx.hdr);
+        VSR_CUDA_TRY(cudaGetLastError());
     }
-    idx_build_kernel<<<1, IDX_THREADS, smem, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.sorted,
-                                                   idx.big);
+    idx_count_kernel<<<nb > 0 ? nb : 1, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_count, idx.big);
     VSR_CUDA_TRY(cudaGetLastError());
+    vsr_status s = launch_scan(idx.cell_count, nullptr, 0, &idx.hdr->ncell, idx.cell_start, st);
+    if (s != VSR_OK) return s;
+    if (ntiles > 0) {
+        idx_copy_kernel<<<nb, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count,
+                                                    idx.sorted);
+        VSR_CUDA_TRY(cudaGetLastError());
+    }
     return VSR_OK;
 }
 

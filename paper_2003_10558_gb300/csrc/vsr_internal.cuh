@@ -122,6 +122,7 @@ struct TileIndex {
     Cone* big;             // ntiles
     float4* geom;          // ntiles: (alpha, latitude, longitude of the axis, h), h = -1 if the tile is empty;
                            // written with the cones by the map kernels
+    uint32_t* cell_count;  // IDX_CELLS_MAX: scratch of the build
 };
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
 // binning of one frame: counts and cursor zeroed by the caller ->

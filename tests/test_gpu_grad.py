@@ -236,3 +236,23 @@ def test_lens_fit_recovers_target(vsr):
     assert abs(got["k"] - 0.2) < 0.01 and abs(got["l"] - 0.7) < 0.01 and abs(got["s"] - 0.9) < 0.01, got
     first_full = next(h[1] for h in res["history"] if h[0] == 0)
     assert res["history"][-1][1] < first_full  # the vertex stage lowers the full-resolution loss
+
+
+def test_empty_scene_and_invalid_calls(vsr):
+    W, H = 64, 48
+    r = vsr.ShadedRenderer(W, H)
+    r.set_lens(0.3, 0.8, 0.9, 200.0)
+    empty = torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda")
+    cols = torch.zeros((0,), dtype=torch.float32, device="cuda")
+    r.scene.update(empty, r.cam)
+    out = vsr.raster_shaded(r.map, r.scene, r.frags, cols)
+    assert float(out["image"].abs().max()) == 0.0 and float(out["cov"].abs().max()) == 0.0
+    assert (out["id"].cpu().numpy().view(np.uint32) == 0xFFFFFFFF).all()
+    g = vsr.raster_backward(r.map, r.scene, r.frags, empty, cols, out["id"],
+                            dimage=torch.ones((H, W), device="cuda"))
+    assert g["dtris"].numel() == 0 and float(g["dlens"].abs().max()) == 0.0
+    assert vsr.last_device_status() == 0
+    # a backward for a map or scene changed since the forward is refused
+    r.set_lens(0.2, 0.8, 0.9, 200.0)
+    with pytest.raises(vsr.VsrError):
+        vsr.raster_backward(r.map, r.scene, r.frags, empty, cols, out["id"], dimage=torch.ones((H, W), device="cuda"))

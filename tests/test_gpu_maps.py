@@ -105,3 +105,20 @@ def test_differentiable_path_on_a_cube_map(vsr):
     assert torch.isfinite(g["dtris"]).all() and g["dtris"].abs().max() > 0
     with pytest.raises(vsr.VsrError):
         vsr.raster_backward(m, sc, fr, td, cd, out["id"], dimage=torch.ones((H, W), device="cuda"), want=("lens",))
+
+
+def test_invalid_specs_are_refused(vsr):
+    for kind, param in [(6, ()), (-1, ()), (1, (180.0,)), (1, (0.0,)), (2, (0.0, 1.0)), (0, (float("nan"), 1, 1, 90))]:
+        with pytest.raises(vsr.VsrError):
+            vsr.Map.from_spec(kind, 64, 64, param)
+    with pytest.raises(vsr.VsrError):
+        vsr.Map.from_spec(vsr.MAP_CUBE, 0, 64)
+    with pytest.raises(vsr.VsrError):
+        vsr.Map.from_spec(vsr.MAP_UNIVERSAL, 64, 64, (0.0, 1.0, 1.0, 180.0), distortion=(float("inf"),))
+    # an empty scene through a generated map and through pstep
+    m = vsr.Map.from_spec(vsr.MAP_EQUIRECT, 64, 32, derivatives=True)
+    sc = vsr.Scene(torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda"))
+    for out in (vsr.raster(m, sc), vsr.raster_pstep(m, sc)):
+        assert (out["id"].cpu().numpy().view(np.uint32) == 0xFFFFFFFF).all()
+        assert float(out["cov"].abs().max()) == 0.0
+    assert vsr.last_device_status() == 0
