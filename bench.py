@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -114,7 +115,7 @@ class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
     def __init__(self, index):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"vsr_clocks_{os.getpid()}.csv")
         self.proc = None
         self.index = index
 
@@ -141,6 +142,15 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.f.close()
+
+    def load(self, step, seconds=0.5):
+        """Keep the GPU under the workload's own load (untimed steps) long
+        enough for several samples before the timed region starts."""
+        import torch
+        t_end = time.time() + seconds
+        while time.time() < t_end:
+            step()
+            torch.cuda.synchronize()
 
     def summary(self):
         if self.proc is None:
@@ -286,6 +296,7 @@ def run_vsr(args, rank, world, local):
     ev0 = [evt() for _ in range(K)]
     stage = [[evt() for _ in range(3)] for _ in range(K)]
     with ClockSampler(local) as clk:
+        clk.load(lambda: (flush.fill_(1.0), step()))
         torch.cuda.synchronize()
         for k in range(K):
             flush.fill_(float(k))
@@ -470,7 +481,7 @@ def run_batched(args, rank, world, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1000.0
 
-    K = max(1, args.steps // 4)
+    K = max(10, args.steps // 2)  # frames of ~0.1 s: about a second per arm
     vb, tb = replicas.combine(len(views) * K, timed(batched, K))
     vp, tp = replicas.combine(len(views) * K, timed(plain, K))
     assert V.last_device_status() == 0
@@ -623,6 +634,7 @@ def run_grad(args, rank, world, local):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     stage = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     with ClockSampler(local) as clk:
+        clk.load(lambda: (flush.fill_(1.0), step()))
         torch.cuda.synchronize()
         for k in range(K):
             flush.fill_(float(k))
