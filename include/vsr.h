@@ -306,7 +306,8 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64
  * maps, map contents, scene buffer and T, output pointers) renders the
  * views eagerly, synchronises `stream` once to size every view's bins, then
  * captures one graph for each S in {1, 2, 4, 8}, times their replays and
- * keeps the fastest (the autotuner); later calls with the same configuration
+ * keeps the fastest, then tries 256 and 1024 triangles per work item of a
+ * long bin at that S (the autotuner); later calls with the same configuration
  * copy only the cameras (into pinned staging of the batch) and replay the
  * graph on `stream`.  Each call waits for the previous frame of the batch to
  * finish; a replay leaves every view's (tile, triangle) pair total in pinned
@@ -322,8 +323,10 @@ vsr_status vsr_batch_create(vsr_batch* out);
 vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const float* tris_dev, int64_t T,
                             const float* cams, uint32_t* const* id_dev, float* const* depth_dev,
                             float* const* cov_dev, void* stream);
-/* The autotuned number of parallel streams and whether a graph is ready. */
-vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed);
+/* The autotuned configuration (any pointer may be NULL): parallel streams
+ * S, whether a graph is ready, and the triangles per work item of a long
+ * bin (a tile whose bin holds more is rasterized by several CTAs). */
+vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed, int* split_max);
 void vsr_batch_free(vsr_batch b);
 
 /* ---- serving ------------------------------------------------------------------

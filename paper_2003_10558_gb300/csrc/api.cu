@@ -779,6 +779,7 @@ struct vsr_batch_s {
     std::vector<uint64_t> key;
     cudaGraphExec_t exec = nullptr;
     int nstreams = 0;
+    int split_max = SPLIT_MAX_DEFAULT;
 };
 
 namespace {
@@ -829,7 +830,7 @@ vsr_status batch_view_front(vsr_batch b, int v, vsr_map m, const float* tris, in
 
 // fill and raster of view v
 vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pairs, uint32_t* id, float* depth,
-                           float* cov, cudaStream_t st)
+                           float* cov, cudaStream_t st, int split_max = SPLIT_MAX_DEFAULT)
 {
     BatchView& bv = b->views[v];
     const int tiles = m->tx * m->ty;
@@ -840,7 +841,7 @@ vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pa
         return s;
     const RasterView rv{m->map, m->p.W, m->p.H, m->tiles, m->tx, bv.rec, (int)T, bv.offsets,
                         bv.ids, bv.cap, id, depth, cov};
-    return launch_raster_items(rv, bv.offsets, (uint32_t)tiles, bv.cap, bv.work, SPLIT_MAX_DEFAULT, status_word(),
+    return launch_raster_items(rv, bv.offsets, (uint32_t)tiles, bv.cap, bv.work, split_max, status_word(),
                                st);
 }
 
@@ -988,17 +989,19 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             return s;
     VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
 
-    // autotune: one graph per stream count, keep the fastest replay
-    const int cand[4] = {1, 2, 4, 8};
+    // autotune: capture one graph per candidate (parallel streams S, triangles
+    // per work item of a long bin), time three replays, keep the fastest;
+    // first the stream counts at the default split, then the splits at the
+    // best stream count
     float best = 1e30f;
     cudaEvent_t e0, e1;
     VSR_CUDA_TRY(cudaEventCreate(&e0));
     VSR_CUDA_TRY(cudaEventCreate(&e1));
-    for (int c : cand) {
-        const int S = c < nviews ? c : nviews;
+    auto candidate = [&](int S, int split) -> vsr_status {
+        S = S < nviews ? S : nviews;
         cudaStream_t cs = b->streams[0];
         cudaGraph_t g = nullptr;
-        VSR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VSR_ERR_CUDA;
         vsr_status cst = VSR_OK;
         if (cudaMemcpyAsync(b->cams_dev, b->cams_host, cam_bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
             cudaEventRecord(b->fork, cs) != cudaSuccess)
@@ -1014,7 +1017,7 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
                 cst = VSR_ERR_CUDA;
             if (cst == VSR_OK)
                 cst = batch_view_back(b, v, maps[v], T, true, out_ptr(id_dev, v), out_ptr(depth_dev, v),
-                                      out_ptr(cov_dev, v), vs);
+                                      out_ptr(cov_dev, v), vs, split);
         }
         for (int i = 1; cst == VSR_OK && i < S; ++i)
             if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
@@ -1024,8 +1027,6 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
         if (cst != VSR_OK || ee != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
             return cst != VSR_OK ? cst : VSR_ERR_CUDA;
         }
         cudaGraphExec_t ex = nullptr;
@@ -1033,7 +1034,7 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) {
             cudaGetLastError();
-            continue;
+            return VSR_OK;  // not this candidate
         }
         float ms = 0.0f;
         bool timed = cudaGraphLaunch(ex, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
@@ -1045,9 +1046,22 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             if (b->exec) cudaGraphExecDestroy(b->exec);
             b->exec = ex;
             b->nstreams = S;
+            b->split_max = split;
         } else {
             cudaGraphExecDestroy(ex);
         }
+        return VSR_OK;
+    };
+    vsr_status ts = VSR_OK;
+    for (int S : {1, 2, 4, 8})
+        if (ts == VSR_OK) ts = candidate(S, SPLIT_MAX_DEFAULT);
+    const int bestS = b->nstreams;
+    for (int split : {256, 1024})
+        if (ts == VSR_OK && b->exec) ts = candidate(bestS, split);
+    if (ts != VSR_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return ts;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1057,11 +1071,12 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     return VSR_OK;
 }
 
-vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed)
+vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed, int* split_max)
 {
     if (!b) return VSR_ERR_INVALID_ARG;
     if (streams) *streams = b->nstreams;
     if (graphed) *graphed = b->exec != nullptr;
+    if (split_max) *split_max = b->split_max;
     return VSR_OK;
 }
 

@@ -126,7 +126,7 @@ def load(path: str = LIB_PATH):
             "vsr_raster_noalloc": ([vp, vp, vp, vp, vp, vp, vp], i32),
             "vsr_batch_create": ([P(vp)], i32),
             "vsr_batch_render": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp], i32),
-            "vsr_batch_config": ([vp, P(i32), P(i32)], i32),
+            "vsr_batch_config": ([vp, P(i32), P(i32), P(i32)], i32),
             "vsr_batch_free": ([vp], None),
             "vsr_serve_create": ([P(ServeCfg), P(vp)], i32),
             "vsr_serve_add_scene": ([vp, vp, i64, P(i32)], i32),
@@ -429,9 +429,9 @@ class Batch:
         self._keep = (tris, maps, outs)
 
     def config(self):
-        g, r = ctypes.c_int(), ctypes.c_int()
-        check(load().vsr_batch_config(self.h, ctypes.byref(g), ctypes.byref(r)), "vsr_batch_config")
-        return {"streams": g.value, "graphed": bool(r.value)}
+        g, r, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(load().vsr_batch_config(self.h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(sp)), "vsr_batch_config")
+        return {"streams": g.value, "graphed": bool(r.value), "split_max": sp.value}
 
     def free(self):
         if self.h:

@@ -68,6 +68,7 @@ def test_batch_equals_per_view_raster(vsr):
         if call >= 1:
             assert b.config()["graphed"]
     assert b.config()["streams"] in (1, 2, 4, 6)
+    assert b.config()["split_max"] in (256, 512, 1024)
 
 
 def test_batch_view_against_oracle(vsr):
