@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
 // themselves (the first item of a split tile); the further items of split
 // tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
 // return at once.
-__global__ void __launch_bounds__(RT, 8) raster_items_kernel(RasterView view, uint32_t n_tiles,
+__global__ void __launch_bounds__(RT, 9) raster_items_kernel(RasterView view, uint32_t n_tiles,
                                                               const uint32_t* __restrict__ nsplit_of,
                                                               const int32_t* __restrict__ split_slot,
                                                               const uint2* __restrict__ extra,
