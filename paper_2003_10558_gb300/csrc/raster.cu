@@ -156,6 +156,9 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
     }
 
     const size_t TT = (size_t)T;
+    static_assert(PPT == 2, "packed pairs hold the thread's two pixels");
+    const float2 dgx2 = make_float2(dgx[0], dgx[1]), dgy2 = make_float2(dgy[0], dgy[1]),
+                 dgz2 = make_float2(dgz[0], dgz[1]), eg2 = make_float2(eg[0], eg[1]);
 
     for (uint32_t base = b0; base < b1; base += CHUNK) {
         const int n = (int)min((uint32_t)CHUNK, b1 - base);
@@ -200,41 +203,38 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             while (mask) {
                 const int j = gbase + __ffs(mask) - 1;
                 mask &= mask - 1;
+                if (STATS) ++cnt_exec;
+                // the four distances of both pixels in packed FP32x2 arithmetic; the miter
+                // in chord form, G - S-hat = (G - a) - (S-hat - a): both differences are at
+                // most the tile radius, so their rounding costs ~1e-9 rad where it matters
                 const float4 a = st.s0[j];
                 const float4 b = st.s1[j];
                 const float4 e = st.s6[j];
-                if (STATS) ++cnt_exec;
-                // miter distance, chord form
-                float g4[PPT];
-#pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    // G - S-hat = (G - a) - (S-hat - a): both differences are at most the tile
-                    // radius, so their rounding costs ~1e-9 rad where the miter matters
-                    g4[p] = miter_distance(dgx[p], dgy[p], dgz[p], e, b, eg[p]);
-                    if (STATS) cnt_alg += g4[p] > lim[p];
-                }
-                const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
-                float g1[PPT], g2[PPT], g3[PPT], g3m[PPT], gm[PPT];
+                const float2 g4p = miter_distance2(dgx2, dgy2, dgz2, e, b, eg2);
+                const float2 g1p = plane_distance2(dgx2, dgy2, dgz2, st.s2[j]);
+                const float2 g2p = plane_distance2(dgx2, dgy2, dgz2, st.s3[j]);
+                const float2 g3p = plane_distance2(dgx2, dgy2, dgz2, st.s4[j]);
+                const float g1[PPT] = {g1p.x, g1p.y}, g2[PPT] = {g2p.x, g2p.y}, g3[PPT] = {g3p.x, g3p.y},
+                            g4[PPT] = {g4p.x, g4p.y};
+                float g3m[PPT], gm[PPT];
                 bool frag[PPT], anyf = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    g1[p] = plane_distance(dgx[p], dgy[p], dgz[p], n1);
-                    g2[p] = plane_distance(dgx[p], dgy[p], dgz[p], n2);
-                    g3[p] = plane_distance(dgx[p], dgy[p], dgz[p], n3);
+                    if (STATS) cnt_alg += g4[p] > lim[p];
                     g3m[p] = fminf(fminf(g1[p], g2[p]), g3[p]);
                     gm[p] = fminf(g3m[p], g4[p]);
                     frag[p] = gm[p] > lim[p];  // gbpxstep on all four distances; never on invalid pixels
                     anyf |= frag[p];
                 }
                 if (!__any_sync(0xffffffffu, anyf)) continue;
-                const float4 pl = st.s5[j];
+                const float2 Dp = plane_distance2(dgx2, dgy2, dgz2, st.s5[j]);
+                const float D2[PPT] = {Dp.x, Dp.y};
                 const unsigned ties = __float_as_uint(a.w);
                 const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     // predicated: every lane computes, non-fragments add nothing
-                    const float D = plane_distance(dgx[p], dgy[p], dgz[p], pl);
-                    const float r = __fdividef(b.w, D);
+                    const float r = __fdividef(b.w, D2[p]);
                     const bool f = frag[p] && r > 0.0f && r < INFINITY;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
                     acc[p] += f ? cov_fixed(m) : 0u;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
 // themselves (the first item of a split tile); the further items of split
 // tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
 // return at once.
-__global__ void __launch_bounds__(RT, 9) raster_items_kernel(RasterView view, uint32_t n_tiles,
+__global__ void __launch_bounds__(RT, 8) raster_items_kernel(RasterView view, uint32_t n_tiles,
                                                               const uint32_t* __restrict__ nsplit_of,
                                                               const int32_t* __restrict__ split_slot,
                                                               const uint2* __restrict__ extra,

@@ -83,6 +83,29 @@ __device__ __forceinline__ float plane_distance(float dgx, float dgy, float dgz,
     return fmaf(dgx, n.x, fmaf(dgy, n.y, fmaf(dgz, n.z, n.w)));
 }
 
+// The same two distances for two pixels at once (x: the first pixel, y: the
+// second) in the packed FP32x2 arithmetic of sm_100+: one instruction per
+// two FMAs, adds or multiplies.  Each component is the scalar
+// function's IEEE result bit for bit -- the same operations in the same
+// order, each rounded once -- so packed and scalar kernels classify every
+// (pixel, triangle) pair identically.
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 miter_distance2(float2 dgx, float2 dgy, float2 dgz, const float4& e, const float4& b,
+                                                  float2 eg)
+{
+    const float2 mx = __fadd2_rn(dgx, bcast2(-e.x)), my = __fadd2_rn(dgy, bcast2(-e.y)),
+                 mz = __fadd2_rn(dgz, bcast2(-e.z));
+    const float2 q = __ffma2_rn(mx, mx, __ffma2_rn(my, my, __fmul2_rn(mz, mz)));
+    // b.y - q as fma(q, -1, b.y): the exact difference, rounded once
+    return __fmul2_rn(__fadd2_rn(__ffma2_rn(q, bcast2(-1.0f), bcast2(b.y)), eg), bcast2(b.z));
+}
+
+__device__ __forceinline__ float2 plane_distance2(float2 dgx, float2 dgy, float2 dgz, const float4& n)
+{
+    return __ffma2_rn(dgx, bcast2(n.x), __ffma2_rn(dgy, bcast2(n.y), __ffma2_rn(dgz, bcast2(n.z), bcast2(n.w))));
+}
+
 // Coverage in 2^-22 fixed point.  m in [0, 1]: fma(m, 2^22, 2^23) lies in
 // [2^23, 2^24), where the float spacing is 1, so its single rounding leaves
 // round-to-nearest(m 2^22) in the low mantissa bits.  Sums of these terms
