@@ -62,13 +62,20 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
     return universal_dir(x, y, p, v);
 }
 
-// Block-wide reduction of the tile cone from per-thread (valid, G, h).
-// Every thread of the block calls it; blockDim.x is a multiple of 32, <= 512.
+// Tile cone from per-pixel (valid, G, h), reduced by the TILE_PIX pixel
+// threads of a CTA (threads 0 .. TILE_PIX-1, all of which must call it; other
+// threads of the CTA must not) on named barrier 1: two rounds of warp
+// shuffles, each closed by one barrier.  Every thread forms the axis itself
+// from the eight warp partials (the same sums in the same order, so the same
+// bits everywhere), so no single thread's work sits between the barriers.
+constexpr int CONE_WARPS = TILE_PIX / 32;
+
+__device__ __forceinline__ void cone_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(TILE_PIX) : "memory"); }
+
 __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom)
 {
-    __shared__ float red[4][16];
-    const int nwarps = blockDim.x >> 5;
-    __shared__ float axis_s[4];
+    __shared__ float4 part[CONE_WARPS];
+    __shared__ float2 part2[CONE_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float sx = valid ? G.x : 0.0f, sy = valid ? G.y : 0.0f, sz = valid ? G.z : 0.0f, cnt = valid ? 1.0f : 0.0f;
     for (int o = 16; o; o >>= 1) {
@@ -77,63 +84,48 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
-    if (lane == 0) {
-        red[0][warp] = sx;
-        red[1][warp] = sy;
-        red[2][warp] = sz;
-        red[3][warp] = cnt;
+    if (lane == 0) part[warp] = make_float4(sx, sy, sz, cnt);
+    cone_barrier();
+    float a = 0.0f, b = 0.0f, c = 0.0f, n = 0.0f;
+#pragma unroll
+    for (int w = 0; w < CONE_WARPS; ++w) {
+        const float4 q = part[w];
+        a += q.x;
+        b += q.y;
+        c += q.z;
+        n += q.w;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float a = 0, b = 0, c = 0, n = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            a += red[0][w];
-            b += red[1][w];
-            c += red[2][w];
-            n += red[3][w];
-        }
-        float len = sqrtf(a * a + b * b + c * c);
-        if (len > 1e-6f * fmaxf(n, 1.0f)) {
-            axis_s[0] = a / len;
-            axis_s[1] = b / len;
-            axis_s[2] = c / len;
-        } else {
-            axis_s[0] = 0.0f;
-            axis_s[1] = 0.0f;
-            axis_s[2] = 1.0f;
-        }
-        axis_s[3] = n;
+    const float len = sqrtf(a * a + b * b + c * c);
+    float ax = 0.0f, ay = 0.0f, az = 1.0f;
+    if (len > 1e-6f * fmaxf(n, 1.0f)) {
+        ax = a / len;
+        ay = b / len;
+        az = c / len;
     }
-    __syncthreads();
-    float ax = axis_s[0], ay = axis_s[1], az = axis_s[2], n = axis_s[3];
     float cmin = valid ? G.x * ax + G.y * ay + G.z * az : 2.0f;
     float hmax = valid ? h : 0.0f;
     for (int o = 16; o; o >>= 1) {
         cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
         hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
     }
-    __syncthreads();
-    if (lane == 0) {
-        red[0][warp] = cmin;
-        red[1][warp] = hmax;
-    }
-    __syncthreads();
+    if (lane == 0) part2[warp] = make_float2(cmin, hmax);
+    cone_barrier();
     if (threadIdx.x == 0) {
-        float c = 2.0f, hh = 0.0f;
-        for (int w = 0; w < nwarps; ++w) {
-            c = fminf(c, red[0][w]);
-            hh = fmaxf(hh, red[1][w]);
+        float cm = 2.0f, hh = 0.0f;
+#pragma unroll
+        for (int w = 0; w < CONE_WARPS; ++w) {
+            cm = fminf(cm, part2[w].x);
+            hh = fmaxf(hh, part2[w].y);
         }
         // widen by a margin that covers the FP32 rounding of the dot products
-        float ca = fmaxf(-1.0f, fminf(1.0f, c - 2e-6f));
+        float ca = fmaxf(-1.0f, fminf(1.0f, cm - 2e-6f));
         if (n == 0.0f) ca = 1.0f;
-        float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
+        const float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
         out->c0 = make_float4(ax, ay, az, ca);
         out->c1 = make_float4(sa, hh, n, 0.0f);
         // the tile's half-angle and the latitude / longitude of its axis, for
         // the tile index (the same functions the index would apply)
-        *geom = make_float4(acosf(fmaxf(-1.0f, fminf(1.0f, ca))), asinf(fmaxf(-1.0f, fminf(1.0f, ay))),
-                            atan2f(ax, az), n > 0.0f ? hh : -1.0f);
+        *geom = make_float4(acosf(ca), asinf(fmaxf(-1.0f, fminf(1.0f, ay))), atan2f(ax, az), n > 0.0f ? hh : -1.0f);
     }
 }
 
@@ -150,27 +142,22 @@ constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation 
 // from, 2 float4 per pixel, for the per-fragment pixel step; the tile
 // cones then carry the widest ramp of either step.
 template <class F>
-__global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, float4* __restrict__ map,
+__global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn, float4* __restrict__ map,
                                                            Cone* __restrict__ tiles, float4* __restrict__ geom,
                                                            float4* __restrict__ deriv = nullptr)
 {
-    __shared__ float3 sv[HW * HW];
-    __shared__ unsigned char sok[HW * HW];
+    // map values of the tile and its halo: direction xyz, w = F's return value
+    __shared__ float4 sv[HW * HW];
     const int tx = blockIdx.x, ty = blockIdx.y;
     const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
     if (threadIdx.x < HW * HW) {
         const int q = threadIdx.x, qi = q % HW, qj = q / HW;
         float3 v = make_float3(0.0f, 0.0f, 0.0f);
         const int ok = fn(i0 + qi, j0 + qj, W, H, v);
-        sv[q] = v;
-        sok[q] = (unsigned char)ok;
+        sv[q] = make_float4(v.x, v.y, v.z, (float)ok);
     }
     __syncthreads();
-    if (threadIdx.x >= TILE_PIX) {
-        // the halo-only threads take part in the cone reduction's barriers
-        reduce_cone(false, make_float3(0.0f, 0.0f, 0.0f), 0.0f, &tiles[ty * gridDim.x + tx], &geom[ty * gridDim.x + tx]);
-        return;
-    }
+    if (threadIdx.x >= TILE_PIX) return;  // halo-only threads: done
     const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
     const int i = tx * TILE + li, j = ty * TILE + lj;
     const int c = (lj + 1) * HW + (li + 1);
@@ -179,32 +166,33 @@ __global__ void __launch_bounds__(MAP_THREADS) map_kernel(int W, int H, F fn, fl
     float h = 0.0f;
     if (i < W && j < H) {
         float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const unsigned char cc = sok[c];
-        if (cc) {
-            const float3 vc = sv[c];
-            const int L = c - 1, Rr = c + 1, U = c - HW, D = c + HW;
-            const bool uL = sok[L] == cc, uR = sok[Rr] == cc, uU = sok[U] == cc, uD = sok[D] == cc;
+        const float4 qc = sv[c];
+        const float cc = qc.w;
+        if (cc != 0.0f) {
+            const float3 vc = make_float3(qc.x, qc.y, qc.z);
+            const float4 qL = sv[c - 1], qR = sv[c + 1], qU = sv[c - HW], qD = sv[c + HW];
+            const bool uL = qL.w == cc, uR = qR.w == cc, uU = qU.w == cc, uD = qD.w == cc;
             float fw = 0.0f;
             float dv[6];
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
-                auto get = [&](int q) { return comp == 0 ? sv[q].x : (comp == 1 ? sv[q].y : sv[q].z); };
-                float vcc = comp == 0 ? vc.x : (comp == 1 ? vc.y : vc.z);
+                auto get = [&](const float4& q) { return comp == 0 ? q.x : (comp == 1 ? q.y : q.z); };
+                const float vcc = comp == 0 ? vc.x : (comp == 1 ? vc.y : vc.z);
                 float di, dj;
                 if (uL && uR)
-                    di = (get(Rr) - get(L)) * 0.5f;
+                    di = (get(qR) - get(qL)) * 0.5f;
                 else if (uR)
-                    di = get(Rr) - vcc;
+                    di = get(qR) - vcc;
                 else if (uL)
-                    di = vcc - get(L);
+                    di = vcc - get(qL);
                 else
                     di = 0.0f;
                 if (uU && uD)
-                    dj = (get(D) - get(U)) * 0.5f;
+                    dj = (get(qD) - get(qU)) * 0.5f;
                 else if (uD)
-                    dj = get(D) - vcc;
+                    dj = get(qD) - vcc;
                 else if (uU)
-                    dj = vcc - get(U);
+                    dj = vcc - get(qU);
                 else
                     dj = 0.0f;
                 fw = fmaxf(fw, fabsf(di) + fabsf(dj));
