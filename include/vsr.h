@@ -281,12 +281,16 @@ vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene s, uint32_t* id_dev, float* d
 vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
 
 /* ---- end to end from host memory ------------------------------------------
- * vsr_render_host: one call from host buffers: copies `tris_host` ([T][3][3]
- * FP32, host) to the device, re-runs the set-up of the work scene `s` (a
- * handle from vsr_scene_create, whose device buffers are reused across
- * calls), rasterizes into the map and copies id/depth/cov (W*H each, host;
- * any may be NULL) back, then synchronises `stream`.  Same outputs as
- * vsr_raster. */
+ * vsr_render_host: one call from host buffers: re-runs the set-up of the
+ * work scene `s` (a handle from vsr_scene_create, whose device buffers are
+ * reused across calls) on `tris_host` ([T][3][3] FP32, host), rasterizes
+ * into the map and returns id/depth/cov (W*H each, host; any may be NULL),
+ * then synchronises `stream`.  Same outputs as vsr_raster.
+ * Buffers in pinned host memory mapped into the device's address space
+ * (cudaHostAlloc, cudaMallocHost, torch pin_memory) are read and written in
+ * place by the kernels over the host link, so the transfers overlap the
+ * set-up and raster kernels; other host memory is staged through device
+ * buffers with copies before and after them. */
 vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
 

@@ -95,6 +95,19 @@ void map_release(vsr_map m)
     m->idx = TileIndex{};
 }
 
+// Device address of host memory that kernels can read and write in place
+// (pinned and mapped into the current device's address space), else NULL.
+void* mapped_host(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 32768 && H <= 32768; }
 
 vsr_status check_params(const vsr_map_params* p)
@@ -601,37 +614,48 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
     if (!m || !sc || !setup_args_ok(tris_host, T, cam)) return VSR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     vsr_status s;
-    if (T > sc->tris_alloc) {
-        cudaFree(sc->tris_dev);
-        sc->tris_dev = nullptr;
-        sc->tris_alloc = 0;
-        if ((s = dalloc(&sc->tris_dev, (size_t)T * 9)) != VSR_OK) return s;
-        sc->tris_alloc = T;
-    }
     const size_t npix = (size_t)m->p.W * m->p.H;
-    if (12 * npix > sc->out_alloc) {
-        cudaFree(sc->out_dev);
-        sc->out_dev = nullptr;
-        sc->out_alloc = 0;
-        if (cudaMalloc(&sc->out_dev, 12 * npix) != cudaSuccess) {
-            cudaGetLastError();
-            return VSR_ERR_OOM;
+    // Host buffers the GPU can address in place (pinned memory mapped into
+    // its address space) are read by the set-up kernel and written by the
+    // raster kernel directly over the host link, so the transfers overlap
+    // the kernels; other host memory is staged through device buffers.
+    const float* tris_src = T > 0 ? (const float*)mapped_host(tris_host) : nullptr;
+    uint32_t* id_d = (uint32_t*)mapped_host(id_host);
+    float* depth_d = (float*)mapped_host(depth_host);
+    float* cov_d = (float*)mapped_host(cov_host);
+    if (T > 0 && !tris_src) {
+        if (T > sc->tris_alloc) {
+            cudaFree(sc->tris_dev);
+            sc->tris_dev = nullptr;
+            sc->tris_alloc = 0;
+            if ((s = dalloc(&sc->tris_dev, (size_t)T * 9)) != VSR_OK) return s;
+            sc->tris_alloc = T;
         }
-        sc->out_alloc = 12 * npix;
-    }
-    uint32_t* id_d = (uint32_t*)sc->out_dev;
-    float* depth_d = (float*)((char*)sc->out_dev + 4 * npix);
-    float* cov_d = (float*)((char*)sc->out_dev + 8 * npix);
-    if (T > 0)
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->tris_dev, tris_host, sizeof(float) * 9 * (size_t)T, cudaMemcpyHostToDevice,
                                      st));
-    if ((s = scene_setup(sc, sc->tris_dev, T, cam, st)) != VSR_OK) return s;
-    if ((s = vsr_raster_ex(m, sc, id_host ? id_d : nullptr, depth_host ? depth_d : nullptr,
-                           cov_host ? cov_d : nullptr, nullptr, stream)) != VSR_OK)
-        return s;
-    if (id_host) VSR_CUDA_TRY(cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st));
-    if (depth_host) VSR_CUDA_TRY(cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st));
-    if (cov_host) VSR_CUDA_TRY(cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+        tris_src = sc->tris_dev;
+    }
+    const bool stage_id = id_host && !id_d, stage_depth = depth_host && !depth_d, stage_cov = cov_host && !cov_d;
+    if (stage_id || stage_depth || stage_cov) {
+        if (12 * npix > sc->out_alloc) {
+            cudaFree(sc->out_dev);
+            sc->out_dev = nullptr;
+            sc->out_alloc = 0;
+            if (cudaMalloc(&sc->out_dev, 12 * npix) != cudaSuccess) {
+                cudaGetLastError();
+                return VSR_ERR_OOM;
+            }
+            sc->out_alloc = 12 * npix;
+        }
+        if (stage_id) id_d = (uint32_t*)sc->out_dev;
+        if (stage_depth) depth_d = (float*)((char*)sc->out_dev + 4 * npix);
+        if (stage_cov) cov_d = (float*)((char*)sc->out_dev + 8 * npix);
+    }
+    if ((s = scene_setup(sc, tris_src, T, cam, st)) != VSR_OK) return s;
+    if ((s = vsr_raster_ex(m, sc, id_d, depth_d, cov_d, nullptr, stream)) != VSR_OK) return s;
+    if (stage_id) VSR_CUDA_TRY(cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+    if (stage_depth) VSR_CUDA_TRY(cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st));
+    if (stage_cov) VSR_CUDA_TRY(cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st));
     VSR_CUDA_TRY(cudaStreamSynchronize(st));
     return VSR_OK;
 }

@@ -253,6 +253,35 @@ def test_render_host_matches_device_path(vsr):
             assert np.array_equal(dev[k].view(np.uint32), host[k].view(np.uint32))
 
 
+def test_render_host_pinned_in_place(vsr):
+    """Pinned (mapped) host buffers are read and written in place by the
+    kernels; the outputs equal the device path's bit for bit, also when only
+    some buffers are pinned (the rest staged)."""
+    lens, tris, cam = scenes.tiny_scene()
+    H, W = lens["H"], lens["W"]
+    m = vsr.Map(W, H, lens["k"], lens["l"], lens["s"], lens["omega"])
+    dev = _gpu_outputs(vsr.raster(m, vsr.Scene(torch.from_numpy(tris).cuda(), cam)))
+    tris_pin = torch.from_numpy(tris).pin_memory().numpy()
+    work = vsr.Scene()
+    for pin_outputs in (("id", "depth", "cov"), ("cov",), ()):
+        out = {}
+        for k, dt in (("id", torch.int32), ("depth", torch.float32), ("cov", torch.float32)):
+            buf = torch.full((H, W), 7, dtype=dt)
+            out[k] = (buf.pin_memory() if k in pin_outputs else buf).numpy()
+        out["id"] = out["id"].view(np.uint32)
+        for _ in range(2):
+            host = vsr.render_host(m, work, tris_pin, cam, out=out)
+            for k in dev:
+                assert np.array_equal(dev[k].view(np.uint32), host[k].view(np.uint32)), (pin_outputs, k)
+    # pageable triangles with pinned outputs
+    out = {k: torch.zeros((H, W), dtype=dt).pin_memory().numpy()
+           for k, dt in (("id", torch.int32), ("depth", torch.float32), ("cov", torch.float32))}
+    out["id"] = out["id"].view(np.uint32)
+    host = vsr.render_host(m, work, tris, cam, out=out)
+    for k in dev:
+        assert np.array_equal(dev[k].view(np.uint32), host[k].view(np.uint32))
+
+
 def test_invalid_arguments(vsr):
     L = vsr.load()
     import ctypes
