@@ -187,8 +187,7 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __res
 // chunks of BIN_BIG_CHUNK cones counts as further pairs -- are concatenated
 // in lane order and handed out one pair per lane per round, so the
 // dependent loads of the search run on all lanes at once instead of one
-// lane walking its whole window; each lane tests its range four cones at a
-// time.
+// lane walking its whole window.
 //
 // count: counts[tile] += 1 per hit (no value returned, so nothing waits),
 // and the hit is recorded as (tile, triangle) in the pair list -- staged per
@@ -206,7 +205,9 @@ constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full
 
 // FILL: false = count + record, true = fill by searching again
 template <bool FILL>
-__global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids, uint32_t cap,
+// 12 CTAs per SM (40 registers): the search is bound by load latency, so
+// resident warps count for more than cones fetched ahead by each lane
+__global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids, uint32_t cap,
                                                    int* status)
 {
     const unsigned FULL = 0xffffffffu;
@@ -314,36 +315,29 @@ __global__ void __launch_bounds__(128) bin_kernel(BinView v, int T, uint32_t* __
                 list = v.big;
             }
         }
-        for (uint32_t k0 = a; k0 < b; k0 += 4) {
-            Cone c[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (k0 + e < b) c[e] = list[k0 + e];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (k0 + e >= b) break;
-                // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
-                const float cg = fmaf(tx, c[e].c0.x, fmaf(ty, c[e].c0.y, tz * c[e].c0.z));
-                if (!(tcb + c[e].c0.w <= 2e-6f || cg >= fmaf(c[e].c0.w, tcb, -c[e].c1.x * tsb) - 2e-6f)) continue;
-                const uint32_t tile = __float_as_uint(c[e].c1.z);
-                if (!FILL) {
-                    atomicAdd(&v.counts[tile], 1u);
-                    if (v.pairs) {
-                        const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
-                        if (j < BIN_STAGE) {
-                            s_hit[warp][j] = make_uint2(tile, tt);
-                        } else {  // a round with more hits than the stage holds: straight to the list
-                            const uint32_t g = atomicAdd(v.cursor, 1u);
-                            if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
-                        }
+        for (uint32_t k = a; k < b; ++k) {
+            const Cone c = list[k];
+            // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
+            const float cg = fmaf(tx, c.c0.x, fmaf(ty, c.c0.y, tz * c.c0.z));
+            if (!(tcb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, tcb, -c.c1.x * tsb) - 2e-6f)) continue;
+            const uint32_t tile = __float_as_uint(c.c1.z);
+            if (!FILL) {
+                atomicAdd(&v.counts[tile], 1u);
+                if (v.pairs) {
+                    const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
+                    if (j < BIN_STAGE) {
+                        s_hit[warp][j] = make_uint2(tile, tt);
+                    } else {  // a round with more hits than the stage holds: straight to the list
+                        const uint32_t g = atomicAdd(v.cursor, 1u);
+                        if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
                     }
-                } else {
-                    const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
-                    if (pos < cap && pos < v.offsets[tile + 1])
-                        ids[pos] = tt;
-                    else
-                        raise_status(status, VSR_ERR_BIN_OVERFLOW);
                 }
+            } else {
+                const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
+                if (pos < cap && pos < v.offsets[tile + 1])
+                    ids[pos] = tt;
+                else
+                    raise_status(status, VSR_ERR_BIN_OVERFLOW);
             }
         }
         if (!FILL && v.pairs) {
