@@ -73,6 +73,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
+    m->idx.ntiles = (uint32_t)nt;
     if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }

@@ -215,11 +215,18 @@ __global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (FILL && v.pairs && *v.cursor <= v.pair_cap) return;  // the pair list is complete: bin_pairs_kernel fills
     const size_t TT = (size_t)T;
-    const TileIndexHdr* __restrict__ hp = v.hdr;
-    const int nlat = hp->nlat, nlon = hp->nlon;
-    const float cell = hp->cell;
-    const float amax = __uint_as_float(hp->alpha_small_max), hmax = __uint_as_float(hp->h_max);
-    const uint32_t nbig = hp->n_big;
+    // The index header, with every count that becomes an index clamped to
+    // the arrays it indexes (identity for an index built by launch_tile_index),
+    // so that no index content can make this kernel read or write out of
+    // bounds.
+    TileIndexHdr h;
+    h.nlat = min(max(v.hdr->nlat, 1), IDX_NLAT_MAX);
+    h.nlon = 2 * h.nlat;
+    h.cell = v.hdr->cell;
+    const int nlat = h.nlat, nlon = h.nlon;
+    const float cell = h.cell;
+    const float amax = __uint_as_float(v.hdr->alpha_small_max), hmax = __uint_as_float(v.hdr->h_max);
+    const uint32_t nbig = min(v.hdr->n_big, v.ntiles);
     const int bigpairs = (int)((nbig + BIN_BIG_CHUNK - 1) / BIN_BIG_CHUNK);
     __shared__ uint2 s_hit[4][BIN_STAGE];
     __shared__ uint32_t s_nhit[4];
@@ -253,14 +260,14 @@ __global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t
             if (gamma < PI_F) {
                 const float lat = asinf(fmaxf(-1.0f, fminf(1.0f, sy)));
                 const float lon = atan2f(sx, sz);
-                r0 = cell_row(lat - gamma, *hp);
-                r1 = cell_row(lat + gamma, *hp);
+                r0 = cell_row(lat - gamma, h);
+                r1 = cell_row(lat + gamma, h);
                 if (fabsf(lat) + gamma < 0.5f * PI_F - 1e-3f) {
                     // longitude half-width of a cap that holds no pole
                     const float dl = asinf(fminf(1.0f, sinf(gamma) / cosf(lat))) + 1e-4f;
                     c0i = (int)floorf((lon - dl + PI_F) / cell);
                     const int c1i = (int)floorf((lon + dl + PI_F) / cell);
-                    ncol = min(nlon, c1i - c0i + 1);
+                    ncol = max(1, min(nlon, c1i - c0i + 1));
                     c0i %= nlon;
                     if (c0i < 0) c0i += nlon;
                 }
@@ -314,6 +321,8 @@ __global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t
                 b = min(nbig, a + BIN_BIG_CHUNK);
                 list = v.big;
             }
+            b = min(b, v.ntiles);
+            a = min(a, b);
         }
         for (uint32_t k = a; k < b; ++k) {
             const Cone c = list[k];
@@ -321,6 +330,7 @@ __global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t
             const float cg = fmaf(tx, c.c0.x, fmaf(ty, c.c0.y, tz * c.c0.z));
             if (!(tcb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, tcb, -c.c1.x * tsb) - 2e-6f)) continue;
             const uint32_t tile = __float_as_uint(c.c1.z);
+            if (tile >= v.ntiles) continue;
             if (!FILL) {
                 atomicAdd(&v.counts[tile], 1u);
                 if (v.pairs) {
@@ -463,7 +473,8 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
                             uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep)
 {
     if (T == 0) return VSR_OK;
-    const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, nullptr, pairs, pair_cap, cursor, pstep};
+    const BinView v{idx.hdr,  idx.cell_start, idx.sorted, idx.big, rec,   counts,
+                    nullptr,  pairs,          pair_cap,   cursor,  pstep, idx.ntiles};
     bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
@@ -475,7 +486,7 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
 {
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, offsets, const_cast<uint2*>(pairs),
-                    pair_cap, const_cast<uint32_t*>(cursor), pstep};
+                    pair_cap, const_cast<uint32_t*>(cursor), pstep, idx.ntiles};
     if (pairs) {
         constexpr int BIN_PAIR_BLOCKS = 152 * 8;
         bin_pairs_kernel<<<BIN_PAIR_BLOCKS, 256, 0, st>>>(pairs, cursor, pair_cap, offsets, counts, ids, cap,

@@ -61,6 +61,10 @@ struct MapEntry {
     vsr_map map = nullptr;
     size_t bytes = 0;
     int refs = 0;
+    // recorded after the map's generation on the stream of the slot that
+    // made it; a slot on another stream that takes the cached map waits for
+    // it on its own stream before reading the map, cones or tile index
+    cudaEvent_t ready = nullptr;
 };
 
 struct Request {
@@ -171,6 +175,11 @@ struct vsr_server_s {
         MapKey key{p.k, p.l, p.s, p.omega_deg, p.W, p.H, p.aov, p.strict_limits};
         auto it = index.find(key);
         if (it != index.end() && used() + extra_need <= (size_t)cfg.budget_bytes) {
+            if (cudaStreamWaitEvent(st, it->second->ready, 0) != cudaSuccess) {
+                cudaGetLastError();
+                *err = VSR_ERR_CUDA;
+                return false;
+            }
             cache.splice(cache.begin(), cache, it->second);
             *out = cache.begin();
             *hit = true;
@@ -178,6 +187,25 @@ struct vsr_server_s {
             return true;
         }
         const size_t need = (it != index.end() ? 0 : map_bytes(p.W, p.H)) + extra_need;
+        // a new map over the budget first takes the place of the least
+        // recently used idle map of its own size: that handle is regenerated
+        // in place (vsr_map_update), which needs no cudaFree -- a
+        // device-wide synchronisation -- and no cudaMalloc
+        vsr_map reuse = nullptr;
+        if (it == index.end() && used() + need > (size_t)cfg.budget_bytes) {
+            for (auto e = cache.end(); e != cache.begin();) {
+                --e;
+                if (e->refs == 0 && e->key.W == p.W && e->key.H == p.H) {
+                    map_bytes_used -= e->bytes;
+                    index.erase(e->key);
+                    reuse = e->map;
+                    if (e->ready) cudaEventDestroy(e->ready);
+                    cache.erase(e);
+                    ++stats.map_evictions;
+                    break;
+                }
+            }
+        }
         // evict idle entries, least recently used first
         for (auto e = cache.end(); e != cache.begin();) {
             --e;
@@ -187,29 +215,46 @@ struct vsr_server_s {
                 map_bytes_used -= e->bytes;
                 index.erase(e->key);
                 vsr_map_free(e->map);
+                if (e->ready) cudaEventDestroy(e->ready);
                 e = cache.erase(e);
                 ++stats.map_evictions;
             }
         }
         if (used() + need > (size_t)cfg.budget_bytes) {
+            if (reuse) vsr_map_free(reuse);
             *err = VSR_ERR_BUDGET;
             return false;
         }
         if (it != index.end()) {  // a hit that needed room for its workspace
+            if (cudaStreamWaitEvent(st, it->second->ready, 0) != cudaSuccess) {
+                cudaGetLastError();
+                *err = VSR_ERR_CUDA;
+                return false;
+            }
             cache.splice(cache.begin(), cache, it->second);
             *out = cache.begin();
             *hit = true;
             ++stats.map_hits;
             return true;
         }
-        vsr_map m = nullptr;
-        vsr_status s = vsr_make_map_ex(&p, st, &m);
+        vsr_map m = reuse;
+        vsr_status s = reuse ? vsr_map_update(reuse, &p, st) : vsr_make_map_ex(&p, st, &m);
         if (s != VSR_OK) {
+            if (reuse) vsr_map_free(reuse);
             *err = s;
             return false;
         }
+        cudaEvent_t ready = nullptr;
+        if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ready, st) != cudaSuccess) {
+            cudaGetLastError();
+            if (ready) cudaEventDestroy(ready);
+            vsr_map_free(m);
+            *err = VSR_ERR_CUDA;
+            return false;
+        }
         const size_t mb = map_bytes(p.W, p.H);
-        cache.push_front(MapEntry{key, m, mb, 0});
+        cache.push_front(MapEntry{key, m, mb, 0, ready});
         index[key] = cache.begin();
         map_bytes_used += mb;
         *out = cache.begin();
@@ -236,7 +281,19 @@ struct vsr_server_s {
             bool progressed = false;
             // completions
             for (Slot& sl : slots) {
-                if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
+                if (!sl.busy) continue;
+                const cudaError_t q = cudaEventQuery(sl.done);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) {
+                    // the slot's work failed on the device: report it instead
+                    // of waiting for an event that will not complete
+                    cudaGetLastError();
+                    sl.map->refs--;
+                    finish(sl.req, VSR_ERR_CUDA, sl.t_start, sl.hit);
+                    sl.busy = false;
+                    progressed = true;
+                    continue;
+                }
                 vsr_scene_s* w = sl.work;
                 if (*w->h_total > w->cap && sl.req.reruns < 3) {
                     // the bins overflowed: vsr_bin grows them from this count; render again
@@ -445,7 +502,10 @@ vsr_status vsr_serve_destroy(vsr_server s)
     for (auto& per_slot : s->work)
         for (vsr_scene w : per_slot) vsr_scene_free(w);
     for (Slot& sl : s->slots) cudaFree(sl.status);
-    for (MapEntry& e : s->cache) vsr_map_free(e.map);
+    for (MapEntry& e : s->cache) {
+        vsr_map_free(e.map);
+        if (e.ready) cudaEventDestroy(e.ready);
+    }
     delete s;
     return VSR_OK;
 }

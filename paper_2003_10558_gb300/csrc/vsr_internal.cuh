@@ -123,6 +123,7 @@ struct TileIndex {
     float4* geom;          // ntiles: (alpha, latitude, longitude of the axis, h), h = -1 if the tile is empty;
                            // written with the cones by the map kernels
     uint32_t* cell_count;  // IDX_CELLS_MAX: scratch of the build
+    uint32_t ntiles;       // tiles of the map (the length of sorted, big and geom)
 };
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
 // binning of one frame: counts and cursor zeroed by the caller ->
@@ -169,6 +170,7 @@ struct BinView {
     uint32_t pair_cap;
     uint32_t* cursor;   // hits recorded (may exceed pair_cap: the list is then incomplete)
     int pstep;          // bins for the per-fragment pixel step (wider caps, see pstep_cap)
+    uint32_t ntiles;    // tiles of the map: every index read from the tile index is clamped to it
 };
 
 // The cap that holds every fragment of the per-fragment pixel step

@@ -62,6 +62,35 @@ def test_results_alone_equal_results_in_the_mix(vsr):
     srv.close()
 
 
+def test_cached_map_shared_while_it_is_made(vsr):
+    """Requests on other slots that take a map from the cache while the slot
+    that made it is still generating it (a 2048 x 2048 map, scenes of a few
+    hundred triangles whose set-up ends long before the map) must wait for
+    it: every result equals the same request rendered alone."""
+    tris = torch.from_numpy(scenes.random_triangles(400, 1.0, 20.0, 0.05, seed=7)).cuda()
+    lens = dict(W=2048, H=2048, k=0.3, l=0.8, s=0.9, omega=200.0)
+    srv = vsr.Server(budget_bytes=8 << 30, slots=4)
+    sid = srv.add_scene(tris)
+    rng = np.random.default_rng(8)
+    reqs = []
+    for _ in range(8):
+        cam = scenes.camera(rng.uniform(-0.5, 0.5, 3))
+        out = _out(lens)
+        reqs.append((cam, out, srv.submit(sid, lens, cam, out)))
+    for cam, out, t in reqs:
+        r = srv.wait(t)
+        assert r["done"] and r["status"] == 0
+    st = srv.stats()
+    assert st["map_misses"] == 1 and st["map_hits"] == 7
+    torch.cuda.synchronize()
+    m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    for cam, out, t in reqs:
+        alone = vsr.raster(m, vsr.Scene(tris, cam))
+        for k in ("id", "depth", "cov"):
+            assert torch.equal(alone[k], out[k]), k
+    srv.close()
+
+
 def test_budget_cancel_and_invalid(vsr):
     tris = torch.from_numpy(scenes.random_triangles(2000, 1.0, 20.0, 0.05, seed=5)).cuda()
     lens = dict(W=256, H=256, k=0.0, l=1.0, s=1.0, omega=180.0)
