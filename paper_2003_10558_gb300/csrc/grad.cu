@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
                 for (int p = 0; p < PPT; ++p) {
                     const float D = plane_distance(dgx[p], dgy[p], dgz[p], pl);
                     const float r = __fdividef(b.w, D);
-                    const bool f = frag[p] && r > 0.0f && r < INFINITY;
+                    const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;  // 0 < r < inf
                     if (!f) continue;
                     if (FILL) {
                         const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));

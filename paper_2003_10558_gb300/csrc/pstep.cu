@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(PT) raster_pstep_kernel(RasterView v, const fl
                                       g4 > -0.5f * w4;
                     const float D = plane_distance(dgx[p], dgy[p], dgz[p], pl);
                     const float r = __fdividef(b.w, D);
-                    const bool f = frag && r > 0.0f && r < INFINITY;
+                    const bool f = frag && __float_as_uint(r) - 1u < 0x7f7fffffu;  // 0 < r < inf
                     const float m = fminf(fminf(__saturatef(__fdividef(g1, fmaxf(w1, 1e-30f)) + 0.5f),
                                                 __saturatef(__fdividef(g2, fmaxf(w2, 1e-30f)) + 0.5f)),
                                           fminf(__saturatef(__fdividef(g3, fmaxf(w3, 1e-30f)) + 0.5f),

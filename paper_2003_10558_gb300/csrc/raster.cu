@@ -235,7 +235,8 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 for (int p = 0; p < PPT; ++p) {
                     // predicated: every lane computes, non-fragments add nothing
                     const float r = __fdividef(b.w, D2[p]);
-                    const bool f = frag[p] && r > 0.0f && r < INFINITY;
+                    // 0 < r < inf (NaN excluded) as one unsigned compare of the bits
+                    const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
                     acc[p] += f ? cov_fixed(m) : 0u;
                     // centre-inside: all three edge distances >= 0, exact zeros by the tie rule

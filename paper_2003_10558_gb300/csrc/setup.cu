@@ -83,18 +83,26 @@ __global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tr
 #pragma unroll
     for (int q = 0; q < 9; ++q) w[q] = tris[(size_t)t * 9 + q];
 
+    // an identity rotation (the common camera) needs only the exact
+    // differences A - O: the pair products by 1 and sums with 0 of the
+    // general transform return those pairs unchanged
+    bool ident = true;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ident = ident && cam.M[q] == ((q % 4 == 0) ? 1.0f : 0.0f);
     df3 V[3];
     bool at_eye = false;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        df d0 = two_sum(w[3 * q + 0], -cam.O[0]);
-        df d1 = two_sum(w[3 * q + 1], -cam.O[1]);
-        df d2 = two_sum(w[3 * q + 2], -cam.O[2]);
-        df c[3];
+        const df d0 = two_sum(w[3 * q + 0], -cam.O[0]);
+        const df d1 = two_sum(w[3 * q + 1], -cam.O[1]);
+        const df d2 = two_sum(w[3 * q + 2], -cam.O[2]);
+        df c[3] = {d0, d1, d2};
+        if (!ident) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-            c[r] = df_add(df_add(df_mul_f(d0, cam.M[3 * r + 0]), df_mul_f(d1, cam.M[3 * r + 1])),
-                          df_mul_f(d2, cam.M[3 * r + 2]));
+            for (int r = 0; r < 3; ++r)
+                c[r] = df_add(df_add(df_mul_f(d0, cam.M[3 * r + 0]), df_mul_f(d1, cam.M[3 * r + 1])),
+                              df_mul_f(d2, cam.M[3 * r + 2]));
+        }
         V[q] = {c[0], c[1], c[2]};
         at_eye |= (c[0].hi == 0.0f && c[1].hi == 0.0f && c[2].hi == 0.0f);
     }
