@@ -60,7 +60,7 @@ def parse():
                          "1M-triangle scene, batched launch vs per-view plain launches")
     ap.add_argument("--views", type=int, default=64)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
-    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per lens stream")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals per lens stream")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     return ap.parse_args()
 

@@ -207,7 +207,6 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 // the four distances of both pixels in packed FP32x2 arithmetic; the miter
                 // in chord form, G - S-hat = (G - a) - (S-hat - a): both differences are at
                 // most the tile radius, so their rounding costs ~1e-9 rad where it matters
-                const float4 a = st.s0[j];
                 const float4 b = st.s1[j];
                 const float4 e = st.s6[j];
                 const float2 g4p = miter_distance2(dgx2, dgy2, dgz2, e, b, eg2);
@@ -229,7 +228,6 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 if (!__any_sync(0xffffffffu, anyf)) continue;
                 const float2 Dp = plane_distance2(dgx2, dgy2, dgz2, st.s5[j]);
                 const float D2[PPT] = {Dp.x, Dp.y};
-                const unsigned ties = __float_as_uint(a.w);
                 const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
@@ -239,8 +237,16 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                     const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
                     const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
                     acc[p] += f ? cov_fixed(m) : 0u;
-                    // centre-inside: all three edge distances >= 0, exact zeros by the tie rule
-                    const bool in = f && centre_inside(g1[p], g2[p], g3[p], g3m[p], ties);
+                    // centre-inside: all three edge distances >= 0; an exact zero (rare)
+                    // takes the tie rule on the three distances, recomputed from the
+                    // staged planes (the scalar form gives the packed values bit for
+                    // bit), so they need not stay live in registers until here
+                    bool in = f && g3m[p] > 0.0f;
+                    if (f && g3m[p] == 0.0f)
+                        in = centre_inside(plane_distance(dgx[p], dgy[p], dgz[p], st.s2[j]),
+                                           plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
+                                           plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
+                                           __float_as_uint(st.s0[j].w));
                     const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
                     key[p] = in && k < key[p] ? k : key[p];
                     if (STATS) cnt_in[p] += in;
