@@ -19,6 +19,8 @@
 // the raster kernel's result does not depend on it.
 #include <math.h>
 
+#include <atomic>
+
 
 #include "vsr_internal.cuh"
 
@@ -203,12 +205,14 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __res
 constexpr int BIN_BIG_CHUNK = 16;
 constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full)
 
-// FILL: false = count + record, true = fill by searching again
-template <bool FILL>
-// 12 CTAs per SM (40 registers): the search is bound by load latency, so
-// resident warps count for more than cones fetched ahead by each lane
-__global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids, uint32_t cap,
-                                                   int* status)
+// FILL: false = count + record, true = fill by searching again.
+// CB: cones each lane fetches per step.  The search is bound by load latency:
+// a grid larger than one resident wave hides it with warps (CB = 1: 40
+// registers, 12 CTAs per SM), a smaller one with loads in flight per lane
+// (CB = 4, 7 CTAs per SM).
+template <bool FILL, int CB>
+__global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids,
+                                                                     uint32_t cap, int* status)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -324,30 +328,38 @@ __global__ void __launch_bounds__(128, 12) bin_kernel(BinView v, int T, uint32_t
             b = min(b, v.ntiles);
             a = min(a, b);
         }
-        for (uint32_t k = a; k < b; ++k) {
-            const Cone c = list[k];
-            // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
-            const float cg = fmaf(tx, c.c0.x, fmaf(ty, c.c0.y, tz * c.c0.z));
-            if (!(tcb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, tcb, -c.c1.x * tsb) - 2e-6f)) continue;
-            const uint32_t tile = __float_as_uint(c.c1.z);
-            if (tile >= v.ntiles) continue;
-            if (!FILL) {
-                atomicAdd(&v.counts[tile], 1u);
-                if (v.pairs) {
-                    const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
-                    if (j < BIN_STAGE) {
-                        s_hit[warp][j] = make_uint2(tile, tt);
-                    } else {  // a round with more hits than the stage holds: straight to the list
-                        const uint32_t g = atomicAdd(v.cursor, 1u);
-                        if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
+        for (uint32_t k0 = a; k0 < b; k0 += CB) {
+            Cone cs[CB];
+#pragma unroll
+            for (int e = 0; e < CB; ++e)
+                if (k0 + e < b) cs[e] = list[k0 + e];
+#pragma unroll
+            for (int e = 0; e < CB; ++e) {
+                if (k0 + e >= b) break;
+                const Cone& c = cs[e];
+                // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
+                const float cg = fmaf(tx, c.c0.x, fmaf(ty, c.c0.y, tz * c.c0.z));
+                if (!(tcb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, tcb, -c.c1.x * tsb) - 2e-6f)) continue;
+                const uint32_t tile = __float_as_uint(c.c1.z);
+                if (tile >= v.ntiles) continue;
+                if (!FILL) {
+                    atomicAdd(&v.counts[tile], 1u);
+                    if (v.pairs) {
+                        const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
+                        if (j < BIN_STAGE) {
+                            s_hit[warp][j] = make_uint2(tile, tt);
+                        } else {  // a round with more hits than the stage holds: straight to the list
+                            const uint32_t g = atomicAdd(v.cursor, 1u);
+                            if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
+                        }
                     }
+                } else {
+                    const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
+                    if (pos < cap && pos < v.offsets[tile + 1])
+                        ids[pos] = tt;
+                    else
+                        raise_status(status, VSR_ERR_BIN_OVERFLOW);
                 }
-            } else {
-                const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
-                if (pos < cap && pos < v.offsets[tile + 1])
-                    ids[pos] = tt;
-                else
-                    raise_status(status, VSR_ERR_BIN_OVERFLOW);
             }
         }
         if (!FILL && v.pairs) {
@@ -469,13 +481,33 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
     return VSR_OK;
 }
 
+// SMs of the current device (looked up once per device), or -1.
+static int sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    const int slot = dev & 63;
+    int n = cache[slot].load();
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return -1;
+    cache[slot].store(n);
+    return n;
+}
+
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
                             uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep)
 {
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr,  idx.cell_start, idx.sorted, idx.big, rec,   counts,
                     nullptr,  pairs,          pair_cap,   cursor,  pstep, idx.ntiles};
-    bin_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
+    const int blocks = (T + 127) / 128;
+    int sms = 0;
+    if ((sms = sm_count()) < 0) return VSR_ERR_CUDA;
+    if (blocks > 7 * sms)
+        bin_kernel<false, 1><<<blocks, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
+    else
+        bin_kernel<false, 4><<<blocks, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -493,7 +525,13 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
                                                           status);
         VSR_CUDA_TRY(cudaGetLastError());
     }
-    bin_kernel<true><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status);
+    const int blocks = (T + 127) / 128;
+    int sms = 0;
+    if ((sms = sm_count()) < 0) return VSR_ERR_CUDA;
+    if (blocks > 7 * sms)
+        bin_kernel<true, 1><<<blocks, 128, 0, st>>>(v, T, ids, cap, status);
+    else
+        bin_kernel<true, 4><<<blocks, 128, 0, st>>>(v, T, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
