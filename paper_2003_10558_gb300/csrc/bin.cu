@@ -387,10 +387,15 @@ __global__ void __launch_bounds__(256) bin_pairs_kernel(const uint2* __restrict_
                                                          const uint32_t* __restrict__ cursor, uint32_t pair_cap,
                                                          const uint32_t* __restrict__ offsets,
                                                          uint32_t* __restrict__ counts, uint32_t* __restrict__ ids,
-                                                         uint32_t cap, int* status)
+                                                         uint32_t cap, int* status, int overflow_here)
 {
     const uint32_t n = *cursor;
-    if (n > pair_cap) return;  // incomplete: the search-based fill runs instead
+    if (n > pair_cap) {
+        // incomplete: the search-based fill runs instead -- or, when the list
+        // holds as many pairs as the bins, the bins overflow too: report it
+        if (overflow_here && blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
+        return;
+    }
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const uint2 e = pairs[p];
         const uint32_t pos = offsets[e.x] + atomicSub(&counts[e.x], 1u) - 1u;
@@ -519,12 +524,16 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr, idx.cell_start, idx.sorted, idx.big, rec, counts, offsets, const_cast<uint2*>(pairs),
                     pair_cap, const_cast<uint32_t*>(cursor), pstep, idx.ntiles};
+    // a pair list as long as the bins is complete unless the bins overflow,
+    // so the search-based fill is needed only without one or with a shorter one
+    const bool search = !pairs || pair_cap < cap;
     if (pairs) {
         constexpr int BIN_PAIR_BLOCKS = 152 * 8;
         bin_pairs_kernel<<<BIN_PAIR_BLOCKS, 256, 0, st>>>(pairs, cursor, pair_cap, offsets, counts, ids, cap,
-                                                          status);
+                                                          status, search ? 0 : 1);
         VSR_CUDA_TRY(cudaGetLastError());
     }
+    if (!search) return VSR_OK;
     const int blocks = (T + 127) / 128;
     int sms = 0;
     if ((sms = sm_count()) < 0) return VSR_ERR_CUDA;
