@@ -178,6 +178,110 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __res
     sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
 }
 
+// The whole index in one CTA, for maps of at most IDX_FUSED_TILES tiles: the
+// same four steps with the histogram, the per-cell counts and their scan in
+// shared memory (IDX_CELLS_MAX counters), closed by barriers instead of
+// kernel boundaries, and the header written once at the end -- one launch
+// and no memsets instead of four launches and two memsets.
+constexpr int IDX_FUSED_THREADS = 1024;
+constexpr int IDX_FUSED_TILES = 32768;
+constexpr size_t IDX_FUSED_SMEM = sizeof(uint32_t) * IDX_CELLS_MAX;
+
+__global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone* __restrict__ tiles,
+                                                                       const float4* __restrict__ geom, int ntiles,
+                                                                       TileIndexHdr* __restrict__ hdr,
+                                                                       uint32_t* __restrict__ cell_start,
+                                                                       Cone* __restrict__ sorted,
+                                                                       Cone* __restrict__ big)
+{
+    extern __shared__ uint32_t s_cell[];  // per-cell counts, then running slots
+    __shared__ TileIndexHdr s_h;
+    __shared__ uint32_t s_wsum[IDX_FUSED_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_h = TileIndexHdr{};
+    __syncthreads();
+    // 1. histogram of half-angles (one add per group of equal bins in a
+    // warp), valid tiles, widest ramp (one atomic per warp)
+    uint32_t nv = 0u, hm = 0u;
+    for (int base = 0; base < ntiles; base += IDX_FUSED_THREADS) {
+        const int i = base + tid;
+        const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+        const bool ok = g.w >= 0.0f;
+        const int bin = ok ? hist_bin(g.x) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h.hist[bin], (unsigned)__popc(peers));
+        nv += ok;
+        hm = max(hm, ok ? __float_as_uint(g.w) : 0u);  // non-negative floats order as their bits
+    }
+    for (int o = 16; o; o >>= 1) {
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    }
+    if (lane == 0 && nv) {
+        atomicAdd(&s_h.n_valid, nv);
+        atomicMax(&s_h.h_max, hm);
+    }
+    __syncthreads();
+    // 2. the grid plan
+    if (tid == 0) index_plan(&s_h, s_h);
+    __syncthreads();
+    const int ncell = s_h.ncell;
+    for (int c = tid; c < ncell; c += IDX_FUSED_THREADS) s_cell[c] = 0u;
+    __syncthreads();
+    // 3. per-cell counts; big tiles to their own list
+    uint32_t am = 0u;
+    for (int i = tid; i < ntiles; i += IDX_FUSED_THREADS) {
+        const float4 g = geom[i];
+        if (g.w < 0.0f) continue;
+        if (g.x > s_h.alpha_cut) {
+            big[atomicAdd(&s_h.n_big, 1u)] = index_entry(tiles[i], i);
+        } else {
+            atomicAdd(&s_cell[home_cell_geom(g, s_h)], 1u);
+            am = max(am, __float_as_uint(g.x));
+        }
+    }
+    for (int o = 16; o; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+    if (lane == 0 && am) atomicMax(&s_h.alpha_small_max, am);
+    __syncthreads();
+    // 4. exclusive scan of the counts: thread t owns the cells [t per, (t+1) per)
+    const int per = (ncell + IDX_FUSED_THREADS - 1) / IDX_FUSED_THREADS;
+    const int c0 = min(ncell, tid * per), c1 = min(ncell, c0 + per);
+    uint32_t local = 0;
+    for (int c = c0; c < c1; ++c) local += s_cell[c];
+    uint32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - local + (warp > 0 ? s_wsum[warp - 1] : 0u);
+    for (int c = c0; c < c1; ++c) {
+        const uint32_t n = s_cell[c];
+        s_cell[c] = run;
+        cell_start[c] = run;
+        run += n;
+    }
+    if (tid == IDX_FUSED_THREADS - 1) cell_start[ncell] = run;  // the last run ends at ncell
+    __syncthreads();
+    // 5. cell-sorted copies of the small tiles
+    for (int i = tid; i < ntiles; i += IDX_FUSED_THREADS) {
+        const float4 g = geom[i];
+        if (g.w < 0.0f || g.x > s_h.alpha_cut) continue;
+        sorted[atomicAdd(&s_cell[home_cell_geom(g, s_h)], 1u)] = index_entry(tiles[i], i);
+    }
+    if (tid == 0) *hdr = s_h;
+}
+
 // ---- per-triangle binning ---------------------------------------------------
 //
 // The candidate tiles of a triangle are the cones of its search window: the
@@ -467,6 +571,22 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
+    if (ntiles <= IDX_FUSED_TILES) {
+        // the shared-memory opt-in of the fused kernel, once per device
+        static std::atomic<uint64_t> attr_set{0};
+        int dev = 0;
+        VSR_CUDA_TRY(cudaGetDevice(&dev));
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!(attr_set.load() & bit)) {
+            VSR_CUDA_TRY(cudaFuncSetAttribute(idx_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)IDX_FUSED_SMEM));
+            attr_set.fetch_or(bit);
+        }
+        idx_fused_kernel<<<1, IDX_FUSED_THREADS, IDX_FUSED_SMEM, st>>>(tiles, idx.geom, ntiles, idx.hdr,
+                                                                        idx.cell_start, idx.sorted, idx.big);
+        VSR_CUDA_TRY(cudaGetLastError());
+        return VSR_OK;
+    }
     const int nb = (ntiles + IDX_THREADS - 1) / IDX_THREADS;
     VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
     VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));

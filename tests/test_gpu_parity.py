@@ -192,6 +192,19 @@ def test_single_view_workload_sampled(vsr):
     assert rep["n_valid"] == len(pixels)
 
 
+def test_large_map_grid_wide_tile_index(vsr):
+    """A 4096 x 2176 map has 34,816 tiles, more than the single-CTA tile index
+    takes, so its index is built by the grid-wide kernels: sampled pixels
+    against the oracle."""
+    lens = dict(W=4096, H=2176, k=0.0, l=1.0, s=1.0, omega=180.0)
+    tris = scenes.random_triangles(2000, 1.0, 20.0, 0.05, seed=21)
+    rng = np.random.default_rng(22)
+    pixels = rng.integers(0, lens["W"] * lens["H"], 4096)
+    m32, rec, exp, out = _raster_shared_map(vsr, lens, tris, scenes.camera(), pixels=pixels)
+    rep = compare(m32, rec, exp, _gpu_outputs(out), pixels=pixels)
+    assert rep["n_valid"] == len(pixels)
+
+
 def test_watertight_icosphere_gpu_map(vsr):
     """Level-5 icosphere around the eye on the GPU's own 1080p map: exactly
     one centre-inside triangle per pixel, coverage 1 away from vertices."""
