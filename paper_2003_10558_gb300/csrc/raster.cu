@@ -32,6 +32,8 @@
 // Work culling: the triangles of a chunk are first tested lane-parallel
 // (lane j <-> triangle j) against each warp's own 8x8-pixel view cone; the
 // surviving ones are then evaluated for all 64 pixels.
+#include <type_traits>
+
 #include "stage.cuh"
 
 namespace {
@@ -229,28 +231,41 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 const float2 Dp = plane_distance2(dgx2, dgy2, dgz2, st.s5[j]);
                 const float D2[PPT] = {Dp.x, Dp.y};
                 const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
+                // The exact-zero tie rule needs its branch only where some pixel of
+                // the warp has a fragment on an edge plane (rare): decide once for
+                // the warp, and run a copy of the loop without the branch otherwise.
+                auto post = [&](auto tie_t) {
+                    constexpr bool TIE = decltype(tie_t)::value;
 #pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    // predicated: every lane computes, non-fragments add nothing
-                    const float r = __fdividef(b.w, D2[p]);
-                    // 0 < r < inf (NaN excluded) as one unsigned compare of the bits
-                    const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
-                    const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
-                    acc[p] += f ? cov_fixed(m) : 0u;
-                    // centre-inside: all three edge distances >= 0; an exact zero (rare)
-                    // takes the tie rule on the three distances, recomputed from the
-                    // staged planes (the scalar form gives the packed values bit for
-                    // bit), so they need not stay live in registers until here
-                    bool in = f && g3m[p] > 0.0f;
-                    if (f && g3m[p] == 0.0f)
-                        in = centre_inside(plane_distance(dgx[p], dgy[p], dgz[p], st.s2[j]),
-                                           plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
-                                           plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
-                                           __float_as_uint(st.s0[j].w));
-                    const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
-                    key[p] = in && k < key[p] ? k : key[p];
-                    if (STATS) cnt_in[p] += in;
-                }
+                    for (int p = 0; p < PPT; ++p) {
+                        // predicated: every lane computes, non-fragments add nothing
+                        const float r = __fdividef(b.w, D2[p]);
+                        // 0 < r < inf (NaN excluded) as one unsigned compare of the bits
+                        const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
+                        const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
+                        acc[p] += f ? cov_fixed(m) : 0u;
+                        // centre-inside: all three edge distances >= 0; an exact zero
+                        // takes the tie rule on the three distances, recomputed from
+                        // the staged planes (the scalar form gives the packed values
+                        // bit for bit), so they need not stay live in registers here
+                        bool in = f && g3m[p] > 0.0f;
+                        if (TIE && f && g3m[p] == 0.0f)
+                            in = centre_inside(plane_distance(dgx[p], dgy[p], dgz[p], st.s2[j]),
+                                               plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
+                                               plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
+                                               __float_as_uint(st.s0[j].w));
+                        const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
+                        key[p] = in && k < key[p] ? k : key[p];
+                        if (STATS) cnt_in[p] += in;
+                    }
+                };
+                bool z = false;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) z |= frag[p] && g3m[p] == 0.0f;
+                if (__any_sync(0xffffffffu, z))
+                    post(std::true_type{});
+                else
+                    post(std::false_type{});
             }
         }
     }
