@@ -236,6 +236,8 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                 // the warp, and run a copy of the loop without the branch otherwise.
                 auto post = [&](auto tie_t) {
                     constexpr bool TIE = decltype(tie_t)::value;
+                    float rr[PPT];
+                    bool inn[PPT];
 #pragma unroll
                     for (int p = 0; p < PPT; ++p) {
                         // predicated: every lane computes, non-fragments add nothing
@@ -254,9 +256,18 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
                                                plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
                                                plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
                                                __float_as_uint(st.s0[j].w));
-                        const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | tbits;
-                        key[p] = in && k < key[p] ? k : key[p];
+                        rr[p] = r;
+                        inn[p] = in;
                         if (STATS) cnt_in[p] += in;
+                    }
+                    // the visibility keys only where some lane of the warp has a
+                    // centre-inside fragment of this triangle
+                    if (__any_sync(0xffffffffu, inn[0] || inn[1])) {
+#pragma unroll
+                        for (int p = 0; p < PPT; ++p) {
+                            const unsigned long long k = ((unsigned long long)__float_as_uint(rr[p]) << 32) | tbits;
+                            key[p] = inn[p] && k < key[p] ? k : key[p];
+                        }
                     }
                 };
                 bool z = false;
