@@ -314,13 +314,16 @@ constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full
 // a grid larger than one resident wave hides it with warps (CB = 1: 40
 // registers, 12 CTAs per SM), a smaller one with loads in flight per lane
 // (CB = 4, 7 CTAs per SM).
-template <bool FILL, int CB>
+// TPW: triangles per warp (lanes 0 .. TPW-1 run phase 1; phase 2 spreads
+// their pairs over all 32 lanes).  8 for small scenes, so that they still
+// give the GPU enough warps to hide the search's latency.
+template <bool FILL, int CB, int TPW>
 __global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids,
                                                                      uint32_t cap, int* status)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(blockIdx.x * 4 + warp) * TPW + lane;
     if (FILL && v.pairs && *v.cursor <= v.pair_cap) return;  // the pair list is complete: bin_pairs_kernel fills
     const size_t TT = (size_t)T;
     // The index header, with every count that becomes an index clamped to
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, i
     // phase 1: this lane's triangle
     float sx = 0.0f, sy = 0.0f, sz = 1.0f, cb = 1.0f, sb = 0.0f;
     int r0 = 0, c0i = 0, ncol = 0, segs = 1, rowpairs = 0, npairs = 0;
-    if (t < T) {
+    if (lane < TPW && t < T) {
         const float4 q0 = v.rec[RF_CAP * TT + t];
         const float4 q1 = v.rec[RF_CAP2 * TT + t];
         if (q1.w != 0.0f) {
@@ -620,19 +623,30 @@ static int sm_count()
     return n;
 }
 
+// The binner's launch shape for T triangles on `sms` SMs: 0 = one cone per
+// step and 32 triangles per warp (grids beyond one resident wave at 7 CTAs
+// per SM), 1 = four cones per step, 2 = four cones and 8 triangles per warp
+// (scenes whose 8-per-warp grid still fits that wave).
+static int bin_shape(int T, int sms)
+{
+    if ((T + 127) / 128 > 7 * sms) return 0;
+    if ((T + 31) / 32 <= 7 * sms) return 2;
+    return 1;
+}
+
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
                             uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep)
 {
     if (T == 0) return VSR_OK;
     const BinView v{idx.hdr,  idx.cell_start, idx.sorted, idx.big, rec,   counts,
                     nullptr,  pairs,          pair_cap,   cursor,  pstep, idx.ntiles};
-    const int blocks = (T + 127) / 128;
-    int sms = 0;
-    if ((sms = sm_count()) < 0) return VSR_ERR_CUDA;
-    if (blocks > 7 * sms)
-        bin_kernel<false, 1><<<blocks, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
-    else
-        bin_kernel<false, 4><<<blocks, 128, 0, st>>>(v, T, nullptr, 0, nullptr);
+    const int sms = sm_count();
+    if (sms < 0) return VSR_ERR_CUDA;
+    switch (bin_shape(T, sms)) {
+    case 0: bin_kernel<false, 1, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
+    case 1: bin_kernel<false, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
+    default: bin_kernel<false, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
+    }
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -654,13 +668,13 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
         VSR_CUDA_TRY(cudaGetLastError());
     }
     if (!search) return VSR_OK;
-    const int blocks = (T + 127) / 128;
-    int sms = 0;
-    if ((sms = sm_count()) < 0) return VSR_ERR_CUDA;
-    if (blocks > 7 * sms)
-        bin_kernel<true, 1><<<blocks, 128, 0, st>>>(v, T, ids, cap, status);
-    else
-        bin_kernel<true, 4><<<blocks, 128, 0, st>>>(v, T, ids, cap, status);
+    const int sms = sm_count();
+    if (sms < 0) return VSR_ERR_CUDA;
+    switch (bin_shape(T, sms)) {
+    case 0: bin_kernel<true, 1, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
+    case 1: bin_kernel<true, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
+    default: bin_kernel<true, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, ids, cap, status); break;
+    }
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
