@@ -147,6 +147,12 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
             b0 = min(b0, v.cap);
         }
     }
+    // the thread's two pixels side by side for the packed FP32x2 distances
+    // (bit for bit the scalar ones, so the classification is the coverage
+    // kernel's)
+    static_assert(PPT == 2, "packed pairs hold the thread's two pixels");
+    const float2 dgx2 = make_float2(dgx[0], dgx[1]), dgy2 = make_float2(dgy[0], dgy[1]),
+                 dgz2 = make_float2(dgz[0], dgz[1]), eg2 = make_float2(eg[0], eg[1]);
 
     for (uint32_t base = b0; base < b1; base += STAGE_CHUNK) {
         const int n = (int)min((uint32_t)STAGE_CHUNK, b1 - base);
@@ -184,35 +190,36 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
                 const float4 a = st.s0[j];
                 const float4 b = st.s1[j];
                 const float4 e = st.s6[j];
-                float g4[PPT];
+                const float2 g4p = miter_distance2(dgx2, dgy2, dgz2, e, b, eg2);
+                const float g4[PPT] = {g4p.x, g4p.y};
                 bool p4[PPT], any4 = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    g4[p] = miter_distance(dgx[p], dgy[p], dgz[p], e, b, eg[p]);
                     p4[p] = pv[p] && g4[p] > -h[p];
                     any4 |= p4[p];
                 }
                 if (!__any_sync(0xffffffffu, any4)) continue;
-                const float4 n1 = st.s2[j], n2 = st.s3[j], n3 = st.s4[j];
-                float g1[PPT], g2[PPT], g3[PPT], g3m[PPT], gm[PPT];
+                const float2 g1p = plane_distance2(dgx2, dgy2, dgz2, st.s2[j]);
+                const float2 g2p = plane_distance2(dgx2, dgy2, dgz2, st.s3[j]);
+                const float2 g3p = plane_distance2(dgx2, dgy2, dgz2, st.s4[j]);
+                const float g1[PPT] = {g1p.x, g1p.y}, g2[PPT] = {g2p.x, g2p.y}, g3[PPT] = {g3p.x, g3p.y};
+                float g3m[PPT], gm[PPT];
                 bool frag[PPT], anyf = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    g1[p] = plane_distance(dgx[p], dgy[p], dgz[p], n1);
-                    g2[p] = plane_distance(dgx[p], dgy[p], dgz[p], n2);
-                    g3[p] = plane_distance(dgx[p], dgy[p], dgz[p], n3);
                     g3m[p] = fminf(fminf(g1[p], g2[p]), g3[p]);
                     gm[p] = fminf(g3m[p], g4[p]);
                     frag[p] = p4[p] && gm[p] > -h[p];
                     anyf |= frag[p];
                 }
                 if (!__any_sync(0xffffffffu, anyf)) continue;
-                const float4 pl = st.s5[j];
+                const float2 Dp = plane_distance2(dgx2, dgy2, dgz2, st.s5[j]);
+                const float D2[PPT] = {Dp.x, Dp.y};
                 const unsigned ties = __float_as_uint(a.w);
                 const uint32_t t = __float_as_uint(e.w);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    const float D = plane_distance(dgx[p], dgy[p], dgz[p], pl);
+                    const float D = D2[p];
                     const float r = __fdividef(b.w, D);
                     const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;  // 0 < r < inf
                     if (!f) continue;
