@@ -74,6 +74,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     m->idx.ntiles = (uint32_t)nt;
+    m->idx_built = false;
     if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }
@@ -92,6 +93,7 @@ void map_release(vsr_map m)
     cudaFree(m->deriv);
     m->deriv = nullptr;
     m->map = nullptr;
+    m->idx_built = false;
     m->tiles = nullptr;
     m->idx = TileIndex{};
 }
@@ -141,11 +143,21 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
     bool plain = m->spec.kind == VSR_MAP_UNIVERSAL && !m->deriv;
     for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
-    vsr_status s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map,
-                                      m->tiles, m->idx.geom, st)
-                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, st);
+    // the first generation builds the whole tile index after the map; a
+    // later one files the tiles from the map kernel itself, into the grid
+    // planned from the previous generation, so only the scan and the copy
+    // follow the map kernel
+    const bool file = m->idx_built;
+    vsr_status s = VSR_OK;
+    if (file && (s = launch_tile_index_reset(m->idx, st)) != VSR_OK) return s;
+    const TileIndex* into = file ? &m->idx : nullptr;
+    s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles,
+                           m->idx.geom, into, st)
+              : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, into, st);
     if (s != VSR_OK) return s;
-    s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
+    s = file ? launch_tile_index_finish(m->tiles, m->tx * m->ty, m->idx, st)
+             : launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
+    if (s == VSR_OK) m->idx_built = true;
     m->gen = g_gen.fetch_add(1);
     return s;
 }

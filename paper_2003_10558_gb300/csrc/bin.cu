@@ -26,28 +26,9 @@
 
 namespace {
 
-constexpr float PI_F = 3.14159265358979f;
-
-__device__ __forceinline__ int hist_bin(float a)
-{
-    // third-of-an-octave bins from 2^-17 rad
-    int b = (int)floorf((log2f(fmaxf(a, 1e-30f)) + 17.0f) * 3.0f);
-    return min(IDX_HIST - 1, max(0, b));
-}
+constexpr float PI_F = IDX_PI;
 
 __device__ __forceinline__ float hist_upper(int b) { return exp2f((float)(b + 1) / 3.0f - 17.0f); }
-
-__device__ __forceinline__ int cell_row(float lat, const TileIndexHdr& h)
-{
-    return min(h.nlat - 1, max(0, (int)floorf((lat + 0.5f * PI_F) / h.cell)));
-}
-
-__device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
-{
-    int c = (int)floorf((lon + PI_F) / h.cell);
-    c %= h.nlon;
-    return c < 0 ? c + h.nlon : c;
-}
 
 // ---- tile index -------------------------------------------------------------
 //
@@ -62,18 +43,6 @@ __device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
 
 constexpr int IDX_THREADS = 256;
 
-__device__ __forceinline__ Cone index_entry(const Cone& c, int i)
-{
-    Cone e;
-    e.c0 = c.c0;
-    e.c1 = make_float4(c.c1.x, c.c1.y, __uint_as_float((uint32_t)i), 0.0f);
-    return e;
-}
-
-__device__ __forceinline__ int home_cell_geom(const float4& g, const TileIndexHdr& h)
-{
-    return cell_row(g.y, h) * h.nlon + cell_col(g.z, h);
-}
 
 // hdr zeroed by the caller
 __global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const float4* __restrict__ geom, int ntiles,
@@ -176,6 +145,70 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __res
     if (g.w < 0.0f || g.x > s_h.alpha_cut) return;
     const int c = home_cell_geom(g, s_h);
     sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
+}
+
+// A later generation of a map files its tiles into the grid of the
+// previous one (see launch_tile_index_reset): the plan comes from the
+// previous generation's histogram, which the full build and the filing
+// map kernels both leave in the header; the counters start from zero.
+// One CTA of IDX_RESET_THREADS threads.
+constexpr int IDX_RESET_THREADS = 1024;
+
+__global__ void __launch_bounds__(IDX_RESET_THREADS) idx_reset_kernel(TileIndexHdr* __restrict__ hdr,
+                                                                       uint32_t* __restrict__ cell_count)
+{
+    __shared__ int s_ncell;
+    if (threadIdx.x == 0) {
+        TileIndexHdr h = *hdr;
+        unsigned nv = 0u;
+        for (int b = 0; b < IDX_HIST; ++b) nv += h.hist[b];
+        h.n_valid = nv;
+        index_plan(&h, h);
+        hdr->nlat = h.nlat;
+        hdr->nlon = h.nlon;
+        hdr->ncell = h.ncell;
+        hdr->cell = h.cell;
+        hdr->alpha_cut = h.alpha_cut;
+        hdr->alpha_small_max = 0u;
+        hdr->h_max = 0u;
+        hdr->n_big = 0u;
+        hdr->n_valid = 0u;
+        s_ncell = min(h.ncell, IDX_CELLS_MAX);
+    }
+    __syncthreads();  // the histogram is read before it is cleared
+    if (threadIdx.x < IDX_HIST) hdr->hist[threadIdx.x] = 0u;
+    for (int c = threadIdx.x; c < s_ncell; c += IDX_RESET_THREADS) cell_count[c] = 0u;
+}
+
+// After the filing map kernel and the scan of the cell counts: the
+// cell-sorted copies of the small tiles (slot by decrementing the cell
+// count), the widest ramp of all tiles and the largest small half-angle.
+__global__ void __launch_bounds__(IDX_THREADS) idx_finish_kernel(const Cone* __restrict__ tiles,
+                                                                  const float4* __restrict__ geom, int ntiles,
+                                                                  TileIndexHdr* __restrict__ hdr,
+                                                                  const uint32_t* __restrict__ cell_start,
+                                                                  uint32_t* __restrict__ cell_count,
+                                                                  Cone* __restrict__ sorted)
+{
+    __shared__ TileIndexHdr s_h;
+    if (threadIdx.x == 0) s_h = *hdr;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * IDX_THREADS + threadIdx.x;
+    const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    const bool valid = g.w >= 0.0f;
+    const bool small = valid && g.x <= s_h.alpha_cut;
+    if (small) {
+        const int c = home_cell_geom(g, s_h);
+        sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
+    }
+    unsigned hm = valid ? __float_as_uint(g.w) : 0u, am = small ? __float_as_uint(g.x) : 0u;
+    for (int o = 16; o; o >>= 1) {
+        hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    if (lane == 0 && hm) atomicMax(&hdr->h_max, hm);
+    if (lane == 0 && am) atomicMax(&hdr->alpha_small_max, am);
 }
 
 // The whole index in one CTA, for maps of at most IDX_FUSED_TILES tiles: the
@@ -632,6 +665,25 @@ static int bin_shape(int T, int sms)
     if ((T + 127) / 128 > 7 * sms) return 0;
     if ((T + 31) / 32 <= 7 * sms) return 2;
     return 1;
+}
+
+vsr_status launch_tile_index_reset(TileIndex idx, cudaStream_t st)
+{
+    idx_reset_kernel<<<1, IDX_RESET_THREADS, 0, st>>>(idx.hdr, idx.cell_count);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
+{
+    vsr_status s = launch_scan(idx.cell_count, nullptr, 0, &idx.hdr->ncell, idx.cell_start, st);
+    if (s != VSR_OK) return s;
+    if (ntiles > 0) {
+        idx_finish_kernel<<<(ntiles + IDX_THREADS - 1) / IDX_THREADS, IDX_THREADS, 0, st>>>(
+            tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
+        VSR_CUDA_TRY(cudaGetLastError());
+    }
+    return VSR_OK;
 }
 
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,

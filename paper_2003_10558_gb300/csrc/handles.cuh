@@ -32,6 +32,7 @@ struct vsr_map_s {
     float4* map = nullptr;
     Cone* tiles = nullptr;
     TileIndex idx = {};
+    bool idx_built = false;  // a tile index (and its histogram) exists: later generations file into it
     int tx = 0, ty = 0;
     uint64_t gen = 0;
 };

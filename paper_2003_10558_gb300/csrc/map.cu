@@ -72,7 +72,12 @@ constexpr int CONE_WARPS = TILE_PIX / 32;
 
 __device__ __forceinline__ void cone_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(TILE_PIX) : "memory"); }
 
-__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom)
+// file_into (optional): the tile index of a later generation of the map
+// (prepared by launch_tile_index_reset); thread 0 then files the tile
+// (index `tile`) into it: its histogram bin, and its cell's count or, past
+// the plan's small-tile half-angle, the big list.
+__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom, const TileIndex* file_into = nullptr,
+                            int tile = 0)
 {
     __shared__ float4 part[CONE_WARPS];
     __shared__ float2 part2[CONE_WARPS];
@@ -121,11 +126,23 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         float ca = fmaxf(-1.0f, fminf(1.0f, cm - 2e-6f));
         if (n == 0.0f) ca = 1.0f;
         const float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
-        out->c0 = make_float4(ax, ay, az, ca);
-        out->c1 = make_float4(sa, hh, n, 0.0f);
+        const Cone cone{make_float4(ax, ay, az, ca), make_float4(sa, hh, n, 0.0f)};
+        *out = cone;
         // the tile's half-angle and the latitude / longitude of its axis, for
         // the tile index (the same functions the index would apply)
-        *geom = make_float4(acosf(ca), asinf(fmaxf(-1.0f, fminf(1.0f, ay))), atan2f(ax, az), n > 0.0f ? hh : -1.0f);
+        const float4 g =
+            make_float4(acosf(ca), asinf(fmaxf(-1.0f, fminf(1.0f, ay))), atan2f(ax, az), n > 0.0f ? hh : -1.0f);
+        *geom = g;
+        if (file_into && g.w >= 0.0f) {
+            TileIndexHdr* hdr = file_into->hdr;
+            atomicAdd(&hdr->hist[hist_bin(g.x)], 1u);
+            if (g.x > hdr->alpha_cut) {
+                const uint32_t b = atomicAdd(&hdr->n_big, 1u);
+                if (b < file_into->ntiles) file_into->big[b] = index_entry(cone, tile);
+            } else {
+                atomicAdd(&file_into->cell_count[home_cell_geom(g, *hdr)], 1u);
+            }
+        }
     }
 }
 
@@ -144,7 +161,8 @@ constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation 
 template <class F>
 __global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn, float4* __restrict__ map,
                                                            Cone* __restrict__ tiles, float4* __restrict__ geom,
-                                                           float4* __restrict__ deriv = nullptr)
+                                                           float4* __restrict__ deriv, TileIndex file_into,
+                                                           int file)
 {
     // map values of the tile and its halo: direction xyz, w = F's return value
     __shared__ float4 sv[HW * HW];
@@ -219,7 +237,8 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn,
         }
         map[(size_t)j * W + i] = o;
     }
-    reduce_cone(valid, G, h, &tiles[ty * gridDim.x + tx], &geom[ty * gridDim.x + tx]);
+    const int t = ty * gridDim.x + tx;
+    reduce_cone(valid, G, h, &tiles[t], &geom[t], file ? &file_into : nullptr, t);
 }
 
 // The Universal perspective map function.
@@ -352,17 +371,18 @@ MapP make_params(int W, int H, int aov, float k, float l, float s, float omega_d
 }  // namespace
 
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      float4* geom, cudaStream_t st)
+                      float4* geom, const TileIndex* file_into, cudaStream_t st)
 {
     const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom, nullptr,
+                                             file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, float4* geom, float4* deriv,
-                           cudaStream_t st)
+                           const TileIndex* file_into, cudaStream_t st)
 {
     SpecFn f;
     f.kind = sp.kind;
@@ -380,7 +400,8 @@ vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, flo
         f.a[3] = sp.param[2];
     }
     dim3 grid((sp.W + TILE - 1) / TILE, (sp.H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv);
+    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv,
+                                             file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -102,13 +102,17 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
     } while (0)
 
 // Kernel launchers (defined in the .cu files, called by the host library).
+// file_into (optional): the map's tile index, prepared by
+// launch_tile_index_reset; the map kernel then files every tile into it
+// (launch_tile_index_finish completes the index).
+struct TileIndex;
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      float4* geom, cudaStream_t st);
+                      float4* geom, const TileIndex* file_into, cudaStream_t st);
 vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st);
 // a map of any vsr_map_kind (param after limits for the Universal kind);
 // deriv (optional): 2 float4 per pixel, (d_i G, d_j G) for the pixel step
 vsr_status launch_map_spec(const vsr_map_spec& spec, float4* map, Cone* tiles, float4* geom, float4* deriv,
-                           cudaStream_t st);
+                           const TileIndex* file_into, cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
@@ -125,7 +129,54 @@ struct TileIndex {
     uint32_t* cell_count;  // IDX_CELLS_MAX: scratch of the build
     uint32_t ntiles;       // tiles of the map (the length of sorted, big and geom)
 };
+// The whole index from the tile cones and geometry (any generation).
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
+// A later generation of the same map, in three steps on one stream:
+// launch_tile_index_reset (the grid plan from the previous generation's
+// histogram, counters zeroed) -> the map kernel with file_into = the index
+// (each tile adds itself to the histogram and to its cell's count, or to
+// the big list) -> launch_tile_index_finish (scan of the cell counts,
+// cell-sorted copies, the widest ramp and the largest small half-angle).
+vsr_status launch_tile_index_reset(TileIndex idx, cudaStream_t st);
+vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
+
+// Grid arithmetic of the tile index, shared by its build (bin.cu) and the
+// map kernels that file their tiles into it (map.cu).
+constexpr float IDX_PI = 3.14159265358979f;
+
+__device__ __forceinline__ int hist_bin(float a)
+{
+    // third-of-an-octave bins from 2^-17 rad
+    int b = (int)floorf((log2f(fmaxf(a, 1e-30f)) + 17.0f) * 3.0f);
+    return min(IDX_HIST - 1, max(0, b));
+}
+
+__device__ __forceinline__ int cell_row(float lat, const TileIndexHdr& h)
+{
+    return min(h.nlat - 1, max(0, (int)floorf((lat + 0.5f * IDX_PI) / h.cell)));
+}
+
+__device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
+{
+    int c = (int)floorf((lon + IDX_PI) / h.cell);
+    c %= h.nlon;
+    return c < 0 ? c + h.nlon : c;
+}
+
+__device__ __forceinline__ int home_cell_geom(const float4& g, const TileIndexHdr& h)
+{
+    return cell_row(g.y, h) * h.nlon + cell_col(g.z, h);
+}
+
+// The index's copy of tile i's cone: (axis xyz, cos alpha), (sin alpha, h,
+// tile index bits, 0).
+__device__ __forceinline__ Cone index_entry(const Cone& c, int i)
+{
+    Cone e;
+    e.c0 = c.c0;
+    e.c1 = make_float4(c.c1.x, c.c1.y, __uint_as_float((uint32_t)i), 0.0f);
+    return e;
+}
 // binning of one frame: counts and cursor zeroed by the caller ->
 // launch_bin_count (records (tile, triangle) into pairs[0, pair_cap)
 // and counts them in *cursor; pairs may be NULL) -> launch_scan(counts,
