@@ -143,11 +143,15 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
     bool plain = m->spec.kind == VSR_MAP_UNIVERSAL && !m->deriv;
     for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
-    // the first generation builds the whole tile index after the map; a
-    // later one files the tiles from the map kernel itself, into the grid
-    // planned from the previous generation, so only the scan and the copy
-    // follow the map kernel
-    const bool file = m->idx_built;
+    // The first generation builds the whole tile index after the map.  A
+    // later generation of the same projection (the same spec: a map rebuilt
+    // each frame) files the tiles from the map kernel itself, into the grid
+    // planned from the previous generation's histogram -- the plan a whole
+    // build would make -- so only the scan and the copy follow the map
+    // kernel.  After a change of lens the previous plan may fit the new
+    // tiles badly (every tile past its cut goes to the big list, which every
+    // triangle tests), so the index is built whole again.
+    const bool file = m->idx_built && memcmp(&m->idx_spec, &m->spec, sizeof(vsr_map_spec)) == 0;
     vsr_status s = VSR_OK;
     if (file && (s = launch_tile_index_reset(m->idx, st)) != VSR_OK) return s;
     const TileIndex* into = file ? &m->idx : nullptr;
@@ -157,7 +161,10 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
     if (s != VSR_OK) return s;
     s = file ? launch_tile_index_finish(m->tiles, m->tx * m->ty, m->idx, st)
              : launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
-    if (s == VSR_OK) m->idx_built = true;
+    if (s == VSR_OK) {
+        m->idx_built = true;
+        m->idx_spec = m->spec;
+    }
     m->gen = g_gen.fetch_add(1);
     return s;
 }

@@ -32,7 +32,8 @@ struct vsr_map_s {
     float4* map = nullptr;
     Cone* tiles = nullptr;
     TileIndex idx = {};
-    bool idx_built = false;  // a tile index (and its histogram) exists: later generations file into it
+    bool idx_built = false;     // a tile index (and its histogram) exists
+    vsr_map_spec idx_spec = {};  // the projection it was built for: a generation of the same one files into it
     int tx = 0, ty = 0;
     uint64_t gen = 0;
 };
