@@ -252,6 +252,21 @@ vsr_status vsr_raster_ex(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_
 vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
                             const vsr_raster_stats* stats, void* stream);
 
+/* vsr_raster_dense: the same outputs as vsr_raster, computed without tile
+ * binning: every pixel of the map against every triangle of the scene --
+ * the rasterization equation (Sec. 1.1.2; the four plane distances, gpstep /
+ * gbpxstep / bstep of Sec. 1.1.1, the depth of Sec. 1.1.4, the merge of Sec.
+ * 1.4) with no region mask (Sec. 1.1.3) at all.  The miter distance is taken
+ * first and a triangle whose enlarged cap misses a warp's 64 pixels is
+ * skipped after it, as the FP64 reference skips it per pixel.  Costs W*H*T
+ * pair tests: a baseline that shows what the binning saves, not a fast path.
+ * The scene must hold set-up records (vsr_setup / vsr_scene_update).
+ * Outputs as vsr_raster (caller-owned device memory, W*H each, any may be
+ * NULL), bit for bit equal to vsr_raster's.  Asynchronous on `stream`;
+ * device errors go to the scene's status word as for vsr_raster. */
+vsr_status vsr_raster_dense(vsr_map m, vsr_scene s, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            void* stream);
+
 /* vsr_raster_noalloc: the same rasterization as vsr_raster, for callers that
  * cannot allocate device memory while they render (a host framework that
  * owns all device memory and forbids side allocations, or a real-time loop
@@ -268,7 +283,9 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene s, uint32_t* id_dev, float* dep
  * leaves the outputs incomplete).
  * status_dev: optional caller-owned device int32 that receives VSR_OK or the
  * device-side error of this call (cleared by the call).  With NULL the
- * status goes to a word of the library's array.
+ * status goes to a private word of the library's array that no call reads
+ * (vsr_last_device_status does not see it), so a bin overflow -- outputs
+ * incomplete -- cannot be observed: pass status_dev to learn of it.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make it before any stream capture.  Every call
  * shares the one array: calls that overlap on the GPU (other streams, other

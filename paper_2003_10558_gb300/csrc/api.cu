@@ -152,6 +152,9 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
     // tiles badly (every tile past its cut goes to the big list, which every
     // triangle tests), so the index is built whole again.
     const bool file = m->idx_built && memcmp(&m->idx_spec, &m->spec, sizeof(vsr_map_spec)) == 0;
+    // the reset clears the histogram the plan is made from: until this
+    // generation has completed, the next one must build the index whole
+    m->idx_built = false;
     vsr_status s = VSR_OK;
     if (file && (s = launch_tile_index_reset(m->idx, st)) != VSR_OK) return s;
     const TileIndex* into = file ? &m->idx : nullptr;
@@ -602,6 +605,15 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
                          depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
                          stats ? (unsigned long long*)stats->n_exec_dev : nullptr,
                          stats ? stats->n_inside_dev : nullptr, scene_status(sc), (cudaStream_t)stream);
+}
+
+vsr_status vsr_raster_dense(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            void* stream)
+{
+    if (!m || !sc || sc->T < 0) return VSR_ERR_INVALID_ARG;
+    const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, nullptr,
+                       nullptr, 0u, id_dev, depth_dev, cov_dev};
+    return launch_raster_dense(v, scene_status(sc), (cudaStream_t)stream);
 }
 
 vsr_status vsr_raster_ex(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,

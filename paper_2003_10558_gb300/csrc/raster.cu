@@ -3,10 +3,9 @@
 // One CTA of 128 threads per 16x16 tile; warp w covers the 8x8 pixel block
 // (w & 1, w >> 1) of the tile and each lane two pixels of it, (x, y) and
 // (x, y + 4), so every shared-memory load, vote and branch per triangle
-// serves two pixels.  For every
-// pixel G (unit direction, global delta) and every triangle t of the tile's
-// bin the kernel evaluates the four plane distances of the rasterization
-// equation (Sec. 1.1.2):
+// serves two pixels.  For every pixel G (unit direction, global delta) and
+// every triangle t of the tile's bin the kernel evaluates the four plane
+// distances of the rasterization equation (Sec. 1.1.2):
 //   g_1..3 = G.n_i                   edge planes through the eye (Sec. 1.1)
 //   g_4    = (G.S-hat - cos rho)/sin rho   miter cap, in the same angular
 //            units as the edge distances, computed in the chord form
@@ -29,9 +28,13 @@
 // on |G - a| <= the tile's angular radius, so its rounding error in units of
 // the ramp is ~(tile size in pixels) x 2^-23, a few 1e-6 of coverage.
 //
-// Work culling: the triangles of a chunk are first tested lane-parallel
-// (lane j <-> triangle j) against each warp's own 8x8-pixel view cone; the
-// surviving ones are then evaluated for all 64 pixels.
+// Work culling (the paper's low-resolution region mask, Sec. 1.1.3, at the
+// granularity of a warp's 8x8 pixels): the triangles of a staged chunk are
+// first tested lane-parallel (lane j <-> triangle j) against each warp's
+// view cone, cap and edge planes alike; the survivors are then evaluated for
+// all 64 pixels, one triangle per step for the whole warp.  A culled pair is
+// never a fragment, and both the coverage sum and the visibility key are
+// order-free, so the result does not depend on the cull.
 #include <type_traits>
 
 #include "stage.cuh"
@@ -42,14 +45,18 @@ constexpr int RT = 128;          // threads per CTA (one 16x16 tile)
 constexpr int PPT = 2;           // pixels per thread: (x, y) and (x, y + 4) of the warp's 8x8 block
 constexpr int CHUNK = RT;        // triangles staged per pass
 static_assert(CHUNK == STAGE_CHUNK, "one staging slot per thread");
-constexpr int SPLIT_MAX = 4 * CHUNK;  // triangles per work item of a split tile
 static_assert(RT * PPT == TILE_PIX, "one CTA covers one tile");
+// resident CTAs per SM the timed kernel is compiled for (its register cap)
+#ifndef VSR_RASTER_CTAS_PER_SM
+#define VSR_RASTER_CTAS_PER_SM 8
+#endif
 
 // One 16x16 tile of one view.  Called by every thread of a CTA of RT
 // threads; `st` is the CTA's staging area (reusable across calls: every use
 // is fenced by the barriers of the chunk loop).
-// Split tiles: a tile whose bin is longer than SPLIT_MAX triangles is
-// processed as several work items of at most SPLIT_MAX triangles each.  The
+// Split tiles: a tile whose bin is longer than split_max triangles (a
+// multiple of CHUNK) is processed as several work items of at most
+// split_max triangles each.  The
 // items of one tile add their coverage (2^-22 fixed point) and take the
 // minimum of their visibility keys in the tile's accumulator slot with
 // atomics -- both are order-free, so the result is exactly that of one item
@@ -60,6 +67,153 @@ struct SplitAcc {
     unsigned long long* key;  // [slot][TILE_PIX], ~0 between frames
     uint32_t* done;           // [slot], zero between frames
 };
+
+// A cone (axis, cos, sin, widest ramp half-width) may hold a fragment of the
+// staged triangle (cap a, b; edge normals n1..n3): the cap test, and unless
+// counting algorithmic tests (defined by the cap alone) the edge planes.
+// Every pixel G of the cone is within alpha of the axis c, so
+// G.n <= c.n + sin(alpha) + (1 - cos(alpha)) for a unit normal n; a triangle
+// with some edge plane below -h there has no fragment.
+__device__ __forceinline__ bool cone_may_hit(const float4& a, const float4& b, const float4& n1, const float4& n2,
+                                             const float4& n3, const float4& c0, const float4& c1, bool count_alg)
+{
+    bool keep = cap_hits_cone(make_float3(a.x, a.y, a.z), 1.0f - 0.5f * b.y, b.x, make_float3(c0.x, c0.y, c0.z),
+                              c0.w, c1.x, c1.y);
+    const float lim = -(c1.y + c1.x + (1.0f - c0.w) + 1e-6f);
+    return keep && (count_alg || (fmaf(c0.x, n1.x, fmaf(c0.y, n1.y, c0.z * n1.z)) > lim &&
+                                  fmaf(c0.x, n2.x, fmaf(c0.y, n2.y, c0.z * n2.z)) > lim &&
+                                  fmaf(c0.x, n3.x, fmaf(c0.y, n3.y, c0.z * n3.z)) > lim));
+}
+
+// View cone of a group of WIDTH lanes (xor-shuffle width; 32: the warp's
+// block) from the lanes' valid pixels: axis = normalised sum, cos alpha = min G.axis less a margin, h =
+// the widest ramp half-width; a group without a valid pixel gets valid = 0,
+// a degenerate sum the whole sphere.
+template <int WIDTH>
+__device__ __forceinline__ void group_cone(const float* gx, const float* gy, const float* gz, const float* h,
+                                           const bool* pv, float4& c0, float4& c1)
+{
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f, cn = 0.0f, hw = 0.0f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+        if (pv[p]) {
+            sx += gx[p];
+            sy += gy[p];
+            sz += gz[p];
+            cn += 1.0f;
+            hw = fmaxf(hw, h[p]);
+        }
+#pragma unroll
+    for (int o = 1; o < WIDTH; o <<= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        cn += __shfl_xor_sync(0xffffffffu, cn, o);
+        hw = fmaxf(hw, __shfl_xor_sync(0xffffffffu, hw, o));
+    }
+    const float len = sqrtf(sx * sx + sy * sy + sz * sz);
+    const bool deg = !(len > 1e-6f * fmaxf(cn, 1.0f));
+    const float ax = deg ? 0.0f : sx / len, ay = deg ? 0.0f : sy / len, az = deg ? 1.0f : sz / len;
+    float cm = 2.0f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+        if (pv[p]) cm = fminf(cm, gx[p] * ax + gy[p] * ay + gz[p] * az);
+#pragma unroll
+    for (int o = 1; o < WIDTH; o <<= 1) cm = fminf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    float cs = fmaxf(-1.0f, fminf(1.0f, cm - 2e-6f));
+    if (deg) cs = -1.0f;
+    c0 = make_float4(ax, ay, az, cs);
+    c1 = make_float4(sqrtf(fmaxf(0.0f, 1.0f - cs * cs)), hw, cn > 0.0f ? 1.0f : 0.0f, 0.0f);
+}
+
+// One lane's two pixels as the evaluation sees them.
+struct PixPair {
+    float2 dgx, dgy, dgz;  // G - a (tile axis) of both pixels
+    float2 eg;             // |G|^2 - 1
+    float delta[PPT];      // global delta (0: invalid pixel)
+    float lim[PPT];        // fragment iff min distance > lim (-1/(2 delta); +inf if invalid)
+    uint32_t acc[PPT];     // coverage, 2^-22 fixed point
+    unsigned long long key[PPT];  // (bits(r) << 32) | t of the nearest centre-inside fragment
+    int32_t cnt_in[PPT];   // centre-inside fragments (statistics)
+};
+
+// Evaluate staged slot j at the lane's two pixels and merge the fragments into the pixels' coverage and keys.
+// Called by all 32 lanes of a warp together (warp votes).
+template <bool STATS>
+__device__ __forceinline__ void eval_slot(const Stage& st, int j, PixPair& q, uint32_t& cnt_alg)
+{
+    // the four distances of both pixels in packed FP32x2 arithmetic; the miter
+    // in chord form, G - S-hat = (G - a) - (S-hat - a): both differences are at
+    // most the tile radius, so their rounding costs ~1e-9 rad where it matters
+    const float4 b = st.s1[j];
+    const float4 e = st.s6[j];
+    const float2 g4p = miter_distance2(q.dgx, q.dgy, q.dgz, e, b, q.eg);
+    const float2 g1p = plane_distance2(q.dgx, q.dgy, q.dgz, st.s2[j]);
+    const float2 g2p = plane_distance2(q.dgx, q.dgy, q.dgz, st.s3[j]);
+    const float2 g3p = plane_distance2(q.dgx, q.dgy, q.dgz, st.s4[j]);
+    const float g4[PPT] = {g4p.x, g4p.y};
+    float g3m[PPT] = {fminf(fminf(g1p.x, g2p.x), g3p.x), fminf(fminf(g1p.y, g2p.y), g3p.y)};
+    float gm[PPT];
+    bool frag[PPT], anyf = false;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if (STATS) cnt_alg += g4[p] > q.lim[p];
+        gm[p] = fminf(g3m[p], g4[p]);
+        frag[p] = gm[p] > q.lim[p];  // gbpxstep on all four distances; never on invalid pixels
+        anyf |= frag[p];
+    }
+    if (!__any_sync(0xffffffffu, anyf)) return;
+    const float2 Dp = plane_distance2(q.dgx, q.dgy, q.dgz, st.s5[j]);
+    const float D2[PPT] = {Dp.x, Dp.y};
+    const float dgx[PPT] = {q.dgx.x, q.dgx.y}, dgy[PPT] = {q.dgy.x, q.dgy.y}, dgz[PPT] = {q.dgz.x, q.dgz.y};
+    const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
+    // The exact-zero tie rule needs its branch only where some pixel of
+    // the warp has a fragment on an edge plane (rare): decide once for
+    // the warp, and run a copy of the loop without the branch otherwise.
+    auto post = [&](auto tie_t) {
+        constexpr bool TIE = decltype(tie_t)::value;
+        float rr[PPT];
+        bool inn[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            // predicated: every lane computes, non-fragments add nothing
+            const float r = __fdividef(b.w, D2[p]);
+            // 0 < r < inf (NaN excluded) as one unsigned compare of the bits
+            const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
+            const float m = __saturatef(fmaf(gm[p], q.delta[p], 0.5f));
+            q.acc[p] += f ? cov_fixed(m) : 0u;
+            // centre-inside: all three edge distances >= 0; an exact zero
+            // takes the tie rule on the three distances, recomputed from
+            // the staged planes (the scalar form gives the packed values
+            // bit for bit), so they need not stay live in registers here
+            bool in = f && g3m[p] > 0.0f;
+            if (TIE && f && g3m[p] == 0.0f)
+                in = centre_inside(plane_distance(dgx[p], dgy[p], dgz[p], st.s2[j]),
+                                   plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
+                                   plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
+                                   __float_as_uint(st.s0[j].w));
+            rr[p] = r;
+            inn[p] = in;
+            if (STATS) q.cnt_in[p] += in;
+        }
+        // the visibility keys only where some lane of the warp has a
+        // centre-inside fragment
+        if (__any_sync(0xffffffffu, inn[0] || inn[1])) {
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const unsigned long long k = ((unsigned long long)__float_as_uint(rr[p]) << 32) | tbits;
+                q.key[p] = inn[p] && k < q.key[p] ? k : q.key[p];
+            }
+        }
+    };
+    bool z = false;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) z |= frag[p] && g3m[p] == 0.0f;
+    if (__any_sync(0xffffffffu, z))
+        post(std::true_type{});
+    else
+        post(std::false_type{});
+}
 
 template <bool STATS>
 __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, Stage& st, bool count_alg,
@@ -80,17 +234,18 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
 
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = tx * TILE + (warp & 1) * 8 + (lane & 7);
-    const int py0 = ty * TILE + (warp >> 1) * 8 + (lane >> 3);
+    // pixel (in tile) of this lane's first pixel; its second is four rows below
+    const int lx = (warp & 1) * 8 + (lane & 7);
+    const int ly0 = (warp >> 1) * 8 + (lane >> 3);
+    const int px = tx * TILE + lx;
+    const int py0 = ty * TILE + ly0;
 
     const Cone tc = tiles[tile];
     const float ax = tc.c0.x, ay = tc.c0.y, az = tc.c0.z;
 
-    float gx[PPT], gy[PPT], gz[PPT], dgx[PPT], dgy[PPT], dgz[PPT], delta[PPT], h[PPT], lim[PPT], eg[PPT];
+    float gx[PPT], gy[PPT], gz[PPT], h[PPT];
     bool pv[PPT], inimg[PPT];
-    uint32_t acc[PPT];
-    unsigned long long key[PPT];
-    int32_t cnt_in[PPT];
+    PixPair q;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int py = py0 + 4 * p;
@@ -101,45 +256,23 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         gx[p] = g.x;
         gy[p] = g.y;
         gz[p] = g.z;
-        delta[p] = g.w;
         h[p] = pv[p] ? 0.5f / g.w : 0.0f;
-        lim[p] = pv[p] ? -h[p] : INFINITY;  // fragment iff min distance > lim
-        eg[p] = pv[p] ? norm2_minus_one(g.x, g.y, g.z) : 0.0f;
-        dgx[p] = g.x - ax;
-        dgy[p] = g.y - ay;
-        dgz[p] = g.z - az;
-        acc[p] = 0u;
-        key[p] = ~0ull;
-        cnt_in[p] = 0;
+        q.delta[p] = g.w;
+        q.lim[p] = pv[p] ? -h[p] : INFINITY;
+        q.acc[p] = 0u;
+        q.key[p] = ~0ull;
+        q.cnt_in[p] = 0;
     }
+    q.dgx = make_float2(gx[0] - ax, gx[1] - ax);
+    q.dgy = make_float2(gy[0] - ay, gy[1] - ay);
+    q.dgz = make_float2(gz[0] - az, gz[1] - az);
+    q.eg = make_float2(pv[0] ? norm2_minus_one(gx[0], gy[0], gz[0]) : 0.0f,
+                       pv[1] ? norm2_minus_one(gx[1], gy[1], gz[1]) : 0.0f);
 
     // the warp's own view cone (its 8x8 pixels)
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f, cn = 0.0f, hw = 0.0f;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p)
-        if (pv[p]) {
-            sx += gx[p];
-            sy += gy[p];
-            sz += gz[p];
-            cn += 1.0f;
-            hw = fmaxf(hw, h[p]);
-        }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    sz = warp_sum(sz);
-    const float wcnt = warp_sum(cn);
-    const float wh = warp_max(hw);
-    const float wl = sqrtf(sx * sx + sy * sy + sz * sz);
-    const bool wdeg = !(wl > 1e-6f * fmaxf(wcnt, 1.0f));
-    const float wax = wdeg ? 0.0f : sx / wl, way = wdeg ? 0.0f : sy / wl, waz = wdeg ? 1.0f : sz / wl;
-    float cm = 2.0f;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p)
-        if (pv[p]) cm = fminf(cm, gx[p] * wax + gy[p] * way + gz[p] * waz);
-    float wcos = fmaxf(-1.0f, fminf(1.0f, warp_min(cm) - 2e-6f));
-    if (wdeg) wcos = -1.0f;
-    const float wsin = sqrtf(fmaxf(0.0f, 1.0f - wcos * wcos));
-    const bool warp_active = wcnt > 0.0f;
+    float4 wc0, wc1;
+    group_cone<32>(gx, gy, gz, h, pv, wc0, wc1);
+    const bool warp_active = wc1.z > 0.0f;
 
     uint32_t b0 = 0, b1 = 0;
     if (tc.c1.z > 0.0f) {
@@ -159,14 +292,12 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
 
     const size_t TT = (size_t)T;
     static_assert(PPT == 2, "packed pairs hold the thread's two pixels");
-    const float2 dgx2 = make_float2(dgx[0], dgx[1]), dgy2 = make_float2(dgy[0], dgy[1]),
-                 dgz2 = make_float2(dgz[0], dgz[1]), eg2 = make_float2(eg[0], eg[1]);
 
     for (uint32_t base = b0; base < b1; base += CHUNK) {
         const int n = (int)min((uint32_t)CHUNK, b1 - base);
         // saturate once per chunk: at most CHUNK terms of <= COV_ONE each were added since
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) acc[p] = min(acc[p], COV_ONE);
+        for (int p = 0; p < PPT; ++p) q.acc[p] = min(q.acc[p], COV_ONE);
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t t = ids[base + threadIdx.x];
@@ -185,114 +316,30 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             // lane-parallel cull of 32 triangles against this warp's cone
             bool keep = false;
             const int jj = gbase + lane;
-            if (jj < n && __float_as_uint(st.s6[jj].w) != STAGE_EMPTY) {
-                const float4 a = st.s0[jj];
-                const float4 b = st.s1[jj];
-                keep = cap_hits_cone(make_float3(a.x, a.y, a.z), 1.0f - 0.5f * b.y, b.x, make_float3(wax, way, waz),
-                                     wcos, wsin, wh);
-                // every pixel G of the warp is within alpha of the warp axis w, so
-                // G.n <= w.n + sin(alpha) + (1 - cos(alpha)) for a unit normal n;
-                // a triangle with some edge plane below -h there has no fragment
-                // (skipped while counting algorithmic tests, which are defined
-                // by the cap alone)
-                const float lim = -(wh + wsin + (1.0f - wcos) + 1e-6f);
-                const float4 n1 = st.s2[jj], n2 = st.s3[jj], n3 = st.s4[jj];
-                keep = keep && (count_alg || (fmaf(wax, n1.x, fmaf(way, n1.y, waz * n1.z)) > lim &&
-                       fmaf(wax, n2.x, fmaf(way, n2.y, waz * n2.z)) > lim &&
-                       fmaf(wax, n3.x, fmaf(way, n3.y, waz * n3.z)) > lim));
-            }
+            if (jj < n && __float_as_uint(st.s6[jj].w) != STAGE_EMPTY)
+                keep = cone_may_hit(st.s0[jj], st.s1[jj], st.s2[jj], st.s3[jj], st.s4[jj], wc0, wc1, count_alg);
             unsigned mask = __ballot_sync(0xffffffffu, keep);
             while (mask) {
                 const int j = gbase + __ffs(mask) - 1;
                 mask &= mask - 1;
                 if (STATS) ++cnt_exec;
-                // the four distances of both pixels in packed FP32x2 arithmetic; the miter
-                // in chord form, G - S-hat = (G - a) - (S-hat - a): both differences are at
-                // most the tile radius, so their rounding costs ~1e-9 rad where it matters
-                const float4 b = st.s1[j];
-                const float4 e = st.s6[j];
-                const float2 g4p = miter_distance2(dgx2, dgy2, dgz2, e, b, eg2);
-                const float2 g1p = plane_distance2(dgx2, dgy2, dgz2, st.s2[j]);
-                const float2 g2p = plane_distance2(dgx2, dgy2, dgz2, st.s3[j]);
-                const float2 g3p = plane_distance2(dgx2, dgy2, dgz2, st.s4[j]);
-                const float g1[PPT] = {g1p.x, g1p.y}, g2[PPT] = {g2p.x, g2p.y}, g3[PPT] = {g3p.x, g3p.y},
-                            g4[PPT] = {g4p.x, g4p.y};
-                float g3m[PPT], gm[PPT];
-                bool frag[PPT], anyf = false;
-#pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    if (STATS) cnt_alg += g4[p] > lim[p];
-                    g3m[p] = fminf(fminf(g1[p], g2[p]), g3[p]);
-                    gm[p] = fminf(g3m[p], g4[p]);
-                    frag[p] = gm[p] > lim[p];  // gbpxstep on all four distances; never on invalid pixels
-                    anyf |= frag[p];
-                }
-                if (!__any_sync(0xffffffffu, anyf)) continue;
-                const float2 Dp = plane_distance2(dgx2, dgy2, dgz2, st.s5[j]);
-                const float D2[PPT] = {Dp.x, Dp.y};
-                const unsigned long long tbits = (unsigned long long)__float_as_uint(e.w);
-                // The exact-zero tie rule needs its branch only where some pixel of
-                // the warp has a fragment on an edge plane (rare): decide once for
-                // the warp, and run a copy of the loop without the branch otherwise.
-                auto post = [&](auto tie_t) {
-                    constexpr bool TIE = decltype(tie_t)::value;
-                    float rr[PPT];
-                    bool inn[PPT];
-#pragma unroll
-                    for (int p = 0; p < PPT; ++p) {
-                        // predicated: every lane computes, non-fragments add nothing
-                        const float r = __fdividef(b.w, D2[p]);
-                        // 0 < r < inf (NaN excluded) as one unsigned compare of the bits
-                        const bool f = frag[p] && __float_as_uint(r) - 1u < 0x7f7fffffu;
-                        const float m = __saturatef(fmaf(gm[p], delta[p], 0.5f));
-                        acc[p] += f ? cov_fixed(m) : 0u;
-                        // centre-inside: all three edge distances >= 0; an exact zero
-                        // takes the tie rule on the three distances, recomputed from
-                        // the staged planes (the scalar form gives the packed values
-                        // bit for bit), so they need not stay live in registers here
-                        bool in = f && g3m[p] > 0.0f;
-                        if (TIE && f && g3m[p] == 0.0f)
-                            in = centre_inside(plane_distance(dgx[p], dgy[p], dgz[p], st.s2[j]),
-                                               plane_distance(dgx[p], dgy[p], dgz[p], st.s3[j]),
-                                               plane_distance(dgx[p], dgy[p], dgz[p], st.s4[j]), g3m[p],
-                                               __float_as_uint(st.s0[j].w));
-                        rr[p] = r;
-                        inn[p] = in;
-                        if (STATS) cnt_in[p] += in;
-                    }
-                    // the visibility keys only where some lane of the warp has a
-                    // centre-inside fragment of this triangle
-                    if (__any_sync(0xffffffffu, inn[0] || inn[1])) {
-#pragma unroll
-                        for (int p = 0; p < PPT; ++p) {
-                            const unsigned long long k = ((unsigned long long)__float_as_uint(rr[p]) << 32) | tbits;
-                            key[p] = inn[p] && k < key[p] ? k : key[p];
-                        }
-                    }
-                };
-                bool z = false;
-#pragma unroll
-                for (int p = 0; p < PPT; ++p) z |= frag[p] && g3m[p] == 0.0f;
-                if (__any_sync(0xffffffffu, z))
-                    post(std::true_type{});
-                else
-                    post(std::false_type{});
+                eval_slot<STATS>(st, j, q, cnt_alg);
             }
         }
     }
 
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) acc[p] = min(acc[p], COV_ONE);
+    for (int p = 0; p < PPT; ++p) q.acc[p] = min(q.acc[p], COV_ONE);
 
     if (split_slot >= 0) {
         // merge into the tile's slot; the last item to arrive writes it out
-        const int lp0 = (warp & 1) * 8 + (lane & 7) + TILE * ((warp >> 1) * 8 + (lane >> 3));
+        const int lp0 = lx + TILE * ly0;
         unsigned long long* __restrict__ sacc = split.acc + (size_t)split_slot * TILE_PIX;
         unsigned long long* __restrict__ skey = split.key + (size_t)split_slot * TILE_PIX;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            if (acc[p]) atomicAdd(&sacc[lp0 + TILE * 4 * p], (unsigned long long)acc[p]);
-            if (key[p] != ~0ull) atomicMin(&skey[lp0 + TILE * 4 * p], key[p]);
+            if (q.acc[p]) atomicAdd(&sacc[lp0 + TILE * 4 * p], (unsigned long long)q.acc[p]);
+            if (q.key[p] != ~0ull) atomicMin(&skey[lp0 + TILE * 4 * p], q.key[p]);
         }
         __threadfence();
         __syncthreads();
@@ -303,8 +350,8 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         __threadfence();
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            acc[p] = (uint32_t)min(atomicExch(&sacc[lp0 + TILE * 4 * p], 0ull), (unsigned long long)COV_ONE);
-            key[p] = atomicExch(&skey[lp0 + TILE * 4 * p], ~0ull);
+            q.acc[p] = (uint32_t)min(atomicExch(&sacc[lp0 + TILE * 4 * p], 0ull), (unsigned long long)COV_ONE);
+            q.key[p] = atomicExch(&skey[lp0 + TILE * 4 * p], ~0ull);
         }
         if (threadIdx.x == 0) split.done[split_slot] = 0u;
     }
@@ -313,11 +360,11 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
     for (int p = 0; p < PPT; ++p) {
         if (!inimg[p]) continue;
         const size_t o = (size_t)(py0 + 4 * p) * W + px;
-        const bool hit = key[p] != ~0ull;
-        if (out_id) out_id[o] = hit ? (uint32_t)(key[p] & 0xffffffffull) : 0xffffffffu;
-        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(key[p] >> 32)) : INFINITY;
-        if (out_cov) out_cov[o] = (float)acc[p] * (1.0f / (float)COV_ONE);
-        if (STATS && n_inside) n_inside[o] = cnt_in[p];
+        const bool hit = q.key[p] != ~0ull;
+        if (out_id) out_id[o] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
+        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(q.key[p] >> 32)) : INFINITY;
+        if (out_cov) out_cov[o] = (float)q.acc[p] * (1.0f / (float)COV_ONE);
+        if (STATS && n_inside) n_inside[o] = q.cnt_in[p];
     }
 }
 
@@ -359,7 +406,7 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
 // themselves (the first item of a split tile); the further items of split
 // tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
 // return at once.
-__global__ void __launch_bounds__(RT, 8) raster_items_kernel(RasterView view, uint32_t n_tiles,
+__global__ void __launch_bounds__(RT, VSR_RASTER_CTAS_PER_SM) raster_items_kernel(RasterView view, uint32_t n_tiles,
                                                               const uint32_t* __restrict__ nsplit_of,
                                                               const int32_t* __restrict__ split_slot,
                                                               const uint2* __restrict__ extra,
@@ -383,8 +430,86 @@ __global__ void __launch_bounds__(RT, 8) raster_items_kernel(RasterView view, ui
     if (nsplit == 1)
         raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status);
     else
-        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max, (int)(k + 1) * split_max,
-                           split_slot[u], nsplit, split);
+        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max,
+                           (int)(k + 1) * split_max, split_slot[u], nsplit, split);
+}
+
+// Dense reference of the same rasterization: every pixel of a tile against
+// every triangle of the scene, with no binning and no cull.  As in the
+// oracle, the miter distance is evaluated first: a triangle whose enlarged
+// cap holds none of the warp's 64 pixels is skipped after it (a warp vote),
+// else the coverage kernel's own evaluation follows.  The outputs equal the
+// binned path's bit for bit (the same arithmetic per pair, and the merge is
+// order-free); its cost is that of W x H x T pair tests.
+__global__ void __launch_bounds__(RT) raster_dense_kernel(RasterView view, int* __restrict__ status)
+{
+    __shared__ Stage st;
+    const int tile = blockIdx.x;
+    const int W = view.W, H = view.H, T = view.T;
+    const int tx = tile % view.tiles_x, ty = tile / view.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+    const int py0 = ty * TILE + (warp >> 1) * 8 + (lane >> 3);
+    const Cone tc = view.tiles[tile];
+    const float ax = tc.c0.x, ay = tc.c0.y, az = tc.c0.z;
+    PixPair q;
+    float gx[PPT], gy[PPT], gz[PPT];
+    bool pv[PPT], inimg[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int py = py0 + 4 * p;
+        inimg[p] = px < W && py < H;
+        float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (inimg[p]) g = view.map[(size_t)py * W + px];
+        pv[p] = g.w > 0.0f;
+        gx[p] = g.x;
+        gy[p] = g.y;
+        gz[p] = g.z;
+        q.delta[p] = g.w;
+        q.lim[p] = pv[p] ? -0.5f / g.w : INFINITY;
+        q.acc[p] = 0u;
+        q.key[p] = ~0ull;
+        q.cnt_in[p] = 0;
+    }
+    q.dgx = make_float2(gx[0] - ax, gx[1] - ax);
+    q.dgy = make_float2(gy[0] - ay, gy[1] - ay);
+    q.dgz = make_float2(gz[0] - az, gz[1] - az);
+    q.eg = make_float2(pv[0] ? norm2_minus_one(gx[0], gy[0], gz[0]) : 0.0f,
+                       pv[1] ? norm2_minus_one(gx[1], gy[1], gz[1]) : 0.0f);
+    const bool active = tc.c1.z > 0.0f;
+    const size_t TT = (size_t)T;
+    uint32_t unused = 0;
+    for (int base = 0; active && base < T; base += CHUNK) {
+        const int n = min(CHUNK, T - base);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) q.acc[p] = min(q.acc[p], COV_ONE);
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t t = (uint32_t)(base + threadIdx.x);
+            if (view.rec[RF_CAP2 * TT + t].w == 0.0f)  // culled at set-up
+                st.s6[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(STAGE_EMPTY));
+            else
+                stage_triangle(view.rec, TT, t, ax, ay, az, st, threadIdx.x);
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float4 e = st.s6[j];
+            if (__float_as_uint(e.w) == STAGE_EMPTY) continue;
+            const float2 g4 = miter_distance2(q.dgx, q.dgy, q.dgz, e, st.s1[j], q.eg);
+            if (!__any_sync(0xffffffffu, g4.x > q.lim[0] || g4.y > q.lim[1])) continue;
+            eval_slot<false>(st, j, q, unused);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if (!inimg[p]) continue;
+        const size_t o = (size_t)(py0 + 4 * p) * W + px;
+        const uint32_t acc = min(q.acc[p], COV_ONE);
+        const bool hit = q.key[p] != ~0ull;
+        if (view.out_id) view.out_id[o] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
+        if (view.out_depth) view.out_depth[o] = hit ? __uint_as_float((uint32_t)(q.key[p] >> 32)) : INFINITY;
+        if (view.out_cov) view.out_cov[o] = (float)acc * (1.0f / (float)COV_ONE);
+    }
 }
 
 // Work items per tile: ceil(bin / split_max) when a split slot and room in
@@ -447,6 +572,15 @@ vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, 
     raster_items_kernel<<<n_tiles + extra_cap, RT, 0, st>>>(view, n_tiles, w.nsplit_of, w.split_slot, w.extra,
                                                             w.counters + 1, split_max, SplitAcc{w.acc, w.key, w.done},
                                                             status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_raster_dense(const RasterView& view, int* status, cudaStream_t st)
+{
+    const int n_tiles = view.tiles_x * ((view.H + TILE - 1) / TILE);
+    if (n_tiles == 0) return VSR_OK;
+    raster_dense_kernel<<<n_tiles, RT, 0, st>>>(view, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -262,6 +262,8 @@ struct RasterWork {
 // (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items)
 vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
                                RasterWork w, int split_max, int* status, cudaStream_t st);
+// the dense reference: every pixel against every triangle, no bins
+vsr_status launch_raster_dense(const RasterView& view, int* status, cudaStream_t st);
 // allocate / free a RasterWork for up to n_tiles tiles (accumulators
 // initialised)
 vsr_status raster_work_alloc(RasterWork* w, uint32_t n_tiles);

@@ -34,7 +34,7 @@ EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_down
            "vsr_map_from_device", "vsr_map_update", "vsr_map_params_effective",
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
-           "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_batch_create", "vsr_batch_render",
+           "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_raster_dense", "vsr_batch_create", "vsr_batch_render",
            "vsr_batch_config", "vsr_batch_free", "vsr_serve_create", "vsr_serve_add_scene", "vsr_serve_submit",
            "vsr_serve_poll", "vsr_serve_wait", "vsr_serve_cancel", "vsr_serve_stats_get", "vsr_serve_now",
            "vsr_serve_destroy",
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
             "vsr_raster_tiles": ([vp, vp, vp, vp, vp, P(RasterStats), vp], i32),
             "vsr_scene_bin_pairs": ([vp, vp, P(i64)], i32),
             "vsr_raster_noalloc": ([vp, vp, vp, vp, vp, vp, vp], i32),
+            "vsr_raster_dense": ([vp, vp, vp, vp, vp, vp], i32),
             "vsr_batch_create": ([P(vp)], i32),
             "vsr_batch_render": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_batch_config": ([vp, P(i32), P(i32), P(i32)], i32),
@@ -367,6 +368,21 @@ def raster(m: Map, sc: Scene, out=None, stats=False, n_inside=False, stream=None
     if stats:
         c = cnt.cpu()
         out["n_alg"], out["n_exec"] = int(c[0]), int(c[1])
+    return out
+
+
+def raster_dense(m: Map, sc: Scene, out=None, stream=None):
+    """The dense reference (vsr_raster_dense): every pixel against every
+    triangle of the scene, no tile bins.  Same outputs as raster()."""
+    import torch
+    H, W = m.shape
+    dev = torch.device("cuda")
+    if out is None:
+        out = {"id": torch.empty((H, W), dtype=torch.int32, device=dev),
+               "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+               "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
+    check(load().vsr_raster_dense(m.h, sc.h, _dptr(out.get("id")), _dptr(out.get("depth")), _dptr(out.get("cov")),
+                                  _stream_ptr(stream)), "vsr_raster_dense")
     return out
 
 

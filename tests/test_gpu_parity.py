@@ -214,6 +214,51 @@ def test_regenerated_map_files_into_previous_index(vsr):
                 assert np.array_equal(got[k].view(np.uint32), fresh[k].view(np.uint32)), (lens, k)
 
 
+@pytest.mark.parametrize("lens", [dict(W=256, H=256, k=0.0, l=1.0, s=1.0, omega=180.0),
+                                  dict(W=333, H=197, k=-1.0, l=1.0, s=1.0, omega=180.0),
+                                  dict(W=300, H=200, k=0.0, l=0.5, s=0.7, omega=360.0)],
+                         ids=lambda d: f"{d['W']}x{d['H']}k{d['k']}")
+def test_dense_reference_equals_binned(vsr, lens):
+    """vsr_raster_dense (every pixel against every triangle, no tile bins)
+    gives vsr_raster's outputs bit for bit: ragged tiles, invalid corners, a
+    360-degree wrap, triangles culled at set-up (a vertex at the eye, a
+    plane through it) and more than one chunk of triangles per tile."""
+    tris = np.concatenate([scenes.random_triangles(900, 1.0, 10.0, 0.15, seed=31),
+                           scenes.random_triangles(300, 0.5, 3.0, 0.4, seed=32)])
+    tris[5, 0] = 0.0                       # a vertex at the eye
+    tris[6, 2] = 2.0 * tris[6, 0]          # A, B, C on one line through the eye... 
+    tris[6, 1] = 3.0 * tris[6, 0]          # ...so the plane holds the eye (det = 0)
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), scenes.camera())
+    m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+    binned = _gpu_outputs(vsr.raster(m, sc))
+    dense = _gpu_outputs(vsr.raster_dense(m, sc))
+    assert vsr.last_device_status() == 0
+    for k in binned:
+        assert np.array_equal(binned[k].view(np.uint32), dense[k].view(np.uint32)), k
+    assert (binned["id"] != oracle.NO_ID).mean() > 0.2
+
+
+def test_large_map_regenerated_into_grid_wide_index(vsr):
+    """A 4096 x 2176 map (34,816 tiles: its first index comes from the
+    grid-wide kernels, not the single-CTA build) updated twice with the same
+    lens: each update files its tiles into the plan the grid-wide build left.
+    Both frames equal a freshly made map's bit for bit; a change of lens in
+    between rebuilds the index whole and also matches."""
+    W, H = 4096, 2176
+    lens_a, lens_b = (0.0, 1.0, 1.0, 180.0), (0.32, 0.62, 0.86, 270.0)
+    tris = scenes.random_triangles(4000, 1.0, 20.0, 0.05, seed=24)
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), scenes.camera())
+    m = vsr.Map(W, H, *lens_a)
+    for lens in (lens_a, lens_b):
+        fresh = _gpu_outputs(vsr.raster(vsr.Map(W, H, *lens), sc))
+        for _ in range(2):
+            m.update(W, H, *lens)
+            got = _gpu_outputs(vsr.raster(m, sc))
+            assert vsr.last_device_status() == 0
+            for k in got:
+                assert np.array_equal(got[k].view(np.uint32), fresh[k].view(np.uint32)), (lens, k)
+
+
 def test_large_map_grid_wide_tile_index(vsr):
     """A 4096 x 2176 map has 34,816 tiles, more than the single-CTA tile index
     takes, so its index is built by the grid-wide kernels: sampled pixels
