@@ -238,6 +238,74 @@ def test_lens_fit_recovers_target(vsr):
     assert res["history"][-1][1] < first_full  # the vertex stage lowers the full-resolution loss
 
 
+def test_lens_fit_full_size_workload(vsr):
+    """The differentiation workload at its own size: 1024 x 1024, 10,000
+    triangles, start (0.6, 1, 1) with N(0, 0.01^2) vertex noise, target
+    rendered at (0.2, 0.7, 0.9) from the true vertices.  The coarse-to-fine
+    fit recovers the lens within 0.01."""
+    from paper_2003_10558_gb300 import fit
+    target, start, tris, noisy, colors, W, H = scenes.grad_scene()
+    assert (W, H, len(tris)) == (1024, 1024, 10_000)
+    r = vsr.ShadedRenderer(W, H)
+    col = torch.from_numpy(colors).cuda()
+    lt = torch.tensor([target["k"], target["l"], target["s"], target["omega"]], dtype=torch.float64)
+    with torch.no_grad():
+        tgt = vsr.render_shaded(torch.from_numpy(tris).cuda(), col, lt, r)[0].clone()
+    res = fit.fit_lens(tgt, torch.from_numpy(noisy).cuda(), col, start, r, steps=30, vertex_steps=30)
+    got = res["lens"]
+    print(f"fit 1024^2: {got} in {len(res['history'])} steps, {res['seconds']:.2f} s")
+    assert abs(got["k"] - 0.2) < 0.01 and abs(got["l"] - 0.7) < 0.01 and abs(got["s"] - 0.9) < 0.01, got
+
+
+def test_lens_fit_checkpoint_resume(vsr, tmp_path):
+    """A fit saved after any step and loaded into a fresh LensFit continues
+    where it stopped.  The lens stages are deterministic: a resumed run
+    repeats the uninterrupted one bit for bit (loss, k, l, s of every step,
+    the final lens and Adam moments).  The vertex stage sums per-triangle
+    gradients with float atomics: its state is restored bit for bit, and the
+    continued steps agree with the uninterrupted run to rounding."""
+    from paper_2003_10558_gb300 import fit
+    target, start, tris, noisy, colors, W, H = scenes.grad_scene(W=256, H=256)
+    col = torch.from_numpy(colors).cuda()
+    lt = torch.tensor([target["k"], target["l"], target["s"], target["omega"]], dtype=torch.float64)
+    r = vsr.ShadedRenderer(W, H)
+    with torch.no_grad():
+        tgt = vsr.render_shaded(torch.from_numpy(tris).cuda(), col, lt, r)[0].clone()
+    nz = torch.from_numpy(noisy).cuda()
+    kw = dict(sigmas=(16, 4, 0), steps=8, vertex_steps=6)
+
+    def make():
+        return fit.LensFit(tgt, nz, col, start, vsr.ShadedRenderer(W, H), **kw)
+
+    full = make().run()
+    again = make().run(max_steps=24)  # the lens stages of a second uninterrupted run
+    assert full.history[:24] == again.history  # deterministic lens stages
+    # stop inside the second lens stage, save, resume in a fresh fit
+    a = make().run(max_steps=11)
+    path = tmp_path / "fit.pt"
+    a.save(path)
+    b = make().load(path)
+    sa, sb = a.state_dict(), b.state_dict()
+    assert torch.equal(sa["lens"], sb["lens"]) and torch.equal(sa["verts"], sb["verts"])
+    assert (b.stage, b.step_in_stage) == (1, 3)
+    b.run(max_steps=13)  # to the end of the lens stages
+    assert b.history == full.history[:24]
+    ma = full.opt.state_dict()["state"][0]
+    mb = b.opt.state_dict()["state"][0]
+    assert torch.equal(ma["exp_avg"], mb["exp_avg"]) and torch.equal(ma["exp_avg_sq"], mb["exp_avg_sq"])
+    # into the vertex stage: save after two of its steps, resume
+    b.run(max_steps=2)
+    b.save(path)
+    c = make().load(path)
+    assert torch.equal(c.verts.detach(), b.verts.detach()) and c.stage == 3 and c.step_in_stage == 2
+    c.run()
+    assert c.done() and len(c.history) == len(full.history)
+    for hc, hf in zip(c.history, full.history):
+        assert abs(hc[1] - hf[1]) <= 1e-4 * abs(hf[1]) and max(abs(x - y) for x, y in zip(hc[2:], hf[2:])) < 1e-5
+    with pytest.raises(ValueError):
+        fit.LensFit(tgt, nz, col, start, r, sigmas=(8, 0), steps=8, vertex_steps=6).load(path)
+
+
 def test_empty_scene_and_invalid_calls(vsr):
     W, H = 64, 48
     r = vsr.ShadedRenderer(W, H)
