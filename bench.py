@@ -37,13 +37,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pixel x triangle tests/s"
+WORKLOAD = "single-view 1920x1080, k=0.32 l=0.62 s=0.86 Omega=270, icosphere L5 + 200k triangles"
 UNIT = "tests/s"
 OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
 LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
-# kernels of libvsr.so per step: map, tile index, set-up, bin count, bin scan,
-# bin pair fill, bin search fill (returns at once when the pair list is
-# complete), work items, raster
-LAUNCHES_PER_STEP = 9
+# kernels of libvsr.so per step: tile-index reset, map, index cell scan,
+# index finish (the map stream), set-up, bin count, bin scan, bin pair fill,
+# work items, raster
+LAUNCHES_PER_STEP = 10
 
 
 def parse():
@@ -62,6 +63,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals per lens stream")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="single workload: skip the dense, batched and serving legs of the JSON line")
+    ap.add_argument("--leg-frames", type=int, default=30, help="batched leg: timed frames per arm")
+    ap.add_argument("--leg-seconds", type=float, default=10.0, help="serving leg: seconds of arrivals")
     return ap.parse_args()
 
 
@@ -217,8 +222,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "single-view 1920x1080, icosphere L5 + 200k triangles",
-                                            "W": lens["W"], "H": lens["H"], "T": int(len(tris))},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "W": lens["W"], "H": lens["H"],
+                                            "T": int(len(tris))},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -350,6 +355,30 @@ def run_vsr(args, rank, world, local):
     assert V.last_device_status() == 0
     pstep_ms = a.elapsed_time(b) / K
     del pm, ps_sc
+    # the dense reference (no binning: every pixel against every triangle) on
+    # the same frame, its outputs against the binned path's
+    dense = None
+    if not args.no_legs:
+        V.bin(m, sc)
+        ref = {k: v.clone() for k, v in V.raster(m, sc, binned=True).items()}
+        dout = V.raster_dense(m, sc)
+        torch.cuda.synchronize()
+        same = all(torch.equal(ref[k], dout[k]) for k in ("id", "depth", "cov"))
+        KD = 2
+        a, b = evt(), evt()
+        a.record(stream)
+        for _ in range(KD):
+            V.raster_dense(m, sc, out=dout)
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert V.last_device_status() == 0
+        dense_ms = a.elapsed_time(b) / KD
+        dense = {"kernel": "raster_dense_kernel", "ms": dense_ms, "launches": KD,
+                 "pair_tests_per_frame": W * H * T,
+                 "binned_bin_plus_raster_ms": stage_ms["bin"] + stage_ms["raster"],
+                 "speedup_binned_vs_dense": dense_ms / (stage_ms["bin"] + stage_ms["raster"]),
+                 "outputs_identical": bool(same)}
+        del ref, dout
     # replicas: tests summed over ranks, time of the slowest rank
     total_units, tot_s = replicas.combine(n_alg * K, sum(step_ms) / 1000.0)
     ms_per_step = 1000.0 * tot_s / K
@@ -382,6 +411,23 @@ def run_vsr(args, rank, world, local):
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T * 36,
                "d2h_bytes_per_step": W * H * 12, "ms_per_step": 1000.0 * e2e_s / K}
 
+    # the batched and serving workloads, short (single GPU only)
+    batched = serving = None
+    if not args.no_legs and world == 1:
+        del flush
+        torch.cuda.empty_cache()
+        vb, tb, vp, tp, same_b, cfg, all_views = batched_leg(args, rank, world, dev, args.leg_frames)
+        batched = {"value": vb / tb, "unit": "views/s", "plain_value": vp / tp,
+                   "speedup_vs_plain": (vb / tb) / (vp / tp), "frames": args.leg_frames,
+                   "ms_per_frame": 1000 * tb / args.leg_frames, "plain_ms_per_frame": 1000 * tp / args.leg_frames,
+                   "outputs_identical": bool(same_b), "batch": cfg,
+                   "workload": f"{len(all_views)} mixed views (512^2..2048x1024) of one 1M-triangle scene, "
+                               "maps cached, CUDA-event timed"}
+        res, server = serving_leg(args, dev, args.leg_seconds, streams=("pooled",))
+        serving = dict(res["pooled"], server=server,
+                       workload="Poisson arrivals at %g/s for %g s, lenses from a pool of 256, 4 resident scenes "
+                                "(100k-1M triangles), views of the batched distribution, host clock"
+                                % (args.rate, args.leg_seconds))
     if rank != 0:
         return
     pk, pk_kind = peaks()
@@ -391,11 +437,27 @@ def run_vsr(args, rank, world, local):
     rast_mean_s = statistics.mean(rast_ms) / 1000.0
     achieved = n_alg * OPS_PER_TEST / rast_mean_s
     traffic = raster_traffic()
+    # achieved HBM bandwidth of the memory-bound stages (algorithmic bytes /
+    # their live CUDA-event times): the map with its tile cones and index
+    # (16 B per pixel + 48 B cone/geometry + 32 B index entry per tile), the
+    # set-up (36 B read + 160 B written per triangle) and the raster's own
+    # streams (16 B map read + 12 B outputs written per pixel)
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    ntiles = ((W + 15) // 16) * ((H + 15) // 16)
+
+    def bw(nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"bytes": int(nbytes), "ms": ms, "GB_per_s": gbs, "frac": gbs / hbm_peak}
+
+    hbm = {"peak_GB_per_s": hbm_peak, "peak_source": f"{pk_kind} hbm_gbs",
+           "map_with_index": bw(16 * W * H + 80 * ntiles, stage_ms["map alone"]),
+           "setup": bw(196 * T, stage_ms["setup alone"]),
+           "raster_map_read_and_outputs": bw(28 * W * H, statistics.mean(rast_ms))}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded scene generator)",
-        "config": {"workload": "single-view 1920x1080, k=0.32 l=0.62 s=0.86 Omega=270, icosphere L5 + 200k triangles",
+        "config": {"workload": WORKLOAD,
                    "W": W, "H": H, "T": T, "l2": "flushed before every step (256 MB write, outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "frames_per_s": world * K / tot_s,
@@ -411,7 +473,14 @@ def run_vsr(args, rank, world, local):
                      f"{LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} sm_max_mhz)"},
         "clocks": clk.summary(),
         "gpu_launches": LAUNCHES_PER_STEP * K,
+        "hbm": hbm,
     }
+    if dense is not None:
+        line["dense"] = dense
+    if batched is not None:
+        line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
@@ -422,32 +491,22 @@ def run_vsr(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, world, local):
-    """64 views of one 1M-triangle scene (sizes from {512^2, 1024^2,
-    2048x1024, 1920x1080}, k ~ U[-1,1], l, s ~ U[0.5,1], Omega ~ U[90,360],
-    eye uniform in a radius-5 ball), maps cached.  Frames/s (views/s) of the
-    batched path (one persistent raster launch per frame, CUDA-graph replay)
-    against per-view plain launches (set-up, binning, raster per view), with
-    the outputs of the last frame compared bit for bit."""
+def batched_leg(args, rank, world, dev, K):
+    """The batched workload: 64 views of one 1M-triangle scene (sizes from
+    {512^2, 1024^2, 2048x1024, 1920x1080}, k ~ U[-1,1], l, s ~ U[0.5,1],
+    Omega ~ U[90,360], eye uniform in a radius-5 ball), maps cached.  Views/s
+    of the batched path (one CUDA graph of per-view chains per frame) against
+    per-view plain launches (set-up, binning, raster per view), each over K
+    timed frames (CUDA events), with the outputs of the last frame compared
+    bit for bit.  Returns (views_batched, s_batched, views_plain, s_plain,
+    same, batch config, all views)."""
     import torch
     from paper_2003_10558_gb300 import vsr as V
-    from paper_2003_10558_gb300 import build as B
-    from paper_2003_10558_gb300 import scenes
-
-    import torch.distributed as dist
-    from paper_2003_10558_gb300 import replicas
-
-    torch.cuda.set_device(local)
-    if world > 1 and not dist.is_initialized():
-        dist.init_process_group("nccl")
-    B.build()
-    V.load()
-    dev = torch.device("cuda", local)
+    from paper_2003_10558_gb300 import scenes, replicas
     all_views = scenes.batched_views(args.views)
     # replicas: each rank renders its share of the views (pixel-balanced)
     views = [all_views[i] for i in replicas.shard_views([v["W"] * v["H"] for v in all_views], rank, world)]
     tris = torch.from_numpy(scenes.batched_scene()).to(dev)
-    T = tris.shape[0]
     maps = [V.Map(v["W"], v["H"], v["k"], v["l"], v["s"], v["omega"]) for v in views]
     cams = np.stack([v["cam"] for v in views])
 
@@ -469,7 +528,7 @@ def run_batched(args, rank, world, local):
             sc.update(tris, v["cam"])
             V.raster(m, sc, out=o)
 
-    def timed(fn, K):
+    def timed(fn):
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
@@ -481,11 +540,33 @@ def run_batched(args, rank, world, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1000.0
 
-    K = max(10, args.steps // 2)  # frames of ~0.1 s: about a second per arm
-    vb, tb = replicas.combine(len(views) * K, timed(batched, K))
-    vp, tp = replicas.combine(len(views) * K, timed(plain, K))
+    vb, tb = replicas.combine(len(views) * K, timed(batched))
+    vp, tp = replicas.combine(len(views) * K, timed(plain))
     assert V.last_device_status() == 0
     same = all(torch.equal(a[k], b[k]) for a, b in zip(ob, op) for k in ("id", "depth", "cov"))
+    cfg = batch.config()
+    del ob, op, batch, plain_scenes, maps, tris
+    torch.cuda.empty_cache()
+    return vb, tb, vp, tp, same, cfg, all_views
+
+
+def run_batched(args, rank, world, local):
+    """64 views of one 1M-triangle scene, batched graph against per-view
+    plain launches (see batched_leg); max(10, steps // 2) frames per arm."""
+    import torch
+    import torch.distributed as dist
+    from paper_2003_10558_gb300 import vsr as V
+    from paper_2003_10558_gb300 import build as B
+    from paper_2003_10558_gb300 import scenes
+
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    B.build()
+    V.load()
+    dev = torch.device("cuda", local)
+    K = max(10, args.steps // 2)  # frames of ~0.1 s: about a second per arm
+    vb, tb, vp, tp, same, cfg, all_views = batched_leg(args, rank, world, dev, K)
     if rank != 0:
         return
     npx = sum(v["W"] * v["H"] for v in all_views)
@@ -493,32 +574,27 @@ def run_batched(args, rank, world, local):
             "plain_value": vp / tp, "speedup_vs_plain": (vb / tb) / (vp / tp), "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_frame": 1000 * tb / K, "plain_ms_per_frame": 1000 * tp / K,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded scene generator)",
-            "outputs_identical": bool(same), "batch": batch.config(),
+            "outputs_identical": bool(same), "batch": cfg,
             "scaling": "strong",
             "config": {"workload": f"{len(all_views)} mixed views (512^2..2048x1024), one 1M-triangle scene",
-                       "views": len(all_views), "pixels": npx, "T": int(T), "maps": "cached",
+                       "views": len(all_views), "pixels": npx, "T": 1_000_000, "maps": "cached",
                        "parallelism": f"views sharded over {world} replicas" if world > 1 else "single GPU"}}
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, rank, world, local):
-    """Poisson arrivals over 4 resident scenes of {100k, 300k, 600k, 1M}
-    triangles (the batched workload's generator, seeds 30-33), views drawn
-    from the batched workload's distribution, 40 GB budget.  Two lens
-    streams: every request a fresh lens draw (map cache ~always misses), and
-    lenses drawn from a pool of 256 (the cache hits).  Latency = result
-    ready minus arrival; the client owns 96 output buffer sets and waits
-    for a set's previous request before reusing it (that wait counts in the
-    latency)."""
+def serving_leg(args, dev, duration, streams=("fresh", "pooled"), seed=3):
+    """Poisson arrivals at args.rate over 4 resident scenes of {100k, 300k,
+    600k, 1M} triangles (the batched workload's generator, seeds 30-33),
+    views drawn from the batched workload's distribution, 40 GB budget.  Two
+    lens streams: every request a fresh lens draw (map cache ~always misses),
+    and lenses drawn from a pool of 256 (the cache hits).  Latency = result
+    ready minus arrival (host clock); the client owns 96 output buffer sets
+    and waits for a set's previous request before reusing it (that wait
+    counts in the latency).  Returns {stream: stats} and the server's
+    counters."""
     import torch
     from paper_2003_10558_gb300 import vsr as V
-    from paper_2003_10558_gb300 import build as B
     from paper_2003_10558_gb300 import scenes
-
-    torch.cuda.set_device(local)
-    B.build()
-    V.load()
-    dev = torch.device("cuda", local)
     sizes = [100_000, 300_000, 600_000, 1_000_000]
     srv = V.Server(budget_bytes=40 << 30, slots=args.slots)
     scene_t = [torch.from_numpy(scenes.random_triangles(n, 1.0, 60.0, 0.0096, 30 + i)).to(dev)
@@ -529,7 +605,7 @@ def run_serving(args, rank, world, local):
     bufs = [{"id": torch.empty(Wm * Hm, dtype=torch.int32, device=dev),
              "depth": torch.empty(Wm * Hm, dtype=torch.float32, device=dev),
              "cov": torch.empty(Wm * Hm, dtype=torch.float32, device=dev)} for _ in range(nbuf)]
-    rng = np.random.default_rng(3 + 17 * rank)
+    rng = np.random.default_rng(seed)
 
     def draw_lens(r):
         W, H = scenes.VIEW_SIZES[r.integers(len(scenes.VIEW_SIZES))]
@@ -539,7 +615,7 @@ def run_serving(args, rank, world, local):
     pool = [draw_lens(rng) for _ in range(256)]
 
     def run_stream(pooled):
-        n = int(args.rate * args.duration)
+        n = int(args.rate * duration)
         arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n))
         pending = [None] * nbuf
         done = []
@@ -564,23 +640,47 @@ def run_serving(args, rank, world, local):
         ok = all(r["status"] == 0 for _, r in done)
         span = max(r["t_done"] for _, r in done) - t0
         hits = np.mean([r["map_cache_hit"] for _, r in done])
+        # latency over the first and the last tenth of the arrivals: a queue
+        # that grows without bound shows as a rising p50
+        tenth = max(1, len(lat) // 10)
         return {"requests": n, "all_ok": ok, "frames_per_s": n / span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
-                "p99_ms": 1000 * float(np.percentile(lat, 99)), "map_hit_rate": float(hits),
-                "offered_rate": args.rate, "seconds": span}
+                "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                "p50_first_tenth_ms": 1000 * float(np.percentile(lat[:tenth], 50)),
+                "p50_last_tenth_ms": 1000 * float(np.percentile(lat[-tenth:], 50)),
+                "map_hit_rate": float(hits), "offered_rate": args.rate, "seconds": span}
 
-    fresh = run_stream(False)
-    pooled = run_stream(True)
+    out = {}
+    for name in streams:
+        out[name] = run_stream(name == "pooled")
     st = srv.stats()
     srv.close()
+    del bufs, scene_t
+    torch.cuda.empty_cache()
+    return out, {"slots": args.slots, "budget_bytes": 40 << 30, "reruns": st["reruns"],
+                 "map_evictions": st["map_evictions"], "bytes_in_use": st["bytes_in_use"]}
+
+
+def run_serving(args, rank, world, local):
+    """The serving workload (see serving_leg): both lens streams, each
+    args.duration seconds of arrivals."""
+    import torch
+    from paper_2003_10558_gb300 import vsr as V
+    from paper_2003_10558_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    B.build()
+    V.load()
+    dev = torch.device("cuda", local)
+    res, server = serving_leg(args, dev, args.duration, seed=3 + 17 * rank)
     if rank != 0:
         return
-    line = {"metric": "serving frames/s and p50/p99 latency", "value": pooled["frames_per_s"], "unit": "frames/s",
-            "higher_is_better": True, "n_gpus": world, "dtype": "f32", "data": "synthetic (seeded scene generator)",
-            "pooled_lenses": pooled, "fresh_lenses": fresh,
-            "server": {"slots": args.slots, "budget_bytes": 40 << 30, "reruns": st["reruns"],
-                       "map_evictions": st["map_evictions"], "bytes_in_use": st["bytes_in_use"]},
+    line = {"metric": "serving frames/s and p50/p99 latency", "value": res["pooled"]["frames_per_s"],
+            "unit": "frames/s", "higher_is_better": True, "n_gpus": world, "dtype": "f32",
+            "data": "synthetic (seeded scene generator)", "pooled_lenses": res["pooled"],
+            "fresh_lenses": res["fresh"], "server": server,
             "config": {"workload": "Poisson arrivals, 4 resident scenes (100k-1M triangles), mixed views",
-                       "rate": args.rate, "duration_s": args.duration, "scenes": sizes}}
+                       "rate": args.rate, "duration_s": args.duration, "scenes": [100_000, 300_000, 600_000,
+                                                                                  1_000_000]}}
     print(json.dumps(line), flush=True)
 
 
