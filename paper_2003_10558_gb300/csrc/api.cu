@@ -145,22 +145,18 @@ vsr_status map_generate(vsr_map m, cudaStream_t st)
     for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
     // The first generation builds the whole tile index after the map.  A
     // later generation of the same projection (the same spec: a map rebuilt
-    // each frame) files the tiles from the map kernel itself, into the grid
-    // planned from the previous generation's histogram -- the plan a whole
-    // build would make -- so only the scan and the copy follow the map
-    // kernel.  After a change of lens the previous plan may fit the new
-    // tiles badly (every tile past its cut goes to the big list, which every
-    // triangle tests), so the index is built whole again.
+    // each frame) has the same tiles and the same grid plan, so the map
+    // kernel files its tiles into the plan the index header holds and one
+    // small kernel completes the index.  After a change of lens the plan
+    // may fit the new tiles badly (every tile past its cut goes to the big
+    // list, which every triangle tests), so the index is built whole again.
     const bool file = m->idx_built && memcmp(&m->idx_spec, &m->spec, sizeof(vsr_map_spec)) == 0;
-    // the reset clears the histogram the plan is made from: until this
-    // generation has completed, the next one must build the index whole
+    // until this generation has completed, the next one must build the index whole
     m->idx_built = false;
-    vsr_status s = VSR_OK;
-    if (file && (s = launch_tile_index_reset(m->idx, st)) != VSR_OK) return s;
     const TileIndex* into = file ? &m->idx : nullptr;
-    s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles,
-                           m->idx.geom, into, st)
-              : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, into, st);
+    vsr_status s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map,
+                                      m->tiles, m->idx.geom, into, st)
+                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, into, st);
     if (s != VSR_OK) return s;
     s = file ? launch_tile_index_finish(m->tiles, m->tx * m->ty, m->idx, st)
              : launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
@@ -439,7 +435,8 @@ vsr_status vsr_scene_create(vsr_scene* out)
         return VSR_ERR_OOM;
     }
     *sc->h_total = 0;
-    if (cudaEventCreateWithFlags(&sc->total_event, cudaEventDisableTiming) != cudaSuccess) {
+    sc->h_total_dev = (uint32_t*)mapped_host(sc->h_total);
+    if (!sc->h_total_dev || cudaEventCreateWithFlags(&sc->total_event, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         cudaFreeHost(sc->h_total);
         delete sc;
@@ -531,13 +528,14 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
     sc->last_ntiles = ntiles;
     uint32_t* counts = sc->counts;
     // Bin capacity.  Sized synchronously the first time and whenever the
-    // number of tiles or triangles changes; otherwise the pair total of the
-    // previous binning (copied to pinned memory, read only once its event has
-    // completed, never waited for) grows the capacity ahead of need, and the
-    // fill kernel reports any overflow in the status word.
+    // number of tiles or triangles changes (the first time only, for a scene
+    // with async_sizing); otherwise the pair total of the previous binning
+    // (copied to pinned memory, read only once its event has completed, never
+    // waited for) grows the capacity ahead of need, and the fill kernel
+    // reports any overflow in the status word.
     // the bins' sizes depend on the map, the scene and the step's cap width
     const uint64_t shape = ((uint64_t)ntiles << 32) ^ (uint64_t)sc->T ^ ((uint64_t)(pstep != 0) << 63);
-    const bool resize = sc->cap == 0 || sc->sized_shape != shape;
+    const bool resize = sc->cap == 0 || (!sc->async_sizing && sc->sized_shape != shape);
     if (!resize && sc->total_pending && cudaEventQuery(sc->total_event) == cudaSuccess) {
         sc->total_pending = false;
         const uint64_t last = *sc->h_total;
@@ -552,9 +550,14 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
     uint2* pairs = sc->pairs;
     const uint32_t pair_cap = sc->cap;
     if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st, pstep)) != VSR_OK) return s;
-    if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st)) != VSR_OK) return s;
-    if (!sc->total_pending) {
-        VSR_CUDA_TRY(cudaMemcpyAsync(sc->h_total, sc->offsets + ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    // the scan also stores the pair total into the pinned host word (its
+    // device address) unless an earlier total has not been read yet -- and
+    // always when this binning sizes the bins, which reads this total
+    const bool record = resize || !sc->total_pending;
+    if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st, record ? sc->h_total_dev : nullptr)) !=
+        VSR_OK)
+        return s;
+    if (record) {
         VSR_CUDA_TRY(cudaEventRecord(sc->total_event, st));
         sc->total_pending = true;
     }

@@ -147,60 +147,105 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __res
     sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
 }
 
-// A later generation of a map files its tiles into the grid of the
-// previous one (see launch_tile_index_reset): the plan comes from the
-// previous generation's histogram, which the full build and the filing
-// map kernels both leave in the header; the counters start from zero.
-// One CTA of IDX_RESET_THREADS threads.
-constexpr int IDX_RESET_THREADS = 1024;
+// The tile loops of the one-CTA index kernels take IDX_BATCH tiles per
+// thread at a time and issue each step for all of them before the next
+// (geometry loads, then slots, then cone loads, then stores), so their
+// memory latencies overlap instead of adding up tile after tile.
+constexpr int IDX_BATCH = 4;
 
-__global__ void __launch_bounds__(IDX_RESET_THREADS) idx_reset_kernel(TileIndexHdr* __restrict__ hdr,
-                                                                       uint32_t* __restrict__ cell_count)
+__device__ __forceinline__ void load_geom_batch(const float4* __restrict__ geom, int ntiles, int base, int stride,
+                                                float4 (&g)[IDX_BATCH])
 {
-    __shared__ int s_ncell;
-    if (threadIdx.x == 0) {
-        TileIndexHdr h = *hdr;
-        unsigned nv = 0u;
-        for (int b = 0; b < IDX_HIST; ++b) nv += h.hist[b];
-        h.n_valid = nv;
-        index_plan(&h, h);
-        hdr->nlat = h.nlat;
-        hdr->nlon = h.nlon;
-        hdr->ncell = h.ncell;
-        hdr->cell = h.cell;
-        hdr->alpha_cut = h.alpha_cut;
-        hdr->alpha_small_max = 0u;
-        hdr->h_max = 0u;
-        hdr->n_big = 0u;
-        hdr->n_valid = 0u;
-        s_ncell = min(h.ncell, IDX_CELLS_MAX);
+#pragma unroll
+    for (int u = 0; u < IDX_BATCH; ++u) {
+        const int i = base + u * stride;
+        g[u] = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
-    __syncthreads();  // the histogram is read before it is cleared
-    if (threadIdx.x < IDX_HIST) hdr->hist[threadIdx.x] = 0u;
-    for (int c = threadIdx.x; c < s_ncell; c += IDX_RESET_THREADS) cell_count[c] = 0u;
 }
 
-// After the filing map kernel and the scan of the cell counts: the
-// cell-sorted copies of the small tiles (slot by decrementing the cell
-// count), the widest ramp of all tiles and the largest small half-angle.
-__global__ void __launch_bounds__(IDX_THREADS) idx_finish_kernel(const Cone* __restrict__ tiles,
-                                                                  const float4* __restrict__ geom, int ntiles,
-                                                                  TileIndexHdr* __restrict__ hdr,
-                                                                  const uint32_t* __restrict__ cell_start,
-                                                                  uint32_t* __restrict__ cell_count,
-                                                                  Cone* __restrict__ sorted)
+// Exclusive scan of n counts in shared memory, in place, by a CTA of
+// NT threads (all of which call it; ends with a barrier); returns the total
+// to every thread.  Warp w owns a contiguous segment of cells and walks it 32
+// cells at a time, lane l on cell 32 k + l of the step (no bank conflicts),
+// with a shuffle scan per step.
+template <int NT>
+__device__ uint32_t block_scan_smem(uint32_t* s, int n, uint32_t* s_wsum /* NT / 32 words */)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg = ((n + NW - 1) / NW + 31) & ~31;
+    const int b0 = min(n, warp * seg), b1 = min(n, b0 + seg);
+    uint32_t tot = 0;
+    for (int c = b0 + lane; c < b1; c += 32) tot += s[c];
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) s_wsum[warp] = tot;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_wsum[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    uint32_t carry = warp > 0 ? s_wsum[warp - 1] : 0u;
+    const uint32_t total = s_wsum[NW - 1];
+    for (int c0 = b0; c0 < b1; c0 += 32) {
+        const int c = c0 + lane;
+        const uint32_t v = c < b1 ? s[c] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (c < b1) s[c] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    __syncthreads();
+    return total;
+}
+
+// After a filing map kernel and the scan of its cell counts (cell_start):
+// the cell-sorted copies of the small tiles (slot by decrementing the cell
+// count, which returns the counts to zero for the next generation), the
+// widest ramp of all tiles and the largest small half-angle (into maxima the
+// filing map kernel cleared); block 0 moves the filing's work counters
+// (histogram, big-list length) into the header and clears them.
+__global__ void __launch_bounds__(IDX_THREADS) idx_file_copy_kernel(const Cone* __restrict__ tiles,
+                                                                     const float4* __restrict__ geom, int ntiles,
+                                                                     TileIndexHdr* __restrict__ hdr,
+                                                                     const uint32_t* __restrict__ cell_start,
+                                                                     uint32_t* __restrict__ cell_count,
+                                                                     Cone* __restrict__ sorted)
 {
     __shared__ TileIndexHdr s_h;
-    if (threadIdx.x == 0) s_h = *hdr;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        s_h.nlat = min(max(hdr->nlat, 1), IDX_NLAT_MAX);
+        s_h.nlon = 2 * s_h.nlat;
+        s_h.cell = hdr->cell;
+        s_h.alpha_cut = hdr->alpha_cut;
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * IDX_THREADS + threadIdx.x;
+    if (blockIdx.x == 0) {
+        if (tid == 0) {
+            hdr->n_big = min(hdr->n_big_work, (unsigned)ntiles);
+            hdr->n_big_work = 0u;
+        }
+        if (tid < IDX_HIST) {
+            hdr->hist[tid] = hdr->hist_work[tid];
+            hdr->hist_work[tid] = 0u;
+        }
+    }
+    const int i = blockIdx.x * IDX_THREADS + tid;
     const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     const bool valid = g.w >= 0.0f;
     const bool small = valid && g.x <= s_h.alpha_cut;
     if (small) {
         const int c = home_cell_geom(g, s_h);
-        sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
+        const uint32_t slot = cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u;
+        if (slot < (uint32_t)ntiles) sorted[slot] = index_entry(tiles[i], i);
     }
     unsigned hm = valid ? __float_as_uint(g.w) : 0u, am = small ? __float_as_uint(g.x) : 0u;
     for (int o = 16; o; o >>= 1) {
@@ -218,16 +263,20 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_finish_kernel(const Cone* __r
 // and no memsets instead of four launches and two memsets.
 constexpr int IDX_FUSED_THREADS = 1024;
 constexpr int IDX_FUSED_TILES = 32768;
-constexpr size_t IDX_FUSED_SMEM = sizeof(uint32_t) * IDX_CELLS_MAX;
+static_assert(IDX_CELLS_MAX <= 65535, "home cells are kept as 16-bit indices");
+constexpr size_t IDX_FUSED_SMEM = sizeof(uint32_t) * IDX_CELLS_MAX + sizeof(uint16_t) * IDX_FUSED_TILES;
 
 __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone* __restrict__ tiles,
                                                                        const float4* __restrict__ geom, int ntiles,
                                                                        TileIndexHdr* __restrict__ hdr,
                                                                        uint32_t* __restrict__ cell_start,
                                                                        Cone* __restrict__ sorted,
-                                                                       Cone* __restrict__ big)
+                                                                       Cone* __restrict__ big,
+                                                                       uint32_t* __restrict__ cell_count)
 {
     extern __shared__ uint32_t s_cell[];  // per-cell counts, then running slots
+    // each small tile's home cell (0xffff: big or empty), from step 3 to step 5
+    uint16_t* s_tcell = reinterpret_cast<uint16_t*>(s_cell + IDX_CELLS_MAX);
     __shared__ TileIndexHdr s_h;
     __shared__ uint32_t s_wsum[IDX_FUSED_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -236,15 +285,19 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
     // 1. histogram of half-angles (one add per group of equal bins in a
     // warp), valid tiles, widest ramp (one atomic per warp)
     uint32_t nv = 0u, hm = 0u;
-    for (int base = 0; base < ntiles; base += IDX_FUSED_THREADS) {
-        const int i = base + tid;
-        const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-        const bool ok = g.w >= 0.0f;
-        const int bin = ok ? hist_bin(g.x) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h.hist[bin], (unsigned)__popc(peers));
-        nv += ok;
-        hm = max(hm, ok ? __float_as_uint(g.w) : 0u);  // non-negative floats order as their bits
+    for (int base = 0; base < ntiles; base += IDX_FUSED_THREADS * IDX_BATCH) {
+        float4 gb[IDX_BATCH];
+        load_geom_batch(geom, ntiles, base + tid, IDX_FUSED_THREADS, gb);
+#pragma unroll
+        for (int u = 0; u < IDX_BATCH; ++u) {
+            const float4 g = gb[u];
+            const bool ok = g.w >= 0.0f;
+            const int bin = ok ? hist_bin(g.x) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h.hist[bin], (unsigned)__popc(peers));
+            nv += ok;
+            hm = max(hm, ok ? __float_as_uint(g.w) : 0u);  // non-negative floats order as their bits
+        }
     }
     for (int o = 16; o; o >>= 1) {
         nv += __shfl_xor_sync(0xffffffffu, nv, o);
@@ -263,56 +316,56 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
     __syncthreads();
     // 3. per-cell counts; big tiles to their own list
     uint32_t am = 0u;
-    for (int i = tid; i < ntiles; i += IDX_FUSED_THREADS) {
-        const float4 g = geom[i];
-        if (g.w < 0.0f) continue;
-        if (g.x > s_h.alpha_cut) {
-            big[atomicAdd(&s_h.n_big, 1u)] = index_entry(tiles[i], i);
-        } else {
-            atomicAdd(&s_cell[home_cell_geom(g, s_h)], 1u);
-            am = max(am, __float_as_uint(g.x));
+    for (int base = tid; base < ntiles; base += IDX_FUSED_THREADS * IDX_BATCH) {
+        float4 gb[IDX_BATCH];
+        load_geom_batch(geom, ntiles, base, IDX_FUSED_THREADS, gb);
+#pragma unroll
+        for (int u = 0; u < IDX_BATCH; ++u) {
+            const float4 g = gb[u];
+            const int i = base + u * IDX_FUSED_THREADS;
+            if (i >= ntiles) continue;
+            uint16_t home = 0xffffu;
+            if (g.w >= 0.0f) {
+                if (g.x > s_h.alpha_cut) {
+                    big[atomicAdd(&s_h.n_big, 1u)] = index_entry(tiles[i], i);
+                } else {
+                    const int c = home_cell_geom(g, s_h);
+                    atomicAdd(&s_cell[c], 1u);
+                    home = (uint16_t)c;
+                    am = max(am, __float_as_uint(g.x));
+                }
+            }
+            s_tcell[i] = home;
         }
     }
     for (int o = 16; o; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
     if (lane == 0 && am) atomicMax(&s_h.alpha_small_max, am);
     __syncthreads();
-    // 4. exclusive scan of the counts: thread t owns the cells [t per, (t+1) per)
-    const int per = (ncell + IDX_FUSED_THREADS - 1) / IDX_FUSED_THREADS;
-    const int c0 = min(ncell, tid * per), c1 = min(ncell, c0 + per);
-    uint32_t local = 0;
-    for (int c = c0; c < c1; ++c) local += s_cell[c];
-    uint32_t x = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = s_wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    // 4. exclusive scan of the counts (in place: they become running slots),
+    // the starts out (coalesced)
+    const uint32_t total = block_scan_smem<IDX_FUSED_THREADS>(s_cell, ncell, s_wsum);
+    for (int c = tid; c < ncell; c += IDX_FUSED_THREADS) cell_start[c] = s_cell[c];
+    if (tid == 0) cell_start[ncell] = total;
+    // 5. cell-sorted copies of the small tiles (slots, then cone loads, then stores)
+    for (int base = tid; base < ntiles; base += IDX_FUSED_THREADS * IDX_BATCH) {
+        uint32_t slot[IDX_BATCH];
+#pragma unroll
+        for (int u = 0; u < IDX_BATCH; ++u) {
+            const int i = base + u * IDX_FUSED_THREADS;
+            const uint16_t c = i < ntiles ? s_tcell[i] : (uint16_t)0xffffu;
+            slot[u] = c != 0xffffu ? atomicAdd(&s_cell[c], 1u) : 0xffffffffu;
         }
-        s_wsum[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = x - local + (warp > 0 ? s_wsum[warp - 1] : 0u);
-    for (int c = c0; c < c1; ++c) {
-        const uint32_t n = s_cell[c];
-        s_cell[c] = run;
-        cell_start[c] = run;
-        run += n;
-    }
-    if (tid == IDX_FUSED_THREADS - 1) cell_start[ncell] = run;  // the last run ends at ncell
-    __syncthreads();
-    // 5. cell-sorted copies of the small tiles
-    for (int i = tid; i < ntiles; i += IDX_FUSED_THREADS) {
-        const float4 g = geom[i];
-        if (g.w < 0.0f || g.x > s_h.alpha_cut) continue;
-        sorted[atomicAdd(&s_cell[home_cell_geom(g, s_h)], 1u)] = index_entry(tiles[i], i);
+        Cone cn[IDX_BATCH];
+#pragma unroll
+        for (int u = 0; u < IDX_BATCH; ++u)
+            if (slot[u] < (uint32_t)ntiles) cn[u] = tiles[base + u * IDX_FUSED_THREADS];
+#pragma unroll
+        for (int u = 0; u < IDX_BATCH; ++u)
+            if (slot[u] < (uint32_t)ntiles) sorted[slot[u]] = index_entry(cn[u], base + u * IDX_FUSED_THREADS);
     }
     if (tid == 0) *hdr = s_h;
+    // the filing of later generations adds into the global cell counts
+    for (int c = tid; c < IDX_CELLS_MAX; c += IDX_FUSED_THREADS) cell_count[c] = 0u;
 }
 
 // ---- per-triangle binning ---------------------------------------------------
@@ -338,6 +391,10 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
 // caller without a list) the fill searches again instead, with the same
 // decrement.  The counts return to zero either way; the order of ids inside
 // a bin is not fixed and the raster kernels' results do not depend on it.
+// (Keeping each hit's slot -- the old value of its counter -- would spare
+// the fill its atomics, but makes the count pass wait for each counter's
+// return: measured 44.3 -> 58.7 us for the count against 17.2 -> 8.6 us for
+// the fill on the 1080p frame.)
 
 constexpr int BIN_BIG_CHUNK = 16;
 constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full)
@@ -552,7 +609,8 @@ __global__ void __launch_bounds__(256) bin_pairs_kernel(const uint2* __restrict_
 // chunks.  n comes from n_dev when it is not NULL.
 __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__ counts,
                                                      const uint32_t* __restrict__ extra, int n_host,
-                                                     const int* __restrict__ n_dev, uint32_t* __restrict__ offsets)
+                                                     const int* __restrict__ n_dev, uint32_t* __restrict__ offsets,
+                                                     volatile uint32_t* total_host)
 {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry_s;
@@ -592,15 +650,21 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__
         if (tid == 0) carry_s += warp_sums[31];
         __syncthreads();
     }
-    if (tid == 0) offsets[n] = carry_s;
+    if (tid == 0) {
+        offsets[n] = carry_s;
+        if (total_host) {  // the total straight into the host's pinned word (read after an event)
+            *total_host = carry_s;
+            __threadfence_system();
+        }
+    }
 }
 
 }  // namespace
 
 vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
-                       cudaStream_t st)
+                       cudaStream_t st, uint32_t* total_host)
 {
-    scan_kernel<<<1, 1024, 0, st>>>(counts, extra, n, n_dev, offsets);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, extra, n, n_dev, offsets, total_host);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -619,7 +683,8 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
             attr_set.fetch_or(bit);
         }
         idx_fused_kernel<<<1, IDX_FUSED_THREADS, IDX_FUSED_SMEM, st>>>(tiles, idx.geom, ntiles, idx.hdr,
-                                                                        idx.cell_start, idx.sorted, idx.big);
+                                                                        idx.cell_start, idx.sorted, idx.big,
+                                                                        idx.cell_count);
         VSR_CUDA_TRY(cudaGetLastError());
         return VSR_OK;
     }
@@ -667,22 +732,13 @@ static int bin_shape(int T, int sms)
     return 1;
 }
 
-vsr_status launch_tile_index_reset(TileIndex idx, cudaStream_t st)
-{
-    idx_reset_kernel<<<1, IDX_RESET_THREADS, 0, st>>>(idx.hdr, idx.cell_count);
-    VSR_CUDA_TRY(cudaGetLastError());
-    return VSR_OK;
-}
-
 vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
     vsr_status s = launch_scan(idx.cell_count, nullptr, 0, &idx.hdr->ncell, idx.cell_start, st);
     if (s != VSR_OK) return s;
-    if (ntiles > 0) {
-        idx_finish_kernel<<<(ntiles + IDX_THREADS - 1) / IDX_THREADS, IDX_THREADS, 0, st>>>(
-            tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
-        VSR_CUDA_TRY(cudaGetLastError());
-    }
+    idx_file_copy_kernel<<<ntiles > 0 ? (ntiles + IDX_THREADS - 1) / IDX_THREADS : 1, IDX_THREADS, 0, st>>>(
+        tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
+    VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 

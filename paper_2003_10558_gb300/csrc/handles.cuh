@@ -53,6 +53,7 @@ struct vsr_scene_s {
     uint32_t cap = 0;
     uint64_t sized_shape = 0;           // (tiles, T) the bins were last sized for
     uint32_t* h_total = nullptr;        // pinned: pair total of a recent binning
+    uint32_t* h_total_dev = nullptr;    // its device address (the scan kernel stores the total there)
     cudaEvent_t total_event = nullptr;  // completion of that copy
     bool total_pending = false;
     int last_ntiles = 0;
@@ -67,6 +68,12 @@ struct vsr_scene_s {
     // device status word of this scene's kernels: NULL = the per-device word
     // of vsr_last_device_status; the server gives its workspaces their own
     int* status = nullptr;
+    // bins sized without waiting for the device when the map's shape changes
+    // (the capacity of earlier binnings is kept and only grows): an owner
+    // that renders a request again after a bin overflow (the server) needs
+    // no synchronisation per new shape; everyone else gets exact bins on
+    // every call
+    bool async_sizing = false;
 };
 
 inline int* scene_status(const vsr_scene_s* s) { return s->status ? s->status : status_word(); }

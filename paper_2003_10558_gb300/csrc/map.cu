@@ -72,10 +72,11 @@ constexpr int CONE_WARPS = TILE_PIX / 32;
 
 __device__ __forceinline__ void cone_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(TILE_PIX) : "memory"); }
 
-// file_into (optional): the tile index of a later generation of the map
-// (prepared by launch_tile_index_reset); thread 0 then files the tile
-// (index `tile`) into it: its histogram bin, and its cell's count or, past
-// the plan's small-tile half-angle, the big list.
+// file_into (optional): the tile index of a later generation of the same
+// map; thread 0 then files the tile (index `tile`) into the plan the index
+// header holds: its histogram bin, and its cell's count or, past the plan's
+// small-tile half-angle, the big list (the header's work counters).  Tile 0
+// also clears the index's two maxima, which the index finish then forms.
 __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom, const TileIndex* file_into = nullptr,
                             int tile = 0)
 {
@@ -103,9 +104,10 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
     const float len = sqrtf(a * a + b * b + c * c);
     float ax = 0.0f, ay = 0.0f, az = 1.0f;
     if (len > 1e-6f * fmaxf(n, 1.0f)) {
-        ax = a / len;
-        ay = b / len;
-        az = c / len;
+        const float inv = 1.0f / len;
+        ax = a * inv;
+        ay = b * inv;
+        az = c * inv;
     }
     float cmin = valid ? G.x * ax + G.y * ay + G.z * az : 2.0f;
     float hmax = valid ? h : 0.0f;
@@ -133,11 +135,15 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         const float4 g =
             make_float4(acosf(ca), asinf(fmaxf(-1.0f, fminf(1.0f, ay))), atan2f(ax, az), n > 0.0f ? hh : -1.0f);
         *geom = g;
+        if (file_into && tile == 0) {
+            file_into->hdr->h_max = 0u;
+            file_into->hdr->alpha_small_max = 0u;
+        }
         if (file_into && g.w >= 0.0f) {
             TileIndexHdr* hdr = file_into->hdr;
-            atomicAdd(&hdr->hist[hist_bin(g.x)], 1u);
+            atomicAdd(&hdr->hist_work[hist_bin(g.x)], 1u);
             if (g.x > hdr->alpha_cut) {
-                const uint32_t b = atomicAdd(&hdr->n_big, 1u);
+                const uint32_t b = atomicAdd(&hdr->n_big_work, 1u);
                 if (b < file_into->ntiles) file_into->big[b] = index_entry(cone, tile);
             } else {
                 atomicAdd(&file_into->cell_count[home_cell_geom(g, *hdr)], 1u);
@@ -192,6 +198,17 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn,
             const bool uL = qL.w == cc, uR = qR.w == cc, uU = qU.w == cc, uD = qD.w == cc;
             float fw = 0.0f;
             float dv[6];
+            if (uL && uR && uU && uD) {
+                // every neighbour usable (almost every pixel): central differences
+                const float a[3] = {qR.x - qL.x, qR.y - qL.y, qR.z - qL.z};
+                const float b[3] = {qD.x - qU.x, qD.y - qU.y, qD.z - qU.z};
+#pragma unroll
+                for (int comp = 0; comp < 3; ++comp) {
+                    dv[comp] = a[comp] * 0.5f;
+                    dv[3 + comp] = b[comp] * 0.5f;
+                    fw = fmaxf(fw, fabsf(dv[comp]) + fabsf(dv[3 + comp]));
+                }
+            } else {
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
                 auto get = [&](const float4& q) { return comp == 0 ? q.x : (comp == 1 ? q.y : q.z); };
@@ -216,6 +233,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn,
                 fw = fmaxf(fw, fabsf(di) + fabsf(dj));
                 dv[comp] = di;
                 dv[3 + comp] = dj;
+            }
             }
             if (fw > 0.0f) {
                 o = make_float4(vc.x, vc.y, vc.z, __frcp_rn(fw));

@@ -12,9 +12,11 @@
 // evicts idle cache entries until it fits, waits while other requests hold
 // memory, and fails with VSR_ERR_BUDGET when it cannot fit even alone.
 // Completion is detected by polling CUDA events from the worker thread (no
-// device-side waits).  A request whose bins outgrew their capacity (known
-// from the pair count once it has finished) is rendered again with grown
-// bins; the slots' workspaces report to status words of their own, so such
+// device-side waits).  The workspaces size their bins without waiting for
+// the device when a request's map shape differs from the previous one's
+// (the capacity only grows), so admitting a request never blocks the worker;
+// a request whose bins outgrew their capacity (known from the pair count
+// once it has finished) is rendered again with grown bins; the slots' workspaces report to status words of their own, so such
 // handled overflows do not reach vsr_last_device_status.  Every request's
 // output equals that of rendering it alone: the arithmetic is per request and
 // order-free.
@@ -295,14 +297,16 @@ struct vsr_server_s {
                     continue;
                 }
                 vsr_scene_s* w = sl.work;
-                if (*w->h_total > w->cap && sl.req.reruns < 3) {
+                const bool overflow = *w->h_total > w->cap;
+                if (overflow && sl.req.reruns < 3) {
                     // the bins overflowed: vsr_bin grows them from this count; render again
                     ++sl.req.reruns;
                     ++stats.reruns;
                     if (launch(sl) == VSR_OK) continue;
                 }
                 sl.map->refs--;
-                finish(sl.req, VSR_OK, sl.t_start, sl.hit);
+                // outputs of bins that still overflow are incomplete: say so
+                finish(sl.req, overflow ? VSR_ERR_BIN_OVERFLOW : VSR_OK, sl.t_start, sl.hit);
                 sl.busy = false;
                 progressed = true;
             }
@@ -333,6 +337,7 @@ struct vsr_server_s {
                         continue;
                     }
                     w->status = sl.status;  // overflows are handled here, not reported globally
+                    w->async_sizing = true;  // a bin overflow renders the request again (below)
                 }
                 sl.req = q;
                 sl.map = me;

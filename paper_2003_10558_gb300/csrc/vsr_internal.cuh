@@ -69,6 +69,10 @@ struct TileIndexHdr {
     unsigned n_big;
     unsigned n_valid;
     unsigned hist[IDX_HIST];    // third-of-an-octave histogram of half-angles
+    // counters a filing map kernel adds into (zero between generations; the
+    // index finish moves them to n_big / hist)
+    unsigned n_big_work;
+    unsigned hist_work[IDX_HIST];
 };
 
 // Device-side status word (vsr_status values; 0 = OK), one int per device
@@ -102,8 +106,8 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
     } while (0)
 
 // Kernel launchers (defined in the .cu files, called by the host library).
-// file_into (optional): the map's tile index, prepared by
-// launch_tile_index_reset; the map kernel then files every tile into it
+// file_into (optional): the map's tile index of an earlier generation of
+// the same projection; the map kernel then files every tile into it
 // (launch_tile_index_finish completes the index).
 struct TileIndex;
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
@@ -131,13 +135,14 @@ struct TileIndex {
 };
 // The whole index from the tile cones and geometry (any generation).
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
-// A later generation of the same map, in three steps on one stream:
-// launch_tile_index_reset (the grid plan from the previous generation's
-// histogram, counters zeroed) -> the map kernel with file_into = the index
-// (each tile adds itself to the histogram and to its cell's count, or to
-// the big list) -> launch_tile_index_finish (scan of the cell counts,
-// cell-sorted copies, the widest ramp and the largest small half-angle).
-vsr_status launch_tile_index_reset(TileIndex idx, cudaStream_t st);
+// A later generation of the same map (the same projection, hence the same
+// tiles and the same grid plan), in two steps on one stream: the map kernel
+// with file_into = the index files every tile into the plan the header
+// holds (the half-angle histogram, its cell's count or the big list, into
+// the header's work counters and cell_count, which are zero between
+// generations) -> launch_tile_index_finish (the scan of the cell counts,
+// then the cell-sorted copies, the widest ramp and the largest small
+// half-angle, the work counters moved into the header and zeroed).
 vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
 
 // Grid arithmetic of the tile index, shared by its build (bin.cu) and the
@@ -184,8 +189,10 @@ __device__ __forceinline__ Cone index_entry(const Cone& c, int i)
 // else a second search; pass the count pass's pairs / pair_cap, or NULL)
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,
                             uint2* pairs, uint32_t pair_cap, cudaStream_t st, int pstep = 0);
+// total_host (optional): the device address of a pinned host word that
+// also receives the total
 vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
-                       cudaStream_t st);
+                       cudaStream_t st, uint32_t* total_host = nullptr);
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
                            const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
                            int* status, cudaStream_t st, int pstep = 0);

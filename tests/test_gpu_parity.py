@@ -312,6 +312,24 @@ def test_end_to_end_against_oracle(vsr):
     assert (got["id"] == exp["id"]).mean() > 0.999
 
 
+def test_bins_resized_for_a_new_map_shape(vsr):
+    """One scene rendered twice on a small map -- the second binning leaves
+    its pair total unread -- then on a map with 340 times the tiles: the
+    bins are sized from the new frame's own total, and the frame equals a
+    fresh scene's with no overflow reported."""
+    tris = torch.from_numpy(scenes.random_triangles(20000, 1.0, 30.0, 0.03, seed=25)).cuda()
+    sc = vsr.Scene(tris, scenes.camera())
+    small = vsr.Map(64, 48, 0.2, 0.9, 0.9, 120.0)
+    big = vsr.Map(1920, 1080, 0.32, 0.62, 0.86, 270.0)
+    for _ in range(2):
+        vsr.raster(small, sc)
+    got = _gpu_outputs(vsr.raster(big, sc))
+    assert vsr.last_device_status() == 0
+    ref = _gpu_outputs(vsr.raster(big, vsr.Scene(tris, scenes.camera())))
+    for k in got:
+        assert np.array_equal(got[k].view(np.uint32), ref[k].view(np.uint32)), k
+
+
 def test_deterministic(vsr):
     lens, tris, cam = scenes.tiny_scene()
     m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])

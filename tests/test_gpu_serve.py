@@ -62,6 +62,37 @@ def test_results_alone_equal_results_in_the_mix(vsr):
     srv.close()
 
 
+def test_growing_map_shape_reruns_without_blocking(vsr):
+    """One slot, so one workspace per scene: a small map, then maps with
+    many times its tile count.  The workspace keeps its bins' capacity
+    across shapes instead of waiting for the device to size them, so the
+    larger maps outgrow it; the server renders those requests again with
+    grown bins, and every result equals the plain path's."""
+    tris = torch.from_numpy(scenes.random_triangles(12000, 1.0, 40.0, 0.02, seed=31)).cuda()
+    srv = vsr.Server(budget_bytes=8 << 30, slots=1)
+    sid = srv.add_scene(tris)
+    lenses = [dict(W=64, H=48, k=0.2, l=0.9, s=0.9, omega=120.0),
+              dict(W=1024, H=1024, k=-0.3, l=0.8, s=0.7, omega=300.0),
+              dict(W=2048, H=1024, k=0.5, l=0.7, s=0.9, omega=250.0),
+              dict(W=64, H=48, k=0.2, l=0.9, s=0.9, omega=120.0)]
+    outs, tickets = [], []
+    for lens in lenses:
+        out = _out(lens)
+        outs.append(out)
+        tickets.append(srv.submit(sid, lens, scenes.camera(), out))
+    for t in tickets:
+        assert srv.wait(t)["status"] == 0
+    st = srv.stats()
+    srv.close()
+    assert st["reruns"] >= 1, st
+    torch.cuda.synchronize()
+    for lens, out in zip(lenses, outs):
+        m = vsr.Map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
+        alone = vsr.raster(m, vsr.Scene(tris, scenes.camera()))
+        for k in ("id", "depth", "cov"):
+            assert torch.equal(alone[k], out[k]), (lens["W"], k)
+
+
 def test_cached_map_shared_while_it_is_made(vsr):
     """Requests on other slots that take a map from the cache while the slot
     that made it is still generating it (a 2048 x 2048 map, scenes of a few
