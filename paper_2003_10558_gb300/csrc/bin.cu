@@ -45,7 +45,8 @@ constexpr int IDX_THREADS = 256;
 
 
 // hdr zeroed by the caller
-__global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const float4* __restrict__ geom, int ntiles,
+__global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const Cone* __restrict__ tiles,
+                                                                const float4* __restrict__ geom, int ntiles,
                                                                 TileIndexHdr* __restrict__ hdr)
 {
     __shared__ unsigned s_hist[IDX_HIST];
@@ -59,13 +60,16 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const float4* __r
     const unsigned peers = __match_any_sync(0xffffffffu, bin);
     if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(peers));
     unsigned nv = ok, hm = ok ? __float_as_uint(g.w) : 0u;  // non-negative floats order as their bits
+    unsigned va = ok ? view_angle_bits(tiles[i], g.x) : 0u;
     for (int o = 16; o; o >>= 1) {
         nv += __shfl_xor_sync(0xffffffffu, nv, o);
         hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        va = max(va, __shfl_xor_sync(0xffffffffu, va, o));
     }
     if (lane == 0 && nv) {
         atomicAdd(&hdr->n_valid, nv);
         atomicMax(&hdr->h_max, hm);
+        atomicMax(&hdr->view_angle, va);
     }
     __syncthreads();
     if (tid < IDX_HIST && s_hist[tid]) atomicAdd(&hdr->hist[tid], s_hist[tid]);
@@ -210,7 +214,8 @@ __device__ uint32_t block_scan_smem(uint32_t* s, int n, uint32_t* s_wsum /* NT /
 // the cell-sorted copies of the small tiles (slot by decrementing the cell
 // count, which returns the counts to zero for the next generation), the
 // widest ramp of all tiles and the largest small half-angle (into maxima the
-// filing map kernel cleared); block 0 moves the filing's work counters
+// filing map kernel cleared), and the view angle; block 0 moves the
+// filing's work counters
 // (histogram, big-list length) into the header and clears them.
 __global__ void __launch_bounds__(IDX_THREADS) idx_file_copy_kernel(const Cone* __restrict__ tiles,
                                                                      const float4* __restrict__ geom, int ntiles,
@@ -248,12 +253,15 @@ __global__ void __launch_bounds__(IDX_THREADS) idx_file_copy_kernel(const Cone* 
         if (slot < (uint32_t)ntiles) sorted[slot] = index_entry(tiles[i], i);
     }
     unsigned hm = valid ? __float_as_uint(g.w) : 0u, am = small ? __float_as_uint(g.x) : 0u;
+    unsigned va = valid ? view_angle_bits(tiles[i], g.x) : 0u;
     for (int o = 16; o; o >>= 1) {
         hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
         am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+        va = max(va, __shfl_xor_sync(0xffffffffu, va, o));
     }
     if (lane == 0 && hm) atomicMax(&hdr->h_max, hm);
     if (lane == 0 && am) atomicMax(&hdr->alpha_small_max, am);
+    if (lane == 0 && va) atomicMax(&hdr->view_angle, va);
 }
 
 // The whole index in one CTA, for maps of at most IDX_FUSED_TILES tiles: the
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
     __syncthreads();
     // 1. histogram of half-angles (one add per group of equal bins in a
     // warp), valid tiles, widest ramp (one atomic per warp)
-    uint32_t nv = 0u, hm = 0u;
+    uint32_t nv = 0u, hm = 0u, va = 0u;
     for (int base = 0; base < ntiles; base += IDX_FUSED_THREADS * IDX_BATCH) {
         float4 gb[IDX_BATCH];
         load_geom_batch(geom, ntiles, base + tid, IDX_FUSED_THREADS, gb);
@@ -297,15 +305,18 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
             if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h.hist[bin], (unsigned)__popc(peers));
             nv += ok;
             hm = max(hm, ok ? __float_as_uint(g.w) : 0u);  // non-negative floats order as their bits
+            if (ok) va = max(va, view_angle_bits(tiles[base + tid + u * IDX_FUSED_THREADS], g.x));
         }
     }
     for (int o = 16; o; o >>= 1) {
         nv += __shfl_xor_sync(0xffffffffu, nv, o);
         hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        va = max(va, __shfl_xor_sync(0xffffffffu, va, o));
     }
     if (lane == 0 && nv) {
         atomicAdd(&s_h.n_valid, nv);
         atomicMax(&s_h.h_max, hm);
+        atomicMax(&s_h.view_angle, va);
     }
     __syncthreads();
     // 2. the grid plan
@@ -397,6 +408,10 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
 // the fill on the 1080p frame.)
 
 constexpr int BIN_BIG_CHUNK = 16;
+// cones per step of the search for grids beyond one resident wave
+#ifndef VSR_BIN_CB_LARGE
+#define VSR_BIN_CB_LARGE 1
+#endif
 constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full)
 
 // FILL: false = count + record, true = fill by searching again.
@@ -408,7 +423,8 @@ constexpr int BIN_STAGE = 256;  // hits staged per warp (appended when half full
 // their pairs over all 32 lanes).  8 for small scenes, so that they still
 // give the GPU enough warps to hide the search's latency.
 template <bool FILL, int CB, int TPW>
-__global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, int T, uint32_t* __restrict__ ids,
+__global__ void __launch_bounds__(128, CB == 1 ? 12 : (CB == 2 ? 10 : 1)) bin_kernel(BinView v, int T,
+                                                                                   uint32_t* __restrict__ ids,
                                                                      uint32_t cap, int* status)
 {
     const unsigned FULL = 0xffffffffu;
@@ -427,6 +443,13 @@ __global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, i
     const int nlat = h.nlat, nlon = h.nlon;
     const float cell = h.cell;
     const float amax = __uint_as_float(v.hdr->alpha_small_max), hmax = __uint_as_float(v.hdr->h_max);
+    // the map's field of view: a cone about +z of half-angle view_angle
+    // holding every tile cone; a cap that misses it misses every tile (a
+    // view angle of pi or more holds the whole sphere: no cap misses it)
+    const float vang = __uint_as_float(v.hdr->view_angle);
+    const bool fov = vang < PI_F;
+    float vcos, vsin;
+    sincosf(fminf(vang, PI_F), &vsin, &vcos);
     const uint32_t nbig = min(v.hdr->n_big, v.ntiles);
     const int bigpairs = (int)((nbig + BIN_BIG_CHUNK - 1) / BIN_BIG_CHUNK);
     __shared__ uint2 s_hit[4][BIN_STAGE];
@@ -454,8 +477,15 @@ __global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, i
                 cb = fmaxf(-1.0f, fminf(1.0f, q0.w - hmax * q1.x));
                 sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
             }
+            // outside the field of view: no window, no pairs.  The cap of
+            // radius beta reaches the view cone iff angle(S, +z) <= beta +
+            // view angle, i.e. S.z >= cos(beta + view angle) while the sum
+            // is below pi; with both angles in [0, pi) the sum is below pi
+            // exactly when its sine is positive
+            const float cbv = fmaf(cb, vcos, -sb * vsin), sbv = fmaf(sb, vcos, cb * vsin);
+            const bool outside = fov && sbv > 0.0f && sz < cbv - 2e-6f;
             // search radius: enlarged cap + largest small tile
-            const float gamma = acosf(cb) + amax + 1e-4f;
+            const float gamma = outside ? PI_F : acosf(cb) + amax + 1e-4f;
             int r1 = nlat - 1;
             ncol = nlon;
             if (gamma < PI_F) {
@@ -475,7 +505,7 @@ __global__ void __launch_bounds__(128, CB == 1 ? 12 : 1) bin_kernel(BinView v, i
             }
             segs = c0i + ncol <= nlon ? 1 : 2;
             rowpairs = (r1 - r0 + 1) * segs;
-            npairs = rowpairs + bigpairs;
+            npairs = outside ? 0 : rowpairs + bigpairs;
         }
     }
     int incl = npairs;
@@ -692,7 +722,7 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
     VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
     VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
     if (ntiles > 0) {
-        idx_hist_kernel<<<nb, IDX_THREADS, 0, st>>>(idx.geom, ntiles, idx.hdr);
+        idx_hist_kernel<<<nb, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr);
         VSR_CUDA_TRY(cudaGetLastError());
     }
     idx_count_kernel<<<nb > 0 ? nb : 1, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_count, idx.big);
@@ -751,7 +781,7 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
     const int sms = sm_count();
     if (sms < 0) return VSR_ERR_CUDA;
     switch (bin_shape(T, sms)) {
-    case 0: bin_kernel<false, 1, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
+    case 0: bin_kernel<false, VSR_BIN_CB_LARGE, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
     case 1: bin_kernel<false, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
     default: bin_kernel<false, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
     }
@@ -779,7 +809,7 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
     const int sms = sm_count();
     if (sms < 0) return VSR_ERR_CUDA;
     switch (bin_shape(T, sms)) {
-    case 0: bin_kernel<true, 1, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
+    case 0: bin_kernel<true, VSR_BIN_CB_LARGE, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
     case 1: bin_kernel<true, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
     default: bin_kernel<true, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, ids, cap, status); break;
     }

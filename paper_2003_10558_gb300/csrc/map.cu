@@ -76,7 +76,7 @@ __device__ __forceinline__ void cone_barrier() { asm volatile("bar.sync 1, %0;" 
 // map; thread 0 then files the tile (index `tile`) into the plan the index
 // header holds: its histogram bin, and its cell's count or, past the plan's
 // small-tile half-angle, the big list (the header's work counters).  Tile 0
-// also clears the index's two maxima, which the index finish then forms.
+// also clears the index's maxima, which the index finish then forms.
 __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom, const TileIndex* file_into = nullptr,
                             int tile = 0)
 {
@@ -138,6 +138,7 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         if (file_into && tile == 0) {
             file_into->hdr->h_max = 0u;
             file_into->hdr->alpha_small_max = 0u;
+            file_into->hdr->view_angle = 0u;
         }
         if (file_into && g.w >= 0.0f) {
             TileIndexHdr* hdr = file_into->hdr;

@@ -68,6 +68,10 @@ struct TileIndexHdr {
     unsigned h_max;             // float bits: largest ramp half-width 1/(2 delta)
     unsigned n_big;
     unsigned n_valid;
+    // float bits: the half-angle about the camera's +z axis of a cone that
+    // holds every tile cone (the map's field of view), plus a margin; 0 for a
+    // map without a valid pixel
+    unsigned view_angle;
     unsigned hist[IDX_HIST];    // third-of-an-octave histogram of half-angles
     // counters a filing map kernel adds into (zero between generations; the
     // index finish moves them to n_big / hist)
@@ -171,6 +175,14 @@ __device__ __forceinline__ int cell_col(float lon, const TileIndexHdr& h)
 __device__ __forceinline__ int home_cell_geom(const float4& g, const TileIndexHdr& h)
 {
     return cell_row(g.y, h) * h.nlon + cell_col(g.z, h);
+}
+
+// A tile's reach from the camera's +z axis, as float bits (non-negative, so
+// they order as the floats): the angle of its axis from +z plus its
+// half-angle and a margin for the FP32 rounding.
+__device__ __forceinline__ unsigned view_angle_bits(const Cone& c, float alpha)
+{
+    return __float_as_uint(acosf(fmaxf(-1.0f, fminf(1.0f, c.c0.z))) + alpha + 1e-5f);
 }
 
 // The index's copy of tile i's cone: (axis xyz, cos alpha), (sin alpha, h,

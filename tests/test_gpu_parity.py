@@ -216,13 +216,16 @@ def test_regenerated_map_files_into_previous_index(vsr):
 
 @pytest.mark.parametrize("lens", [dict(W=256, H=256, k=0.0, l=1.0, s=1.0, omega=180.0),
                                   dict(W=333, H=197, k=-1.0, l=1.0, s=1.0, omega=180.0),
-                                  dict(W=300, H=200, k=0.0, l=0.5, s=0.7, omega=360.0)],
-                         ids=lambda d: f"{d['W']}x{d['H']}k{d['k']}")
+                                  dict(W=300, H=200, k=0.0, l=0.5, s=0.7, omega=360.0),
+                                  dict(W=320, H=240, k=1.0, l=1.0, s=1.0, omega=60.0)],
+                         ids=lambda d: f"{d['W']}x{d['H']}k{d['k']}o{d['omega']:.0f}")
 def test_dense_reference_equals_binned(vsr, lens):
     """vsr_raster_dense (every pixel against every triangle, no tile bins)
     gives vsr_raster's outputs bit for bit: ragged tiles, invalid corners, a
-    360-degree wrap, triangles culled at set-up (a vertex at the eye, a
-    plane through it) and more than one chunk of triangles per tile."""
+    360-degree wrap, a 60-degree view that most triangles miss (the binner
+    skips caps outside the map's field of view), triangles culled at set-up
+    (a vertex at the eye, a plane through it) and more than one chunk of
+    triangles per tile."""
     tris = np.concatenate([scenes.random_triangles(900, 1.0, 10.0, 0.15, seed=31),
                            scenes.random_triangles(300, 0.5, 3.0, 0.4, seed=32)])
     tris[5, 0] = 0.0                       # a vertex at the eye
