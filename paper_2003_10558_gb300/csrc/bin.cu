@@ -409,6 +409,12 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
 
 constexpr int BIN_BIG_CHUNK = 16;
 // cones per step of the search for grids beyond one resident wave
+// The longest cone range of a warp round, in steps of the flattened walk,
+// above which the round walks its cones flattened across the warp.
+#ifndef VSR_BIN_FLAT_RATIO
+#define VSR_BIN_FLAT_RATIO 2
+#endif
+
 #ifndef VSR_BIN_CB_LARGE
 #define VSR_BIN_CB_LARGE 1
 #endif
@@ -555,38 +561,85 @@ __global__ void __launch_bounds__(128, CB == 1 ? 12 : (CB == 2 ? 10 : 1)) bin_ke
             b = min(b, v.ntiles);
             a = min(a, b);
         }
-        for (uint32_t k0 = a; k0 < b; k0 += CB) {
-            Cone cs[CB];
-#pragma unroll
-            for (int e = 0; e < CB; ++e)
-                if (k0 + e < b) cs[e] = list[k0 + e];
-#pragma unroll
-            for (int e = 0; e < CB; ++e) {
-                if (k0 + e >= b) break;
-                const Cone& c = cs[e];
-                // angle(S, axis) <= alpha + beta  (always when alpha + beta >= pi)
-                const float cg = fmaf(tx, c.c0.x, fmaf(ty, c.c0.y, tz * c.c0.z));
-                if (!(tcb + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, tcb, -c.c1.x * tsb) - 2e-6f)) continue;
-                const uint32_t tile = __float_as_uint(c.c1.z);
-                if (tile >= v.ntiles) continue;
-                if (!FILL) {
-                    atomicAdd(&v.counts[tile], 1u);
-                    if (v.pairs) {
-                        const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
-                        if (j < BIN_STAGE) {
-                            s_hit[warp][j] = make_uint2(tile, tt);
-                        } else {  // a round with more hits than the stage holds: straight to the list
-                            const uint32_t g = atomicAdd(v.cursor, 1u);
-                            if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tt);
-                        }
+        // a hit: count and record it (count pass) or take a slot and fill it
+        auto hit = [&](uint32_t tile, uint32_t tri) {
+            if (!FILL) {
+                atomicAdd(&v.counts[tile], 1u);
+                if (v.pairs) {
+                    const uint32_t j = atomicAdd(&s_nhit[warp], 1u);
+                    if (j < BIN_STAGE) {
+                        s_hit[warp][j] = make_uint2(tile, tri);
+                    } else {  // a round with more hits than the stage holds: straight to the list
+                        const uint32_t g = atomicAdd(v.cursor, 1u);
+                        if (g < v.pair_cap) v.pairs[g] = make_uint2(tile, tri);
                     }
-                } else {
-                    const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
-                    if (pos < cap && pos < v.offsets[tile + 1])
-                        ids[pos] = tt;
-                    else
-                        raise_status(status, VSR_ERR_BIN_OVERFLOW);
                 }
+            } else {
+                const uint32_t pos = v.offsets[tile] + atomicSub(&v.counts[tile], 1u) - 1u;
+                if (pos < cap && pos < v.offsets[tile + 1])
+                    ids[pos] = tri;
+                else
+                    raise_status(status, VSR_ERR_BIN_OVERFLOW);
+            }
+        };
+        // the cap / cone test: angle(S, axis) <= alpha + beta (always when
+        // alpha + beta >= pi)
+        auto reaches = [&](const Cone& c, float x, float y, float z, float cbt, float sbt) {
+            const float cg = fmaf(x, c.c0.x, fmaf(y, c.c0.y, z * c.c0.z));
+            return cbt + c.c0.w <= 2e-6f || cg >= fmaf(c.c0.w, cbt, -c.c1.x * sbt) - 2e-6f;
+        };
+        // Two ways through the round's cones.  Each lane walks its own range
+        // -- as many steps as the longest range, the other lanes idle once
+        // theirs ends -- or, where the ranges are very unequal, the cones are
+        // numbered across the warp (lane l's range is [excl_l, excl_l +
+        // len_l)) and every lane takes the next cone each step, finding the
+        // lane whose range holds it by a search over the lanes.  The second
+        // costs more per step (the search and the range's parameters by
+        // shuffle), so it is taken when the longest range is over
+        // VSR_BIN_FLAT_RATIO times its step count.
+        const int len = (int)(b - a);
+        int incl = len, lmax = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+            lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
+        }
+        const int ncones = __shfl_sync(FULL, incl, 31);
+        if (lmax <= VSR_BIN_FLAT_RATIO * ((ncones + 31) / 32)) {
+            for (uint32_t k0 = a; k0 < b; k0 += CB) {
+                Cone cs[CB];
+#pragma unroll
+                for (int e = 0; e < CB; ++e)
+                    if (k0 + e < b) cs[e] = list[k0 + e];
+#pragma unroll
+                for (int e = 0; e < CB; ++e) {
+                    if (k0 + e >= b) break;
+                    if (!reaches(cs[e], tx, ty, tz, tcb, tsb)) continue;
+                    const uint32_t tile = __float_as_uint(cs[e].c1.z);
+                    if (tile < v.ntiles) hit(tile, tt);
+                }
+            }
+        } else {
+            const int excl = incl - len;
+            const int rel = (int)a - excl;  // list index = cone number + rel
+            const int isbig = list == v.big;
+            for (int k0 = 0; k0 < ncones; k0 += 32) {
+                const int idx = k0 + lane;
+                int o = 0;  // the last lane whose range starts at or before cone idx
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int e = __shfl_sync(FULL, excl, o + st);
+                    if (e <= idx) o += st;
+                }
+                const float ox = __shfl_sync(FULL, tx, o), oy = __shfl_sync(FULL, ty, o),
+                            oz = __shfl_sync(FULL, tz, o);
+                const float ocb = __shfl_sync(FULL, tcb, o), osb = __shfl_sync(FULL, tsb, o);
+                const uint32_t ot = (uint32_t)__shfl_sync(FULL, (int)tt, o);
+                const int orel = __shfl_sync(FULL, rel, o), obig = __shfl_sync(FULL, isbig, o);
+                if (idx >= ncones) continue;
+                const Cone c = (obig ? v.big : v.sorted)[idx + orel];
+                if (!reaches(c, ox, oy, oz, ocb, osb)) continue;
+                const uint32_t tile = __float_as_uint(c.c1.z);
+                if (tile < v.ntiles) hit(tile, ot);
             }
         }
         if (!FILL && v.pairs) {
