@@ -302,12 +302,24 @@ vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
  * work scene `s` (a handle from vsr_scene_create, whose device buffers are
  * reused across calls) on `tris_host` ([T][3][3] FP32, host), rasterizes
  * into the map and returns id/depth/cov (W*H each, host; any may be NULL),
- * then synchronises `stream`.  Same outputs as vsr_raster.
+ * then synchronises `stream`.  Same outputs as vsr_raster, but always
+ * complete: since the call waits for the frame, a frame that outgrew the
+ * scene's bins (see vsr_raster) is rendered again with grown bins before it
+ * returns, and a bin overflow that persists is returned by the call
+ * (VSR_ERR_BIN_OVERFLOW) instead of being raised in the per-device status.
  * Buffers in pinned host memory mapped into the device's address space
  * (cudaHostAlloc, cudaMallocHost, torch pin_memory) are read and written in
  * place by the kernels over the host link, so the transfers overlap the
  * set-up and raster kernels; other host memory is staged through device
- * buffers with copies before and after them. */
+ * buffers with copies before and after them.
+ * The set-up (and the triangles' copy) runs on a stream of the scene's own
+ * that waits only for the last queued use of `s` (by any call, on any
+ * stream, from the first vsr_render_host on `s` on; at that first call,
+ * for all work queued on `stream`).  Work queued on `stream` before the
+ * call that does not use `s` -- a vsr_map_update of `m` -- therefore runs
+ * beside the set-up; binning and raster follow on `stream` after both.
+ * Uses of `s` inside a stream capture are not tracked: their graph
+ * launches must complete before this call. */
 vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
 

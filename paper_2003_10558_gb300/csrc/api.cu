@@ -183,7 +183,7 @@ vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const flo
     // the record layout is field-major with stride T: keep it dense
     vsr_status s = launch_setup(tris_dev, (int)T, cam, sc->rec, st);
     sc->gen = g_gen.fetch_add(1);
-    return s;
+    return s == VSR_OK ? scene_used(sc, st) : s;
 }
 
 // bin ids and the count pass's pair list, both of `want` entries (frees the
@@ -493,6 +493,10 @@ void vsr_scene_free(vsr_scene sc)
         cudaEventDestroy(sc->total_event);
     }
     if (sc->h_total) cudaFreeHost(sc->h_total);
+    if (sc->side) cudaStreamDestroy(sc->side);
+    if (sc->use_event) cudaEventDestroy(sc->use_event);
+    if (sc->setup_event) cudaEventDestroy(sc->setup_event);
+    cudaFree(sc->host_status);
     delete sc;
 }
 
@@ -514,7 +518,8 @@ vsr_status vsr_raster_pstep(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
     if (s != VSR_OK) return s;
     const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
                        sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
-    return launch_raster_pstep(v, m->deriv, scene_status(sc), st);
+    s = launch_raster_pstep(v, m->deriv, scene_status(sc), st);
+    return s == VSR_OK ? scene_used(sc, st) : s;
 }
 
 }  // extern "C"
@@ -560,6 +565,8 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
     if (record) {
         VSR_CUDA_TRY(cudaEventRecord(sc->total_event, st));
         sc->total_pending = true;
+        sc->total_map = m->gen;
+        sc->total_scene = sc->gen;
     }
     if (resize) {
         VSR_CUDA_TRY(cudaEventSynchronize(sc->total_event));
@@ -578,13 +585,12 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
         return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
-    return VSR_OK;
+    return scene_used(sc, st);
 }
 
-extern "C" {
-
-vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
-                            const vsr_raster_stats* stats, void* stream)
+// host_out: the outputs are pinned host memory written in place
+static vsr_status raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                               const vsr_raster_stats* stats, void* stream, bool host_out)
 {
     if (!m || !sc) return VSR_ERR_INVALID_ARG;
     if (sc->binned_map != m->gen || sc->binned_scene != sc->gen) return VSR_ERR_INVALID_ARG;
@@ -600,14 +606,25 @@ vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
         }
         const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
                            sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
-        return launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT, scene_status(sc),
-                                   (cudaStream_t)stream);
+        const vsr_status s = launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT,
+                                                 scene_status(sc), (cudaStream_t)stream, host_out);
+        return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
     }
     // diagnostics: one CTA per tile, whole bins, counters
-    return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
-                         depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
-                         stats ? (unsigned long long*)stats->n_exec_dev : nullptr,
-                         stats ? stats->n_inside_dev : nullptr, scene_status(sc), (cudaStream_t)stream);
+    const vsr_status s =
+        launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
+                      depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
+                      stats ? (unsigned long long*)stats->n_exec_dev : nullptr, stats ? stats->n_inside_dev : nullptr,
+                      scene_status(sc), (cudaStream_t)stream);
+    return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
+}
+
+extern "C" {
+
+vsr_status vsr_raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
+                            const vsr_raster_stats* stats, void* stream)
+{
+    return raster_tiles(m, sc, id_dev, depth_dev, cov_dev, stats, stream, false);
 }
 
 vsr_status vsr_raster_dense(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
@@ -616,7 +633,8 @@ vsr_status vsr_raster_dense(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
     if (!m || !sc || sc->T < 0) return VSR_ERR_INVALID_ARG;
     const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, nullptr,
                        nullptr, 0u, id_dev, depth_dev, cov_dev};
-    return launch_raster_dense(v, scene_status(sc), (cudaStream_t)stream);
+    const vsr_status s = launch_raster_dense(v, scene_status(sc), (cudaStream_t)stream);
+    return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
 }
 
 vsr_status vsr_raster_ex(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* depth_dev, float* cov_dev,
@@ -658,6 +676,32 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
     uint32_t* id_d = (uint32_t*)mapped_host(id_host);
     float* depth_d = (float*)mapped_host(depth_host);
     float* cov_d = (float*)mapped_host(cov_host);
+    // The set-up (and the triangles' copy) runs on the scene's own stream and
+    // waits only for the scene's last queued use, so it overlaps work queued
+    // on `stream` before this call that leaves the scene alone -- a map
+    // update; the binning, on `stream`, waits for both.
+    if (!sc->side) {
+        if (cudaStreamCreateWithFlags(&sc->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sc->use_event, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sc->setup_event, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc((void**)&sc->host_status, sizeof(int)) != cudaSuccess ||
+            cudaMemset(sc->host_status, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            if (sc->side) cudaStreamDestroy(sc->side);
+            if (sc->use_event) cudaEventDestroy(sc->use_event);
+            if (sc->setup_event) cudaEventDestroy(sc->setup_event);
+            cudaFree(sc->host_status);
+            sc->side = nullptr;
+            sc->use_event = nullptr;
+            sc->setup_event = nullptr;
+            sc->host_status = nullptr;
+            return VSR_ERR_CUDA;
+        }
+        // uses queued before the tracking began are unknown: this once, the
+        // set-up waits for all the work queued on `stream`
+        VSR_CUDA_TRY(cudaEventRecord(sc->use_event, st));
+    }
+    VSR_CUDA_TRY(cudaStreamWaitEvent(sc->side, sc->use_event, 0));
     if (T > 0 && !tris_src) {
         if (T > sc->tris_alloc) {
             cudaFree(sc->tris_dev);
@@ -667,7 +711,7 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
             sc->tris_alloc = T;
         }
         VSR_CUDA_TRY(cudaMemcpyAsync(sc->tris_dev, tris_host, sizeof(float) * 9 * (size_t)T, cudaMemcpyHostToDevice,
-                                     st));
+                                     sc->side));
         tris_src = sc->tris_dev;
     }
     const bool stage_id = id_host && !id_d, stage_depth = depth_host && !depth_d, stage_cov = cov_host && !cov_d;
@@ -686,13 +730,39 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
         if (stage_depth) depth_d = (float*)((char*)sc->out_dev + 4 * npix);
         if (stage_cov) cov_d = (float*)((char*)sc->out_dev + 8 * npix);
     }
-    if ((s = scene_setup(sc, tris_src, T, cam, st)) != VSR_OK) return s;
-    if ((s = vsr_raster_ex(m, sc, id_d, depth_d, cov_d, nullptr, stream)) != VSR_OK) return s;
-    if (stage_id) VSR_CUDA_TRY(cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st));
-    if (stage_depth) VSR_CUDA_TRY(cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st));
-    if (stage_cov) VSR_CUDA_TRY(cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st));
-    VSR_CUDA_TRY(cudaStreamSynchronize(st));
-    return VSR_OK;
+    if ((s = scene_setup(sc, tris_src, T, cam, sc->side)) != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaEventRecord(sc->setup_event, sc->side));
+    VSR_CUDA_TRY(cudaStreamWaitEvent(st, sc->setup_event, 0));
+    const bool in_place = (id_host && !stage_id) || (depth_host && !stage_depth) || (cov_host && !stage_cov);
+    // Binning and raster report to the scene's own status word.  The call
+    // waits for the frame anyway, so a frame that outgrew its bins (the pair
+    // total, stored into pinned memory by the scan, above the capacity) is
+    // rendered again: the next binning grows the bins from that total.
+    int* const saved_status = sc->status;
+    sc->status = sc->host_status;
+    for (int attempt = 0;; ++attempt) {
+        if ((s = vsr_bin(m, sc, stream)) == VSR_OK)
+            s = raster_tiles(m, sc, id_d, depth_d, cov_d, nullptr, stream, in_place);
+        if (s == VSR_OK && stage_id && cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st))
+            s = VSR_ERR_CUDA;
+        if (s == VSR_OK && stage_depth &&
+            cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st))
+            s = VSR_ERR_CUDA;
+        if (s == VSR_OK && stage_cov && cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st))
+            s = VSR_ERR_CUDA;
+        if (s == VSR_OK && cudaStreamSynchronize(st) != cudaSuccess) s = VSR_ERR_CUDA;
+        const bool outgrew = s == VSR_OK && sc->total_pending && sc->total_map == m->gen &&
+                             sc->total_scene == sc->gen && *sc->h_total > sc->cap;
+        if (!outgrew) break;
+        if (attempt == 2 || cudaMemsetAsync(sc->host_status, 0, sizeof(int), st) != cudaSuccess) {
+            cudaGetLastError();
+            s = VSR_ERR_BIN_OVERFLOW;
+            break;
+        }
+    }
+    sc->status = saved_status;
+    if (s != VSR_OK) cudaGetLastError();
+    return s;
 }
 
 }  // extern "C"
@@ -776,8 +846,10 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
     if ((s = launch_bin_fill(sc->rec, T, m->idx, offsets, counts, nullptr, nullptr, 0, ids, NA_PAIRS_MAX, status,
                              st)) != VSR_OK)
         return s;
-    return launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, T, offsets, ids, NA_PAIRS_MAX, id_dev, depth_dev,
-                         cov_dev, nullptr, nullptr, nullptr, status, st);
+    if ((s = launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, T, offsets, ids, NA_PAIRS_MAX, id_dev,
+                           depth_dev, cov_dev, nullptr, nullptr, nullptr, status, st)) != VSR_OK)
+        return s;
+    return scene_used(sc, st);
 }
 
 // ---------------------------------------------------------------------------

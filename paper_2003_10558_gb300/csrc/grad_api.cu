@@ -143,7 +143,7 @@ vsr_status vsr_raster_shaded(vsr_map m, vsr_scene sc, const float* colors_dev, v
     f->W = W;
     f->H = H;
     f->valid = true;
-    return VSR_OK;
+    return scene_used(sc, st);
 }
 
 vsr_status vsr_raster_backward(vsr_map m, vsr_scene sc, const float* tris_dev, const float* colors_dev, vsr_frags f,
@@ -181,7 +181,7 @@ vsr_status vsr_raster_backward(vsr_map m, vsr_scene sc, const float* tris_dev, c
                                      f->lens_part, dlens_dev, st)) != VSR_OK)
             return s;
     }
-    return VSR_OK;
+    return scene_used(sc, st);
 }
 
 }  // extern "C"

@@ -56,6 +56,7 @@ struct vsr_scene_s {
     uint32_t* h_total_dev = nullptr;    // its device address (the scan kernel stores the total there)
     cudaEvent_t total_event = nullptr;  // completion of that copy
     bool total_pending = false;
+    uint64_t total_map = 0, total_scene = 0;  // generations of the binning whose total it is
     int last_ntiles = 0;
     uint64_t binned_map = 0, binned_scene = 0;  // generations the current bins belong to
     RasterWork work = {};
@@ -74,6 +75,35 @@ struct vsr_scene_s {
     // no synchronisation per new shape; everyone else gets exact bins on
     // every call
     bool async_sizing = false;
+    // vsr_render_host runs the set-up on a stream of the scene's own, beside
+    // work the caller queued before the call that does not touch the scene
+    // (a map update).  From its first call on, use_event is recorded after
+    // every queued use of the scene's buffers, so that stream waits for
+    // exactly those.
+    cudaStream_t side = nullptr;
+    cudaEvent_t use_event = nullptr;
+    cudaEvent_t setup_event = nullptr;
+    // its device status word: a frame that outgrew its bins is rendered
+    // again, so the overflow it raised goes here, not to the per-device word
+    int* host_status = nullptr;
 };
 
 inline int* scene_status(const vsr_scene_s* s) { return s->status ? s->status : status_word(); }
+
+// Note a use of the scene's buffers queued on st (see use_event).
+inline vsr_status scene_used(vsr_scene_s* s, cudaStream_t st)
+{
+    if (!s->use_event) return VSR_OK;
+    // uses inside a stream capture run when their graph is launched: the
+    // caller orders those launches
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return VSR_ERR_CUDA;
+    }
+    if (cs == cudaStreamCaptureStatusNone && cudaEventRecord(s->use_event, st) != cudaSuccess) {
+        cudaGetLastError();
+        return VSR_ERR_CUDA;
+    }
+    return VSR_OK;
+}

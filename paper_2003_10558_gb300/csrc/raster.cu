@@ -215,7 +215,9 @@ __device__ __forceinline__ void eval_slot(const Stage& st, int j, PixPair& q, ui
         post(std::false_type{});
 }
 
-template <bool STATS>
+// ROWS: the outputs go through shared memory and leave in whole tile rows
+// (pinned host outputs written in place over the host link).
+template <bool STATS, bool ROWS = false>
 __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, Stage& st, bool count_alg,
                                             uint32_t& cnt_alg, uint32_t& cnt_exec, int32_t* __restrict__ n_inside,
                                             int* __restrict__ status, int range_lo = 0, int range_hi = -1,
@@ -356,15 +358,41 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         if (threadIdx.x == 0) split.done[split_slot] = 0u;
     }
 
+    if (!ROWS) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (!inimg[p]) continue;
+            const size_t o = (size_t)(py0 + 4 * p) * W + px;
+            const bool hit = q.key[p] != ~0ull;
+            if (out_id) out_id[o] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
+            if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(q.key[p] >> 32)) : INFINITY;
+            if (out_cov) out_cov[o] = (float)q.acc[p] * (1.0f / (float)COV_ONE);
+            if (STATS && n_inside) n_inside[o] = q.cnt_in[p];
+        }
+        return;
+    }
+    // Through shared memory, so that each warp store covers two whole tile
+    // rows (16 pixels, 64 B each) instead of four 8-pixel pieces: over the
+    // host link 32-byte pieces cost about a quarter of its bandwidth.
+    __shared__ uint32_t s_out[3][TILE_PIX];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        if (!inimg[p]) continue;
-        const size_t o = (size_t)(py0 + 4 * p) * W + px;
+        const int lp = lx + TILE * (ly0 + 4 * p);
         const bool hit = q.key[p] != ~0ull;
-        if (out_id) out_id[o] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
-        if (out_depth) out_depth[o] = hit ? __uint_as_float((uint32_t)(q.key[p] >> 32)) : INFINITY;
-        if (out_cov) out_cov[o] = (float)q.acc[p] * (1.0f / (float)COV_ONE);
-        if (STATS && n_inside) n_inside[o] = q.cnt_in[p];
+        s_out[0][lp] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
+        s_out[1][lp] = hit ? (uint32_t)(q.key[p] >> 32) : __float_as_uint(INFINITY);
+        s_out[2][lp] = __float_as_uint((float)q.acc[p] * (1.0f / (float)COV_ONE));
+        if (STATS && n_inside && inimg[p]) n_inside[(size_t)(py0 + 4 * p) * W + px] = q.cnt_in[p];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = threadIdx.x; i < TILE_PIX; i += RT) {
+        const int ox = tx * TILE + (i % TILE), oy = ty * TILE + i / TILE;
+        if (ox >= W || oy >= H) continue;
+        const size_t o = (size_t)oy * W + ox;
+        if (out_id) out_id[o] = s_out[0][i];
+        if (out_depth) out_depth[o] = __uint_as_float(s_out[1][i]);
+        if (out_cov) out_cov[o] = __uint_as_float(s_out[2][i]);
     }
 }
 
@@ -406,6 +434,7 @@ __global__ void __launch_bounds__(RT, 7) raster_kernel(RasterView view, unsigned
 // themselves (the first item of a split tile); the further items of split
 // tiles are listed in `extra` as (tile, k).  CTAs past the end of the list
 // return at once.
+template <bool ROWS>
 __global__ void __launch_bounds__(RT, VSR_RASTER_CTAS_PER_SM) raster_items_kernel(RasterView view, uint32_t n_tiles,
                                                               const uint32_t* __restrict__ nsplit_of,
                                                               const int32_t* __restrict__ split_slot,
@@ -428,9 +457,9 @@ __global__ void __launch_bounds__(RT, VSR_RASTER_CTAS_PER_SM) raster_items_kerne
     const int nsplit = (int)nsplit_of[u];
     uint32_t ca = 0, ce = 0;
     if (nsplit == 1)
-        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status);
+        raster_tile<false, ROWS>(view, (int)u, st, false, ca, ce, nullptr, status);
     else
-        raster_tile<false>(view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max,
+        raster_tile<false, ROWS>(view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max,
                            (int)(k + 1) * split_max, split_slot[u], nsplit, split);
 }
 
@@ -558,7 +587,7 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
 }
 
 vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
-                               RasterWork w, int split_max, int* status, cudaStream_t st)
+                               RasterWork w, int split_max, int* status, cudaStream_t st, bool host_out)
 {
     if (n_tiles == 0) return VSR_OK;
     split_max = split_max < CHUNK ? CHUNK : (split_max / CHUNK) * CHUNK;
@@ -569,9 +598,9 @@ vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, 
     items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, n_tiles, split_max, w.nsplit_of, w.split_slot,
                                                         w.counters, w.split_cap, w.extra, extra_cap);
     VSR_CUDA_TRY(cudaGetLastError());
-    raster_items_kernel<<<n_tiles + extra_cap, RT, 0, st>>>(view, n_tiles, w.nsplit_of, w.split_slot, w.extra,
-                                                            w.counters + 1, split_max, SplitAcc{w.acc, w.key, w.done},
-                                                            status);
+    auto kern = host_out ? raster_items_kernel<true> : raster_items_kernel<false>;
+    kern<<<n_tiles + extra_cap, RT, 0, st>>>(view, n_tiles, w.nsplit_of, w.split_slot, w.extra, w.counters + 1,
+                                             split_max, SplitAcc{w.acc, w.key, w.done}, status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

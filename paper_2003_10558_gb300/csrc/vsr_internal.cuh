@@ -278,9 +278,10 @@ struct RasterWork {
     uint32_t* done;           // split_cap, zero between frames
 };
 // items + raster over all tiles of a view; offsets: its bin offsets
-// (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items)
+// (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items);
+// host_out: the outputs are pinned host memory (written in whole tile rows)
 vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
-                               RasterWork w, int split_max, int* status, cudaStream_t st);
+                               RasterWork w, int split_max, int* status, cudaStream_t st, bool host_out = false);
 // the dense reference: every pixel against every triangle, no bins
 vsr_status launch_raster_dense(const RasterView& view, int* status, cudaStream_t st);
 // allocate / free a RasterWork for up to n_tiles tiles (accumulators

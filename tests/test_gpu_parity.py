@@ -383,6 +383,38 @@ def test_render_host_pinned_in_place(vsr):
         assert np.array_equal(dev[k].view(np.uint32), host[k].view(np.uint32))
 
 
+def test_render_host_beside_map_update(vsr):
+    """A lens's map update is queued on the stream just before
+    vsr_render_host, whose set-up runs beside it on the scene's own stream;
+    once, a use of the work scene queued on another stream in between must be
+    waited for.  Every frame equals vsr_raster on a fresh map of the same lens
+    bit for bit (ragged 333 x 197 tiles, outputs written in place in whole
+    tile rows, split tiles)."""
+    W, H = 333, 197
+    tris = scenes.random_triangles(30000, 1.0, 30.0, 0.03, seed=21)
+    cam = scenes.camera()
+    td = torch.from_numpy(tris).cuda()
+    lenses = [(0.3, 0.8, 0.9, 200.0), (-0.4, 0.7, 0.8, 250.0), (0.0, 1.0, 1.0, 120.0)]
+    tris_pin = torch.from_numpy(tris).pin_memory().numpy()
+    out = {k: torch.zeros((H, W), dtype=dt).pin_memory().numpy()
+           for k, dt in (("id", torch.int32), ("depth", torch.float32), ("cov", torch.float32))}
+    out["id"] = out["id"].view(np.uint32)
+    m = vsr.Map(W, H, *lenses[0])
+    work = vsr.Scene()
+    side = torch.cuda.Stream()
+    for i, lens in enumerate(lenses * 2):
+        m.update(W, H, *lens)
+        if i == 3:
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                kept = vsr.raster(m, work, stream=side)  # noqa: F841 (outputs live past the call)
+        host = vsr.render_host(m, work, tris_pin, cam, out=out)
+        ref = _gpu_outputs(vsr.raster(vsr.Map(W, H, *lens), vsr.Scene(td, cam)))
+        for k in ref:
+            assert np.array_equal(ref[k].view(np.uint32), host[k].view(np.uint32)), (i, k)
+    assert vsr.last_device_status() == 0
+
+
 def test_invalid_arguments(vsr):
     L = vsr.load()
     import ctypes
