@@ -338,9 +338,14 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64
  * any entry may be NULL).  The first call for a configuration (the same
  * maps, map contents, scene buffer and T, output pointers) renders the
  * views eagerly, synchronises `stream` once to size every view's bins, then
- * captures one graph for each S in {1, 2, 4, 8}, times their replays and
- * keeps the fastest, then tries 256 and 1024 triangles per work item of a
- * long bin at that S (the autotuner); later calls with the same configuration
+ * captures graphs of two kinds for each S in {1, 2, 4, 8}: each view's chain
+ * ending in its own raster launch, and chains that end after binning and
+ * work-item assignment followed by ONE pooled raster launch -- persistent
+ * CTAs (resident CTAs per SM x SMs) that take the (view, item) work of all
+ * views from a shared queue (an atomic counter; no CTA waits for another).
+ * It times their replays, keeps the fastest, then tries 256 and 1024
+ * triangles per work item of a long bin at that S and kind (the autotuner;
+ * vsr_batch_set_mode can restrict the kinds); later calls with the same configuration
  * copy only the cameras (into pinned staging of the batch) and replay the
  * graph on `stream`.  Each call waits for the previous frame of the batch to
  * finish; a replay leaves every view's (tile, triangle) pair total in pinned
@@ -360,6 +365,15 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
  * S, whether a graph is ready, and the triangles per work item of a long
  * bin (a tile whose bin holds more is rasterized by several CTAs). */
 vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed, int* split_max);
+/* vsr_batch_config plus `pooled`: 1 if the kept graph rasterizes all views
+ * in the one pooled launch. */
+vsr_status vsr_batch_config_ex(vsr_batch b, int* streams, int* graphed, int* split_max, int* pooled);
+/* Graph kinds the autotuner may keep: VSR_BATCH_AUTO (both; the default),
+ * VSR_BATCH_CHAINS (per-view raster launches only) or VSR_BATCH_POOLED (the
+ * pooled raster launch only).  A change takes effect at the next render,
+ * which tunes again.  VSR_ERR_INVALID_ARG for another value. */
+enum { VSR_BATCH_AUTO = 0, VSR_BATCH_CHAINS = 1, VSR_BATCH_POOLED = 2 };
+vsr_status vsr_batch_set_mode(vsr_batch b, int mode);
 void vsr_batch_free(vsr_batch b);
 
 /* ---- serving ------------------------------------------------------------------

@@ -911,6 +911,13 @@ struct vsr_batch_s {
     cudaGraphExec_t exec = nullptr;
     int nstreams = 0;
     int split_max = SPLIT_MAX_DEFAULT;
+    int mode = VSR_BATCH_AUTO;
+    bool pooled = false;  // the graph rasterizes all views in one pooled launch
+    // the pooled launch's views, item ranges and queue counter (device)
+    PoolView* pool_views = nullptr;
+    uint32_t* pool_start = nullptr;
+    uint32_t* pool_queue = nullptr;
+    int pool_alloc = 0;
 };
 
 namespace {
@@ -959,9 +966,10 @@ vsr_status batch_view_front(vsr_batch b, int v, vsr_map m, const float* tris, in
                           : launch_scan_large(bv.counts, nullptr, tiles, bv.partials, bv.offsets, st);
 }
 
-// fill and raster of view v
+// fill and raster of view v (pooled: fill and item assignment only; the
+// pooled launch rasterizes the view)
 vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pairs, uint32_t* id, float* depth,
-                           float* cov, cudaStream_t st, int split_max = SPLIT_MAX_DEFAULT)
+                           float* cov, cudaStream_t st, int split_max = SPLIT_MAX_DEFAULT, bool pooled = false)
 {
     BatchView& bv = b->views[v];
     const int tiles = m->tx * m->ty;
@@ -970,10 +978,61 @@ vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pa
                              use_pairs ? bv.pairs : nullptr, use_pairs ? bv.cap : 0u, bv.ids, bv.cap, status_word(),
                              st)) != VSR_OK)
         return s;
+    if (pooled) return launch_raster_assign(bv.offsets, (uint32_t)tiles, bv.cap, bv.work, split_max, st);
     const RasterView rv{m->map, m->p.W, m->p.H, m->tiles, m->tx, bv.rec, (int)T, bv.offsets,
                         bv.ids, bv.cap, id, depth, cov};
     return launch_raster_items(rv, bv.offsets, (uint32_t)tiles, bv.cap, bv.work, split_max, status_word(),
                                st);
+}
+
+// The pooled launch's per-view work and item ranges for this configuration
+// and split, uploaded once (outside any capture).
+vsr_status batch_pool_upload(vsr_batch b, int nviews, const vsr_map* maps, int64_t T, uint32_t* const* id,
+                             float* const* depth, float* const* cov, int split_max)
+{
+    if (nviews > b->pool_alloc) {
+        cudaFree(b->pool_views);
+        cudaFree(b->pool_start);
+        cudaFree(b->pool_queue);
+        b->pool_views = nullptr;
+        b->pool_start = nullptr;
+        b->pool_queue = nullptr;
+        b->pool_alloc = 0;
+        if (cudaMalloc((void**)&b->pool_views, sizeof(PoolView) * (size_t)nviews) != cudaSuccess ||
+            cudaMalloc((void**)&b->pool_start, sizeof(uint32_t) * ((size_t)nviews + 1)) != cudaSuccess ||
+            cudaMalloc((void**)&b->pool_queue, sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return VSR_ERR_OOM;
+        }
+        b->pool_alloc = nviews;
+    }
+    std::vector<PoolView> pv((size_t)nviews);
+    std::vector<uint32_t> start((size_t)nviews + 1, 0u);
+    uint64_t items = 0;
+    for (int v = 0; v < nviews; ++v) {
+        const BatchView& bv = b->views[v];
+        const vsr_map m = maps[v];
+        const uint32_t tiles = (uint32_t)(m->tx * m->ty);
+        pv[v].view = RasterView{m->map, m->p.W, m->p.H, m->tiles, m->tx, bv.rec, (int)T, bv.offsets,
+                                bv.ids, bv.cap, id ? id[v] : nullptr, depth ? depth[v] : nullptr,
+                                cov ? cov[v] : nullptr};
+        pv[v].n_tiles = tiles;
+        pv[v].nsplit_of = bv.work.nsplit_of;
+        pv[v].split_slot = bv.work.split_slot;
+        pv[v].extra = bv.work.extra;
+        pv[v].n_extra = bv.work.counters + 1;
+        pv[v].acc = bv.work.acc;
+        pv[v].key = bv.work.key;
+        pv[v].done = bv.work.done;
+        start[v] = (uint32_t)items;
+        items += tiles + raster_extra_cap(bv.cap, bv.work, split_max);
+        if (items > 0xffffffffull) return VSR_ERR_INVALID_ARG;
+    }
+    start[nviews] = (uint32_t)items;
+    VSR_CUDA_TRY(cudaMemcpy(b->pool_views, pv.data(), sizeof(PoolView) * (size_t)nviews, cudaMemcpyHostToDevice));
+    VSR_CUDA_TRY(
+        cudaMemcpy(b->pool_start, start.data(), sizeof(uint32_t) * ((size_t)nviews + 1), cudaMemcpyHostToDevice));
+    return VSR_OK;
 }
 
 }  // namespace
@@ -1015,6 +1074,9 @@ void vsr_batch_free(vsr_batch b)
     }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cams_done) cudaEventDestroy(b->cams_done);
+    cudaFree(b->pool_views);
+    cudaFree(b->pool_start);
+    cudaFree(b->pool_queue);
     delete b;
 }
 
@@ -1128,8 +1190,12 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     cudaEvent_t e0, e1;
     VSR_CUDA_TRY(cudaEventCreate(&e0));
     VSR_CUDA_TRY(cudaEventCreate(&e1));
-    auto candidate = [&](int S, int split) -> vsr_status {
+    auto candidate = [&](int S, int split, bool pooled) -> vsr_status {
         S = S < nviews ? S : nviews;
+        if (pooled) {
+            const vsr_status us = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, split);
+            if (us != VSR_OK) return us;
+        }
         cudaStream_t cs = b->streams[0];
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VSR_ERR_CUDA;
@@ -1148,12 +1214,14 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
                 cst = VSR_ERR_CUDA;
             if (cst == VSR_OK)
                 cst = batch_view_back(b, v, maps[v], T, true, out_ptr(id_dev, v), out_ptr(depth_dev, v),
-                                      out_ptr(cov_dev, v), vs, split);
+                                      out_ptr(cov_dev, v), vs, split, pooled);
         }
         for (int i = 1; cst == VSR_OK && i < S; ++i)
             if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
                 cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess)
                 cst = VSR_ERR_CUDA;
+        if (cst == VSR_OK && pooled)
+            cst = launch_raster_pool(b->pool_views, b->pool_start, nviews, b->pool_queue, split, status_word(), cs);
         const cudaError_t ee = cudaStreamEndCapture(cs, &g);
         if (cst != VSR_OK || ee != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
@@ -1178,17 +1246,27 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             b->exec = ex;
             b->nstreams = S;
             b->split_max = split;
+            b->pooled = pooled;
         } else {
             cudaGraphExecDestroy(ex);
         }
         return VSR_OK;
     };
+    // the per-view raster launches and the pooled one: each at every stream
+    // count and the default split, then the splits at the best of them
     vsr_status ts = VSR_OK;
-    for (int S : {1, 2, 4, 8})
-        if (ts == VSR_OK) ts = candidate(S, SPLIT_MAX_DEFAULT);
+    const bool try_chains = b->mode != VSR_BATCH_POOLED, try_pool = b->mode != VSR_BATCH_CHAINS;
+    for (int S : {1, 2, 4, 8}) {
+        if (ts == VSR_OK && try_chains) ts = candidate(S, SPLIT_MAX_DEFAULT, false);
+        if (ts == VSR_OK && try_pool) ts = candidate(S, SPLIT_MAX_DEFAULT, true);
+    }
     const int bestS = b->nstreams;
+    const bool best_pooled = b->pooled;
     for (int split : {256, 1024})
-        if (ts == VSR_OK && b->exec) ts = candidate(bestS, split);
+        if (ts == VSR_OK && b->exec) ts = candidate(bestS, split, best_pooled);
+    // the kept graph's pooled views must carry its split
+    if (ts == VSR_OK && b->exec && b->pooled)
+        ts = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, b->split_max);
     if (ts != VSR_OK) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1204,10 +1282,26 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
 
 vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed, int* split_max)
 {
+    return vsr_batch_config_ex(b, streams, graphed, split_max, nullptr);
+}
+
+vsr_status vsr_batch_config_ex(vsr_batch b, int* streams, int* graphed, int* split_max, int* pooled)
+{
     if (!b) return VSR_ERR_INVALID_ARG;
     if (streams) *streams = b->nstreams;
     if (graphed) *graphed = b->exec != nullptr;
     if (split_max) *split_max = b->split_max;
+    if (pooled) *pooled = b->exec != nullptr && b->pooled;
+    return VSR_OK;
+}
+
+vsr_status vsr_batch_set_mode(vsr_batch b, int mode)
+{
+    if (!b || mode < VSR_BATCH_AUTO || mode > VSR_BATCH_POOLED) return VSR_ERR_INVALID_ARG;
+    if (mode != b->mode) {
+        b->mode = mode;
+        b->key.clear();  // the next render tunes again
+    }
     return VSR_OK;
 }
 

@@ -790,8 +790,7 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
     return VSR_OK;
 }
 
-// SMs of the current device (looked up once per device), or -1.
-static int sm_count()
+int sm_count()
 {
     static std::atomic<int> cache[64];
     int dev = 0;

@@ -463,6 +463,58 @@ __global__ void __launch_bounds__(RT, VSR_RASTER_CTAS_PER_SM) raster_items_kerne
                            (int)(k + 1) * split_max, split_slot[u], nsplit, split);
 }
 
+// The work items of several views in one persistent launch: each CTA takes
+// the next item of a shared queue (an atomic counter over the views' item
+// ranges, item_start[v] .. item_start[v + 1]: the view's tiles, then room
+// for its extra items) until none is left, and rasterizes it exactly as
+// raster_items_kernel does.  The views' items must have been assigned
+// (items_kernel) on the launching stream before.
+__global__ void __launch_bounds__(RT, VSR_RASTER_CTAS_PER_SM) raster_pool_kernel(const PoolView* __restrict__ views,
+                                                                                 const uint32_t* __restrict__ item_start,
+                                                                                 int nviews, uint32_t* __restrict__ queue,
+                                                                                 int split_max, int* __restrict__ status)
+{
+    __shared__ Stage st;
+    __shared__ uint32_t s_item;
+    const uint32_t total = item_start[nviews];
+    for (;;) {
+        __syncthreads();  // the previous item is done with the shared memory
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= total) return;
+        int v = 0;  // the last view whose items start at or before `it`
+        for (int hi = nviews - 1; v < hi;) {
+            const int mid = (v + hi + 1) >> 1;
+            if (item_start[mid] <= it)
+                v = mid;
+            else
+                hi = mid - 1;
+        }
+        const PoolView& pv = views[v];
+        const uint32_t e = it - item_start[v];
+        uint32_t u, k = 0;
+        if (e < pv.n_tiles) {
+            u = e;
+        } else {
+            const uint32_t x = e - pv.n_tiles;
+            if (x >= *pv.n_extra) continue;
+            const uint2 uk = pv.extra[x];
+            if (uk.x == 0xffffffffu) continue;
+            u = uk.x;
+            k = uk.y;
+        }
+        const int nsplit = (int)pv.nsplit_of[u];
+        uint32_t ca = 0, ce = 0;
+        if (nsplit == 1)
+            raster_tile<false>(pv.view, (int)u, st, false, ca, ce, nullptr, status);
+        else
+            raster_tile<false>(pv.view, (int)u, st, false, ca, ce, nullptr, status, (int)k * split_max,
+                               (int)(k + 1) * split_max, pv.split_slot[u], nsplit,
+                               SplitAcc{pv.acc, pv.key, pv.done});
+    }
+}
+
 // Dense reference of the same rasterization: every pixel of a tile against
 // every triangle of the scene, with no binning and no cull.  As in the
 // oracle, the miter distance is evaluated first: a triangle whose enlarged
@@ -586,18 +638,48 @@ vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, con
     return VSR_OK;
 }
 
+int raster_split_items(int split_max) { return split_max < CHUNK ? CHUNK : (split_max / CHUNK) * CHUNK; }
+
+uint32_t raster_extra_cap(uint32_t cap, const RasterWork& w, int split_max)
+{
+    // enough extra items for every pair of the bins, bounded by the list
+    const uint64_t bound = (uint64_t)cap / (uint64_t)raster_split_items(split_max) + 1;
+    return bound < w.extra_cap ? (uint32_t)bound : w.extra_cap;
+}
+
+vsr_status launch_raster_assign(const uint32_t* offsets, uint32_t n_tiles, uint32_t cap, RasterWork w, int split_max,
+                                cudaStream_t st)
+{
+    if (n_tiles == 0) return VSR_OK;
+    VSR_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), st));
+    items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, n_tiles, raster_split_items(split_max),
+                                                        w.nsplit_of, w.split_slot, w.counters, w.split_cap, w.extra,
+                                                        raster_extra_cap(cap, w, split_max));
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status launch_raster_pool(const PoolView* views_dev, const uint32_t* item_start_dev, int nviews,
+                              uint32_t* queue, int split_max, int* status, cudaStream_t st)
+{
+    if (nviews == 0) return VSR_OK;
+    const int sms = sm_count();
+    if (sms < 0) return VSR_ERR_CUDA;
+    VSR_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(uint32_t), st));
+    raster_pool_kernel<<<sms * VSR_RASTER_CTAS_PER_SM, RT, 0, st>>>(views_dev, item_start_dev, nviews, queue,
+                                                                    raster_split_items(split_max), status);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
 vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
                                RasterWork w, int split_max, int* status, cudaStream_t st, bool host_out)
 {
     if (n_tiles == 0) return VSR_OK;
-    split_max = split_max < CHUNK ? CHUNK : (split_max / CHUNK) * CHUNK;
-    // enough extra items for every pair of the bins, bounded by the list
-    const uint64_t bound = (uint64_t)cap / (uint64_t)split_max + 1;
-    const uint32_t extra_cap = bound < w.extra_cap ? (uint32_t)bound : w.extra_cap;
-    VSR_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), st));
-    items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, n_tiles, split_max, w.nsplit_of, w.split_slot,
-                                                        w.counters, w.split_cap, w.extra, extra_cap);
-    VSR_CUDA_TRY(cudaGetLastError());
+    vsr_status s = launch_raster_assign(offsets, n_tiles, cap, w, split_max, st);
+    if (s != VSR_OK) return s;
+    const uint32_t extra_cap = raster_extra_cap(cap, w, split_max);
+    split_max = raster_split_items(split_max);
     auto kern = host_out ? raster_items_kernel<true> : raster_items_kernel<false>;
     kern<<<n_tiles + extra_cap, RT, 0, st>>>(view, n_tiles, w.nsplit_of, w.split_slot, w.extra, w.counters + 1,
                                              split_max, SplitAcc{w.acc, w.key, w.done}, status);

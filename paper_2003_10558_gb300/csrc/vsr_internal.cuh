@@ -277,6 +277,34 @@ struct RasterWork {
     unsigned long long* key;  // split_cap x TILE_PIX, all ones between frames
     uint32_t* done;           // split_cap, zero between frames
 };
+// SMs of the current device (looked up once per device), or -1.
+int sm_count();
+
+// A view's raster work for the pooled launch: the view, its item assignment
+// (from launch_raster_assign) and its split accumulators.
+struct PoolView {
+    RasterView view;
+    uint32_t n_tiles;
+    const uint32_t* nsplit_of;
+    const int32_t* split_slot;
+    const uint2* extra;
+    const uint32_t* n_extra;  // the work's counters + 1
+    unsigned long long* acc;
+    unsigned long long* key;
+    uint32_t* done;
+};
+// items of a tile's split (a multiple of the staging chunk) and the room for
+// extra items a view's work gets for bins of capacity cap
+int raster_split_items(int split_max);
+uint32_t raster_extra_cap(uint32_t cap, const RasterWork& w, int split_max);
+// the work items of one view (split tiles, extra items), for the pooled launch
+vsr_status launch_raster_assign(const uint32_t* offsets, uint32_t n_tiles, uint32_t cap, RasterWork w, int split_max,
+                                cudaStream_t st);
+// one persistent raster launch over the items of several views: view v owns
+// items item_start[v] .. item_start[v + 1] - 1 (its tiles, then its extra
+// items); queue: a device counter (zeroed here)
+vsr_status launch_raster_pool(const PoolView* views_dev, const uint32_t* item_start_dev, int nviews,
+                              uint32_t* queue, int split_max, int* status, cudaStream_t st);
 // items + raster over all tiles of a view; offsets: its bin offsets
 // (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items);
 // host_out: the outputs are pinned host memory (written in whole tile rows)

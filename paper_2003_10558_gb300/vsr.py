@@ -35,7 +35,7 @@ EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_down
            "vsr_map_data", "vsr_map_download", "vsr_map_free", "vsr_setup", "vsr_scene_create", "vsr_scene_update",
            "vsr_scene_free", "vsr_scene_size", "vsr_raster", "vsr_raster_ex", "vsr_bin", "vsr_raster_tiles",
            "vsr_scene_bin_pairs", "vsr_raster_noalloc", "vsr_raster_dense", "vsr_batch_create", "vsr_batch_render",
-           "vsr_batch_config", "vsr_batch_free", "vsr_serve_create", "vsr_serve_add_scene", "vsr_serve_submit",
+           "vsr_batch_config", "vsr_batch_config_ex", "vsr_batch_set_mode", "vsr_batch_free", "vsr_serve_create", "vsr_serve_add_scene", "vsr_serve_submit",
            "vsr_serve_poll", "vsr_serve_wait", "vsr_serve_cancel", "vsr_serve_stats_get", "vsr_serve_now",
            "vsr_serve_destroy",
            "vsr_frags_create", "vsr_frags_free", "vsr_raster_shaded", "vsr_raster_backward",
@@ -128,6 +128,8 @@ def load(path: str = LIB_PATH):
             "vsr_batch_create": ([P(vp)], i32),
             "vsr_batch_render": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp], i32),
             "vsr_batch_config": ([vp, P(i32), P(i32), P(i32)], i32),
+            "vsr_batch_config_ex": ([vp, P(i32), P(i32), P(i32), P(i32)], i32),
+            "vsr_batch_set_mode": ([vp, i32], i32),
             "vsr_batch_free": ([vp], None),
             "vsr_serve_create": ([P(ServeCfg), P(vp)], i32),
             "vsr_serve_add_scene": ([vp, vp, i64, P(i32)], i32),
@@ -394,8 +396,8 @@ def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "dept
         cam = [0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1]
     tris = np.ascontiguousarray(tris, dtype=np.float32)
     T = tris.size // 9
-    H, W = m.shape
     if out is None:
+        H, W = m.shape
         out = {}
         if "id" in want:
             out["id"] = np.empty((H, W), dtype=np.uint32)
@@ -405,11 +407,11 @@ def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "dept
             out["cov"] = np.empty((H, W), dtype=np.float32)
     c = _cam_array(cam)
 
-    def p(a):
-        return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    def p(a):  # the array's address (cheaper than a.ctypes.data_as)
+        return None if a is None else ctypes.c_void_p(a.__array_interface__["data"][0])
 
-    check(load().vsr_render_host(m.h, sc.h, p(tris), T, c.ctypes.data_as(ctypes.c_void_p), p(out.get("id")),
-                                 p(out.get("depth")), p(out.get("cov")), _stream_ptr(stream)), "vsr_render_host")
+    check(load().vsr_render_host(m.h, sc.h, p(tris), T, p(c), p(out.get("id")), p(out.get("depth")),
+                                 p(out.get("cov")), _stream_ptr(stream)), "vsr_render_host")
     return out
 
 
@@ -444,10 +446,17 @@ class Batch:
               "vsr_batch_render")
         self._keep = (tris, maps, outs)
 
+    AUTO, CHAINS, POOLED = 0, 1, 2  # vsr_batch_set_mode
+
+    def set_mode(self, mode):
+        """Graph kinds the autotuner may keep (Batch.AUTO / CHAINS / POOLED)."""
+        check(load().vsr_batch_set_mode(self.h, int(mode)), "vsr_batch_set_mode")
+
     def config(self):
-        g, r, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        check(load().vsr_batch_config(self.h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(sp)), "vsr_batch_config")
-        return {"streams": g.value, "graphed": bool(r.value), "split_max": sp.value}
+        g, r, sp, po = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(load().vsr_batch_config_ex(self.h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(sp), ctypes.byref(po)),
+              "vsr_batch_config_ex")
+        return {"streams": g.value, "graphed": bool(r.value), "split_max": sp.value, "pooled": bool(po.value)}
 
     def free(self):
         if self.h:

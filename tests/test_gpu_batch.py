@@ -42,12 +42,17 @@ def _np(o):
     return {k: o[k].cpu().numpy().view(np.uint32) if k == "id" else o[k].cpu().numpy() for k in ("id", "depth", "cov")}
 
 
-def test_batch_equals_per_view_raster(vsr):
+@pytest.mark.parametrize("mode", ["auto", "chains", "pooled"])
+def test_batch_equals_per_view_raster(vsr, mode):
+    """Each graph kind the autotuner may keep -- per-view raster launches, or
+    one pooled persistent launch over all views' work items -- equals
+    per-view vsr_raster bit for bit, also after the cameras move."""
     views = _views(6, seed=3)
     tris_np = scenes.random_triangles(20000, 1.0, 30.0, 0.03, seed=8)
     tris = torch.from_numpy(tris_np).cuda()
     maps = [vsr.Map(v["W"], v["H"], v["k"], v["l"], v["s"], v["omega"]) for v in views]
     b = vsr.Batch()
+    b.set_mode({"auto": vsr.Batch.AUTO, "chains": vsr.Batch.CHAINS, "pooled": vsr.Batch.POOLED}[mode])
     outs = _outs(views)
     rng = np.random.default_rng(5)
     for call in range(4):
@@ -69,6 +74,8 @@ def test_batch_equals_per_view_raster(vsr):
             assert b.config()["graphed"]
     assert b.config()["streams"] in (1, 2, 4, 6)
     assert b.config()["split_max"] in (256, 512, 1024)
+    if mode != "auto":
+        assert b.config()["pooled"] == (mode == "pooled")
 
 
 def test_batch_view_against_oracle(vsr):
