@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     ap.add_argument("--no-legs", action="store_true",
                     help="single workload: skip the dense, batched and serving legs of the JSON line")
-    ap.add_argument("--leg-frames", type=int, default=30, help="batched leg: timed frames per arm")
+    ap.add_argument("--leg-frames", type=int, default=50, help="batched leg: timed frames per arm")
     ap.add_argument("--leg-seconds", type=float, default=10.0, help="serving leg: seconds of arrivals")
     return ap.parse_args()
 
