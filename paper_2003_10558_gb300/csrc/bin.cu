@@ -415,6 +415,14 @@ constexpr int BIN_BIG_CHUNK = 16;
 #define VSR_BIN_FLAT_RATIO 2
 #endif
 
+// triangles per warp of the large-grid shape: 16 (measured on the 1080p
+// frame's 220k triangles: bin stage 65.9 us against 73.8 us at 32 and 67.7 us
+// at 8) -- the grid is then two resident waves, and each warp's chain of
+// dependent loads (window rows, then cones) half as long
+#ifndef VSR_BIN_TPW_LARGE
+#define VSR_BIN_TPW_LARGE 16
+#endif
+
 #ifndef VSR_BIN_CB_LARGE
 #define VSR_BIN_CB_LARGE 1
 #endif
@@ -804,7 +812,7 @@ int sm_count()
 }
 
 // The binner's launch shape for T triangles on `sms` SMs: 0 = one cone per
-// step and 32 triangles per warp (grids beyond one resident wave at 7 CTAs
+// step and VSR_BIN_TPW_LARGE triangles per warp (grids beyond one resident wave at 7 CTAs
 // per SM), 1 = four cones per step, 2 = four cones and 8 triangles per warp
 // (scenes whose 8-per-warp grid still fits that wave).
 static int bin_shape(int T, int sms)
@@ -833,7 +841,10 @@ vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* c
     const int sms = sm_count();
     if (sms < 0) return VSR_ERR_CUDA;
     switch (bin_shape(T, sms)) {
-    case 0: bin_kernel<false, VSR_BIN_CB_LARGE, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
+    case 0:
+        bin_kernel<false, VSR_BIN_CB_LARGE, VSR_BIN_TPW_LARGE>
+            <<<(T + 4 * VSR_BIN_TPW_LARGE - 1) / (4 * VSR_BIN_TPW_LARGE), 128, 0, st>>>(v, T, nullptr, 0, nullptr);
+        break;
     case 1: bin_kernel<false, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
     default: bin_kernel<false, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, nullptr, 0, nullptr); break;
     }
@@ -861,7 +872,10 @@ vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32
     const int sms = sm_count();
     if (sms < 0) return VSR_ERR_CUDA;
     switch (bin_shape(T, sms)) {
-    case 0: bin_kernel<true, VSR_BIN_CB_LARGE, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
+    case 0:
+        bin_kernel<true, VSR_BIN_CB_LARGE, VSR_BIN_TPW_LARGE>
+            <<<(T + 4 * VSR_BIN_TPW_LARGE - 1) / (4 * VSR_BIN_TPW_LARGE), 128, 0, st>>>(v, T, ids, cap, status);
+        break;
     case 1: bin_kernel<true, 4, 32><<<(T + 127) / 128, 128, 0, st>>>(v, T, ids, cap, status); break;
     default: bin_kernel<true, 4, 8><<<(T + 31) / 32, 128, 0, st>>>(v, T, ids, cap, status); break;
     }
