@@ -42,150 +42,17 @@ __device__ __forceinline__ bool vless(const float* P, const float* Q)
     return false;
 }
 
-__device__ __forceinline__ df3 normalize3(df3 v) { return df3_scale(v, df_rsqrt(df_dot(v, v))); }
-
-__device__ __forceinline__ df3 edge_normal(const float* Pw, const float* Qw, const df3& P, const df3& Q, bool flip)
-{
-    df3 x;
-    if (vless(Qw, Pw))
-        x = df3_neg(df_cross(Q, P));
-    else
-        x = df_cross(P, Q);
-    df3 n = normalize3(x);
-    return flip ? df3_neg(n) : n;
-}
-
-__device__ __forceinline__ unsigned first_positive(const df3& n)
-{
-    if (n.x.hi != 0.0f) return n.x.hi > 0.0f;
-    if (n.y.hi != 0.0f) return n.y.hi > 0.0f;
-    return n.z.hi > 0.0f;
-}
-
-// VIEWS: blockIdx.y is a view; its camera is read from cams_dev (12 floats)
-// and its records go to rec + view * REC_F * T.
-template <bool VIEWS>
-__global__ void __launch_bounds__(128) setup_kernel(const float* __restrict__ tris, int T, Cam cam0,
-                                                     const float* __restrict__ cams_dev, float4* __restrict__ rec0)
-{
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    Cam cam = cam0;
-    float4* __restrict__ rec = rec0;
-    if (VIEWS) {
-        const float* c = cams_dev + 12 * blockIdx.y;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) cam.O[q] = c[q];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) cam.M[q] = c[3 + q];
-        rec = rec0 + (size_t)blockIdx.y * REC_F * (size_t)T;
-    }
-    float w[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) w[q] = tris[(size_t)t * 9 + q];
-
-    // an identity rotation (the common camera) needs only the exact
-    // differences A - O: the pair products by 1 and sums with 0 of the
-    // general transform return those pairs unchanged
-    bool ident = true;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) ident = ident && cam.M[q] == ((q % 4 == 0) ? 1.0f : 0.0f);
-    df3 V[3];
-    bool at_eye = false;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const df d0 = two_sum(w[3 * q + 0], -cam.O[0]);
-        const df d1 = two_sum(w[3 * q + 1], -cam.O[1]);
-        const df d2 = two_sum(w[3 * q + 2], -cam.O[2]);
-        df c[3] = {d0, d1, d2};
-        if (!ident) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                c[r] = df_add(df_add(df_mul_f(d0, cam.M[3 * r + 0]), df_mul_f(d1, cam.M[3 * r + 1])),
-                              df_mul_f(d2, cam.M[3 * r + 2]));
-        }
-        V[q] = {c[0], c[1], c[2]};
-        at_eye |= (c[0].hi == 0.0f && c[1].hi == 0.0f && c[2].hi == 0.0f);
-    }
-    df det = df_dot(V[0], df_cross(V[1], V[2]));
-
-    const size_t TT = (size_t)T;
-    float4 invalid = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (at_eye || det.hi == 0.0f || !isfinite(det.hi)) {
-#pragma unroll
-        for (int f = 0; f < REC_F; ++f) rec[f * TT + t] = invalid;
-        return;
-    }
-    const bool flip = det.hi < 0.0f;
-    df3 n1 = edge_normal(w + 0, w + 3, V[0], V[1], flip);
-    df3 n2 = edge_normal(w + 3, w + 6, V[1], V[2], flip);
-    df3 n3 = edge_normal(w + 6, w + 0, V[2], V[0], flip);
-
-    // miter: smallest circle over the unit vertices
-    df3 U0 = normalize3(V[0]), U1 = normalize3(V[1]), U2 = normalize3(V[2]);
-    df3 ea = df3_sub(U1, U2), eb = df3_sub(U2, U0), ec = df3_sub(U0, U1);
-    df a2 = df_dot(ea, ea), b2 = df_dot(eb, eb), c2 = df_dot(ec, ec);
-    df Os = df_mul(a2, df_sub(df_add(b2, c2), a2));
-    df Ot = df_mul(b2, df_sub(df_add(c2, a2), b2));
-    df Op = df_mul(c2, df_sub(df_add(a2, b2), c2));
-    df3 S;
-    const df half = df_make(0.5f);
-    if (Os.hi <= 0.0f)
-        S = df3_scale(df3_add(U1, U2), half);
-    else if (Ot.hi <= 0.0f)
-        S = df3_scale(df3_add(U2, U0), half);
-    else if (Op.hi <= 0.0f)
-        S = df3_scale(df3_add(U0, U1), half);
-    else {
-        df3 num = df3_add(df3_add(df3_scale(U0, Os), df3_scale(U1, Ot)), df3_scale(U2, Op));
-        S = df3_scale(num, df_recip(df_add(df_add(Os, Ot), Op)));
-    }
-    const df s2len = df_dot(S, S);
-    const df rs = df_rsqrt(s2len);
-    df slen = df_mul(s2len, rs);  // |S| = |S|^2 / |S|
-    df one = df_make(1.0f);
-    df omc = df_sub(one, slen);                    // 1 - cos rho
-    df sr = df_sqrt(df_mul(omc, df_add(one, slen)));  // sin rho
-    if (!(slen.hi > 0.0f) || !(sr.hi > 0.0f)) {
-#pragma unroll
-        for (int f = 0; f < REC_F; ++f) rec[f * TT + t] = invalid;
-        return;
-    }
-    df3 Sh = df3_scale(S, rs);
-    float K = __fmul_rn(2.0f, omc.hi);                   // 2 (1 - cos rho) = 4 sin^2(rho/2)
-    float inv2sr = __fdiv_rn(1.0f, __fmul_rn(2.0f, sr.hi));
-
-    // plane
-    df3 N = df_cross(df3_sub(V[0], V[1]), df3_sub(V[2], V[1]));
-    df3 Nh = normalize3(N);
-    df dN = df_dot(V[0], Nh);
-
-    unsigned ties = first_positive(n1) | (first_positive(n2) << 1) | (first_positive(n3) << 2);
-    rec[RF_CAP * TT + t] = make_float4(Sh.x.hi, Sh.y.hi, Sh.z.hi, slen.hi);
-    rec[RF_CAP2 * TT + t] = make_float4(sr.hi, K, inv2sr, 1.0f);
-    rec[RF_N1 * TT + t] = make_float4(n1.x.hi, n1.y.hi, n1.z.hi, __uint_as_float(ties));
-    rec[RF_N2 * TT + t] = make_float4(n2.x.hi, n2.y.hi, n2.z.hi, 0.0f);
-    rec[RF_N3 * TT + t] = make_float4(n3.x.hi, n3.y.hi, n3.z.hi, 0.0f);
-    rec[RF_PL * TT + t] = make_float4(Nh.x.hi, Nh.y.hi, Nh.z.hi, dN.hi);
-    rec[RF_N1L * TT + t] = make_float4(n1.x.lo, n1.y.lo, n1.z.lo, Sh.x.lo);
-    rec[RF_N2L * TT + t] = make_float4(n2.x.lo, n2.y.lo, n2.z.lo, Sh.y.lo);
-    rec[RF_N3L * TT + t] = make_float4(n3.x.lo, n3.y.lo, n3.z.lo, Sh.z.lo);
-    rec[RF_PLL * TT + t] = make_float4(Nh.x.lo, Nh.y.lo, Nh.z.lo, 0.0f);
-}
-
 // resident CTAs per SM the pair kernel is compiled for (its register cap)
 #ifndef VSR_SETUP_PAIR_CTAS
 #define VSR_SETUP_PAIR_CTAS 1
 #endif
-#ifndef VSR_SETUP_PAIRS
-#define VSR_SETUP_PAIRS 1
-#endif
 
-// The same set-up for two triangles per thread, every double-word step in
-// packed FP32x2 arithmetic (component x: triangle t0, y: t1 = t0 + 1); the
-// branches of the scalar kernel become per-component selects (the edge
-// operand order, the miter case, the invalid triangles), so each record is
-// bit for bit the scalar kernel's.
+// The set-up of two triangles per thread, every double-word step in packed
+// FP32x2 arithmetic (component x: triangle t0, y: t1 = t0 + 1; df2.cuh), so
+// each record is bit for bit what the scalar double-word algorithms of
+// df.cuh give for its triangle.  What would branch per triangle is a
+// per-component select: the canonical operand order of each edge, the miter
+// case (every case is formed), the invalid triangles.
 __device__ __forceinline__ df3_2 normalize3_2(df3_2 v) { return df3_2_scale(v, df2_rsqrt(df2_dot(v, v))); }
 
 __device__ __forceinline__ df3_2 edge_normal2(const float* P0, const float* Q0, const float* P1, const float* Q1,
@@ -206,11 +73,23 @@ __device__ __forceinline__ unsigned first_positive_c(float x, float y, float z)
     return z > 0.0f;
 }
 
-__global__ void __launch_bounds__(128, VSR_SETUP_PAIR_CTAS) setup_pair_kernel(const float* __restrict__ tris, int T, Cam cam,
-                                                         float4* __restrict__ rec)
+// VIEWS: blockIdx.y is a view; its camera is read from cams_dev (12 floats)
+// and its records go to rec + view * REC_F * T.
+template <bool VIEWS>
+__global__ void __launch_bounds__(128, VSR_SETUP_PAIR_CTAS) setup_pair_kernel(const float* __restrict__ tris, int T,
+                                                                             Cam cam, const float* __restrict__ cams_dev,
+                                                                             float4* __restrict__ rec)
 {
     const int t0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (t0 >= T) return;
+    if (VIEWS) {
+        const float* cv = cams_dev + 12 * blockIdx.y;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cam.O[q] = cv[q];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) cam.M[q] = cv[3 + q];
+        rec += (size_t)blockIdx.y * REC_F * (size_t)T;
+    }
     const bool has1 = t0 + 1 < T;
     const int t1 = has1 ? t0 + 1 : t0;
     float w0[9], w1[9];
@@ -219,6 +98,9 @@ __global__ void __launch_bounds__(128, VSR_SETUP_PAIR_CTAS) setup_pair_kernel(co
         w0[q] = tris[(size_t)t0 * 9 + q];
         w1[q] = tris[(size_t)t1 * 9 + q];
     }
+    // an identity rotation (the common camera) needs only the exact
+    // differences A - O: the pair products by 1 and sums with 0 of the
+    // general transform return those pairs unchanged
     bool ident = true;
 #pragma unroll
     for (int q = 0; q < 9; ++q) ident = ident && cam.M[q] == ((q % 4 == 0) ? 1.0f : 0.0f);
@@ -318,12 +200,8 @@ vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* r
     Cam c;
     for (int q = 0; q < 3; ++q) c.O[q] = cam[q];
     for (int q = 0; q < 9; ++q) c.M[q] = cam[3 + q];
-#if VSR_SETUP_PAIRS
     const int pairs = (T + 1) / 2;
-    setup_pair_kernel<<<(pairs + 127) / 128, 128, 0, st>>>(tris, T, c, rec);
-#else
-    setup_kernel<false><<<(T + 127) / 128, 128, 0, st>>>(tris, T, c, nullptr, rec);
-#endif
+    setup_pair_kernel<false><<<(pairs + 127) / 128, 128, 0, st>>>(tris, T, c, nullptr, rec);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
@@ -333,7 +211,8 @@ vsr_status launch_setup_views(const float* tris, int T, const float* cams_dev, i
 {
     if (T == 0 || nviews == 0) return VSR_OK;
     Cam c = {};
-    setup_kernel<true><<<dim3((T + 127) / 128, nviews), 128, 0, st>>>(tris, T, c, cams_dev, rec);
+    const int pairs = (T + 1) / 2;
+    setup_pair_kernel<true><<<dim3((pairs + 127) / 128, nviews), 128, 0, st>>>(tris, T, c, cams_dev, rec);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
