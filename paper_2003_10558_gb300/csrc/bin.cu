@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
     uint16_t* s_tcell = reinterpret_cast<uint16_t*>(s_cell + IDX_CELLS_MAX);
     __shared__ TileIndexHdr s_h;
     __shared__ uint32_t s_wsum[IDX_FUSED_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) s_h = TileIndexHdr{};
     __syncthreads();
     // 1. histogram of half-angles (one add per group of equal bins in a

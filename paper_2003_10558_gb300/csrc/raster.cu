@@ -358,7 +358,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
         if (threadIdx.x == 0) split.done[split_slot] = 0u;
     }
 
-    if (!ROWS) {
+    if constexpr (!ROWS) {
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             if (!inimg[p]) continue;
@@ -369,30 +369,30 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
             if (out_cov) out_cov[o] = (float)q.acc[p] * (1.0f / (float)COV_ONE);
             if (STATS && n_inside) n_inside[o] = q.cnt_in[p];
         }
-        return;
-    }
-    // Through shared memory, so that each warp store covers two whole tile
-    // rows (16 pixels, 64 B each) instead of four 8-pixel pieces: over the
-    // host link 32-byte pieces cost about a quarter of its bandwidth.
-    __shared__ uint32_t s_out[3][TILE_PIX];
+    } else {
+        // Through shared memory, so that each warp store covers two whole tile
+        // rows (16 pixels, 64 B each) instead of four 8-pixel pieces: over the
+        // host link 32-byte pieces cost about a quarter of its bandwidth.
+        __shared__ uint32_t s_out[3][TILE_PIX];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const int lp = lx + TILE * (ly0 + 4 * p);
-        const bool hit = q.key[p] != ~0ull;
-        s_out[0][lp] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
-        s_out[1][lp] = hit ? (uint32_t)(q.key[p] >> 32) : __float_as_uint(INFINITY);
-        s_out[2][lp] = __float_as_uint((float)q.acc[p] * (1.0f / (float)COV_ONE));
-        if (STATS && n_inside && inimg[p]) n_inside[(size_t)(py0 + 4 * p) * W + px] = q.cnt_in[p];
-    }
-    __syncthreads();
+        for (int p = 0; p < PPT; ++p) {
+            const int lp = lx + TILE * (ly0 + 4 * p);
+            const bool hit = q.key[p] != ~0ull;
+            s_out[0][lp] = hit ? (uint32_t)(q.key[p] & 0xffffffffull) : 0xffffffffu;
+            s_out[1][lp] = hit ? (uint32_t)(q.key[p] >> 32) : __float_as_uint(INFINITY);
+            s_out[2][lp] = __float_as_uint((float)q.acc[p] * (1.0f / (float)COV_ONE));
+            if (STATS && n_inside && inimg[p]) n_inside[(size_t)(py0 + 4 * p) * W + px] = q.cnt_in[p];
+        }
+        __syncthreads();
 #pragma unroll
-    for (int i = threadIdx.x; i < TILE_PIX; i += RT) {
-        const int ox = tx * TILE + (i % TILE), oy = ty * TILE + i / TILE;
-        if (ox >= W || oy >= H) continue;
-        const size_t o = (size_t)oy * W + ox;
-        if (out_id) out_id[o] = s_out[0][i];
-        if (out_depth) out_depth[o] = __uint_as_float(s_out[1][i]);
-        if (out_cov) out_cov[o] = __uint_as_float(s_out[2][i]);
+        for (int i = threadIdx.x; i < TILE_PIX; i += RT) {
+            const int ox = tx * TILE + (i % TILE), oy = ty * TILE + i / TILE;
+            if (ox >= W || oy >= H) continue;
+            const size_t o = (size_t)oy * W + ox;
+            if (out_id) out_id[o] = s_out[0][i];
+            if (out_depth) out_depth[o] = __uint_as_float(s_out[1][i]);
+            if (out_cov) out_cov[o] = __uint_as_float(s_out[2][i]);
+        }
     }
 }
 
