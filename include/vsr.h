@@ -323,6 +323,24 @@ vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
 vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
 
+/* vsr_render_host_async: vsr_render_host without the wait -- the frame is
+ * queued on `stream` (the set-up on the scene's own stream as above) and the
+ * call returns; vsr_render_host_wait(s) waits for it.  Frames of different
+ * (map, scene) pairs queued on different streams run at the same time on the
+ * device, so one frame's host transfers and raster overlap the next frame's
+ * map, set-up and binning (two maps and two scenes used in turn pipeline a
+ * stream of frames).  Until the wait returns, the scene, the map, the
+ * triangles and the output buffers must not be touched, and a second
+ * vsr_render_host(_async) on `s` returns VSR_ERR_INVALID_ARG.  Overlap needs
+ * pinned buffers (in place); pageable ones are staged with copies.
+ * vsr_render_host_wait returns VSR_OK (outputs complete),
+ * VSR_ERR_BIN_OVERFLOW (the frame outgrew the scene's bins: its outputs are
+ * incomplete; the next render of the scene grows them -- render it again),
+ * or VSR_ERR_CUDA; VSR_OK also when no frame of `s` is queued. */
+vsr_status vsr_render_host_async(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
+                                 uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
+vsr_status vsr_render_host_wait(vsr_scene s);
+
 /* ---- batched multi-view rendering -------------------------------------------
  * A batch renders V views of one scene as one CUDA graph.  Each view is the
  * chain of vsr_setup (with the view's camera, Sec. 1.1, 1.1.2, 1.1.4), vsr_bin

@@ -493,6 +493,10 @@ void vsr_scene_free(vsr_scene sc)
         cudaEventDestroy(sc->total_event);
     }
     if (sc->h_total) cudaFreeHost(sc->h_total);
+    if (sc->host_done) {
+        cudaEventSynchronize(sc->host_done);
+        cudaEventDestroy(sc->host_done);
+    }
     if (sc->side) cudaStreamDestroy(sc->side);
     if (sc->use_event) cudaEventDestroy(sc->use_event);
     if (sc->setup_event) cudaEventDestroy(sc->setup_event);
@@ -661,21 +665,36 @@ vsr_status vsr_scene_bin_pairs(vsr_scene sc, void* stream, int64_t* pairs)
     return VSR_OK;
 }
 
-vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int64_t T, const float cam[12],
-                           uint32_t* id_host, float* depth_host, float* cov_host, void* stream)
+}  // extern "C"
+
+namespace {
+
+// One frame of the host path: the device addresses of the host buffers (or
+// of their staging), and whether the raster writes them in place.
+struct HostFrame {
+    uint32_t* id_d = nullptr;
+    float* depth_d = nullptr;
+    float* cov_d = nullptr;
+    bool stage_id = false, stage_depth = false, stage_cov = false, in_place = false;
+    size_t npix = 0;
+};
+
+// Queue the front of a host frame: the scene's own stream and events (made
+// at the first call), the triangles' copy when they are not addressable in
+// place, and the set-up on that stream; `st` then waits for the set-up.
+vsr_status host_frame_front(vsr_map m, vsr_scene sc, const float* tris_host, int64_t T, const float cam[12],
+                            uint32_t* id_host, float* depth_host, float* cov_host, cudaStream_t st, HostFrame* f)
 {
-    if (!m || !sc || !setup_args_ok(tris_host, T, cam)) return VSR_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
     vsr_status s;
-    const size_t npix = (size_t)m->p.W * m->p.H;
+    f->npix = (size_t)m->p.W * m->p.H;
     // Host buffers the GPU can address in place (pinned memory mapped into
     // its address space) are read by the set-up kernel and written by the
     // raster kernel directly over the host link, so the transfers overlap
     // the kernels; other host memory is staged through device buffers.
     const float* tris_src = T > 0 ? (const float*)mapped_host(tris_host) : nullptr;
-    uint32_t* id_d = (uint32_t*)mapped_host(id_host);
-    float* depth_d = (float*)mapped_host(depth_host);
-    float* cov_d = (float*)mapped_host(cov_host);
+    f->id_d = (uint32_t*)mapped_host(id_host);
+    f->depth_d = (float*)mapped_host(depth_host);
+    f->cov_d = (float*)mapped_host(cov_host);
     // The set-up (and the triangles' copy) runs on the scene's own stream and
     // waits only for the scene's last queued use, so it overlaps work queued
     // on `stream` before this call that leaves the scene alone -- a map
@@ -684,16 +703,17 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
         if (cudaStreamCreateWithFlags(&sc->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sc->use_event, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&sc->setup_event, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sc->host_done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc((void**)&sc->host_status, sizeof(int)) != cudaSuccess ||
             cudaMemset(sc->host_status, 0, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             if (sc->side) cudaStreamDestroy(sc->side);
             if (sc->use_event) cudaEventDestroy(sc->use_event);
             if (sc->setup_event) cudaEventDestroy(sc->setup_event);
+            if (sc->host_done) cudaEventDestroy(sc->host_done);
             cudaFree(sc->host_status);
             sc->side = nullptr;
-            sc->use_event = nullptr;
-            sc->setup_event = nullptr;
+            sc->use_event = sc->setup_event = sc->host_done = nullptr;
             sc->host_status = nullptr;
             return VSR_ERR_CUDA;
         }
@@ -714,55 +734,110 @@ vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int6
                                      sc->side));
         tris_src = sc->tris_dev;
     }
-    const bool stage_id = id_host && !id_d, stage_depth = depth_host && !depth_d, stage_cov = cov_host && !cov_d;
-    if (stage_id || stage_depth || stage_cov) {
-        if (12 * npix > sc->out_alloc) {
+    f->stage_id = id_host && !f->id_d;
+    f->stage_depth = depth_host && !f->depth_d;
+    f->stage_cov = cov_host && !f->cov_d;
+    if (f->stage_id || f->stage_depth || f->stage_cov) {
+        if (12 * f->npix > sc->out_alloc) {
             cudaFree(sc->out_dev);
             sc->out_dev = nullptr;
             sc->out_alloc = 0;
-            if (cudaMalloc(&sc->out_dev, 12 * npix) != cudaSuccess) {
+            if (cudaMalloc(&sc->out_dev, 12 * f->npix) != cudaSuccess) {
                 cudaGetLastError();
                 return VSR_ERR_OOM;
             }
-            sc->out_alloc = 12 * npix;
+            sc->out_alloc = 12 * f->npix;
         }
-        if (stage_id) id_d = (uint32_t*)sc->out_dev;
-        if (stage_depth) depth_d = (float*)((char*)sc->out_dev + 4 * npix);
-        if (stage_cov) cov_d = (float*)((char*)sc->out_dev + 8 * npix);
+        if (f->stage_id) f->id_d = (uint32_t*)sc->out_dev;
+        if (f->stage_depth) f->depth_d = (float*)((char*)sc->out_dev + 4 * f->npix);
+        if (f->stage_cov) f->cov_d = (float*)((char*)sc->out_dev + 8 * f->npix);
     }
+    f->in_place = (id_host && !f->stage_id) || (depth_host && !f->stage_depth) || (cov_host && !f->stage_cov);
     if ((s = scene_setup(sc, tris_src, T, cam, sc->side)) != VSR_OK) return s;
     VSR_CUDA_TRY(cudaEventRecord(sc->setup_event, sc->side));
     VSR_CUDA_TRY(cudaStreamWaitEvent(st, sc->setup_event, 0));
-    const bool in_place = (id_host && !stage_id) || (depth_host && !stage_depth) || (cov_host && !stage_cov);
-    // Binning and raster report to the scene's own status word.  The call
-    // waits for the frame anyway, so a frame that outgrew its bins (the pair
-    // total, stored into pinned memory by the scan, above the capacity) is
-    // rendered again: the next binning grows the bins from that total.
+    return VSR_OK;
+}
+
+// Queue the back of a host frame on `st`: binning and raster, reporting to
+// the scene's own status word, then the copies of staged outputs.
+vsr_status host_frame_back(vsr_map m, vsr_scene sc, const HostFrame& f, uint32_t* id_host, float* depth_host,
+                           float* cov_host, cudaStream_t st)
+{
     int* const saved_status = sc->status;
     sc->status = sc->host_status;
-    for (int attempt = 0;; ++attempt) {
-        if ((s = vsr_bin(m, sc, stream)) == VSR_OK)
-            s = raster_tiles(m, sc, id_d, depth_d, cov_d, nullptr, stream, in_place);
-        if (s == VSR_OK && stage_id && cudaMemcpyAsync(id_host, id_d, 4 * npix, cudaMemcpyDeviceToHost, st))
-            s = VSR_ERR_CUDA;
-        if (s == VSR_OK && stage_depth &&
-            cudaMemcpyAsync(depth_host, depth_d, 4 * npix, cudaMemcpyDeviceToHost, st))
-            s = VSR_ERR_CUDA;
-        if (s == VSR_OK && stage_cov && cudaMemcpyAsync(cov_host, cov_d, 4 * npix, cudaMemcpyDeviceToHost, st))
-            s = VSR_ERR_CUDA;
-        if (s == VSR_OK && cudaStreamSynchronize(st) != cudaSuccess) s = VSR_ERR_CUDA;
-        const bool outgrew = s == VSR_OK && sc->total_pending && sc->total_map == m->gen &&
-                             sc->total_scene == sc->gen && *sc->h_total > sc->cap;
-        if (!outgrew) break;
-        if (attempt == 2 || cudaMemsetAsync(sc->host_status, 0, sizeof(int), st) != cudaSuccess) {
-            cudaGetLastError();
-            s = VSR_ERR_BIN_OVERFLOW;
-            break;
-        }
-    }
+    vsr_status s = vsr_bin(m, sc, st);
+    if (s == VSR_OK) s = raster_tiles(m, sc, f.id_d, f.depth_d, f.cov_d, nullptr, st, f.in_place);
     sc->status = saved_status;
+    if (s == VSR_OK && f.stage_id && cudaMemcpyAsync(id_host, f.id_d, 4 * f.npix, cudaMemcpyDeviceToHost, st))
+        s = VSR_ERR_CUDA;
+    if (s == VSR_OK && f.stage_depth &&
+        cudaMemcpyAsync(depth_host, f.depth_d, 4 * f.npix, cudaMemcpyDeviceToHost, st))
+        s = VSR_ERR_CUDA;
+    if (s == VSR_OK && f.stage_cov && cudaMemcpyAsync(cov_host, f.cov_d, 4 * f.npix, cudaMemcpyDeviceToHost, st))
+        s = VSR_ERR_CUDA;
     if (s != VSR_OK) cudaGetLastError();
     return s;
+}
+
+// After the frame completed: did it outgrow its bins (the pair total, stored
+// into pinned memory by the scan, above the capacity)?
+bool host_frame_outgrew(vsr_scene sc, uint64_t map_gen)
+{
+    return sc->total_pending && sc->total_map == map_gen && sc->total_scene == sc->gen && *sc->h_total > sc->cap;
+}
+
+}  // namespace
+
+extern "C" {
+
+vsr_status vsr_render_host(vsr_map m, vsr_scene sc, const float* tris_host, int64_t T, const float cam[12],
+                           uint32_t* id_host, float* depth_host, float* cov_host, void* stream)
+{
+    if (!m || !sc || !setup_args_ok(tris_host, T, cam)) return VSR_ERR_INVALID_ARG;
+    if (sc->host_pending) return VSR_ERR_INVALID_ARG;  // an asynchronous frame of this scene is not waited for
+    cudaStream_t st = (cudaStream_t)stream;
+    HostFrame f;
+    vsr_status s = host_frame_front(m, sc, tris_host, T, cam, id_host, depth_host, cov_host, st, &f);
+    if (s != VSR_OK) return s;
+    // The call waits for the frame anyway, so a frame that outgrew its bins
+    // is rendered again: the next binning grows the bins from its total.
+    for (int attempt = 0;; ++attempt) {
+        s = host_frame_back(m, sc, f, id_host, depth_host, cov_host, st);
+        if (s == VSR_OK && cudaStreamSynchronize(st) != cudaSuccess) s = VSR_ERR_CUDA;
+        if (s != VSR_OK || !host_frame_outgrew(sc, m->gen)) break;
+        if (attempt == 2) return VSR_ERR_BIN_OVERFLOW;
+    }
+    if (s != VSR_OK) cudaGetLastError();
+    return s;
+}
+
+vsr_status vsr_render_host_async(vsr_map m, vsr_scene sc, const float* tris_host, int64_t T, const float cam[12],
+                                 uint32_t* id_host, float* depth_host, float* cov_host, void* stream)
+{
+    if (!m || !sc || !setup_args_ok(tris_host, T, cam)) return VSR_ERR_INVALID_ARG;
+    if (sc->host_pending) return VSR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HostFrame f;
+    vsr_status s = host_frame_front(m, sc, tris_host, T, cam, id_host, depth_host, cov_host, st, &f);
+    if (s == VSR_OK) s = host_frame_back(m, sc, f, id_host, depth_host, cov_host, st);
+    if (s != VSR_OK) return s;
+    VSR_CUDA_TRY(cudaEventRecord(sc->host_done, st));
+    sc->host_pending = true;
+    sc->host_map_gen = m->gen;
+    return VSR_OK;
+}
+
+vsr_status vsr_render_host_wait(vsr_scene sc)
+{
+    if (!sc) return VSR_ERR_INVALID_ARG;
+    if (!sc->host_pending) return VSR_OK;
+    sc->host_pending = false;
+    if (cudaEventSynchronize(sc->host_done) != cudaSuccess) {
+        cudaGetLastError();
+        return VSR_ERR_CUDA;
+    }
+    return host_frame_outgrew(sc, sc->host_map_gen) ? VSR_ERR_BIN_OVERFLOW : VSR_OK;
 }
 
 }  // extern "C"

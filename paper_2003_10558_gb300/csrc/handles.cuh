@@ -86,6 +86,11 @@ struct vsr_scene_s {
     // its device status word: a frame that outgrew its bins is rendered
     // again, so the overflow it raised goes here, not to the per-device word
     int* host_status = nullptr;
+    // vsr_render_host_async: the frame's completion, whether one is queued
+    // and not yet waited for, and the map generation it was binned against
+    cudaEvent_t host_done = nullptr;
+    bool host_pending = false;
+    uint64_t host_map_gen = 0;
 };
 
 inline int* scene_status(const vsr_scene_s* s) { return s->status ? s->status : status_word(); }

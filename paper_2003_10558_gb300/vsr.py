@@ -39,7 +39,8 @@ EXPORTS = ("vsr_make_map", "vsr_make_map_ex", "vsr_make_map_spec", "vsr_map_down
            "vsr_serve_poll", "vsr_serve_wait", "vsr_serve_cancel", "vsr_serve_stats_get", "vsr_serve_now",
            "vsr_serve_destroy",
            "vsr_frags_create", "vsr_frags_free", "vsr_raster_shaded", "vsr_raster_backward",
-           "vsr_render_host", "vsr_status_str", "vsr_last_device_status", "vsr_version")
+           "vsr_render_host", "vsr_render_host_async", "vsr_render_host_wait", "vsr_status_str",
+           "vsr_last_device_status", "vsr_version")
 
 
 class VsrError(RuntimeError):
@@ -141,6 +142,8 @@ def load(path: str = LIB_PATH):
             "vsr_serve_now": ([], ctypes.c_double),
             "vsr_serve_destroy": ([vp], i32),
             "vsr_render_host": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+            "vsr_render_host_async": ([vp, vp, vp, i64, vp, vp, vp, vp, vp], i32),
+            "vsr_render_host_wait": ([vp], i32),
             "vsr_frags_create": ([P(vp)], i32),
             "vsr_frags_free": ([vp], None),
             "vsr_raster_shaded": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
@@ -388,10 +391,7 @@ def raster_dense(m: Map, sc: Scene, out=None, stream=None):
     return out
 
 
-def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "depth", "cov"), out=None, stream=None):
-    """End to end from host memory (vsr_render_host): numpy triangles in,
-    numpy id (uint32) / depth / cov out.  `out` may hold preallocated
-    (ideally pinned) arrays."""
+def _host_frame_args(m, tris, cam, want, out):
     if cam is None:
         cam = [0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1]
     tris = np.ascontiguousarray(tris, dtype=np.float32)
@@ -410,9 +410,38 @@ def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "dept
     def p(a):  # the array's address (cheaper than a.ctypes.data_as)
         return None if a is None else ctypes.c_void_p(a.__array_interface__["data"][0])
 
-    check(load().vsr_render_host(m.h, sc.h, p(tris), T, p(c), p(out.get("id")), p(out.get("depth")),
-                                 p(out.get("cov")), _stream_ptr(stream)), "vsr_render_host")
+    return (p(tris), T, p(c), p(out.get("id")), p(out.get("depth")), p(out.get("cov"))), (tris, c), out
+
+
+def render_host(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "depth", "cov"), out=None, stream=None):
+    """End to end from host memory (vsr_render_host): numpy triangles in,
+    numpy id (uint32) / depth / cov out.  `out` may hold preallocated
+    (ideally pinned) arrays."""
+    args, _keep, out = _host_frame_args(m, tris, cam, want, out)
+    check(load().vsr_render_host(m.h, sc.h, *args, _stream_ptr(stream)), "vsr_render_host")
     return out
+
+
+def render_host_async(m: Map, sc: Scene, tris: np.ndarray, cam=None, want=("id", "depth", "cov"), out=None,
+                      stream=None):
+    """Queue one frame from host memory (vsr_render_host_async) and return its
+    outputs (filled once render_host_wait(sc) has returned).  The arrays must
+    stay alive and untouched until then; pinned ones are written in place."""
+    args, keep, out = _host_frame_args(m, tris, cam, want, out)
+    check(load().vsr_render_host_async(m.h, sc.h, *args, _stream_ptr(stream)), "vsr_render_host_async")
+    sc._host_keep = (keep, out)
+    return out
+
+
+def render_host_wait(sc: Scene):
+    """Wait for the scene's queued host frame: 0 (complete) or
+    VSR_ERR_BIN_OVERFLOW (it outgrew the scene's bins: render it again);
+    raises on a CUDA error."""
+    r = load().vsr_render_host_wait(sc.h)
+    sc._host_keep = None
+    if r not in (0, VSR_ERR_BIN_OVERFLOW):
+        check(r, "vsr_render_host_wait")
+    return r
 
 
 class Batch:

@@ -415,6 +415,61 @@ def test_render_host_beside_map_update(vsr):
     assert vsr.last_device_status() == 0
 
 
+def test_render_host_async_pipeline(vsr):
+    """Frames queued with vsr_render_host_async on two (map, scene) pairs in
+    turn, each pair on its own stream, overlap on the device; each frame,
+    once waited for, equals vsr_raster on a fresh map of its lens bit for bit.
+    A frame that outgrew its scene's bins is reported by the wait
+    (VSR_ERR_BIN_OVERFLOW) and rendered again; a second queue on a scene whose
+    frame was not waited for is refused."""
+    W, H = 333, 197
+    tris = scenes.random_triangles(30000, 1.0, 30.0, 0.03, seed=21)
+    cam = scenes.camera()
+    td = torch.from_numpy(tris).cuda()
+    lenses = [(0.3, 0.8, 0.9, 200.0), (-0.4, 0.7, 0.8, 250.0), (0.0, 1.0, 1.0, 120.0), (0.6, 0.9, 0.7, 300.0)] * 2
+    tris_pin = torch.from_numpy(tris).pin_memory().numpy()
+
+    def pinned_outputs():
+        o = {k: torch.zeros((H, W), dtype=dt).pin_memory().numpy()
+             for k, dt in (("id", torch.int32), ("depth", torch.float32), ("cov", torch.float32))}
+        o["id"] = o["id"].view(np.uint32)
+        return o
+
+    outs = [pinned_outputs(), pinned_outputs()]
+    maps = [vsr.Map(W, H, *lenses[0]), vsr.Map(W, H, *lenses[1])]
+    works = [vsr.Scene(), vsr.Scene()]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pending = [None, None]
+    overflowed = []
+
+    def finish(i):
+        k, lens = pending[i]
+        pending[i] = None
+        if vsr.render_host_wait(works[i]) == vsr.VSR_ERR_BIN_OVERFLOW:
+            overflowed.append(k)
+            vsr.render_host(maps[i], works[i], tris_pin, cam, out=outs[i], stream=streams[i])
+        ref = _gpu_outputs(vsr.raster(vsr.Map(W, H, *lens), vsr.Scene(td, cam)))
+        for key in ref:
+            assert np.array_equal(ref[key].view(np.uint32), outs[i][key].view(np.uint32)), (k, key)
+
+    for k, lens in enumerate(lenses):
+        i = k % 2
+        if pending[i] is not None:
+            finish(i)
+        maps[i].update(W, H, *lens, stream=streams[i])
+        vsr.render_host_async(maps[i], works[i], tris_pin, cam, out=outs[i], stream=streams[i])
+        pending[i] = (k, lens)
+        if k == 2:
+            with pytest.raises(vsr.VsrError):
+                vsr.render_host_async(maps[i], works[i], tris_pin, cam, out=outs[i], stream=streams[i])
+    for i in (0, 1):
+        if pending[i] is not None:
+            finish(i)
+    assert vsr.render_host_wait(works[0]) == 0  # nothing queued
+    assert vsr.last_device_status() == 0
+    print("frames rendered again after a bin overflow:", overflowed)
+
+
 def test_invalid_arguments(vsr):
     L = vsr.load()
     import ctypes
