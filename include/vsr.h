@@ -358,9 +358,11 @@ vsr_status vsr_render_host_wait(vsr_scene s);
  * views eagerly, synchronises `stream` once to size every view's bins, then
  * captures graphs of two kinds for each S in {1, 2, 4, 8}: each view's chain
  * ending in its own raster launch, and chains that end after binning and
- * work-item assignment followed by ONE pooled raster launch -- persistent
- * CTAs (resident CTAs per SM x SMs) that take the (view, item) work of all
- * views from a shared queue (an atomic counter; no CTA waits for another).
+ * work-item assignment, the views rasterized in G in {1, 4, 16} pooled
+ * launches -- persistent CTAs (resident CTAs per SM x SMs) that take the
+ * (view, item) work of a group of views from a shared queue (an atomic
+ * counter; no CTA waits for another), each group's launch on a stream of its
+ * own as soon as its views are binned, beside the next groups' chains.
  * It times their replays, keeps the fastest, then tries 256 and 1024
  * triangles per work item of a long bin at that S and kind (the autotuner;
  * vsr_batch_set_mode can restrict the kinds); later calls with the same configuration
@@ -383,8 +385,8 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
  * S, whether a graph is ready, and the triangles per work item of a long
  * bin (a tile whose bin holds more is rasterized by several CTAs). */
 vsr_status vsr_batch_config(vsr_batch b, int* streams, int* graphed, int* split_max);
-/* vsr_batch_config plus `pooled`: 1 if the kept graph rasterizes all views
- * in the one pooled launch. */
+/* vsr_batch_config plus `pooled`: the number of pooled raster launches
+ * (groups of views) of the kept graph, 0 if each view has its own. */
 vsr_status vsr_batch_config_ex(vsr_batch b, int* streams, int* graphed, int* split_max, int* pooled);
 /* Graph kinds the autotuner may keep: VSR_BATCH_AUTO (both; the default),
  * VSR_BATCH_CHAINS (per-view raster launches only) or VSR_BATCH_POOLED (the

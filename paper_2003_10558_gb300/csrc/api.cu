@@ -937,8 +937,10 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
 // graph, so each view keeps its working set in L2 while independent views
 // overlap on the GPU and no launch pays host overhead.  The first call for a
 // configuration runs the views eagerly (sizing every view's bins with one
-// synchronisation), then captures one graph per candidate S in {1, 2, 4, 8},
-// times their replays and keeps the fastest (the autotuner).  Later calls
+// synchronisation), then captures one graph per candidate (S in {1, 2, 4, 8}
+// streams; the views' own raster launches or 1, 4 or 16 pooled ones; then the
+// work-item size), times their replays and keeps the fastest (the
+// autotuner).  Later calls
 // with the same configuration copy the cameras into pinned staging and
 // replay.
 namespace {
@@ -987,12 +989,17 @@ struct vsr_batch_s {
     int nstreams = 0;
     int split_max = SPLIT_MAX_DEFAULT;
     int mode = VSR_BATCH_AUTO;
-    bool pooled = false;  // the graph rasterizes all views in one pooled launch
-    // the pooled launch's views, item ranges and queue counter (device)
+    // the kept graph rasterizes its views in pool_groups pooled launches (0:
+    // one raster launch per view)
+    int pool_groups = 0;
+    // the pooled launches' views, item ranges (per group: its views' starts,
+    // then its total) and queue counters (device), and their stream
     PoolView* pool_views = nullptr;
     uint32_t* pool_start = nullptr;
     uint32_t* pool_queue = nullptr;
     int pool_alloc = 0;
+    cudaStream_t pool_stream = nullptr;
+    cudaEvent_t pool_join = nullptr;
 };
 
 namespace {
@@ -1060,10 +1067,18 @@ vsr_status batch_view_back(vsr_batch b, int v, vsr_map m, int64_t T, bool use_pa
                                st);
 }
 
-// The pooled launch's per-view work and item ranges for this configuration
-// and split, uploaded once (outside any capture).
+constexpr int POOL_GROUPS_MAX = 16;
+
+// Views [first, last) of pool group g of `groups` (contiguous, as even as
+// possible).
+inline int pool_first(int g, int groups, int nviews) { return (int)((int64_t)g * nviews / groups); }
+
+// The pooled launches' per-view work and item ranges for this configuration,
+// split and number of groups, uploaded once (outside any capture).  Group g's
+// item starts sit at pool_start + first(g) + g: its views' starts relative to
+// the group, then the group's total.
 vsr_status batch_pool_upload(vsr_batch b, int nviews, const vsr_map* maps, int64_t T, uint32_t* const* id,
-                             float* const* depth, float* const* cov, int split_max)
+                             float* const* depth, float* const* cov, int split_max, int groups)
 {
     if (nviews > b->pool_alloc) {
         cudaFree(b->pool_views);
@@ -1074,17 +1089,20 @@ vsr_status batch_pool_upload(vsr_batch b, int nviews, const vsr_map* maps, int64
         b->pool_queue = nullptr;
         b->pool_alloc = 0;
         if (cudaMalloc((void**)&b->pool_views, sizeof(PoolView) * (size_t)nviews) != cudaSuccess ||
-            cudaMalloc((void**)&b->pool_start, sizeof(uint32_t) * ((size_t)nviews + 1)) != cudaSuccess ||
-            cudaMalloc((void**)&b->pool_queue, sizeof(uint32_t)) != cudaSuccess) {
+            cudaMalloc((void**)&b->pool_start, sizeof(uint32_t) * ((size_t)nviews + POOL_GROUPS_MAX)) != cudaSuccess ||
+            cudaMalloc((void**)&b->pool_queue, sizeof(uint32_t) * POOL_GROUPS_MAX) != cudaSuccess) {
             cudaGetLastError();
             return VSR_ERR_OOM;
         }
         b->pool_alloc = nviews;
     }
+    if (groups < 1 || groups > POOL_GROUPS_MAX || groups > nviews) return VSR_ERR_INVALID_ARG;
     std::vector<PoolView> pv((size_t)nviews);
-    std::vector<uint32_t> start((size_t)nviews + 1, 0u);
+    std::vector<uint32_t> start((size_t)nviews + POOL_GROUPS_MAX, 0u);
     uint64_t items = 0;
+    int g = 0;
     for (int v = 0; v < nviews; ++v) {
+        if (v == pool_first(g, groups, nviews)) items = 0;  // a group's items count from 0
         const BatchView& bv = b->views[v];
         const vsr_map m = maps[v];
         const uint32_t tiles = (uint32_t)(m->tx * m->ty);
@@ -1099,14 +1117,17 @@ vsr_status batch_pool_upload(vsr_batch b, int nviews, const vsr_map* maps, int64
         pv[v].acc = bv.work.acc;
         pv[v].key = bv.work.key;
         pv[v].done = bv.work.done;
-        start[v] = (uint32_t)items;
+        start[(size_t)v + g] = (uint32_t)items;
         items += tiles + raster_extra_cap(bv.cap, bv.work, split_max);
         if (items > 0xffffffffull) return VSR_ERR_INVALID_ARG;
+        if (v + 1 == pool_first(g + 1, groups, nviews)) {
+            start[(size_t)v + 1 + g] = (uint32_t)items;  // the group's total
+            ++g;
+        }
     }
-    start[nviews] = (uint32_t)items;
     VSR_CUDA_TRY(cudaMemcpy(b->pool_views, pv.data(), sizeof(PoolView) * (size_t)nviews, cudaMemcpyHostToDevice));
-    VSR_CUDA_TRY(
-        cudaMemcpy(b->pool_start, start.data(), sizeof(uint32_t) * ((size_t)nviews + 1), cudaMemcpyHostToDevice));
+    VSR_CUDA_TRY(cudaMemcpy(b->pool_start, start.data(), sizeof(uint32_t) * ((size_t)nviews + groups),
+                            cudaMemcpyHostToDevice));
     return VSR_OK;
 }
 
@@ -1121,7 +1142,9 @@ vsr_status vsr_batch_create(vsr_batch* out)
     vsr_batch b = new (std::nothrow) vsr_batch_s;
     if (!b) return VSR_ERR_OOM;
     bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->cams_done, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->cams_done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->pool_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->pool_join, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < BATCH_STREAMS_MAX; ++i)
         ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
@@ -1152,6 +1175,8 @@ void vsr_batch_free(vsr_batch b)
     cudaFree(b->pool_views);
     cudaFree(b->pool_start);
     cudaFree(b->pool_queue);
+    if (b->pool_stream) cudaStreamDestroy(b->pool_stream);
+    if (b->pool_join) cudaEventDestroy(b->pool_join);
     delete b;
 }
 
@@ -1257,18 +1282,23 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             return s;
     VSR_CUDA_TRY(cudaEventRecord(b->cams_done, st));
 
-    // autotune: capture one graph per candidate (parallel streams S, triangles
-    // per work item of a long bin), time three replays, keep the fastest;
-    // first the stream counts at the default split, then the splits at the
-    // best stream count
+    // autotune: capture one graph per candidate (parallel streams S, raster
+    // kind, triangles per work item of a long bin), time three replays, keep
+    // the fastest; first the stream counts and kinds at the default split,
+    // then the splits at the best of them
     float best = 1e30f;
     cudaEvent_t e0, e1;
     VSR_CUDA_TRY(cudaEventCreate(&e0));
     VSR_CUDA_TRY(cudaEventCreate(&e1));
-    auto candidate = [&](int S, int split, bool pooled) -> vsr_status {
+    // groups > 0: the views' chains end after binning and item assignment,
+    // and each group of views is rasterized by one pooled launch on the pool
+    // stream as soon as its views are binned, beside the next groups' chains
+    auto candidate = [&](int S, int split, int groups) -> vsr_status {
         S = S < nviews ? S : nviews;
+        if (groups > nviews) return VSR_OK;
+        const bool pooled = groups > 0;
         if (pooled) {
-            const vsr_status us = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, split);
+            const vsr_status us = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, split, groups);
             if (us != VSR_OK) return us;
         }
         cudaStream_t cs = b->streams[0];
@@ -1280,6 +1310,9 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             cst = VSR_ERR_CUDA;
         for (int i = 1; cst == VSR_OK && i < S; ++i)
             if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) cst = VSR_ERR_CUDA;
+        if (cst == VSR_OK && pooled && cudaStreamWaitEvent(b->pool_stream, b->fork, 0) != cudaSuccess)
+            cst = VSR_ERR_CUDA;
+        int group = 0;
         for (int v = 0; cst == VSR_OK && v < nviews; ++v) {
             cudaStream_t vs = b->streams[v % S];
             cst = batch_view_front(b, v, maps[v], tris_dev, T, true, vs);
@@ -1290,13 +1323,27 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             if (cst == VSR_OK)
                 cst = batch_view_back(b, v, maps[v], T, true, out_ptr(id_dev, v), out_ptr(depth_dev, v),
                                       out_ptr(cov_dev, v), vs, split, pooled);
+            if (cst == VSR_OK && pooled && v + 1 == pool_first(group + 1, groups, nviews)) {
+                // the group's views are binned once every stream reaches this point
+                for (int i = 0; cst == VSR_OK && i < S; ++i)
+                    if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
+                        cudaStreamWaitEvent(b->pool_stream, b->join[i], 0) != cudaSuccess)
+                        cst = VSR_ERR_CUDA;
+                const int first = pool_first(group, groups, nviews);
+                if (cst == VSR_OK)
+                    cst = launch_raster_pool(b->pool_views + first, b->pool_start + first + group, v + 1 - first,
+                                             b->pool_queue + group, split, status_word(), b->pool_stream);
+                ++group;
+            }
         }
         for (int i = 1; cst == VSR_OK && i < S; ++i)
             if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
                 cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess)
                 cst = VSR_ERR_CUDA;
-        if (cst == VSR_OK && pooled)
-            cst = launch_raster_pool(b->pool_views, b->pool_start, nviews, b->pool_queue, split, status_word(), cs);
+        if (cst == VSR_OK && pooled &&
+            (cudaEventRecord(b->pool_join, b->pool_stream) != cudaSuccess ||
+             cudaStreamWaitEvent(cs, b->pool_join, 0) != cudaSuccess))
+            cst = VSR_ERR_CUDA;
         const cudaError_t ee = cudaStreamEndCapture(cs, &g);
         if (cst != VSR_OK || ee != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
@@ -1310,18 +1357,25 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
             cudaGetLastError();
             return VSR_OK;  // not this candidate
         }
+        // one warm replay, then three timed one at a time: frames of a batch
+        // run alone (each render waits for the previous frame), so a graph
+        // is judged by its own span, not by overlap with the next replay
         float ms = 0.0f;
-        bool timed = cudaGraphLaunch(ex, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess;
-        for (int r = 0; timed && r < 2; ++r) timed = cudaGraphLaunch(ex, st) == cudaSuccess;
-        timed = timed && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        bool timed = cudaGraphLaunch(ex, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+        for (int r = 0; timed && r < 3; ++r) {
+            float one = 0.0f;
+            timed = cudaEventRecord(e0, st) == cudaSuccess && cudaGraphLaunch(ex, st) == cudaSuccess &&
+                    cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&one, e0, e1) == cudaSuccess;
+            ms += one;
+        }
         if (timed && ms < best) {
             best = ms;
             if (b->exec) cudaGraphExecDestroy(b->exec);
             b->exec = ex;
             b->nstreams = S;
             b->split_max = split;
-            b->pooled = pooled;
+            b->pool_groups = groups;
         } else {
             cudaGraphExecDestroy(ex);
         }
@@ -1332,16 +1386,17 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     vsr_status ts = VSR_OK;
     const bool try_chains = b->mode != VSR_BATCH_POOLED, try_pool = b->mode != VSR_BATCH_CHAINS;
     for (int S : {1, 2, 4, 8}) {
-        if (ts == VSR_OK && try_chains) ts = candidate(S, SPLIT_MAX_DEFAULT, false);
-        if (ts == VSR_OK && try_pool) ts = candidate(S, SPLIT_MAX_DEFAULT, true);
+        if (ts == VSR_OK && try_chains) ts = candidate(S, SPLIT_MAX_DEFAULT, 0);
+        for (int groups : {1, 4, 16})
+            if (ts == VSR_OK && try_pool) ts = candidate(S, SPLIT_MAX_DEFAULT, groups);
     }
     const int bestS = b->nstreams;
-    const bool best_pooled = b->pooled;
+    const int best_groups = b->pool_groups;
     for (int split : {256, 1024})
-        if (ts == VSR_OK && b->exec) ts = candidate(bestS, split, best_pooled);
-    // the kept graph's pooled views must carry its split
-    if (ts == VSR_OK && b->exec && b->pooled)
-        ts = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, b->split_max);
+        if (ts == VSR_OK && b->exec) ts = candidate(bestS, split, best_groups);
+    // the kept graph's pooled views must carry its split and grouping
+    if (ts == VSR_OK && b->exec && b->pool_groups > 0)
+        ts = batch_pool_upload(b, nviews, maps, T, id_dev, depth_dev, cov_dev, b->split_max, b->pool_groups);
     if (ts != VSR_OK) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1366,7 +1421,7 @@ vsr_status vsr_batch_config_ex(vsr_batch b, int* streams, int* graphed, int* spl
     if (streams) *streams = b->nstreams;
     if (graphed) *graphed = b->exec != nullptr;
     if (split_max) *split_max = b->split_max;
-    if (pooled) *pooled = b->exec != nullptr && b->pooled;
+    if (pooled) *pooled = b->exec != nullptr ? b->pool_groups : 0;
     return VSR_OK;
 }
 

@@ -485,7 +485,8 @@ class Batch:
         g, r, sp, po = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(load().vsr_batch_config_ex(self.h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(sp), ctypes.byref(po)),
               "vsr_batch_config_ex")
-        return {"streams": g.value, "graphed": bool(r.value), "split_max": sp.value, "pooled": bool(po.value)}
+        return {"streams": g.value, "graphed": bool(r.value), "split_max": sp.value, "pooled": bool(po.value),
+                "pool_groups": po.value}
 
     def free(self):
         if self.h:
