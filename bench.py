@@ -356,6 +356,27 @@ def run_vsr(args, rank, world, local):
     assert V.last_device_status() == 0
     pstep_ms = a.elapsed_time(b) / K
     del pm, ps_sc
+    # the same frame with the diagonal angle of view (Omega spans the image
+    # diagonal): the whole step, L2 flushed before each, with its own N_alg
+    dm = V.Map(W, H, lens["k"], lens["l"], lens["s"], lens["omega"], aov=V.AOV_DIAGONAL)
+    dsc = V.Scene(tris, cam)  # bins sized for this map at its first binning
+    V.bin(dm, dsc)
+    n_alg_diag = V.raster(dm, dsc, stats=True)["n_alg"]
+    diag_ms = []
+    for k in range(K):
+        flush.fill_(float(k))
+        a, b = evt(), evt()
+        a.record(stream)
+        dm.update(W, H, lens["k"], lens["l"], lens["s"], lens["omega"], aov=V.AOV_DIAGONAL)
+        dsc.update(tris, cam)
+        V.bin(dm, dsc)
+        V.raster(dm, dsc, out=out, binned=True)
+        b.record(stream)
+        diag_ms.append((a, b))
+    torch.cuda.synchronize()
+    assert V.last_device_status() == 0
+    diag_ms = statistics.mean(a.elapsed_time(b) for a, b in diag_ms)
+    del dm, dsc
     # the dense reference (no binning: every pixel against every triangle) on
     # the same frame, its outputs against the binned path's
     dense = None
@@ -517,7 +538,10 @@ def run_vsr(args, rank, world, local):
         "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
         "map_cached": {"ms_per_step": cached_ms, "value": n_alg / (cached_ms / 1000.0), "unit": UNIT,
                        "frames_per_s": 1000.0 / cached_ms},
-        "variants": {"pstep_bin_and_raster_ms": pstep_ms},
+        "variants": {"pstep_bin_and_raster_ms": pstep_ms,
+                     "diagonal_aov": {"ms_per_step": diag_ms, "value": n_alg_diag / (diag_ms / 1000.0), "unit": UNIT,
+                                      "n_alg_per_step": n_alg_diag,
+                                      "step": "map, set-up, binning, raster in sequence on one stream"}},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32)",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "raster_items_kernel", "peak_source": f"{props.multi_processor_count} SMs x "
