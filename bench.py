@@ -50,8 +50,8 @@ LAUNCHES_PER_STEP = 10
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="vsr", choices=["vsr", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=200000, help="pixels of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -185,13 +185,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(lens, tris, cam, n_pix, seed=123):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    its raster stage (brute force over every triangle) on n_pix seeded pixels
-    of the oracle's own map.  Returns (tests/s, seconds, n_alg, threads)."""
+def oracle_frame(lens, tris, cam):
+    """The oracle's map and set-up records of the frame (untimed)."""
     import oracle
     m64, _ = oracle.make_map(lens["W"], lens["H"], lens["k"], lens["l"], lens["s"], lens["omega"])
-    rec = oracle.setup(tris, cam)
+    return m64, oracle.setup(tris, cam)
+
+
+def cpu_baseline(lens, tris, cam, n_pix, seed=123, frame=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    its raster stage (brute force over every triangle) on n_pix seeded pixels
+    of the oracle's own map (frame: the map and records, made here if None).
+    Returns (tests/s, seconds, n_alg, threads)."""
+    import oracle
+    m64, rec = frame if frame is not None else oracle_frame(lens, tris, cam)
     rng = np.random.default_rng(seed)
     pix = rng.integers(0, lens["W"] * lens["H"], n_pix)
     threads = os.cpu_count() or 1
@@ -206,14 +213,18 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     lens, tris, cam = workload()
-    # each step: a bounded sample of the frame, so K + W steps end in minutes
-    n_pix = max(256, args.cpu_sample // 4)
+    # each step: a bounded sample of the frame -- the samples of all K steps
+    # together cpu_sample pixels, but at least 8192 a step, since each call
+    # of the oracle's raster carries a fixed ~0.2 s -- so K + W steps end in
+    # a few minutes
+    n_pix = max(8192, args.cpu_sample // max(1, args.steps))
+    frame = oracle_frame(lens, tris, cam)
     for _ in range(args.warmup):
-        cpu_baseline(lens, tris, cam, 64)
+        cpu_baseline(lens, tris, cam, 64, frame=frame)
     vals, tot_alg, tot_t = [], 0, 0.0
     threads = os.cpu_count() or 1
     for k in range(args.steps):
-        v, dt, n_alg, threads = cpu_baseline(lens, tris, cam, n_pix, seed=1000 + k)
+        v, dt, n_alg, threads = cpu_baseline(lens, tris, cam, n_pix, seed=1000 + k, frame=frame)
         vals.append(v)
         tot_alg += n_alg
         tot_t += dt
@@ -533,6 +544,8 @@ def run_vsr(args, rank, world, local):
                    "W": W, "H": H, "T": T, "l2": "flushed before every step (256 MB write, outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "frames_per_s": world * K / tot_s,
+        "step_ms_distribution": {"median": statistics.median(step_ms), "p10": float(np.percentile(step_ms, 10)),
+                                 "p90": float(np.percentile(step_ms, 90)), "steps": len(step_ms)},
         "raster_kernel_ms": statistics.mean(rast_ms),
         "stage_ms": stage_ms,
         "n_alg_per_step": n_alg, "n_exec_per_step": n_exec, "bin_pairs_per_step": pairs,
