@@ -298,7 +298,9 @@ vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene s, uint32_t* id_dev, float* d
 vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
 
 /* ---- end to end from host memory ------------------------------------------
- * vsr_render_host: one call from host buffers: re-runs the set-up of the
+ * vsr_render_host: one call from host buffers -- the operations of
+ * vsr_setup (Sec. 1.1, 1.1.2, 1.1.4) and vsr_raster (Sec. 1.1.1-1.1.4,
+ * 1.4): re-runs the set-up of the
  * work scene `s` (a handle from vsr_scene_create, whose device buffers are
  * reused across calls) on `tris_host` ([T][3][3] FP32, host), rasterizes
  * into the map and returns id/depth/cov (W*H each, host; any may be NULL),
@@ -323,7 +325,8 @@ vsr_status vsr_scene_bin_pairs(vsr_scene s, void* stream, int64_t* pairs);
 vsr_status vsr_render_host(vsr_map m, vsr_scene s, const float* tris_host, int64_t T, const float cam[12],
                            uint32_t* id_host, float* depth_host, float* cov_host, void* stream);
 
-/* vsr_render_host_async: vsr_render_host without the wait -- the frame is
+/* vsr_render_host_async: vsr_render_host (the same operations and
+ * passages) without the wait -- the frame is
  * queued on `stream` (the set-up on the scene's own stream as above) and the
  * call returns; vsr_render_host_wait(s) waits for it.  Frames of different
  * (map, scene) pairs queued on different streams run at the same time on the
