@@ -62,28 +62,42 @@ __device__ __forceinline__ bool map_fn(int i, int j, int W, int H, const MapP& p
     return universal_dir(x, y, p, v);
 }
 
-// Tile cone from per-pixel (valid, G, h), reduced by the TILE_PIX pixel
-// threads of a CTA (threads 0 .. TILE_PIX-1, all of which must call it; other
-// threads of the CTA must not) on named barrier 1: two rounds of warp
-// shuffles, each closed by one barrier.  Every thread forms the axis itself
-// from the eight warp partials (the same sums in the same order, so the same
-// bits everywhere), so no single thread's work sits between the barriers.
-constexpr int CONE_WARPS = TILE_PIX / 32;
-
-__device__ __forceinline__ void cone_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(TILE_PIX) : "memory"); }
+// Tile cone from per-pixel (valid, G, h), reduced by the TILE_PIX / P pixel
+// threads of a CTA, each holding P pixels (threads 0 .. TILE_PIX/P - 1, all
+// of which must call it; other threads of the CTA must not) on named
+// barrier 1: two rounds of warp shuffles, each closed by one barrier.  Every
+// thread forms the axis itself from the warp partials (the same sums in the
+// same order, so the same bits everywhere), so no single thread's work sits
+// between the barriers.
+template <int NT>
+__device__ __forceinline__ void cone_barrier()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
 
 // file_into (optional): the tile index of a later generation of the same
 // map; thread 0 then files the tile (index `tile`) into the plan the index
 // header holds: its histogram bin, and its cell's count or, past the plan's
 // small-tile half-angle, the big list (the header's work counters).  Tile 0
 // also clears the index's maxima, which the index finish then forms.
-__device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* geom, const TileIndex* file_into = nullptr,
-                            int tile = 0)
+template <int P>
+__device__ void reduce_cone(const bool (&valid)[P], const float3 (&G)[P], const float (&hp)[P], Cone* out,
+                            float4* geom, const TileIndex* file_into = nullptr, int tile = 0)
 {
+    constexpr int NT = TILE_PIX / P, CONE_WARPS = NT / 32;
+    static_assert(NT % 32 == 0, "whole warps of pixel threads");
     __shared__ float4 part[CONE_WARPS];
     __shared__ float2 part2[CONE_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float sx = valid ? G.x : 0.0f, sy = valid ? G.y : 0.0f, sz = valid ? G.z : 0.0f, cnt = valid ? 1.0f : 0.0f;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f, cnt = 0.0f;
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+        if (valid[q]) {
+            sx += G[q].x;
+            sy += G[q].y;
+            sz += G[q].z;
+            cnt += 1.0f;
+        }
     for (int o = 16; o; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
@@ -91,7 +105,7 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
     if (lane == 0) part[warp] = make_float4(sx, sy, sz, cnt);
-    cone_barrier();
+    cone_barrier<NT>();
     float a = 0.0f, b = 0.0f, c = 0.0f, n = 0.0f;
 #pragma unroll
     for (int w = 0; w < CONE_WARPS; ++w) {
@@ -109,14 +123,19 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
         ay = b * inv;
         az = c * inv;
     }
-    float cmin = valid ? G.x * ax + G.y * ay + G.z * az : 2.0f;
-    float hmax = valid ? h : 0.0f;
+    float cmin = 2.0f, hmax = 0.0f;
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+        if (valid[q]) {
+            cmin = fminf(cmin, G[q].x * ax + G[q].y * ay + G[q].z * az);
+            hmax = fmaxf(hmax, hp[q]);
+        }
     for (int o = 16; o; o >>= 1) {
         cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
         hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
     }
     if (lane == 0) part2[warp] = make_float2(cmin, hmax);
-    cone_barrier();
+    cone_barrier<NT>();
     if (threadIdx.x == 0) {
         float cm = 2.0f, hh = 0.0f;
 #pragma unroll
@@ -155,40 +174,31 @@ __device__ void reduce_cone(bool valid, float3 G, float h, Cone* out, float4* ge
 
 constexpr int HW = TILE + 2;
 constexpr int MAP_THREADS = ((HW * HW + 31) / 32) * 32;  // one halo evaluation per thread
+// threads and resident CTAs of the map kernel with P pixels per thread: one
+// halo evaluation per thread at P = 1, else the tile's TILE_PIX / P pixel
+// threads evaluate the halo in turns
+constexpr int map_threads(int P) { return P == 1 ? MAP_THREADS : TILE_PIX / P; }
+constexpr int map_ctas(int P) { return P == 1 ? 5 : (P == 2 ? 10 : 16); }
+// pixels per thread of the map kernel: 2 (measured on the 1080p frame:
+// map || set-up 68.4 -> 61.7 us, a new lens's map + tile index 67.9 -> 61.5
+// us against 1; 4: 65.4 / 62.4 us) -- half the pixel threads share the cone
+// reduction's shuffles and barriers, and no register spills
+#ifndef VSR_MAP_PPT
+#define VSR_MAP_PPT 2
+#endif
 
-// One 16x16 tile of a map: the map function F at every pixel centre of the
-// tile and its one-pixel halo (F(i, j, v) returns 0 where the map is
-// undefined, else 1 + the pixel's chart -- the face of a cube map, 0 for
-// single-chart maps), the global delta from central differences over
-// neighbours of the same chart (one-sided next to an unusable neighbour),
-// the map row and the tile cone.
-// deriv (optional): the differences (d_i G, d_j G) the delta is formed
-// from, 2 float4 per pixel, for the per-fragment pixel step; the tile
-// cones then carry the widest ramp of either step.
-template <class F>
-__global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn, float4* __restrict__ map,
-                                                           Cone* __restrict__ tiles, float4* __restrict__ geom,
-                                                           float4* __restrict__ deriv, TileIndex file_into,
-                                                           int file)
+// One pixel of the tile (li, lj) from the staged map values: the global
+// delta from central differences over neighbours of the same chart
+// (one-sided next to an unusable neighbour), the map row and, with deriv,
+// the differences; returns whether the pixel is valid, its direction and its
+// ramp half-width.
+__device__ __forceinline__ void map_pixel(const float4* sv, int li, int lj, int i, int j, int W, int H, float4* map,
+                                          float4* deriv, bool& valid, float3& G, float& h)
 {
-    // map values of the tile and its halo: direction xyz, w = F's return value
-    __shared__ float4 sv[HW * HW];
-    const int tx = blockIdx.x, ty = blockIdx.y;
-    const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
-    if (threadIdx.x < HW * HW) {
-        const int q = threadIdx.x, qi = q % HW, qj = q / HW;
-        float3 v = make_float3(0.0f, 0.0f, 0.0f);
-        const int ok = fn(i0 + qi, j0 + qj, W, H, v);
-        sv[q] = make_float4(v.x, v.y, v.z, (float)ok);
-    }
-    __syncthreads();
-    if (threadIdx.x >= TILE_PIX) return;  // halo-only threads: done
-    const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
-    const int i = tx * TILE + li, j = ty * TILE + lj;
     const int c = (lj + 1) * HW + (li + 1);
-    bool valid = false;
-    float3 G = make_float3(0.0f, 0.0f, 0.0f);
-    float h = 0.0f;
+    valid = false;
+    G = make_float3(0.0f, 0.0f, 0.0f);
+    h = 0.0f;
     if (i < W && j < H) {
         float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const float4 qc = sv[c];
@@ -256,8 +266,47 @@ __global__ void __launch_bounds__(MAP_THREADS, 5) map_kernel(int W, int H, F fn,
         }
         map[(size_t)j * W + i] = o;
     }
+}
+
+// One 16x16 tile of a map: the map function F at every pixel centre of the
+// tile and its one-pixel halo (F(i, j, v) returns 0 where the map is
+// undefined, else 1 + the pixel's chart -- the face of a cube map, 0 for
+// single-chart maps), then map_pixel for each pixel of the tile, P pixels
+// per thread (rows lj and lj + 16/P ...), and the tile cone.
+// deriv (optional): the differences (d_i G, d_j G) the delta is formed
+// from, 2 float4 per pixel, for the per-fragment pixel step; the tile
+// cones then carry the widest ramp of either step.
+template <class F, int P>
+__global__ void __launch_bounds__(map_threads(P), map_ctas(P)) map_kernel(int W, int H, F fn, float4* __restrict__ map,
+                                                                         Cone* __restrict__ tiles,
+                                                                         float4* __restrict__ geom,
+                                                                         float4* __restrict__ deriv,
+                                                                         TileIndex file_into, int file)
+{
+    // map values of the tile and its halo: direction xyz, w = F's return value
+    __shared__ float4 sv[HW * HW];
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const int i0 = tx * TILE - 1, j0 = ty * TILE - 1;
+    for (int q = threadIdx.x; q < HW * HW; q += map_threads(P)) {
+        const int qi = q % HW, qj = q / HW;
+        float3 v = make_float3(0.0f, 0.0f, 0.0f);
+        const int ok = fn(i0 + qi, j0 + qj, W, H, v);
+        sv[q] = make_float4(v.x, v.y, v.z, (float)ok);
+    }
+    __syncthreads();
+    constexpr int NT = TILE_PIX / P;
+    if (threadIdx.x >= NT) return;  // halo-only threads: done
+    const int li = threadIdx.x % TILE, lj0 = threadIdx.x / TILE;
+    bool valid[P];
+    float3 G[P];
+    float h[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int lj = lj0 + q * (TILE / P);
+        map_pixel(sv, li, lj, tx * TILE + li, ty * TILE + lj, W, H, map, deriv, valid[q], G[q], h[q]);
+    }
     const int t = ty * gridDim.x + tx;
-    reduce_cone(valid, G, h, &tiles[t], &geom[t], file ? &file_into : nullptr, t);
+    reduce_cone<P>(valid, G, h, &tiles[t], &geom[t], file ? &file_into : nullptr, t);
 }
 
 // The Universal perspective map function.
@@ -358,7 +407,10 @@ __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict
             h = 0.5f / o.w;
         }
     }
-    reduce_cone(valid, G, h, &tiles[blockIdx.y * gridDim.x + blockIdx.x], &geom[blockIdx.y * gridDim.x + blockIdx.x]);
+    const bool vv[1] = {valid};
+    const float3 gg[1] = {G};
+    const float hh[1] = {h};
+    reduce_cone<1>(vv, gg, hh, &tiles[blockIdx.y * gridDim.x + blockIdx.x], &geom[blockIdx.y * gridDim.x + blockIdx.x]);
 }
 
 }  // namespace
@@ -394,7 +446,7 @@ vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float om
 {
     const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom, nullptr,
+    map_kernel<UniversalFn, VSR_MAP_PPT><<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom, nullptr,
                                              file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
@@ -419,7 +471,7 @@ vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, flo
         f.a[3] = sp.param[2];
     }
     dim3 grid((sp.W + TILE - 1) / TILE, (sp.H + TILE - 1) / TILE);
-    map_kernel<<<grid, MAP_THREADS, 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv,
+    map_kernel<SpecFn, VSR_MAP_PPT><<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv,
                                              file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
