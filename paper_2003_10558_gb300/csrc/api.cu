@@ -1359,7 +1359,7 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
         }
         // one warm replay, then three timed one at a time: frames of a batch
         // run alone (each render waits for the previous frame), so a graph
-        // is judged by its own span, not by overlap with the next replay
+        // is measured by its own span, not by overlap with the next replay
         float ms = 0.0f;
         bool timed = cudaGraphLaunch(ex, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
         for (int r = 0; timed && r < 3; ++r) {
