@@ -186,22 +186,15 @@ vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const flo
     return s == VSR_OK ? scene_used(sc, st) : s;
 }
 
-// bin ids and the count pass's pair list, both of `want` entries (frees the
-// old ones, which waits for the launches still using them)
+// bin ids of `want` entries (frees the old ones, which waits for the
+// launches still using them)
 vsr_status bins_realloc(vsr_scene sc, uint32_t want)
 {
     cudaFree(sc->ids);
-    cudaFree(sc->pairs);
     sc->ids = nullptr;
-    sc->pairs = nullptr;
     sc->cap = 0;
     vsr_status s;
     if ((s = dalloc(&sc->ids, (size_t)want)) != VSR_OK) return s;
-    if ((s = dalloc(&sc->pairs, (size_t)want)) != VSR_OK) {
-        cudaFree(sc->ids);
-        sc->ids = nullptr;
-        return s;
-    }
     sc->cap = want;
     return VSR_OK;
 }
@@ -209,12 +202,12 @@ vsr_status bins_realloc(vsr_scene sc, uint32_t want)
 vsr_status ensure_ws(vsr_scene sc, int ntiles)
 {
     if (ntiles <= sc->ws_tiles) return VSR_OK;
-    cudaFree(sc->counts);
+    cudaFree(sc->ends);
     cudaFree(sc->offsets);
-    sc->counts = sc->offsets = nullptr;
+    sc->ends = sc->offsets = nullptr;
     sc->ws_tiles = 0;
     vsr_status s;
-    if ((s = dalloc(&sc->counts, (size_t)ntiles + 1)) != VSR_OK) return s;  // counts | pair cursor
+    if ((s = dalloc(&sc->ends, (size_t)ntiles)) != VSR_OK) return s;
     if ((s = dalloc(&sc->offsets, (size_t)ntiles + 1)) != VSR_OK) return s;
     sc->ws_tiles = ntiles;
     sc->sized_shape = 0;
@@ -481,10 +474,10 @@ void vsr_scene_free(vsr_scene sc)
 {
     if (!sc) return;
     cudaFree(sc->rec);
-    cudaFree(sc->counts);
+    cudaFree(sc->ends);
     cudaFree(sc->offsets);
     cudaFree(sc->ids);
-    cudaFree(sc->pairs);
+    tri_index_free(&sc->tri);
     raster_work_free(&sc->work);
     cudaFree(sc->tris_dev);
     cudaFree(sc->out_dev);
@@ -520,8 +513,8 @@ vsr_status vsr_raster_pstep(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
     cudaStream_t st = (cudaStream_t)stream;
     vsr_status s = bin_scene(m, sc, 1, st);
     if (s != VSR_OK) return s;
-    const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
-                       sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
+    const RasterView v{m->map,  m->p.W, m->p.H, m->tiles, m->tx,     sc->rec,   (int)sc->T, sc->offsets,
+                       sc->ids, sc->cap, id_dev, depth_dev, cov_dev, sc->ends};
     s = launch_raster_pstep(v, m->deriv, scene_status(sc), st);
     return s == VSR_OK ? scene_used(sc, st) : s;
 }
@@ -534,13 +527,13 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
     vsr_status s = ensure_ws(sc, ntiles);
     if (s != VSR_OK) return s;
     const int T = (int)sc->T;
+    if ((s = tri_index_alloc(&sc->tri, T)) != VSR_OK) return s;
     sc->last_ntiles = ntiles;
-    uint32_t* counts = sc->counts;
     // Bin capacity.  Sized synchronously the first time and whenever the
     // number of tiles or triangles changes (the first time only, for a scene
     // with async_sizing); otherwise the pair total of the previous binning
     // (copied to pinned memory, read only once its event has completed, never
-    // waited for) grows the capacity ahead of need, and the fill kernel
+    // waited for) grows the capacity ahead of need, and the binning kernel
     // reports any overflow in the status word.
     // the bins' sizes depend on the map, the scene and the step's cap width
     const uint64_t shape = ((uint64_t)ntiles << 32) ^ (uint64_t)sc->T ^ ((uint64_t)(pstep != 0) << 63);
@@ -554,16 +547,13 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
             if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
         }
     }
-    uint32_t* cursor = counts + ntiles;
-    VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ((size_t)ntiles + 1), st));
-    uint2* pairs = sc->pairs;
-    const uint32_t pair_cap = sc->cap;
-    if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st, pstep)) != VSR_OK) return s;
-    // the scan also stores the pair total into the pinned host word (its
-    // device address) unless an earlier total has not been read yet -- and
-    // always when this binning sizes the bins, which reads this total
+    // one tile-major pass: the pair total also goes to the pinned host word
+    // (its device address) unless an earlier total has not been read yet --
+    // and always when this binning sizes the bins, which reads this total
     const bool record = resize || !sc->total_pending;
-    if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st, record ? sc->h_total_dev : nullptr)) !=
+    // (a sizing pass reports no overflow: its bins are grown and binned again)
+    if ((s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, &sc->tri, sc->offsets, sc->ends, sc->ids, sc->cap,
+                              resize ? nullptr : scene_status(sc), record ? sc->h_total_dev : nullptr, st, pstep)) !=
         VSR_OK)
         return s;
     if (record) {
@@ -580,13 +570,12 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
             uint64_t want = (uint64_t)total + total / 4 + 4096;
             if (want > 0xffffffffull) want = 0xffffffffull;
             if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
-            pairs = nullptr;  // this frame's pair list went with the old buffer: search again
+            if ((s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, &sc->tri, sc->offsets, sc->ends, sc->ids,
+                                      sc->cap, scene_status(sc), nullptr, st, pstep)) != VSR_OK)
+                return s;
         }
         sc->sized_shape = shape;
     }
-    if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->offsets, counts, cursor, pairs, pair_cap, sc->ids, sc->cap,
-                             scene_status(sc), st, pstep)) != VSR_OK)
-        return s;
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
     return scene_used(sc, st);
@@ -608,8 +597,8 @@ static vsr_status raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float*
             if (s != VSR_OK) return s;
             sc->work_tiles = ntiles;
         }
-        const RasterView v{m->map, m->p.W, m->p.H, m->tiles, m->tx, sc->rec, (int)sc->T, sc->offsets,
-                           sc->ids, sc->cap, id_dev, depth_dev, cov_dev};
+        const RasterView v{m->map,  m->p.W, m->p.H, m->tiles, m->tx,     sc->rec,   (int)sc->T, sc->offsets,
+                           sc->ids, sc->cap, id_dev, depth_dev, cov_dev, sc->ends};
         const vsr_status s = launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT,
                                                  scene_status(sc), (cudaStream_t)stream, host_out);
         return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
@@ -619,7 +608,7 @@ static vsr_status raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float*
         launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
                       depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
                       stats ? (unsigned long long*)stats->n_exec_dev : nullptr, stats ? stats->n_inside_dev : nullptr,
-                      scene_status(sc), (cudaStream_t)stream);
+                      scene_status(sc), (cudaStream_t)stream, sc->ends);
     return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
 }
 

@@ -750,12 +750,365 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__
     }
 }
 
+// ---- tile-major binning -----------------------------------------------------
+//
+// Per frame: tri_file (every triangle into its cell) -> bin_tiles (every
+// tile's bin, in one pass).
+
+constexpr float TRI_CELL0 = PI_F / TRI_NLAT0;
+constexpr float TRI_CELL1 = PI_F / TRI_NLAT1;
+constexpr uint32_t BIN_STAGE_HITS = 1024;  // hits a tile's warp stages in shared memory
+// steps of the walk whose loads are issued together: 2 (measured on the
+// 1080p frame: bin stage 38.9 us against 40.7 us at 4; 12 resident CTAs
+// per SM instead of 8, which caps the registers: 40.8 - 48.6 us)
+#ifndef VSR_BIN_WALK_U
+#define VSR_BIN_WALK_U 2
+#endif
+constexpr int BIN_WALK_U = VSR_BIN_WALK_U;
+// resident CTAs per SM the tile pass is compiled for (its register cap)
+#ifndef VSR_BIN_TILES_CTAS
+#define VSR_BIN_TILES_CTAS 8
+#endif
+
+__device__ __forceinline__ int tri_row(float lat, int nlat, float cell)
+{
+    return min(nlat - 1, max(0, (int)floorf((lat + 0.5f * PI_F) / cell)));
+}
+
+__device__ __forceinline__ int tri_col(float lon, int nlon, float cell)
+{
+    int c = (int)floorf((lon + PI_F) / cell);
+    c %= nlon;
+    return c < 0 ? c + nlon : c;
+}
+
+// The enlarged cap of triangle t as the triangle-major search forms it: its
+// centre (q0.xyz) and (cos, sin) of its radius; false for a triangle
+// without a cap.
+__device__ __forceinline__ bool tri_cap(const float4* __restrict__ rec, size_t TT, int t, float hmax, int pstep,
+                                        float4& q0, float& cb, float& sb)
+{
+    q0 = rec[RF_CAP * TT + t];
+    const float4 q1 = rec[RF_CAP2 * TT + t];
+    if (q1.w == 0.0f) return false;
+    if (pstep) {
+        const float2 c = pstep_cap(q0.w, q1.x, hmax);
+        cb = c.x;
+        sb = c.y;
+    } else {
+        cb = fmaxf(-1.0f, fminf(1.0f, q0.w - hmax * q1.x));
+        sb = sqrtf(fmaxf(0.0f, 1.0f - cb * cb));
+    }
+    return true;
+}
+
+// Every triangle into its cell (buffer par): the fine grid when its cap fits
+// and the cell has room, else the coarse grid under the same conditions,
+// else the list; each grid's largest cap radius into the header.  The other
+// buffer is cleared for the next binning (the one that used it is complete,
+// by stream order).
+__global__ void __launch_bounds__(256) tri_file_kernel(const float4* __restrict__ rec, int T,
+                                                       const TileIndexHdr* __restrict__ ihdr, TriIndex ti, int par,
+                                                       int pstep)
+{
+    uint32_t* __restrict__ cnt = ti.counts + (size_t)par * TRI_CELLS;
+    uint32_t* __restrict__ nxt = ti.counts + (size_t)(1 - par) * TRI_CELLS;
+    const int gt = blockIdx.x * 256 + threadIdx.x, gn = gridDim.x * 256;
+    for (int i = gt; i < TRI_CELLS; i += gn) nxt[i] = 0u;
+    if (gt < 4) ti.hdr[4 * (1 - par) + gt] = 0u;
+    unsigned b0 = 0u, b1 = 0u;  // float bits of non-negative radii order as the floats
+    if (gt < T) {
+        const int t = gt;
+        float4 q0;
+        float cb, sb;
+        if (tri_cap(rec, (size_t)T, t, __uint_as_float(ihdr->h_max), pstep, q0, cb, sb)) {
+            const float beta = acosf(cb);
+            const unsigned bb = __float_as_uint(fmaxf(beta, 1e-30f));  // nonzero: the grid holds a triangle
+            uint32_t e = 0xffffffffu;
+            if (beta <= 2.0f * TRI_CELL1) {
+                const float lat = asinf(fmaxf(-1.0f, fminf(1.0f, q0.y)));
+                const float lon = atan2f(q0.x, q0.z);
+                if (beta <= 2.0f * TRI_CELL0) {
+                    const int cell = tri_row(lat, TRI_NLAT0, TRI_CELL0) * TRI_NLON0 + tri_col(lon, TRI_NLON0, TRI_CELL0);
+                    const uint32_t k = atomicAdd(&cnt[cell], 1u);
+                    if (k < (uint32_t)TRI_K0) {
+                        e = (uint32_t)cell * TRI_K0 + k;
+                        b0 = bb;
+                    }
+                }
+                if (e == 0xffffffffu) {
+                    const int cell = tri_row(lat, TRI_NLAT1, TRI_CELL1) * TRI_NLON1 + tri_col(lon, TRI_NLON1, TRI_CELL1);
+                    const uint32_t k = atomicAdd(&cnt[TRI_CELLS0 + cell], 1u);
+                    if (k < (uint32_t)TRI_K1) {
+                        e = TRI_E1 + (uint32_t)cell * TRI_K1 + k;
+                        b1 = bb;
+                    }
+                }
+            }
+            if (e == 0xffffffffu) {
+                // (below the list's capacity unless an earlier binning left its counters behind)
+                const uint32_t k = atomicAdd(&cnt[TRI_LARGE], 1u);
+                if (k < (uint32_t)ti.T) e = TRI_E2 + k;
+            }
+            if (e != 0xffffffffu) {
+                ti.cap[e] = make_float4(q0.x, q0.y, q0.z, cb);
+                ti.cs[e] = make_float2(sb, __uint_as_float((uint32_t)t));
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+        b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (b0) atomicMax(&ti.hdr[4 * par], b0);
+        if (b1) atomicMax(&ti.hdr[4 * par + 1], b1);
+    }
+}
+
+// A window of one grid: rows r0 .. r0 + nr - 1, columns c0 .. c0 + ncol - 1
+// (mod nlon).
+struct TriWin {
+    int r0, nr, c0, ncol;
+};
+
+// The cells holding every direction within gamma of (lat, lon).
+__device__ __forceinline__ TriWin tri_window(float lat, float lon, float gamma, int nlat, float cell)
+{
+    const int nlon = 2 * nlat;
+    TriWin w{0, nlat, 0, nlon};
+    if (!(gamma < PI_F)) return w;
+    const int r0 = tri_row(lat - gamma, nlat, cell), r1 = tri_row(lat + gamma, nlat, cell);
+    w.r0 = r0;
+    w.nr = r1 - r0 + 1;
+    if (fabsf(lat) + gamma < 0.5f * PI_F - 1e-3f) {
+        // longitude half-width of a cap that holds no pole
+        const float dl = asinf(fminf(1.0f, sinf(gamma) / cosf(lat))) + 1e-4f;
+        int c0 = (int)floorf((lon - dl + PI_F) / cell);
+        const int c1 = (int)floorf((lon + dl + PI_F) / cell);
+        w.ncol = max(1, min(nlon, c1 - c0 + 1));
+        c0 %= nlon;
+        if (c0 < 0) c0 += nlon;
+        w.c0 = c0;
+    }
+    return w;
+}
+
+__device__ __forceinline__ TriWin shfl_win(const TriWin& w, int src)
+{
+    return TriWin{__shfl_sync(0xffffffffu, w.r0, src), __shfl_sync(0xffffffffu, w.nr, src),
+                  __shfl_sync(0xffffffffu, w.c0, src), __shfl_sync(0xffffffffu, w.ncol, src)};
+}
+
+// One warp per tile, one pass.  The cells of the tile's windows (and the
+// list) go one per lane, 32 at a time; their triangles are numbered across
+// the warp and every lane tests the next one each step (finding the cell
+// that holds it by a search over the lanes), BIN_WALK_U steps' loads at a
+// time.  The hits are staged in shared memory (up to BIN_STAGE_HITS; a
+// longer bin walks again for the rest), the tile's range of the bins is
+// taken with one atomic on the cursor, and the last CTA to finish stores
+// the total.
+__global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(const float4* __restrict__ geom,
+                                                        const Cone* __restrict__ tiles, int ntiles, TriIndex ti,
+                                                        int par, uint32_t* __restrict__ starts,
+                                                        uint32_t* __restrict__ ends, uint32_t* __restrict__ ids,
+                                                        uint32_t cap, int* status, uint32_t* total_host)
+{
+    __shared__ uint32_t s_hit[4][BIN_STAGE_HITS];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * 4 + warp;
+    const uint32_t* __restrict__ cnt = ti.counts + (size_t)par * TRI_CELLS;
+    uint32_t* hdr = ti.hdr + 4 * par;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (tile < ntiles) {
+        const float4 g = geom[tile];  // (alpha, latitude, longitude, h); h < 0: an empty tile
+        float ax = 0.0f, ay = 0.0f, az = 0.0f, ca = 1.0f, sa = 0.0f;
+        TriWin w0{0, 0, 0, 1}, w1{0, 0, 0, 1};
+        int RL = 0;
+        if (g.w >= 0.0f) {
+            const Cone c = tiles[tile];
+            ax = c.c0.x;
+            ay = c.c0.y;
+            az = c.c0.z;
+            ca = c.c0.w;
+            sa = c.c1.x;
+            // lane 0 forms the fine grid's window, lane 1 the coarse grid's
+            // (none for a grid that holds no triangle)
+            TriWin w{0, 0, 0, 1};
+            const unsigned bm = lane < 2 ? hdr[lane] : 0u;
+            if (bm)
+                w = tri_window(g.y, g.z, g.x + __uint_as_float(bm) + 2e-4f, lane ? TRI_NLAT1 : TRI_NLAT0,
+                               lane ? TRI_CELL1 : TRI_CELL0);
+            w0 = shfl_win(w, 0);
+            w1 = shfl_win(w, 1);
+            RL = 1;
+        }
+        const int R0 = w0.nr * w0.ncol, R1 = w1.nr * w1.ncol, R = R0 + R1 + RL;
+        // the walk: sink(rank, triangle) for every hit, in rank order per step
+        auto walk = [&](auto sink) {
+            uint32_t rank = 0;
+            for (int rb = 0; rb < R; rb += 32) {
+                const int i = rb + lane;
+                uint32_t a = 0;
+                int len = 0;
+                if (i < R0) {
+                    const int row = w0.r0 + i / w0.ncol;
+                    int col = w0.c0 + i % w0.ncol;
+                    if (col >= TRI_NLON0) col -= TRI_NLON0;
+                    const int cell = row * TRI_NLON0 + col;
+                    a = (uint32_t)cell * TRI_K0;
+                    len = (int)min(cnt[cell], (uint32_t)TRI_K0);
+                } else if (i < R0 + R1) {
+                    const int j = i - R0;
+                    const int row = w1.r0 + j / w1.ncol;
+                    int col = w1.c0 + j % w1.ncol;
+                    if (col >= TRI_NLON1) col -= TRI_NLON1;
+                    const int cell = row * TRI_NLON1 + col;
+                    a = TRI_E1 + (uint32_t)cell * TRI_K1;
+                    len = (int)min(cnt[TRI_CELLS0 + cell], (uint32_t)TRI_K1);
+                } else if (i < R) {
+                    a = TRI_E2;
+                    len = (int)min(cnt[TRI_LARGE], (uint32_t)ti.T);
+                }
+                int incl = len;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(FULL, incl, 31);
+                const int excl = incl - len;
+                for (int k0 = 0; k0 < total; k0 += 32 * BIN_WALK_U) {
+                    float4 q[BIN_WALK_U];
+                    float2 r[BIN_WALK_U];
+                    bool in[BIN_WALK_U];
+#pragma unroll
+                    for (int u = 0; u < BIN_WALK_U; ++u) {
+                        const int idx = k0 + 32 * u + lane;
+                        int o = 0;  // the last lane whose cell starts at or before triangle idx
+                        for (int st = 16; st > 0; st >>= 1) {
+                            const int x = __shfl_sync(FULL, excl, o + st);
+                            if (x <= idx) o += st;
+                        }
+                        const uint32_t e = __shfl_sync(FULL, a, o) + (uint32_t)(idx - __shfl_sync(FULL, excl, o));
+                        in[u] = idx < total;
+                        if (in[u]) {
+                            q[u] = ti.cap[e];
+                            r[u] = ti.cs[e];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < BIN_WALK_U; ++u) {
+                        bool hit = false;
+                        if (in[u]) {
+                            // the cap / cone test of the triangle-major search, operand for operand
+                            const float cg = fmaf(q[u].x, ax, fmaf(q[u].y, ay, q[u].z * az));
+                            hit = q[u].w + ca <= 2e-6f || cg >= fmaf(ca, q[u].w, -sa * r[u].x) - 2e-6f;
+                        }
+                        const unsigned m = __ballot_sync(FULL, hit);
+                        if (hit) sink(rank + (uint32_t)__popc(m & lt), __float_as_uint(r[u].y));
+                        rank += (uint32_t)__popc(m);
+                    }
+                }
+            }
+            return rank;
+        };
+        uint32_t* __restrict__ stage = s_hit[warp];
+        const uint32_t n = walk([&](uint32_t k, uint32_t t) {
+            if (k < BIN_STAGE_HITS) stage[k] = t;
+        });
+        uint32_t start = 0;
+        if (lane == 0) start = atomicAdd(&hdr[2], n);
+        start = __shfl_sync(FULL, start, 0);
+        __syncwarp();
+        if (lane == 0 && (uint64_t)start + n > cap && status) raise_status(status, VSR_ERR_BIN_OVERFLOW);
+        for (uint32_t j = lane; j < min(n, BIN_STAGE_HITS); j += 32)
+            if (start + j < cap) ids[start + j] = stage[j];
+        if (n > BIN_STAGE_HITS)
+            walk([&](uint32_t k, uint32_t t) {
+                if (k >= BIN_STAGE_HITS && start + k < cap) ids[start + k] = t;
+            });
+        if (lane == 0) {
+            starts[tile] = start;
+            ends[tile] = start + n;
+        }
+    }
+    // the last CTA to finish stores the total
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&hdr[3], 1u) == gridDim.x - 1) {
+            __threadfence();
+            const uint32_t total = atomicAdd(&hdr[2], 0u);
+            starts[ntiles] = total;
+            if (total_host) {  // straight into the host's pinned word (read after an event)
+                *total_host = total;
+                __threadfence_system();
+            }
+        }
+    }
+}
+
 }  // namespace
 
 vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, const int* n_dev, uint32_t* offsets,
                        cudaStream_t st, uint32_t* total_host)
 {
     scan_kernel<<<1, 1024, 0, st>>>(counts, extra, n, n_dev, offsets, total_host);
+    VSR_CUDA_TRY(cudaGetLastError());
+    return VSR_OK;
+}
+
+vsr_status tri_index_alloc(TriIndex* ti, int64_t T)
+{
+    if (!ti->counts) {
+        VSR_CUDA_TRY(cudaMalloc(&ti->counts, sizeof(uint32_t) * 2 * TRI_CELLS));
+        VSR_CUDA_TRY(cudaMalloc(&ti->hdr, sizeof(uint32_t) * 8));
+        // zero before a binning uses them (each binning clears the other buffer)
+        VSR_CUDA_TRY(cudaMemset(ti->counts, 0, sizeof(uint32_t) * 2 * TRI_CELLS));
+        VSR_CUDA_TRY(cudaMemset(ti->hdr, 0, sizeof(uint32_t) * 8));
+        VSR_CUDA_TRY(cudaStreamSynchronize(0));
+        ti->parity = 0;
+    }
+    if (!ti->cap || T > ti->T) {
+        cudaFree(ti->cap);
+        cudaFree(ti->cs);
+        ti->cap = nullptr;
+        ti->cs = nullptr;
+        ti->T = 0;
+        const size_t n = (size_t)TRI_E2 + (size_t)T;
+        VSR_CUDA_TRY(cudaMalloc(&ti->cap, sizeof(float4) * n));
+        VSR_CUDA_TRY(cudaMalloc(&ti->cs, sizeof(float2) * n));
+        ti->T = T;
+    }
+    return VSR_OK;
+}
+
+void tri_index_free(TriIndex* ti)
+{
+    cudaFree(ti->counts);
+    cudaFree(ti->hdr);
+    cudaFree(ti->cap);
+    cudaFree(ti->cs);
+    *ti = TriIndex{};
+}
+
+size_t tri_index_bytes(int64_t T)
+{
+    return sizeof(uint32_t) * (2 * (size_t)TRI_CELLS + 8) + (sizeof(float4) + sizeof(float2)) * ((size_t)TRI_E2 + (size_t)T);
+}
+
+vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
+                            TriIndex* ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
+                            uint32_t* total_host, cudaStream_t st, int pstep)
+{
+    if (T < 0 || (int64_t)T > ti->T || !ti->counts || !ti->cap || ntiles <= 0) return VSR_ERR_INVALID_ARG;
+    const int par = ti->parity;
+    ti->parity ^= 1;
+    tri_file_kernel<<<T > 0 ? (T + 255) / 256 : 1, 256, 0, st>>>(rec, T, idx.hdr, *ti, par, pstep);
+    VSR_CUDA_TRY(cudaGetLastError());
+    bin_tiles_kernel<<<(ntiles + 3) / 4, 128, 0, st>>>(idx.geom, tiles, ntiles, *ti, par, starts, ends, ids, cap,
+                                                       status, total_host);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

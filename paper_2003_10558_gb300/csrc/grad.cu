@@ -54,6 +54,7 @@ struct FragView {
     float* cov;
     uint32_t* out_id;
     float* out_depth;
+    const uint32_t* ends;     // as RasterView::ends
 };
 
 __device__ __forceinline__ bool frag_less(const float4& a, const float4& b)
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(FT) frag_kernel(FragView v, int* __restrict__ 
     uint32_t b0 = 0, b1 = 0;
     if (tc.c1.z > 0.0f) {
         b0 = v.offsets[tile];
-        b1 = v.offsets[tile + 1];
+        b1 = v.ends ? v.ends[tile] : v.offsets[tile + 1];
         if (b1 > v.cap) {
             if (threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
             b1 = v.cap;
@@ -558,7 +559,7 @@ vsr_status launch_frag_count(const FragArgs& a, cudaStream_t st)
 {
     const int tx = (a.W + TILE - 1) / TILE, ty = (a.H + TILE - 1) / TILE;
     FragView v{a.map, a.W, a.H, a.tiles, tx, a.rec, a.T, a.offsets, a.ids, a.cap, a.colors, a.counts,
-               nullptr, nullptr, 0u, nullptr, nullptr, nullptr, nullptr};
+               nullptr, nullptr, 0u, nullptr, nullptr, nullptr, nullptr, a.ends};
     frag_kernel<false><<<tx * ty, FT, 0, st>>>(v, a.status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
@@ -568,7 +569,7 @@ vsr_status launch_frag_fill(const FragArgs& a, cudaStream_t st)
 {
     const int tx = (a.W + TILE - 1) / TILE, ty = (a.H + TILE - 1) / TILE;
     FragView v{a.map,    a.W,   a.H,     a.tiles, tx,    a.rec,   a.T,      a.offsets, a.ids, a.cap,
-               a.colors, nullptr, a.foff, a.frags, a.fcap, a.image, a.cov, a.out_id, a.out_depth};
+               a.colors, nullptr, a.foff, a.frags, a.fcap, a.image, a.cov, a.out_id, a.out_depth, a.ends};
     frag_kernel<true><<<tx * ty, FT, 0, st>>>(v, a.status);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;

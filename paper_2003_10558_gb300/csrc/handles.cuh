@@ -46,11 +46,11 @@ struct vsr_scene_s {
     uint64_t gen = 0;
     // bin workspace
     int ws_tiles = 0;
-    uint32_t* counts = nullptr;
-    uint32_t* offsets = nullptr;
+    uint32_t* offsets = nullptr;  // bin starts (ntiles + 1: the last receives the pair total)
+    uint32_t* ends = nullptr;     // bin ends (ntiles)
     uint32_t* ids = nullptr;
-    uint2* pairs = nullptr;  // (tile, triangle) of every hit of the count pass, cap entries
     uint32_t cap = 0;
+    TriIndex tri = {};  // the frame's triangles by cap cell (tile-major binning)
     uint64_t sized_shape = 0;           // (tiles, T) the bins were last sized for
     uint32_t* h_total = nullptr;        // pinned: pair total of a recent binning
     uint32_t* h_total_dev = nullptr;    // its device address (the scan kernel stores the total there)

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(PT) raster_pstep_kernel(RasterView v, const fl
     uint32_t b0 = 0, b1 = 0;
     if (tc.c1.z > 0.0f) {
         b0 = v.offsets[tile];
-        b1 = v.offsets[tile + 1];
+        b1 = v.ends ? v.ends[tile] : v.offsets[tile + 1];
         if (b1 > v.cap) {
             if (threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
             b1 = v.cap;

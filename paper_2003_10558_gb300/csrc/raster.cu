@@ -279,7 +279,7 @@ __device__ __forceinline__ void raster_tile(const RasterView& view, int tile, St
     uint32_t b0 = 0, b1 = 0;
     if (tc.c1.z > 0.0f) {
         b0 = offsets[tile];
-        b1 = offsets[tile + 1];
+        b1 = view.ends ? view.ends[tile] : offsets[tile + 1];
         if (b1 > cap) {
             if (threadIdx.x == 0) raise_status(status, VSR_ERR_BIN_OVERFLOW);
             b1 = cap;
@@ -595,14 +595,14 @@ __global__ void __launch_bounds__(RT) raster_dense_kernel(RasterView view, int* 
 
 // Work items per tile: ceil(bin / split_max) when a split slot and room in
 // the extra list are free, else 1 (the tile runs in one CTA).
-__global__ void items_kernel(const uint32_t* __restrict__ offsets, uint32_t n_tiles, int split_max,
-                             uint32_t* __restrict__ nsplit_of, int32_t* __restrict__ split_slot,
-                             uint32_t* __restrict__ counters /* n_split, n_extra */, uint32_t split_cap,
-                             uint2* __restrict__ extra, uint32_t extra_cap)
+__global__ void items_kernel(const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ends,
+                             uint32_t n_tiles, int split_max, uint32_t* __restrict__ nsplit_of,
+                             int32_t* __restrict__ split_slot, uint32_t* __restrict__ counters /* n_split, n_extra */,
+                             uint32_t split_cap, uint2* __restrict__ extra, uint32_t extra_cap)
 {
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_tiles) return;
-    const uint32_t c = offsets[u + 1] - offsets[u];
+    const uint32_t c = (ends ? ends[u] : offsets[u + 1]) - offsets[u];
     uint32_t n = 1;
     int32_t slot = -1;
     if (c > (uint32_t)split_max) {
@@ -626,10 +626,10 @@ __global__ void items_kernel(const uint32_t* __restrict__ offsets, uint32_t n_ti
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
-                         int* status, cudaStream_t st)
+                         int* status, cudaStream_t st, const uint32_t* ends)
 {
     const int tx = (W + TILE - 1) / TILE, ty = (H + TILE - 1) / TILE;
-    const RasterView v{map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov};
+    const RasterView v{map, W, H, tiles, tx, rec, T, offsets, ids, cap, id, depth, cov, ends};
     if (n_alg || n_exec || n_inside)
         raster_kernel<true><<<tx * ty, RT, 0, st>>>(v, n_alg, n_exec, n_inside, status);
     else
@@ -648,11 +648,11 @@ uint32_t raster_extra_cap(uint32_t cap, const RasterWork& w, int split_max)
 }
 
 vsr_status launch_raster_assign(const uint32_t* offsets, uint32_t n_tiles, uint32_t cap, RasterWork w, int split_max,
-                                cudaStream_t st)
+                                cudaStream_t st, const uint32_t* ends)
 {
     if (n_tiles == 0) return VSR_OK;
     VSR_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 2 * sizeof(uint32_t), st));
-    items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, n_tiles, raster_split_items(split_max),
+    items_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(offsets, ends, n_tiles, raster_split_items(split_max),
                                                         w.nsplit_of, w.split_slot, w.counters, w.split_cap, w.extra,
                                                         raster_extra_cap(cap, w, split_max));
     VSR_CUDA_TRY(cudaGetLastError());
@@ -676,7 +676,7 @@ vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, 
                                RasterWork w, int split_max, int* status, cudaStream_t st, bool host_out)
 {
     if (n_tiles == 0) return VSR_OK;
-    vsr_status s = launch_raster_assign(offsets, n_tiles, cap, w, split_max, st);
+    vsr_status s = launch_raster_assign(offsets, n_tiles, cap, w, split_max, st, view.ends);
     if (s != VSR_OK) return s;
     const uint32_t extra_cap = raster_extra_cap(cap, w, split_max);
     split_max = raster_split_items(split_max);

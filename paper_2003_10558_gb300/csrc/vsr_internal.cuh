@@ -208,6 +208,56 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 vsr_status launch_bin_fill(const float4* rec, int T, TileIndex idx, const uint32_t* offsets, uint32_t* counts,
                            const uint32_t* cursor, const uint2* pairs, uint32_t pair_cap, uint32_t* ids, uint32_t cap,
                            int* status, cudaStream_t st, int pstep = 0);
+
+// ---------------------------------------------------------------------------
+// Tile-major binning.  The frame's triangles are filed by the cell of their
+// cap centre on one of two latitude-longitude grids of the view sphere (the
+// same latitude / longitude as the tile index): caps of enlarged radius up to
+// two cells of the fine grid (pi / TRI_NLAT0) in its cells, TRI_K0 per cell,
+// a triangle that does not fit (a larger cap or a full cell) in the coarse
+// grid (pi / TRI_NLAT1, TRI_K1 per cell) if its cap is at most two of its
+// cells, and the rest in one list.  Every tile then tests only the triangles
+// of the cells within its half-angle plus each grid's largest cap radius of
+// its axis, and the list: one warp per tile, the same cap / cone test as the
+// triangle-major search.  One pass: the warp stages its hits in shared
+// memory, takes its range of the bins with one atomic, and writes them, so
+// the bins of tile u are ids[starts[u] .. ends[u]) (not ordered by tile);
+// starts[ntiles] receives the total.
+constexpr int TRI_NLAT0 = 128, TRI_NLON0 = 2 * TRI_NLAT0, TRI_K0 = 64;
+constexpr int TRI_NLAT1 = 16, TRI_NLON1 = 2 * TRI_NLAT1, TRI_K1 = 512;
+constexpr int TRI_CELLS0 = TRI_NLAT0 * TRI_NLON0;
+constexpr int TRI_CELLS1 = TRI_NLAT1 * TRI_NLON1;
+constexpr int TRI_LARGE = TRI_CELLS0 + TRI_CELLS1;  // the counter of the list
+constexpr int TRI_CELLS = TRI_LARGE + 1;
+// entry numbers: fine cells, coarse cells, then the list
+constexpr uint32_t TRI_E1 = (uint32_t)TRI_CELLS0 * TRI_K0;
+constexpr uint32_t TRI_E2 = TRI_E1 + (uint32_t)TRI_CELLS1 * TRI_K1;
+
+// Device memory of a triangle index (per scene, up to T triangles).  The
+// counters and header are double-buffered: a binning files into buffer
+// `parity` and clears the other one for the next binning.
+struct TriIndex {
+    uint32_t* counts;  // 2 x TRI_CELLS: triangles filed per cell (may exceed the cell's capacity), list length
+    uint32_t* hdr;     // 2 x 4: largest enlarged cap radius of the fine / coarse grid (float bits),
+                       // bin cursor, finished CTAs
+    float4* cap;       // TRI_E2 + T entries: (S-hat xyz, cos beta)
+    float2* cs;        // TRI_E2 + T entries: (sin beta, triangle bits)
+    int64_t T;         // capacity of the list
+    int parity;        // buffer of the next binning (host side)
+};
+vsr_status tri_index_alloc(TriIndex* ti, int64_t T);
+void tri_index_free(TriIndex* ti);
+size_t tri_index_bytes(int64_t T);
+// binning of one frame, tile-major (flips ti->parity): the triangle index of
+// rec, then every tile of the map.  idx: the map's tile index (its header's
+// widest ramp and each tile's geometry); tiles: the map's ntiles cones;
+// starts / ends: ntiles + 1 / ntiles words; T <= ti->T.  With more pairs
+// than cap the bins are cut at cap and VSR_ERR_BIN_OVERFLOW is raised;
+// total_host (optional): the device address of a pinned host word that
+// also receives the total.
+vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
+                            TriIndex* ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
+                            uint32_t* total_host, cudaStream_t st, int pstep = 0);
 // One view as the raster kernel sees it: its map, tile cones, set-up
 // records, bin offsets (indexed by the view's own tile number), bin ids and
 // outputs.
@@ -224,6 +274,9 @@ struct RasterView {
     uint32_t* out_id;
     float* out_depth;
     float* out_cov;
+    // bins of the tile-major binner: tile u's bin ends at ends[u] (NULL:
+    // bins in tile order, tile u's ending at offsets[u + 1])
+    const uint32_t* ends = nullptr;
 };
 
 // One view as the binner sees it (tile index of the view's map, the view's
@@ -297,16 +350,17 @@ struct PoolView {
 // extra items a view's work gets for bins of capacity cap
 int raster_split_items(int split_max);
 uint32_t raster_extra_cap(uint32_t cap, const RasterWork& w, int split_max);
-// the work items of one view (split tiles, extra items), for the pooled launch
+// the work items of one view (split tiles, extra items), for the pooled
+// launch; ends: as RasterView::ends
 vsr_status launch_raster_assign(const uint32_t* offsets, uint32_t n_tiles, uint32_t cap, RasterWork w, int split_max,
-                                cudaStream_t st);
+                                cudaStream_t st, const uint32_t* ends = nullptr);
 // one persistent raster launch over the items of several views: view v owns
 // items item_start[v] .. item_start[v + 1] - 1 (its tiles, then its extra
 // items); queue: a device counter (zeroed here)
 vsr_status launch_raster_pool(const PoolView* views_dev, const uint32_t* item_start_dev, int nviews,
                               uint32_t* queue, int split_max, int* status, cudaStream_t st);
 // items + raster over all tiles of a view; offsets: its bin offsets
-// (n_tiles + 1 entries); cap: the bins' capacity (bounds the extra items);
+// (n_tiles + 1 entries, or the bins' starts with view.ends); cap: the bins' capacity (bounds the extra items);
 // host_out: the outputs are pinned host memory (written in whole tile rows)
 vsr_status launch_raster_items(const RasterView& view, const uint32_t* offsets, uint32_t n_tiles, uint32_t cap,
                                RasterWork w, int split_max, int* status, cudaStream_t st, bool host_out = false);
@@ -330,7 +384,7 @@ vsr_status launch_scan_large(const uint32_t* counts, const uint32_t* extra, int 
 vsr_status launch_raster(const float4* map, int W, int H, const Cone* tiles, const float4* rec, int T,
                          const uint32_t* offsets, const uint32_t* ids, uint32_t cap, uint32_t* id, float* depth,
                          float* cov, unsigned long long* n_alg, unsigned long long* n_exec, int32_t* n_inside,
-                         int* status, cudaStream_t st);
+                         int* status, cudaStream_t st, const uint32_t* ends = nullptr);
 
 // ---------------------------------------------------------------------------
 // Differentiable path (grad.cu, map.cu).
@@ -363,6 +417,7 @@ struct FragArgs {
     uint32_t* out_id;
     float* out_depth;
     int* status;
+    const uint32_t* ends = nullptr;  // as RasterView::ends
 };
 vsr_status launch_frag_count(const FragArgs& a, cudaStream_t st);
 vsr_status launch_frag_fill(const FragArgs& a, cudaStream_t st);
