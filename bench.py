@@ -41,10 +41,10 @@ WORKLOAD = "single-view 1920x1080, k=0.32 l=0.62 s=0.86 Omega=270, icosphere L5 
 UNIT = "tests/s"
 OPS_PER_TEST = 20  # FP32 ops of one algorithmic test: 4 three-term dots (12 FMA), 3 min, ramp FMA, 4 compares
 LANES_PER_SM = 128  # FP32 lanes per Blackwell SM
-# kernels of libvsr.so per step: map, index cell scan, index filing copy
-# (the map stream), set-up, bin count, bin scan, bin pair fill, work items,
-# raster (the memsets between them are not kernels of the library)
-LAUNCHES_PER_STEP = 9
+# kernels of libvsr.so per step: map (the map stream), set-up, triangle
+# filing, tile bins, work items, raster (the memsets between them are not
+# kernels of the library)
+LAUNCHES_PER_STEP = 6
 
 
 def parse():
@@ -268,8 +268,8 @@ def run_vsr(args, rank, world, local):
            "cov": torch.empty((H, W), dtype=torch.float32, device=dev)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # the map's chain (map kernel, then the one-CTA tile index) gets the
-    # higher priority: the set-up fills the SMs the index build leaves idle
+    # the map kernel's stream gets the higher priority: the set-up fills the
+    # SMs the map leaves idle
     side = torch.cuda.Stream(device=dev, priority=-1)
     ev_fork, ev_map = torch.cuda.Event(), torch.cuda.Event()
 
@@ -521,8 +521,8 @@ def run_vsr(args, rank, world, local):
     achieved = n_alg * OPS_PER_TEST / rast_mean_s
     traffic = raster_traffic()
     # achieved HBM bandwidth of the memory-bound stages (algorithmic bytes /
-    # their live CUDA-event times): the map with its tile cones and index
-    # (16 B per pixel + 48 B cone/geometry + 32 B index entry per tile), the
+    # their live CUDA-event times): the map with its tile cones and geometry
+    # (16 B per pixel + 48 B per tile), the
     # set-up (36 B read + 160 B written per triangle) and the raster's own
     # streams (16 B map read + 12 B outputs written per pixel)
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
@@ -533,7 +533,7 @@ def run_vsr(args, rank, world, local):
         return {"bytes": int(nbytes), "ms": ms, "GB_per_s": gbs, "frac": gbs / hbm_peak}
 
     hbm = {"peak_GB_per_s": hbm_peak, "peak_source": f"{pk_kind} hbm_gbs",
-           "map_with_index": bw(16 * W * H + 80 * ntiles, stage_ms["map alone"]),
+           "map": bw(16 * W * H + 48 * ntiles, stage_ms["map alone"]),
            "setup": bw(196 * T, stage_ms["setup alone"]),
            "raster_map_read_and_outputs": bw(28 * W * H, statistics.mean(rast_ms))}
     line = {

@@ -75,6 +75,10 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     m->idx.ntiles = (uint32_t)nt;
     m->idx_built = false;
+    // the widest-ramp word starts below every generation
+    if (cudaMemset(m->idx.hdr, 0, sizeof(TileIndexHdr)) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+        return VSR_ERR_CUDA;
+    m->hgen = 0;
     if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }
@@ -139,32 +143,40 @@ void set_universal_spec(vsr_map m)
     m->lens_grad = true;
 }
 
+// the next generation of the map's widest-ramp word (after 2^32 - 1 of them
+// the word is cleared on st and they count from 1 again)
+vsr_status next_hgen(vsr_map m, cudaStream_t st)
+{
+    if (++m->hgen == 0) {
+        VSR_CUDA_TRY(cudaMemsetAsync(&m->idx.hdr->h_gen, 0, sizeof(unsigned long long), st));
+        m->hgen = 1;
+    }
+    return VSR_OK;
+}
+
+// One generation of the map: the map kernel writes the map, the tile cones
+// and geometry and the widest ramp, all the tile-major binner needs; the
+// tile index of the triangle-major search is left to its first use.
 vsr_status map_generate(vsr_map m, cudaStream_t st)
 {
     bool plain = m->spec.kind == VSR_MAP_UNIVERSAL && !m->deriv;
     for (int q = 0; q < 6; ++q) plain = plain && m->spec.distortion[q] == 0.0f;
-    // The first generation builds the whole tile index after the map.  A
-    // later generation of the same projection (the same spec: a map rebuilt
-    // each frame) has the same tiles and the same grid plan, so the map
-    // kernel files its tiles into the plan the index header holds and one
-    // small kernel completes the index.  After a change of lens the plan
-    // may fit the new tiles badly (every tile past its cut goes to the big
-    // list, which every triangle tests), so the index is built whole again.
-    const bool file = m->idx_built && memcmp(&m->idx_spec, &m->spec, sizeof(vsr_map_spec)) == 0;
-    // until this generation has completed, the next one must build the index whole
     m->idx_built = false;
-    const TileIndex* into = file ? &m->idx : nullptr;
-    vsr_status s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map,
-                                      m->tiles, m->idx.geom, into, st)
-                         : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, into, st);
+    vsr_status s = next_hgen(m, st);
     if (s != VSR_OK) return s;
-    s = file ? launch_tile_index_finish(m->tiles, m->tx * m->ty, m->idx, st)
-             : launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
-    if (s == VSR_OK) {
-        m->idx_built = true;
-        m->idx_spec = m->spec;
-    }
+    s = plain ? launch_map(m->p.W, m->p.H, m->p.aov, m->p.k, m->p.l, m->p.s, m->p.omega_deg, m->map, m->tiles,
+                           m->idx.geom, &m->idx.hdr->h_gen, m->hgen, st)
+              : launch_map_spec(m->spec, m->map, m->tiles, m->idx.geom, m->deriv, &m->idx.hdr->h_gen, m->hgen, st);
     m->gen = g_gen.fetch_add(1);
+    return s;
+}
+
+// the tile index of the map's current generation (built on first use)
+vsr_status ensure_tile_index(vsr_map m, cudaStream_t st)
+{
+    if (m->idx_built) return VSR_OK;
+    vsr_status s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
+    if (s == VSR_OK) m->idx_built = true;
     return s;
 }
 
@@ -186,15 +198,23 @@ vsr_status scene_setup(vsr_scene sc, const float* tris_dev, int64_t T, const flo
     return s == VSR_OK ? scene_used(sc, st) : s;
 }
 
-// bin ids of `want` entries (frees the old ones, which waits for the
-// launches still using them)
+// bin ids and the triangle-major count pass's pair list, both of `want`
+// entries (frees the old ones, which waits for the launches still using
+// them)
 vsr_status bins_realloc(vsr_scene sc, uint32_t want)
 {
     cudaFree(sc->ids);
+    cudaFree(sc->pairs);
     sc->ids = nullptr;
+    sc->pairs = nullptr;
     sc->cap = 0;
     vsr_status s;
     if ((s = dalloc(&sc->ids, (size_t)want)) != VSR_OK) return s;
+    if ((s = dalloc(&sc->pairs, (size_t)want)) != VSR_OK) {
+        cudaFree(sc->ids);
+        sc->ids = nullptr;
+        return s;
+    }
     sc->cap = want;
     return VSR_OK;
 }
@@ -207,7 +227,7 @@ vsr_status ensure_ws(vsr_scene sc, int ntiles)
     sc->ends = sc->offsets = nullptr;
     sc->ws_tiles = 0;
     vsr_status s;
-    if ((s = dalloc(&sc->ends, (size_t)ntiles)) != VSR_OK) return s;
+    if ((s = dalloc(&sc->ends, (size_t)ntiles + 1)) != VSR_OK) return s;  // (+1: the triangle-major pair cursor)
     if ((s = dalloc(&sc->offsets, (size_t)ntiles + 1)) != VSR_OK) return s;
     sc->ws_tiles = ntiles;
     sc->sized_shape = 0;
@@ -362,8 +382,8 @@ vsr_status vsr_map_from_device(const float* xyzd_dev, int W, int H, void* stream
     if (s == VSR_OK && cudaMemcpyAsync(m->map, xyzd_dev, sizeof(float4) * (size_t)W * H, cudaMemcpyDeviceToDevice,
                                        st) != cudaSuccess)
         s = VSR_ERR_CUDA;
-    if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, m->idx.geom, st);
-    if (s == VSR_OK) s = launch_tile_index(m->tiles, m->tx * m->ty, m->idx, st);
+    if (s == VSR_OK) s = next_hgen(m, st);
+    if (s == VSR_OK) s = launch_map_cones(m->map, W, H, m->tiles, m->idx.geom, &m->idx.hdr->h_gen, m->hgen, st);
     if (s != VSR_OK) {
         map_release(m);
         delete m;
@@ -477,6 +497,7 @@ void vsr_scene_free(vsr_scene sc)
     cudaFree(sc->ends);
     cudaFree(sc->offsets);
     cudaFree(sc->ids);
+    cudaFree(sc->pairs);
     tri_index_free(&sc->tri);
     raster_work_free(&sc->work);
     cudaFree(sc->tris_dev);
@@ -514,7 +535,7 @@ vsr_status vsr_raster_pstep(vsr_map m, vsr_scene sc, uint32_t* id_dev, float* de
     vsr_status s = bin_scene(m, sc, 1, st);
     if (s != VSR_OK) return s;
     const RasterView v{m->map,  m->p.W, m->p.H, m->tiles, m->tx,     sc->rec,   (int)sc->T, sc->offsets,
-                       sc->ids, sc->cap, id_dev, depth_dev, cov_dev, sc->ends};
+                       sc->ids, sc->cap, id_dev, depth_dev, cov_dev, scene_ends(sc)};
     s = launch_raster_pstep(v, m->deriv, scene_status(sc), st);
     return s == VSR_OK ? scene_used(sc, st) : s;
 }
@@ -527,14 +548,22 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
     vsr_status s = ensure_ws(sc, ntiles);
     if (s != VSR_OK) return s;
     const int T = (int)sc->T;
-    if ((s = tri_index_alloc(&sc->tri, T)) != VSR_OK) return s;
     sc->last_ntiles = ntiles;
+    // The binner: tile-major while the triangles are few per tile (each
+    // tile's warp then walks a short window), else the triangle-major search
+    // over the map's tile index (its work spread over the triangles).
+    sc->tile_major = (int64_t)T <= TILE_MAJOR_TRIS_PER_TILE * (int64_t)ntiles;
+    if (sc->tile_major) {
+        if ((s = tri_index_alloc(&sc->tri, T, ntiles)) != VSR_OK) return s;
+    } else if ((s = ensure_tile_index(m, st)) != VSR_OK) {
+        return s;
+    }
     // Bin capacity.  Sized synchronously the first time and whenever the
     // number of tiles or triangles changes (the first time only, for a scene
     // with async_sizing); otherwise the pair total of the previous binning
     // (copied to pinned memory, read only once its event has completed, never
-    // waited for) grows the capacity ahead of need, and the binning kernel
-    // reports any overflow in the status word.
+    // waited for) grows the capacity ahead of need, and the binning kernels
+    // report any overflow in the status word.
     // the bins' sizes depend on the map, the scene and the step's cap width
     const uint64_t shape = ((uint64_t)ntiles << 32) ^ (uint64_t)sc->T ^ ((uint64_t)(pstep != 0) << 63);
     const bool resize = sc->cap == 0 || (!sc->async_sizing && sc->sized_shape != shape);
@@ -547,21 +576,35 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
             if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
         }
     }
-    // one tile-major pass: the pair total also goes to the pinned host word
-    // (its device address) unless an earlier total has not been read yet --
-    // and always when this binning sizes the bins, which reads this total
+    // the pair total also goes to the pinned host word (its device address)
+    // unless an earlier total has not been read yet -- and always when this
+    // binning sizes the bins, which reads this total
     const bool record = resize || !sc->total_pending;
-    // (a sizing pass reports no overflow: its bins are grown and binned again)
-    if ((s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, &sc->tri, sc->offsets, sc->ends, sc->ids, sc->cap,
-                              resize ? nullptr : scene_status(sc), record ? sc->h_total_dev : nullptr, st, pstep)) !=
-        VSR_OK)
-        return s;
+    uint32_t* total_host = record ? sc->h_total_dev : nullptr;
+    // triangle-major: per-tile counters and the pair cursor in the end array
+    uint32_t* counts = sc->ends;
+    uint32_t* cursor = counts + ntiles;
+    uint2* pairs = sc->pairs;
+    const uint32_t pair_cap = sc->cap;
+    if (sc->tile_major) {
+        // one pass (a sizing pass reports no overflow: its bins are grown and
+        // binned again)
+        if ((s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, sc->tri, sc->offsets, sc->ends, sc->ids,
+                                  sc->cap, resize ? nullptr : scene_status(sc), total_host, st, pstep)) != VSR_OK)
+            return s;
+    } else {
+        VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ((size_t)ntiles + 1), st));
+        if ((s = launch_bin_count(sc->rec, T, m->idx, counts, cursor, pairs, pair_cap, st, pstep)) != VSR_OK)
+            return s;
+        if ((s = launch_scan(counts, nullptr, ntiles, nullptr, sc->offsets, st, total_host)) != VSR_OK) return s;
+    }
     if (record) {
         VSR_CUDA_TRY(cudaEventRecord(sc->total_event, st));
         sc->total_pending = true;
         sc->total_map = m->gen;
         sc->total_scene = sc->gen;
     }
+    bool grown = false;
     if (resize) {
         VSR_CUDA_TRY(cudaEventSynchronize(sc->total_event));
         sc->total_pending = false;
@@ -570,11 +613,18 @@ static vsr_status bin_scene(vsr_map m, vsr_scene sc, int pstep, cudaStream_t st)
             uint64_t want = (uint64_t)total + total / 4 + 4096;
             if (want > 0xffffffffull) want = 0xffffffffull;
             if ((s = bins_realloc(sc, (uint32_t)want)) != VSR_OK) return s;
-            if ((s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, &sc->tri, sc->offsets, sc->ends, sc->ids,
-                                      sc->cap, scene_status(sc), nullptr, st, pstep)) != VSR_OK)
-                return s;
+            pairs = nullptr;  // this frame's pair list went with the old buffer: search again
+            grown = true;
         }
         sc->sized_shape = shape;
+    }
+    if (sc->tile_major) {
+        if (grown && (s = launch_bin_tiles(sc->rec, T, m->idx, m->tiles, ntiles, sc->tri, sc->offsets, sc->ends,
+                                           sc->ids, sc->cap, scene_status(sc), nullptr, st, pstep)) != VSR_OK)
+            return s;
+    } else if ((s = launch_bin_fill(sc->rec, T, m->idx, sc->offsets, counts, cursor, pairs, pair_cap, sc->ids,
+                                    sc->cap, scene_status(sc), st, pstep)) != VSR_OK) {
+        return s;
     }
     sc->binned_map = m->gen;
     sc->binned_scene = sc->gen;
@@ -598,7 +648,7 @@ static vsr_status raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float*
             sc->work_tiles = ntiles;
         }
         const RasterView v{m->map,  m->p.W, m->p.H, m->tiles, m->tx,     sc->rec,   (int)sc->T, sc->offsets,
-                           sc->ids, sc->cap, id_dev, depth_dev, cov_dev, sc->ends};
+                           sc->ids, sc->cap, id_dev, depth_dev, cov_dev, scene_ends(sc)};
         const vsr_status s = launch_raster_items(v, sc->offsets, ntiles, sc->cap, sc->work, SPLIT_MAX_DEFAULT,
                                                  scene_status(sc), (cudaStream_t)stream, host_out);
         return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
@@ -608,7 +658,7 @@ static vsr_status raster_tiles(vsr_map m, vsr_scene sc, uint32_t* id_dev, float*
         launch_raster(m->map, m->p.W, m->p.H, m->tiles, sc->rec, (int)sc->T, sc->offsets, sc->ids, sc->cap, id_dev,
                       depth_dev, cov_dev, stats ? (unsigned long long*)stats->n_alg_dev : nullptr,
                       stats ? (unsigned long long*)stats->n_exec_dev : nullptr, stats ? stats->n_inside_dev : nullptr,
-                      scene_status(sc), (cudaStream_t)stream, sc->ends);
+                      scene_status(sc), (cudaStream_t)stream, scene_ends(sc));
     return s == VSR_OK ? scene_used(sc, (cudaStream_t)stream) : s;
 }
 
@@ -648,8 +698,18 @@ vsr_status vsr_scene_bin_pairs(vsr_scene sc, void* stream, int64_t* pairs)
     if (!sc || !pairs || sc->last_ntiles == 0) return VSR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     VSR_CUDA_TRY(cudaStreamSynchronize(st));
-    uint32_t v = 0;
-    VSR_CUDA_TRY(cudaMemcpy(&v, sc->offsets + sc->last_ntiles, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    const size_t n = (size_t)sc->last_ntiles;
+    if (!sc->tile_major) {  // bins in tile order: the scan's total
+        uint32_t v = 0;
+        VSR_CUDA_TRY(cudaMemcpy(&v, sc->offsets + n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        *pairs = v;
+        return VSR_OK;
+    }
+    std::vector<uint32_t> b0(n), b1(n);
+    VSR_CUDA_TRY(cudaMemcpy(b0.data(), sc->offsets, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    VSR_CUDA_TRY(cudaMemcpy(b1.data(), sc->ends, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    int64_t v = 0;
+    for (size_t u = 0; u < n; ++u) v += (int64_t)(b1[u] - b0[u]);
     *pairs = v;
     return VSR_OK;
 }
@@ -904,7 +964,9 @@ extern "C" vsr_status vsr_raster_noalloc(vsr_map m, vsr_scene sc, uint32_t* id_d
     // the array keeps the previous call's contents: clear what starts at zero
     VSR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     VSR_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-    // no pair list: the fill searches again
+    // the triangle-major search over the map's tile index (no pair list: the
+    // fill searches again)
+    if ((s = ensure_tile_index(m, st)) != VSR_OK) return s;
     if ((s = launch_bin_count(sc->rec, T, m->idx, counts, nullptr, nullptr, 0, st)) != VSR_OK) return s;
     if ((s = launch_scan(counts, nullptr, ntiles, nullptr, offsets, st)) != VSR_OK) return s;
     if ((s = launch_bin_fill(sc->rec, T, m->idx, offsets, counts, nullptr, nullptr, 0, ids, NA_PAIRS_MAX, status,
@@ -1241,6 +1303,10 @@ vsr_status vsr_batch_render(vsr_batch b, int nviews, const vsr_map* maps, const 
     memcpy(b->cams_host, cams, cam_bytes);
     VSR_CUDA_TRY(cudaMemcpyAsync(b->cams_dev, b->cams_host, cam_bytes, cudaMemcpyHostToDevice, st));
 
+    // the views' binning searches their maps' tile indexes (built once per
+    // generation of a map; the key holds the generations)
+    for (int v = 0; v < nviews; ++v)
+        if ((s = ensure_tile_index(maps[v], st)) != VSR_OK) return s;
     // eager frame: fronts, one synchronisation to size every view's bins, backs
     for (int v = 0; v < nviews; ++v) {
         if ((s = batch_view_front(b, v, maps[v], tris_dev, T, false, st)) != VSR_OK) return s;

@@ -3,21 +3,25 @@
 //
 // A fragment of triangle t at pixel direction G needs G inside the miter
 // cap enlarged by the ramp half-width (the gbpxstep test of the miter plane,
-// Sec. 1.1.1 / 1.1.2): G.S-hat - cos rho > -h sin rho, h = 1/(2 delta).  The
+// Sec. 1.1.1 / 1.1.2): G.S-hat - cos rho > -h sin rho, h = 1/(2 delta).  A
 // binner keeps (tile, t) when that enlarged cap can reach the tile's view
 // cone (cap_hits_cone).  The paper's analogue is the low-resolution region
 // mask widened by fwidth/2 (getPolygonRegion).
 //
-// The candidate tiles of a triangle come from the map's tile index (a
-// latitude-longitude grid of the view sphere in which every tile is filed
-// once, see TileIndexHdr): only the cells within beta + alpha_small_max of
-// the cap centre are visited, so the work per triangle is a few dozen cone
-// tests whatever the map's size, and no tile is found twice.
-//
-// Per frame: count (atomic per-tile counters) -> exclusive scan -> fill
-// (atomic per-tile cursors).  The order of ids inside a bin is not fixed;
-// the raster kernel's result does not depend on it.
+// Two binners with the same cap / cone test:
+//  * tile-major (every frame of a scene or batch view): the frame's
+//    triangles filed by the cell of their cap centre on a latitude-longitude
+//    grid, then one warp per tile over the cells within its reach, in one
+//    pass (tri_file_kernel, bin_tiles_kernel; see TriIndex);
+//  * triangle-major (the fixed-array path, vsr_raster_noalloc): every
+//    triangle visits the cells of the map's tile index within beta +
+//    alpha_small_max of its cap centre (a few dozen cone tests whatever the
+//    map's size; no tile is found twice); count (atomic per-tile counters)
+//    -> exclusive scan -> fill (atomic per-tile cursors).
+// The order of ids inside a bin is not fixed; the raster kernels' results
+// do not depend on it.
 #include <math.h>
+#include <stddef.h>
 
 #include <atomic>
 
@@ -33,47 +37,10 @@ __device__ __forceinline__ float hist_upper(int b) { return exp2f((float)(b + 1)
 // ---- tile index -------------------------------------------------------------
 //
 // Built from the per-tile geometry the map kernels write (TileIndex::geom:
-// half-angle, axis latitude / longitude, ramp half-width) in four grid-wide
-// steps: the histogram of half-angles (idx_hist_kernel), the grid plan and
-// the per-cell counts (idx_count_kernel, which computes the plan from the
-// histogram in every CTA), the exclusive scan of the cell counts, and the
-// cell-sorted copies of the small tiles' cones (idx_copy_kernel, which takes
-// its slot by decrementing the cell count).  Every step spreads the tiles
-// over the whole GPU; the plan itself is a 64-bin walk.
-
-constexpr int IDX_THREADS = 256;
-
-
-// hdr zeroed by the caller
-__global__ void __launch_bounds__(IDX_THREADS) idx_hist_kernel(const Cone* __restrict__ tiles,
-                                                                const float4* __restrict__ geom, int ntiles,
-                                                                TileIndexHdr* __restrict__ hdr)
-{
-    __shared__ unsigned s_hist[IDX_HIST];
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < IDX_HIST) s_hist[tid] = 0u;
-    __syncthreads();
-    const int i = blockIdx.x * IDX_THREADS + tid;
-    const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-    const bool ok = g.w >= 0.0f;
-    const int bin = ok ? hist_bin(g.x) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, bin);
-    if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(peers));
-    unsigned nv = ok, hm = ok ? __float_as_uint(g.w) : 0u;  // non-negative floats order as their bits
-    unsigned va = ok ? view_angle_bits(tiles[i], g.x) : 0u;
-    for (int o = 16; o; o >>= 1) {
-        nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        va = max(va, __shfl_xor_sync(0xffffffffu, va, o));
-    }
-    if (lane == 0 && nv) {
-        atomicAdd(&hdr->n_valid, nv);
-        atomicMax(&hdr->h_max, hm);
-        atomicMax(&hdr->view_angle, va);
-    }
-    __syncthreads();
-    if (tid < IDX_HIST && s_hist[tid]) atomicAdd(&hdr->hist[tid], s_hist[tid]);
-}
+// half-angle, axis latitude / longitude, ramp half-width) by one CTA
+// (idx_fused_kernel, maps of up to IDX_FUSED_TILES tiles): the histogram of
+// half-angles, the grid plan (a 64-bin walk), the per-cell counts, their
+// exclusive scan and the cell-sorted copies of the small tiles' cones.
 
 // the grid plan: cell size from the 99th percentile of the half-angles
 __device__ void index_plan(const TileIndexHdr* hdr, TileIndexHdr& h)
@@ -94,61 +61,6 @@ __device__ void index_plan(const TileIndexHdr* hdr, TileIndexHdr& h)
     h.ncell = 2 * nlat * nlat;
     h.cell = PI_F / nlat;
     h.alpha_cut = cut;
-}
-
-// cell_count (IDX_CELLS_MAX) zeroed by the caller
-__global__ void __launch_bounds__(IDX_THREADS) idx_count_kernel(const Cone* __restrict__ tiles,
-                                                                 const float4* __restrict__ geom, int ntiles,
-                                                                 TileIndexHdr* __restrict__ hdr,
-                                                                 uint32_t* __restrict__ cell_count,
-                                                                 Cone* __restrict__ big)
-{
-    __shared__ TileIndexHdr s_h;
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0) {
-        index_plan(hdr, s_h);
-        if (blockIdx.x == 0) {
-            hdr->nlat = s_h.nlat;
-            hdr->nlon = s_h.nlon;
-            hdr->ncell = s_h.ncell;
-            hdr->cell = s_h.cell;
-            hdr->alpha_cut = s_h.alpha_cut;
-        }
-    }
-    __syncthreads();
-    const int i = blockIdx.x * IDX_THREADS + tid;
-    unsigned am = 0u;
-    if (i < ntiles) {
-        const float4 g = geom[i];
-        if (g.w >= 0.0f) {
-            if (g.x > s_h.alpha_cut) {
-                big[atomicAdd(&hdr->n_big, 1u)] = index_entry(tiles[i], i);
-            } else {
-                atomicAdd(&cell_count[home_cell_geom(g, s_h)], 1u);
-                am = __float_as_uint(g.x);
-            }
-        }
-    }
-    for (int o = 16; o; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
-    if (lane == 0 && am) atomicMax(&hdr->alpha_small_max, am);
-}
-
-__global__ void __launch_bounds__(IDX_THREADS) idx_copy_kernel(const Cone* __restrict__ tiles,
-                                                                const float4* __restrict__ geom, int ntiles,
-                                                                const TileIndexHdr* __restrict__ hdr,
-                                                                const uint32_t* __restrict__ cell_start,
-                                                                uint32_t* __restrict__ cell_count,
-                                                                Cone* __restrict__ sorted)
-{
-    __shared__ TileIndexHdr s_h;
-    if (threadIdx.x == 0) s_h = *hdr;
-    __syncthreads();
-    const int i = blockIdx.x * IDX_THREADS + threadIdx.x;
-    if (i >= ntiles) return;
-    const float4 g = geom[i];
-    if (g.w < 0.0f || g.x > s_h.alpha_cut) return;
-    const int c = home_cell_geom(g, s_h);
-    sorted[cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u] = index_entry(tiles[i], i);
 }
 
 // The tile loops of the one-CTA index kernels take IDX_BATCH tiles per
@@ -210,65 +122,10 @@ __device__ uint32_t block_scan_smem(uint32_t* s, int n, uint32_t* s_wsum /* NT /
     return total;
 }
 
-// After a filing map kernel and the scan of its cell counts (cell_start):
-// the cell-sorted copies of the small tiles (slot by decrementing the cell
-// count, which returns the counts to zero for the next generation), the
-// widest ramp of all tiles and the largest small half-angle (into maxima the
-// filing map kernel cleared), and the view angle; block 0 moves the
-// filing's work counters
-// (histogram, big-list length) into the header and clears them.
-__global__ void __launch_bounds__(IDX_THREADS) idx_file_copy_kernel(const Cone* __restrict__ tiles,
-                                                                     const float4* __restrict__ geom, int ntiles,
-                                                                     TileIndexHdr* __restrict__ hdr,
-                                                                     const uint32_t* __restrict__ cell_start,
-                                                                     uint32_t* __restrict__ cell_count,
-                                                                     Cone* __restrict__ sorted)
-{
-    __shared__ TileIndexHdr s_h;
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0) {
-        s_h.nlat = min(max(hdr->nlat, 1), IDX_NLAT_MAX);
-        s_h.nlon = 2 * s_h.nlat;
-        s_h.cell = hdr->cell;
-        s_h.alpha_cut = hdr->alpha_cut;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
-        if (tid == 0) {
-            hdr->n_big = min(hdr->n_big_work, (unsigned)ntiles);
-            hdr->n_big_work = 0u;
-        }
-        if (tid < IDX_HIST) {
-            hdr->hist[tid] = hdr->hist_work[tid];
-            hdr->hist_work[tid] = 0u;
-        }
-    }
-    const int i = blockIdx.x * IDX_THREADS + tid;
-    const float4 g = i < ntiles ? geom[i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-    const bool valid = g.w >= 0.0f;
-    const bool small = valid && g.x <= s_h.alpha_cut;
-    if (small) {
-        const int c = home_cell_geom(g, s_h);
-        const uint32_t slot = cell_start[c] + atomicSub(&cell_count[c], 1u) - 1u;
-        if (slot < (uint32_t)ntiles) sorted[slot] = index_entry(tiles[i], i);
-    }
-    unsigned hm = valid ? __float_as_uint(g.w) : 0u, am = small ? __float_as_uint(g.x) : 0u;
-    unsigned va = valid ? view_angle_bits(tiles[i], g.x) : 0u;
-    for (int o = 16; o; o >>= 1) {
-        hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
-        va = max(va, __shfl_xor_sync(0xffffffffu, va, o));
-    }
-    if (lane == 0 && hm) atomicMax(&hdr->h_max, hm);
-    if (lane == 0 && am) atomicMax(&hdr->alpha_small_max, am);
-    if (lane == 0 && va) atomicMax(&hdr->view_angle, va);
-}
-
-// The whole index in one CTA, for maps of at most IDX_FUSED_TILES tiles: the
-// same four steps with the histogram, the per-cell counts and their scan in
-// shared memory (IDX_CELLS_MAX counters), closed by barriers instead of
-// kernel boundaries, and the header written once at the end -- one launch
-// and no memsets instead of four launches and two memsets.
+// The whole index in one CTA, for maps of at most IDX_FUSED_TILES tiles:
+// the histogram, the per-cell counts and their scan in shared memory
+// (IDX_CELLS_MAX counters), steps closed by barriers, and the header written
+// once at the end.
 constexpr int IDX_FUSED_THREADS = 1024;
 constexpr int IDX_FUSED_TILES = 32768;
 static_assert(IDX_CELLS_MAX <= 65535, "home cells are kept as 16-bit indices");
@@ -288,7 +145,10 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
     __shared__ TileIndexHdr s_h;
     __shared__ uint32_t s_wsum[IDX_FUSED_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0) s_h = TileIndexHdr{};
+    if (tid == 0) {
+        s_h = TileIndexHdr{};
+        s_h.h_gen = hdr->h_gen;  // the map kernels' word, kept
+    }
     __syncthreads();
     // 1. histogram of half-angles (one add per group of equal bins in a
     // warp), valid tiles, widest ramp (one atomic per warp)
@@ -757,7 +617,10 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* __restrict__
 
 constexpr float TRI_CELL0 = PI_F / TRI_NLAT0;
 constexpr float TRI_CELL1 = PI_F / TRI_NLAT1;
-constexpr uint32_t BIN_STAGE_HITS = 1024;  // hits a tile's warp stages in shared memory
+// entries of a tile binned by its own warp (its hits staged in shared
+// memory); a tile with more goes to the heavy list
+constexpr uint32_t BIN_STAGE_HITS = 1024;
+constexpr int BIN_HEAVY_WARPS = 16;  // warps per heavy tile
 // steps of the walk whose loads are issued together: 2 (measured on the
 // 1080p frame: bin stage 38.9 us against 40.7 us at 4; 12 resident CTAs
 // per SM instead of 8, which caps the registers: 40.8 - 48.6 us)
@@ -802,26 +665,21 @@ __device__ __forceinline__ bool tri_cap(const float4* __restrict__ rec, size_t T
     return true;
 }
 
-// Every triangle into its cell (buffer par): the fine grid when its cap fits
-// and the cell has room, else the coarse grid under the same conditions,
-// else the list; each grid's largest cap radius into the header.  The other
-// buffer is cleared for the next binning (the one that used it is complete,
-// by stream order).
+// Every triangle into its cell (counters cleared before): the fine grid
+// when its cap fits and the cell has room, else the coarse grid under the
+// same conditions, else the list; each grid's largest cap radius into the
+// header.
 __global__ void __launch_bounds__(256) tri_file_kernel(const float4* __restrict__ rec, int T,
-                                                       const TileIndexHdr* __restrict__ ihdr, TriIndex ti, int par,
-                                                       int pstep)
+                                                       const TileIndexHdr* __restrict__ ihdr, TriIndex ti, int pstep)
 {
-    uint32_t* __restrict__ cnt = ti.counts + (size_t)par * TRI_CELLS;
-    uint32_t* __restrict__ nxt = ti.counts + (size_t)(1 - par) * TRI_CELLS;
-    const int gt = blockIdx.x * 256 + threadIdx.x, gn = gridDim.x * 256;
-    for (int i = gt; i < TRI_CELLS; i += gn) nxt[i] = 0u;
-    if (gt < 4) ti.hdr[4 * (1 - par) + gt] = 0u;
+    uint32_t* __restrict__ cnt = ti.counts;
+    const int gt = blockIdx.x * 256 + threadIdx.x;
     unsigned b0 = 0u, b1 = 0u;  // float bits of non-negative radii order as the floats
     if (gt < T) {
         const int t = gt;
         float4 q0;
         float cb, sb;
-        if (tri_cap(rec, (size_t)T, t, __uint_as_float(ihdr->h_max), pstep, q0, cb, sb)) {
+        if (tri_cap(rec, (size_t)T, t, __uint_as_float((uint32_t)ihdr->h_gen), pstep, q0, cb, sb)) {
             const float beta = acosf(cb);
             const unsigned bb = __float_as_uint(fmaxf(beta, 1e-30f));  // nonzero: the grid holds a triangle
             uint32_t e = 0xffffffffu;
@@ -861,8 +719,8 @@ __global__ void __launch_bounds__(256) tri_file_kernel(const float4* __restrict_
         b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        if (b0) atomicMax(&ti.hdr[4 * par], b0);
-        if (b1) atomicMax(&ti.hdr[4 * par + 1], b1);
+        if (b0) atomicMax(&cnt[TRI_HDR], b0);
+        if (b1) atomicMax(&cnt[TRI_HDR + 1], b1);
     }
 }
 
@@ -900,146 +758,246 @@ __device__ __forceinline__ TriWin shfl_win(const TriWin& w, int src)
                   __shfl_sync(0xffffffffu, w.c0, src), __shfl_sync(0xffffffffu, w.ncol, src)};
 }
 
-// One warp per tile, one pass.  The cells of the tile's windows (and the
-// list) go one per lane, 32 at a time; their triangles are numbered across
-// the warp and every lane tests the next one each step (finding the cell
-// that holds it by a search over the lanes), BIN_WALK_U steps' loads at a
-// time.  The hits are staged in shared memory (up to BIN_STAGE_HITS; a
-// longer bin walks again for the rest), the tile's range of the bins is
-// taken with one atomic on the cursor, and the last CTA to finish stores
-// the total.
+// The candidate triangles of one tile, as one warp sees them: the cells of
+// the tile's two windows and the list, one range of sorted entries each.
+struct TileWalk {
+    float ax, ay, az, ca, sa;  // the tile's cone
+    TriWin w0, w1;             // its windows on the fine and coarse grid
+    int R0, R1, R;             // ranges: fine cells, coarse cells, then the list (none for an empty tile)
+
+    // every lane of the warp, the same tile
+    __device__ __forceinline__ void init(const float4& g, const Cone& c, const uint32_t* __restrict__ hdr, int lane)
+    {
+        ax = c.c0.x;
+        ay = c.c0.y;
+        az = c.c0.z;
+        ca = c.c0.w;
+        sa = c.c1.x;
+        TriWin w{0, 0, 0, 1};
+        R = 0;
+        if (g.w >= 0.0f) {  // h < 0: an empty tile
+            // lane 0 forms the fine grid's window, lane 1 the coarse grid's
+            // (none for a grid that holds no triangle)
+            const unsigned bm = lane < 2 ? hdr[lane] : 0u;
+            if (bm)
+                w = tri_window(g.y, g.z, g.x + __uint_as_float(bm) + 2e-4f, lane ? TRI_NLAT1 : TRI_NLAT0,
+                               lane ? TRI_CELL1 : TRI_CELL0);
+        }
+        w0 = shfl_win(w, 0);
+        w1 = shfl_win(w, 1);
+        R0 = w0.nr * w0.ncol;
+        R1 = w1.nr * w1.ncol;
+        R = g.w >= 0.0f ? R0 + R1 + 1 : 0;
+    }
+
+    // range i < R: first entry and length
+    __device__ __forceinline__ void range(const uint32_t* __restrict__ cnt, uint32_t listcap, int i, uint32_t& a,
+                                          int& len) const
+    {
+        if (i < R0) {
+            const int row = w0.r0 + i / w0.ncol;
+            int col = w0.c0 + i % w0.ncol;
+            if (col >= TRI_NLON0) col -= TRI_NLON0;
+            const int cell = row * TRI_NLON0 + col;
+            a = (uint32_t)cell * TRI_K0;
+            len = (int)min(cnt[cell], (uint32_t)TRI_K0);
+        } else if (i < R0 + R1) {
+            const int j = i - R0;
+            const int row = w1.r0 + j / w1.ncol;
+            int col = w1.c0 + j % w1.ncol;
+            if (col >= TRI_NLON1) col -= TRI_NLON1;
+            const int cell = row * TRI_NLON1 + col;
+            a = TRI_E1 + (uint32_t)cell * TRI_K1;
+            len = (int)min(cnt[TRI_CELLS0 + cell], (uint32_t)TRI_K1);
+        } else {
+            a = TRI_E2;
+            len = (int)min(cnt[TRI_LARGE], listcap);
+        }
+    }
+
+    // entries of all ranges (every lane gets the sum)
+    __device__ __forceinline__ uint32_t entries(const uint32_t* __restrict__ cnt, uint32_t listcap, int lane) const
+    {
+        uint32_t e = 0;
+        for (int rb = 0; rb < R; rb += 32) {
+            uint32_t a = 0;
+            int len = 0;
+            if (rb + lane < R) range(cnt, listcap, rb + lane, a, len);
+            e += (uint32_t)len;
+        }
+        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        return e;
+    }
+
+    // The walk, shared by nwarps warps (this one is number wr): the ranges go
+    // one per lane, 32 at a time; their entries are numbered across the warp
+    // and every lane tests the next one each step, finding the range that
+    // holds it by a search over the lanes; the warps take the steps in turn,
+    // BIN_WALK_U steps' loads at a time.  sink(hit mask, hit, triangle, this
+    // warp's hits before the step) for every step with a hit, on all lanes;
+    // returns this warp's hits.
+    template <class Sink>
+    __device__ __forceinline__ uint32_t walk(const TriIndex& ti, int lane, int wr, int nwarps, Sink sink) const
+    {
+        const unsigned FULL = 0xffffffffu;
+        uint32_t hits = 0;
+        for (int rb = 0; rb < R; rb += 32) {
+            uint32_t a = 0;
+            int len = 0;
+            if (rb + lane < R) range(ti.counts, (uint32_t)ti.T, rb + lane, a, len);
+            int incl = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int excl = incl - len;
+            for (int k0 = 32 * BIN_WALK_U * wr; k0 < total; k0 += 32 * BIN_WALK_U * nwarps) {
+                float4 q[BIN_WALK_U];
+                float2 r[BIN_WALK_U];
+                bool in[BIN_WALK_U];
+#pragma unroll
+                for (int u = 0; u < BIN_WALK_U; ++u) {
+                    const int idx = k0 + 32 * u + lane;
+                    int o = 0;  // the last lane whose range starts at or before entry idx
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int x = __shfl_sync(FULL, excl, o + st);
+                        if (x <= idx) o += st;
+                    }
+                    const uint32_t e = __shfl_sync(FULL, a, o) + (uint32_t)(idx - __shfl_sync(FULL, excl, o));
+                    in[u] = idx < total;
+                    if (in[u]) {
+                        q[u] = ti.cap[e];
+                        r[u] = ti.cs[e];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < BIN_WALK_U; ++u) {
+                    bool hit = false;
+                    if (in[u]) {
+                        // the cap / cone test of the triangle-major search, operand for operand
+                        const float cg = fmaf(q[u].x, ax, fmaf(q[u].y, ay, q[u].z * az));
+                        hit = q[u].w + ca <= 2e-6f || cg >= fmaf(ca, q[u].w, -sa * r[u].x) - 2e-6f;
+                    }
+                    const unsigned m = __ballot_sync(FULL, hit);
+                    if (m) sink(m, hit, __float_as_uint(r[u].y), hits);
+                    hits += (uint32_t)__popc(m);
+                }
+            }
+        }
+        return hits;
+    }
+};
+
+// The tiles, one warp each.  A tile whose ranges hold at most
+// BIN_STAGE_HITS entries is binned here: its hits staged in shared memory,
+// its range of the bins taken with one atomic on the cursor.  A larger tile
+// goes to the heavy list for bin_heavy_kernel.
 __global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(const float4* __restrict__ geom,
-                                                        const Cone* __restrict__ tiles, int ntiles, TriIndex ti,
-                                                        int par, uint32_t* __restrict__ starts,
-                                                        uint32_t* __restrict__ ends, uint32_t* __restrict__ ids,
-                                                        uint32_t cap, int* status, uint32_t* total_host)
+                                                                            const Cone* __restrict__ tiles,
+                                                                            int ntiles, TriIndex ti,
+                                                                            uint32_t* __restrict__ starts,
+                                                                            uint32_t* __restrict__ ends,
+                                                                            uint32_t* __restrict__ ids, uint32_t cap,
+                                                                            int* status)
 {
     __shared__ uint32_t s_hit[4][BIN_STAGE_HITS];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tile = blockIdx.x * 4 + warp;
-    const uint32_t* __restrict__ cnt = ti.counts + (size_t)par * TRI_CELLS;
-    uint32_t* hdr = ti.hdr + 4 * par;
+    uint32_t* hdr = ti.counts + TRI_HDR;
     const uint32_t lt = (1u << lane) - 1u;
     if (tile < ntiles) {
-        const float4 g = geom[tile];  // (alpha, latitude, longitude, h); h < 0: an empty tile
-        float ax = 0.0f, ay = 0.0f, az = 0.0f, ca = 1.0f, sa = 0.0f;
-        TriWin w0{0, 0, 0, 1}, w1{0, 0, 0, 1};
-        int RL = 0;
-        if (g.w >= 0.0f) {
-            const Cone c = tiles[tile];
-            ax = c.c0.x;
-            ay = c.c0.y;
-            az = c.c0.z;
-            ca = c.c0.w;
-            sa = c.c1.x;
-            // lane 0 forms the fine grid's window, lane 1 the coarse grid's
-            // (none for a grid that holds no triangle)
-            TriWin w{0, 0, 0, 1};
-            const unsigned bm = lane < 2 ? hdr[lane] : 0u;
-            if (bm)
-                w = tri_window(g.y, g.z, g.x + __uint_as_float(bm) + 2e-4f, lane ? TRI_NLAT1 : TRI_NLAT0,
-                               lane ? TRI_CELL1 : TRI_CELL0);
-            w0 = shfl_win(w, 0);
-            w1 = shfl_win(w, 1);
-            RL = 1;
-        }
-        const int R0 = w0.nr * w0.ncol, R1 = w1.nr * w1.ncol, R = R0 + R1 + RL;
-        // the walk: sink(rank, triangle) for every hit, in rank order per step
-        auto walk = [&](auto sink) {
-            uint32_t rank = 0;
-            for (int rb = 0; rb < R; rb += 32) {
-                const int i = rb + lane;
-                uint32_t a = 0;
-                int len = 0;
-                if (i < R0) {
-                    const int row = w0.r0 + i / w0.ncol;
-                    int col = w0.c0 + i % w0.ncol;
-                    if (col >= TRI_NLON0) col -= TRI_NLON0;
-                    const int cell = row * TRI_NLON0 + col;
-                    a = (uint32_t)cell * TRI_K0;
-                    len = (int)min(cnt[cell], (uint32_t)TRI_K0);
-                } else if (i < R0 + R1) {
-                    const int j = i - R0;
-                    const int row = w1.r0 + j / w1.ncol;
-                    int col = w1.c0 + j % w1.ncol;
-                    if (col >= TRI_NLON1) col -= TRI_NLON1;
-                    const int cell = row * TRI_NLON1 + col;
-                    a = TRI_E1 + (uint32_t)cell * TRI_K1;
-                    len = (int)min(cnt[TRI_CELLS0 + cell], (uint32_t)TRI_K1);
-                } else if (i < R) {
-                    a = TRI_E2;
-                    len = (int)min(cnt[TRI_LARGE], (uint32_t)ti.T);
-                }
-                int incl = len;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int total = __shfl_sync(FULL, incl, 31);
-                const int excl = incl - len;
-                for (int k0 = 0; k0 < total; k0 += 32 * BIN_WALK_U) {
-                    float4 q[BIN_WALK_U];
-                    float2 r[BIN_WALK_U];
-                    bool in[BIN_WALK_U];
-#pragma unroll
-                    for (int u = 0; u < BIN_WALK_U; ++u) {
-                        const int idx = k0 + 32 * u + lane;
-                        int o = 0;  // the last lane whose cell starts at or before triangle idx
-                        for (int st = 16; st > 0; st >>= 1) {
-                            const int x = __shfl_sync(FULL, excl, o + st);
-                            if (x <= idx) o += st;
-                        }
-                        const uint32_t e = __shfl_sync(FULL, a, o) + (uint32_t)(idx - __shfl_sync(FULL, excl, o));
-                        in[u] = idx < total;
-                        if (in[u]) {
-                            q[u] = ti.cap[e];
-                            r[u] = ti.cs[e];
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < BIN_WALK_U; ++u) {
-                        bool hit = false;
-                        if (in[u]) {
-                            // the cap / cone test of the triangle-major search, operand for operand
-                            const float cg = fmaf(q[u].x, ax, fmaf(q[u].y, ay, q[u].z * az));
-                            hit = q[u].w + ca <= 2e-6f || cg >= fmaf(ca, q[u].w, -sa * r[u].x) - 2e-6f;
-                        }
-                        const unsigned m = __ballot_sync(FULL, hit);
-                        if (hit) sink(rank + (uint32_t)__popc(m & lt), __float_as_uint(r[u].y));
-                        rank += (uint32_t)__popc(m);
-                    }
-                }
-            }
-            return rank;
-        };
-        uint32_t* __restrict__ stage = s_hit[warp];
-        const uint32_t n = walk([&](uint32_t k, uint32_t t) {
-            if (k < BIN_STAGE_HITS) stage[k] = t;
-        });
-        uint32_t start = 0;
-        if (lane == 0) start = atomicAdd(&hdr[2], n);
-        start = __shfl_sync(FULL, start, 0);
-        __syncwarp();
-        if (lane == 0 && (uint64_t)start + n > cap && status) raise_status(status, VSR_ERR_BIN_OVERFLOW);
-        for (uint32_t j = lane; j < min(n, BIN_STAGE_HITS); j += 32)
-            if (start + j < cap) ids[start + j] = stage[j];
-        if (n > BIN_STAGE_HITS)
-            walk([&](uint32_t k, uint32_t t) {
-                if (k >= BIN_STAGE_HITS && start + k < cap) ids[start + k] = t;
+        const float4 g = geom[tile];
+        TileWalk tw;
+        tw.init(g, g.w >= 0.0f ? tiles[tile] : Cone{}, hdr, lane);
+        const uint32_t E = tw.entries(ti.counts, (uint32_t)ti.T, lane);
+        if (E <= BIN_STAGE_HITS) {
+            uint32_t* __restrict__ stage = s_hit[warp];
+            const uint32_t n = tw.walk(ti, lane, 0, 1, [&](unsigned m, bool hit, uint32_t t, uint32_t before) {
+                if (hit) stage[before + (uint32_t)__popc(m & lt)] = t;
             });
-        if (lane == 0) {
-            starts[tile] = start;
-            ends[tile] = start + n;
+            uint32_t start = 0;
+            if (lane == 0 && n) start = atomicAdd(&hdr[TRI_H_CURSOR], n);
+            start = __shfl_sync(FULL, start, 0);
+            __syncwarp();
+            if (lane == 0 && (uint64_t)start + n > cap) raise_status(status, VSR_ERR_BIN_OVERFLOW);
+            for (uint32_t j = lane; j < n; j += 32)
+                if (start + j < cap) ids[start + j] = stage[j];
+            if (lane == 0) {
+                starts[tile] = start;
+                ends[tile] = start + n;
+            }
+        } else if (lane == 0) {
+            const uint32_t j = atomicAdd(&hdr[TRI_H_HEAVY], 1u);
+            if (j < (uint32_t)ntiles) ti.heavy[j] = (uint32_t)tile;
         }
     }
-    // the last CTA to finish stores the total
-    __syncthreads();
+}
+
+// The heavy tiles, one CTA of BIN_HEAVY_WARPS warps each, the CTAs taking
+// the next tile of the list until none is left (a grid of resident CTAs;
+// nothing waits).  The warps take the walk's steps in turn: a first walk
+// counts the tile's hits, one atomic takes its range of the bins, a second
+// walk writes them, each step's hits taking their places from a
+// shared-memory counter.  The last CTA to finish stores the total.
+__global__ void __launch_bounds__(32 * BIN_HEAVY_WARPS) bin_heavy_kernel(const float4* __restrict__ geom,
+                                                                        const Cone* __restrict__ tiles, int ntiles,
+                                                                        TriIndex ti, uint32_t* __restrict__ starts,
+                                                                        uint32_t* __restrict__ ends,
+                                                                        uint32_t* __restrict__ ids, uint32_t cap,
+                                                                        int* status, uint32_t* total_host)
+{
+    __shared__ uint32_t s_tile, s_n, s_start;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* hdr = ti.counts + TRI_HDR;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t nheavy = min(hdr[TRI_H_HEAVY], (uint32_t)ntiles);
+    for (;;) {
+        __syncthreads();  // the previous tile's counter is read
+        if (threadIdx.x == 0) {
+            const uint32_t j = atomicAdd(&hdr[TRI_H_NEXT], 1u);
+            s_tile = j < nheavy ? ti.heavy[j] : 0xffffffffu;
+            s_n = 0u;
+        }
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= (uint32_t)ntiles) break;
+        const float4 g = geom[tile];
+        TileWalk tw;
+        tw.init(g, tiles[tile], hdr, lane);
+        const uint32_t mine = tw.walk(ti, lane, warp, BIN_HEAVY_WARPS, [](unsigned, bool, uint32_t, uint32_t) {});
+        if (lane == 0 && mine) atomicAdd(&s_n, mine);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t n = s_n;
+            const uint32_t start = n ? atomicAdd(&hdr[TRI_H_CURSOR], n) : 0u;
+            if ((uint64_t)start + n > cap) raise_status(status, VSR_ERR_BIN_OVERFLOW);
+            starts[tile] = start;
+            ends[tile] = start + n;
+            s_start = start;
+            s_n = 0u;
+        }
+        __syncthreads();
+        const uint32_t start = s_start;
+        tw.walk(ti, lane, warp, BIN_HEAVY_WARPS, [&](unsigned m, bool hit, uint32_t t, uint32_t) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_n, (uint32_t)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (hit) {
+                const uint32_t pos = start + base + (uint32_t)__popc(m & lt);
+                if (pos < cap) ids[pos] = t;
+            }
+        });
+    }
+    // the last CTA to finish stores the total (every tile's range is taken
+    // by then: the tile pass ran before, and each CTA's own before this)
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&hdr[3], 1u) == gridDim.x - 1) {
+        if (atomicAdd(&hdr[TRI_H_DONE], 1u) == gridDim.x - 1) {
             __threadfence();
-            const uint32_t total = atomicAdd(&hdr[2], 0u);
+            const uint32_t total = atomicAdd(&hdr[TRI_H_CURSOR], 0u);
             starts[ntiles] = total;
             if (total_host) {  // straight into the host's pinned word (read after an event)
                 *total_host = total;
@@ -1059,16 +1017,15 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
     return VSR_OK;
 }
 
-vsr_status tri_index_alloc(TriIndex* ti, int64_t T)
+vsr_status tri_index_alloc(TriIndex* ti, int64_t T, int ntiles)
 {
-    if (!ti->counts) {
-        VSR_CUDA_TRY(cudaMalloc(&ti->counts, sizeof(uint32_t) * 2 * TRI_CELLS));
-        VSR_CUDA_TRY(cudaMalloc(&ti->hdr, sizeof(uint32_t) * 8));
-        // zero before a binning uses them (each binning clears the other buffer)
-        VSR_CUDA_TRY(cudaMemset(ti->counts, 0, sizeof(uint32_t) * 2 * TRI_CELLS));
-        VSR_CUDA_TRY(cudaMemset(ti->hdr, 0, sizeof(uint32_t) * 8));
-        VSR_CUDA_TRY(cudaStreamSynchronize(0));
-        ti->parity = 0;
+    if (!ti->counts) VSR_CUDA_TRY(cudaMalloc(&ti->counts, sizeof(uint32_t) * TRI_WORDS));
+    if (!ti->heavy || ntiles > ti->ntiles) {
+        cudaFree(ti->heavy);
+        ti->heavy = nullptr;
+        ti->ntiles = 0;
+        VSR_CUDA_TRY(cudaMalloc(&ti->heavy, sizeof(uint32_t) * (size_t)(ntiles > 0 ? ntiles : 1)));
+        ti->ntiles = ntiles;
     }
     if (!ti->cap || T > ti->T) {
         cudaFree(ti->cap);
@@ -1087,67 +1044,55 @@ vsr_status tri_index_alloc(TriIndex* ti, int64_t T)
 void tri_index_free(TriIndex* ti)
 {
     cudaFree(ti->counts);
-    cudaFree(ti->hdr);
+    cudaFree(ti->heavy);
     cudaFree(ti->cap);
     cudaFree(ti->cs);
     *ti = TriIndex{};
 }
 
-size_t tri_index_bytes(int64_t T)
+size_t tri_index_bytes(int64_t T, int ntiles)
 {
-    return sizeof(uint32_t) * (2 * (size_t)TRI_CELLS + 8) + (sizeof(float4) + sizeof(float2)) * ((size_t)TRI_E2 + (size_t)T);
+    return sizeof(uint32_t) * ((size_t)TRI_WORDS + (size_t)ntiles) +
+           (sizeof(float4) + sizeof(float2)) * ((size_t)TRI_E2 + (size_t)T);
 }
 
 vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
-                            TriIndex* ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
-                            uint32_t* total_host, cudaStream_t st, int pstep)
+                            const TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap,
+                            int* status, uint32_t* total_host, cudaStream_t st, int pstep)
 {
-    if (T < 0 || (int64_t)T > ti->T || !ti->counts || !ti->cap || ntiles <= 0) return VSR_ERR_INVALID_ARG;
-    const int par = ti->parity;
-    ti->parity ^= 1;
-    tri_file_kernel<<<T > 0 ? (T + 255) / 256 : 1, 256, 0, st>>>(rec, T, idx.hdr, *ti, par, pstep);
+    if (T < 0 || (int64_t)T > ti.T || !ti.counts || !ti.cap || ntiles <= 0 || ntiles > ti.ntiles)
+        return VSR_ERR_INVALID_ARG;
+    VSR_CUDA_TRY(cudaMemsetAsync(ti.counts, 0, sizeof(uint32_t) * TRI_WORDS, st));
+    if (T > 0) {
+        tri_file_kernel<<<(T + 255) / 256, 256, 0, st>>>(rec, T, idx.hdr, ti, pstep);
+        VSR_CUDA_TRY(cudaGetLastError());
+    }
+    bin_tiles_kernel<<<(ntiles + 3) / 4, 128, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap, status);
     VSR_CUDA_TRY(cudaGetLastError());
-    bin_tiles_kernel<<<(ntiles + 3) / 4, 128, 0, st>>>(idx.geom, tiles, ntiles, *ti, par, starts, ends, ids, cap,
-                                                       status, total_host);
+    const int sms = sm_count();
+    if (sms < 0) return VSR_ERR_CUDA;
+    bin_heavy_kernel<<<2 * sms, 32 * BIN_HEAVY_WARPS, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap,
+                                                               status, total_host);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
 {
-    if (ntiles <= IDX_FUSED_TILES) {
-        // the shared-memory opt-in of the fused kernel, once per device
-        static std::atomic<uint64_t> attr_set{0};
-        int dev = 0;
-        VSR_CUDA_TRY(cudaGetDevice(&dev));
-        const uint64_t bit = 1ull << (dev & 63);
-        if (!(attr_set.load() & bit)) {
-            VSR_CUDA_TRY(cudaFuncSetAttribute(idx_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)IDX_FUSED_SMEM));
-            attr_set.fetch_or(bit);
-        }
-        idx_fused_kernel<<<1, IDX_FUSED_THREADS, IDX_FUSED_SMEM, st>>>(tiles, idx.geom, ntiles, idx.hdr,
-                                                                        idx.cell_start, idx.sorted, idx.big,
-                                                                        idx.cell_count);
-        VSR_CUDA_TRY(cudaGetLastError());
-        return VSR_OK;
+    if (ntiles < 0 || ntiles > IDX_FUSED_TILES) return VSR_ERR_INVALID_ARG;
+    // the shared-memory opt-in of the kernel, once per device
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    VSR_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        VSR_CUDA_TRY(cudaFuncSetAttribute(idx_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)IDX_FUSED_SMEM));
+        attr_set.fetch_or(bit);
     }
-    const int nb = (ntiles + IDX_THREADS - 1) / IDX_THREADS;
-    VSR_CUDA_TRY(cudaMemsetAsync(idx.hdr, 0, sizeof(TileIndexHdr), st));
-    VSR_CUDA_TRY(cudaMemsetAsync(idx.cell_count, 0, sizeof(uint32_t) * IDX_CELLS_MAX, st));
-    if (ntiles > 0) {
-        idx_hist_kernel<<<nb, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr);
-        VSR_CUDA_TRY(cudaGetLastError());
-    }
-    idx_count_kernel<<<nb > 0 ? nb : 1, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_count, idx.big);
+    idx_fused_kernel<<<1, IDX_FUSED_THREADS, IDX_FUSED_SMEM, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start,
+                                                                    idx.sorted, idx.big, idx.cell_count);
     VSR_CUDA_TRY(cudaGetLastError());
-    vsr_status s = launch_scan(idx.cell_count, nullptr, 0, &idx.hdr->ncell, idx.cell_start, st);
-    if (s != VSR_OK) return s;
-    if (ntiles > 0) {
-        idx_copy_kernel<<<nb, IDX_THREADS, 0, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count,
-                                                    idx.sorted);
-        VSR_CUDA_TRY(cudaGetLastError());
-    }
     return VSR_OK;
 }
 
@@ -1173,16 +1118,6 @@ static int bin_shape(int T, int sms)
     if ((T + 127) / 128 > 7 * sms) return 0;
     if ((T + 31) / 32 <= 7 * sms) return 2;
     return 1;
-}
-
-vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st)
-{
-    vsr_status s = launch_scan(idx.cell_count, nullptr, 0, &idx.hdr->ncell, idx.cell_start, st);
-    if (s != VSR_OK) return s;
-    idx_file_copy_kernel<<<ntiles > 0 ? (ntiles + IDX_THREADS - 1) / IDX_THREADS : 1, IDX_THREADS, 0, st>>>(
-        tiles, idx.geom, ntiles, idx.hdr, idx.cell_start, idx.cell_count, idx.sorted);
-    VSR_CUDA_TRY(cudaGetLastError());
-    return VSR_OK;
 }
 
 vsr_status launch_bin_count(const float4* rec, int T, TileIndex idx, uint32_t* counts, uint32_t* cursor,

@@ -65,7 +65,7 @@ FragArgs frag_args(vsr_map m, vsr_scene sc, const float* colors, vsr_frags f)
     a.rec = sc->rec;
     a.T = (int)sc->T;
     a.offsets = sc->offsets;
-    a.ends = sc->ends;
+    a.ends = scene_ends(sc);
     a.ids = sc->ids;
     a.cap = sc->cap;
     a.colors = colors;

@@ -31,9 +31,12 @@ struct vsr_map_s {
     float4* deriv = nullptr; // 2 float4 per pixel with VSR_MAP_DERIVATIVES
     float4* map = nullptr;
     Cone* tiles = nullptr;
+    // tile geometry and widest ramp (every generation), and the tile index
+    // of the triangle-major search, built for the current generation on
+    // first use (vsr_raster_noalloc)
     TileIndex idx = {};
-    bool idx_built = false;     // a tile index (and its histogram) exists
-    vsr_map_spec idx_spec = {};  // the projection it was built for: a generation of the same one files into it
+    bool idx_built = false;
+    uint32_t hgen = 0;  // generation of the widest-ramp word (idx.hdr->h_gen)
     int tx = 0, ty = 0;
     uint64_t gen = 0;
 };
@@ -46,9 +49,14 @@ struct vsr_scene_s {
     uint64_t gen = 0;
     // bin workspace
     int ws_tiles = 0;
-    uint32_t* offsets = nullptr;  // bin starts (ntiles + 1: the last receives the pair total)
-    uint32_t* ends = nullptr;     // bin ends (ntiles)
+    // bins: tile-major, tile u's at ids[offsets[u] .. ends[u]) (offsets[ntiles]:
+    // the total); triangle-major, in tile order at ids[offsets[u] ..
+    // offsets[u + 1]), `ends` holding the count pass's counters and cursor
+    bool tile_major = false;
+    uint32_t* offsets = nullptr;  // ntiles + 1
+    uint32_t* ends = nullptr;     // ntiles + 1
     uint32_t* ids = nullptr;
+    uint2* pairs = nullptr;  // (tile, triangle) of every hit of the triangle-major count pass, cap entries
     uint32_t cap = 0;
     TriIndex tri = {};  // the frame's triangles by cap cell (tile-major binning)
     uint64_t sized_shape = 0;           // (tiles, T) the bins were last sized for
@@ -94,6 +102,15 @@ struct vsr_scene_s {
 };
 
 inline int* scene_status(const vsr_scene_s* s) { return s->status ? s->status : status_word(); }
+
+// the bins' end array for the raster views (NULL: bins in tile order)
+inline const uint32_t* scene_ends(const vsr_scene_s* s) { return s->tile_major ? s->ends : nullptr; }
+
+// triangles per tile up to which a scene is binned tile-major: 27 on the
+// 1080p single-view frame (220k triangles, bin stage 65.8 -> ~40 us against
+// the triangle-major search); 122-977 on the batched views' 1M triangles,
+// where the tile-major walk was slower (tiles few and wide)
+constexpr int64_t TILE_MAJOR_TRIS_PER_TILE = 64;
 
 // Note a use of the scene's buffers queued on st (see use_event).
 inline vsr_status scene_used(vsr_scene_s* s, cudaStream_t st)

@@ -75,14 +75,13 @@ __device__ __forceinline__ void cone_barrier()
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
-// file_into (optional): the tile index of a later generation of the same
-// map; thread 0 then files the tile (index `tile`) into the plan the index
-// header holds: its histogram bin, and its cell's count or, past the plan's
-// small-tile half-angle, the big list (the header's work counters).  Tile 0
-// also clears the index's maxima, which the index finish then forms.
+// h_gen (optional): the map's widest-ramp word, (generation << 32) | float
+// bits of the largest ramp half-width; thread 0 raises it to this tile's
+// with generation gen (a 64-bit maximum: a word left by an earlier
+// generation is below every value of this one, so nothing clears it).
 template <int P>
 __device__ void reduce_cone(const bool (&valid)[P], const float3 (&G)[P], const float (&hp)[P], Cone* out,
-                            float4* geom, const TileIndex* file_into = nullptr, int tile = 0)
+                            float4* geom, unsigned long long* h_gen = nullptr, uint32_t gen = 0)
 {
     constexpr int NT = TILE_PIX / P, CONE_WARPS = NT / 32;
     static_assert(NT % 32 == 0, "whole warps of pixel threads");
@@ -154,21 +153,7 @@ __device__ void reduce_cone(const bool (&valid)[P], const float3 (&G)[P], const 
         const float4 g =
             make_float4(acosf(ca), asinf(fmaxf(-1.0f, fminf(1.0f, ay))), atan2f(ax, az), n > 0.0f ? hh : -1.0f);
         *geom = g;
-        if (file_into && tile == 0) {
-            file_into->hdr->h_max = 0u;
-            file_into->hdr->alpha_small_max = 0u;
-            file_into->hdr->view_angle = 0u;
-        }
-        if (file_into && g.w >= 0.0f) {
-            TileIndexHdr* hdr = file_into->hdr;
-            atomicAdd(&hdr->hist_work[hist_bin(g.x)], 1u);
-            if (g.x > hdr->alpha_cut) {
-                const uint32_t b = atomicAdd(&hdr->n_big_work, 1u);
-                if (b < file_into->ntiles) file_into->big[b] = index_entry(cone, tile);
-            } else {
-                atomicAdd(&file_into->cell_count[home_cell_geom(g, *hdr)], 1u);
-            }
-        }
+        if (h_gen && g.w >= 0.0f) atomicMax(h_gen, ((unsigned long long)gen << 32) | __float_as_uint(hh));
     }
 }
 
@@ -281,7 +266,7 @@ __global__ void __launch_bounds__(map_threads(P), map_ctas(P)) map_kernel(int W,
                                                                          Cone* __restrict__ tiles,
                                                                          float4* __restrict__ geom,
                                                                          float4* __restrict__ deriv,
-                                                                         TileIndex file_into, int file)
+                                                                         unsigned long long* h_gen, uint32_t gen)
 {
     // map values of the tile and its halo: direction xyz, w = F's return value
     __shared__ float4 sv[HW * HW];
@@ -306,7 +291,7 @@ __global__ void __launch_bounds__(map_threads(P), map_ctas(P)) map_kernel(int W,
         map_pixel(sv, li, lj, tx * TILE + li, ty * TILE + lj, W, H, map, deriv, valid[q], G[q], h[q]);
     }
     const int t = ty * gridDim.x + tx;
-    reduce_cone<P>(valid, G, h, &tiles[t], &geom[t], file ? &file_into : nullptr, t);
+    reduce_cone<P>(valid, G, h, &tiles[t], &geom[t], h_gen, gen);
 }
 
 // The Universal perspective map function.
@@ -392,7 +377,8 @@ struct SpecFn {
 
 // Cones of a map supplied by the caller.
 __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict__ map, int W, int H,
-                                                         Cone* __restrict__ tiles, float4* __restrict__ geom)
+                                                         Cone* __restrict__ tiles, float4* __restrict__ geom,
+                                                         unsigned long long* h_gen, uint32_t gen)
 {
     const int li = threadIdx.x % TILE, lj = threadIdx.x / TILE;
     const int i = blockIdx.x * TILE + li, j = blockIdx.y * TILE + lj;
@@ -410,7 +396,8 @@ __global__ void __launch_bounds__(TILE_PIX) cone_kernel(const float4* __restrict
     const bool vv[1] = {valid};
     const float3 gg[1] = {G};
     const float hh[1] = {h};
-    reduce_cone<1>(vv, gg, hh, &tiles[blockIdx.y * gridDim.x + blockIdx.x], &geom[blockIdx.y * gridDim.x + blockIdx.x]);
+    const int t = blockIdx.y * gridDim.x + blockIdx.x;
+    reduce_cone<1>(vv, gg, hh, &tiles[t], &geom[t], h_gen, gen);
 }
 
 }  // namespace
@@ -442,18 +429,18 @@ MapP make_params(int W, int H, int aov, float k, float l, float s, float omega_d
 }  // namespace
 
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      float4* geom, const TileIndex* file_into, cudaStream_t st)
+                      float4* geom, unsigned long long* h_gen, uint32_t gen, cudaStream_t st)
 {
     const MapP p = make_params(W, H, aov, k, l, s, omega_deg);
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    map_kernel<UniversalFn, VSR_MAP_PPT><<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom, nullptr,
-                                             file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
+    map_kernel<UniversalFn, VSR_MAP_PPT>
+        <<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(W, H, UniversalFn{p}, map, tiles, geom, nullptr, h_gen, gen);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
 vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, float4* geom, float4* deriv,
-                           const TileIndex* file_into, cudaStream_t st)
+                           unsigned long long* h_gen, uint32_t gen, cudaStream_t st)
 {
     SpecFn f;
     f.kind = sp.kind;
@@ -471,16 +458,17 @@ vsr_status launch_map_spec(const vsr_map_spec& sp, float4* map, Cone* tiles, flo
         f.a[3] = sp.param[2];
     }
     dim3 grid((sp.W + TILE - 1) / TILE, (sp.H + TILE - 1) / TILE);
-    map_kernel<SpecFn, VSR_MAP_PPT><<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv,
-                                             file_into ? *file_into : TileIndex{}, file_into ? 1 : 0);
+    map_kernel<SpecFn, VSR_MAP_PPT>
+        <<<grid, map_threads(VSR_MAP_PPT), 0, st>>>(sp.W, sp.H, f, map, tiles, geom, deriv, h_gen, gen);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }
 
-vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st)
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, unsigned long long* h_gen,
+                            uint32_t gen, cudaStream_t st)
 {
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE);
-    cone_kernel<<<grid, TILE_PIX, 0, st>>>(map, W, H, tiles, geom);
+    cone_kernel<<<grid, TILE_PIX, 0, st>>>(map, W, H, tiles, geom, h_gen, gen);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

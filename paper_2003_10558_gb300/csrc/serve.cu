@@ -102,21 +102,22 @@ size_t map_bytes(int W, int H)
 }
 
 // device memory a (slot, scene) workspace will take once used: records,
-// triangle index, bins (estimated at 4 pairs per triangle) and split
-// accumulators
+// triangle index (tile-major binning), bins and their pair list (estimated
+// at 4 pairs per triangle) and split accumulators
 size_t work_estimate(int64_t T, int W, int H)
 {
     const size_t tiles = (size_t)((W + TILE - 1) / TILE) * ((H + TILE - 1) / TILE);
     const size_t split = tiles < SPLIT_SLOTS ? tiles : SPLIT_SLOTS;
-    return (size_t)T * (REC_F * sizeof(float4) + 4 * sizeof(uint32_t)) + tri_index_bytes(T) +
+    const size_t tri = T <= TILE_MAJOR_TRIS_PER_TILE * (int64_t)tiles ? tri_index_bytes(T, (int)tiles) : 0;
+    return (size_t)T * (REC_F * sizeof(float4) + 4 * (sizeof(uint32_t) + sizeof(uint2))) + tri +
            tiles * 4 * sizeof(uint32_t) + split * TILE_PIX * 2 * sizeof(uint64_t) + EXTRA_ITEMS * sizeof(uint2);
 }
 
 size_t scene_bytes(const vsr_scene_s* s)
 {
     size_t b = (size_t)s->T_alloc * REC_F * sizeof(float4) + (size_t)s->ws_tiles * 2 * sizeof(uint32_t) +
-               (size_t)s->cap * sizeof(uint32_t);
-    if (s->tri.counts) b += tri_index_bytes(s->tri.T);
+               (size_t)s->cap * (sizeof(uint32_t) + sizeof(uint2));
+    if (s->tri.counts) b += tri_index_bytes(s->tri.T, s->tri.ntiles);
     if (s->work_tiles)
         b += (size_t)s->work.split_cap * TILE_PIX * (sizeof(uint64_t) * 2) + (size_t)s->work.extra_cap * sizeof(uint2) +
              (size_t)s->work_tiles * 2 * sizeof(uint32_t);

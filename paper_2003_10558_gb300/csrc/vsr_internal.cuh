@@ -54,12 +54,19 @@ struct Cone {
 // cap has angular radius beta can only reach small tiles whose axis lies
 // within beta + alpha_small_max of the cap centre, i.e. in a small
 // latitude/longitude window of cells.  Grid size and alpha_cut are chosen on
-// the device from the distribution of tile half-angles.
+// the device from the distribution of tile half-angles.  The index serves
+// the triangle-major search of the fixed-array path and is built on its
+// first use after each generation of the map; the header's first word, the
+// widest ramp, is kept by the map kernels for every generation.
 constexpr int IDX_NLAT_MAX = 128;
 constexpr int IDX_CELLS_MAX = IDX_NLAT_MAX * 2 * IDX_NLAT_MAX;
 constexpr int IDX_HIST = 64;
 
 struct TileIndexHdr {
+    // (generation << 32) | float bits of the largest ramp half-width of the
+    // map's latest generation: raised by the map kernels with a 64-bit
+    // maximum, so the widest ramp is known without the rest of the index
+    unsigned long long h_gen;
     int nlat, nlon;             // grid: nlon = 2 nlat, square cells of `cell` radians
     int ncell;                  // nlat * nlon
     float cell;
@@ -73,10 +80,6 @@ struct TileIndexHdr {
     // map without a valid pixel
     unsigned view_angle;
     unsigned hist[IDX_HIST];    // third-of-an-octave histogram of half-angles
-    // counters a filing map kernel adds into (zero between generations; the
-    // index finish moves them to n_big / hist)
-    unsigned n_big_work;
-    unsigned hist_work[IDX_HIST];
 };
 
 // Device-side status word (vsr_status values; 0 = OK), one int per device
@@ -110,17 +113,17 @@ __device__ __forceinline__ bool cap_hits_cone(float3 S, float cos_rho, float sin
     } while (0)
 
 // Kernel launchers (defined in the .cu files, called by the host library).
-// file_into (optional): the map's tile index of an earlier generation of
-// the same projection; the map kernel then files every tile into it
-// (launch_tile_index_finish completes the index).
-struct TileIndex;
+// The map kernels write the tile cones and geometry and raise the map's
+// widest-ramp word h_gen (TileIndexHdr::h_gen) with generation gen, which
+// must exceed every generation the word has seen.
 vsr_status launch_map(int W, int H, int aov, float k, float l, float s, float omega_deg, float4* map, Cone* tiles,
-                      float4* geom, const TileIndex* file_into, cudaStream_t st);
-vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, cudaStream_t st);
+                      float4* geom, unsigned long long* h_gen, uint32_t gen, cudaStream_t st);
+vsr_status launch_map_cones(const float4* map, int W, int H, Cone* tiles, float4* geom, unsigned long long* h_gen,
+                            uint32_t gen, cudaStream_t st);
 // a map of any vsr_map_kind (param after limits for the Universal kind);
 // deriv (optional): 2 float4 per pixel, (d_i G, d_j G) for the pixel step
 vsr_status launch_map_spec(const vsr_map_spec& spec, float4* map, Cone* tiles, float4* geom, float4* deriv,
-                           const TileIndex* file_into, cudaStream_t st);
+                           unsigned long long* h_gen, uint32_t gen, cudaStream_t st);
 vsr_status launch_setup(const float* tris, int T, const float cam[12], float4* rec, cudaStream_t st);
 
 // Device memory of a tile index (sized for IDX_CELLS_MAX cells, ntiles tiles).
@@ -139,18 +142,8 @@ struct TileIndex {
 };
 // The whole index from the tile cones and geometry (any generation).
 vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
-// A later generation of the same map (the same projection, hence the same
-// tiles and the same grid plan), in two steps on one stream: the map kernel
-// with file_into = the index files every tile into the plan the header
-// holds (the half-angle histogram, its cell's count or the big list, into
-// the header's work counters and cell_count, which are zero between
-// generations) -> launch_tile_index_finish (the scan of the cell counts,
-// then the cell-sorted copies, the widest ramp and the largest small
-// half-angle, the work counters moved into the header and zeroed).
-vsr_status launch_tile_index_finish(const Cone* tiles, int ntiles, TileIndex idx, cudaStream_t st);
 
-// Grid arithmetic of the tile index, shared by its build (bin.cu) and the
-// map kernels that file their tiles into it (map.cu).
+// Grid arithmetic of the tile index (bin.cu).
 constexpr float IDX_PI = 3.14159265358979f;
 
 __device__ __forceinline__ int hist_bin(float a)
@@ -233,31 +226,39 @@ constexpr int TRI_CELLS = TRI_LARGE + 1;
 constexpr uint32_t TRI_E1 = (uint32_t)TRI_CELLS0 * TRI_K0;
 constexpr uint32_t TRI_E2 = TRI_E1 + (uint32_t)TRI_CELLS1 * TRI_K1;
 
-// Device memory of a triangle index (per scene, up to T triangles).  The
-// counters and header are double-buffered: a binning files into buffer
-// `parity` and clears the other one for the next binning.
+// Device memory of a triangle index (per scene or view, up to T triangles
+// and ntiles tiles).  Every binning clears the counters and the header first
+// (one memset), so the launches are the same every time and can be captured
+// in a graph.
+constexpr int TRI_HDR = TRI_CELLS;  // header words after the cell counters:
+constexpr int TRI_H_CURSOR = 2;     //   [0..1] largest enlarged cap radius of the fine / coarse grid (float bits),
+constexpr int TRI_H_DONE = 3;       //   bin cursor, finished CTAs of the heavy-tile pass,
+constexpr int TRI_H_HEAVY = 4;      //   heavy tiles listed,
+constexpr int TRI_H_NEXT = 5;       //   heavy tiles taken
+constexpr int TRI_WORDS = TRI_CELLS + 6;
 struct TriIndex {
-    uint32_t* counts;  // 2 x TRI_CELLS: triangles filed per cell (may exceed the cell's capacity), list length
-    uint32_t* hdr;     // 2 x 4: largest enlarged cap radius of the fine / coarse grid (float bits),
-                       // bin cursor, finished CTAs
-    float4* cap;       // TRI_E2 + T entries: (S-hat xyz, cos beta)
-    float2* cs;        // TRI_E2 + T entries: (sin beta, triangle bits)
-    int64_t T;         // capacity of the list
-    int parity;        // buffer of the next binning (host side)
+    // TRI_WORDS: triangles filed per cell (may exceed the cell's capacity)
+    // and the list length, then the header
+    uint32_t* counts;
+    uint32_t* heavy;  // ntiles: tiles binned by a whole CTA (more than BIN_STAGE_HITS entries)
+    float4* cap;      // TRI_E2 + T entries: (S-hat xyz, cos beta)
+    float2* cs;       // TRI_E2 + T entries: (sin beta, triangle bits)
+    int64_t T;        // capacity of the list
+    int ntiles;       // capacity of the heavy list
 };
-vsr_status tri_index_alloc(TriIndex* ti, int64_t T);
+vsr_status tri_index_alloc(TriIndex* ti, int64_t T, int ntiles);
 void tri_index_free(TriIndex* ti);
-size_t tri_index_bytes(int64_t T);
-// binning of one frame, tile-major (flips ti->parity): the triangle index of
-// rec, then every tile of the map.  idx: the map's tile index (its header's
+size_t tri_index_bytes(int64_t T, int ntiles);
+// binning of one frame, tile-major: the triangle index of rec, then every
+// tile of the map.  idx: the map's tile index (its header's
 // widest ramp and each tile's geometry); tiles: the map's ntiles cones;
 // starts / ends: ntiles + 1 / ntiles words; T <= ti->T.  With more pairs
 // than cap the bins are cut at cap and VSR_ERR_BIN_OVERFLOW is raised;
 // total_host (optional): the device address of a pinned host word that
 // also receives the total.
 vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
-                            TriIndex* ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
-                            uint32_t* total_host, cudaStream_t st, int pstep = 0);
+                            const TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap,
+                            int* status, uint32_t* total_host, cudaStream_t st, int pstep = 0);
 // One view as the raster kernel sees it: its map, tile cones, set-up
 // records, bin offsets (indexed by the view's own tile number), bin ids and
 // outputs.

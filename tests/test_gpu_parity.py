@@ -192,12 +192,12 @@ def test_single_view_workload_sampled(vsr):
     assert rep["n_valid"] == len(pixels)
 
 
-def test_regenerated_map_files_into_previous_index(vsr):
-    """A map regenerated in place (vsr_map_update, same size): a change of
-    lens builds the tile index whole, the same lens again has the map kernel
-    file its tiles into the grid planned from the previous generation.
-    Through lenses of very different tile sizes, every frame of either kind
-    equals that of a freshly made map of the same lens, bit for bit."""
+def test_regenerated_map_equals_fresh_map(vsr):
+    """A map regenerated in place (vsr_map_update, same size) through lenses
+    of very different tile sizes, each twice: the binner's widest ramp comes
+    from the map kernels' generation-tagged maximum, never from an earlier
+    generation, so every frame equals that of a freshly made map of the same
+    lens, bit for bit."""
     W, H = 640, 360
     lenses = [(0.32, 0.62, 0.86, 270.0), (-0.5, 0.8, 0.6, 200.0), (1.0, 1.0, 1.0, 100.0), (0.0, 0.5, 0.7, 360.0),
               (0.32, 0.62, 0.86, 270.0)]
@@ -241,12 +241,44 @@ def test_dense_reference_equals_binned(vsr, lens):
     assert (binned["id"] != oracle.NO_ID).mean() > 0.2
 
 
-def test_large_map_regenerated_into_grid_wide_index(vsr):
-    """A 4096 x 2176 map (34,816 tiles: its first index comes from the
-    grid-wide kernels, not the single-CTA build) updated twice with the same
-    lens: each update files its tiles into the plan the grid-wide build left.
-    Both frames equal a freshly made map's bit for bit; a change of lens in
-    between rebuilds the index whole and also matches."""
+@pytest.mark.parametrize("jitter", [0.1, 0.7], ids=["coarse_grid", "large_list"])
+def test_heavy_tiles_equal_dense(vsr, jitter):
+    """2500 triangles near the eye with wide caps -- past the fine grid's two
+    cells (coarse grid) or past the coarse grid's (the list every tile
+    tests: every tile's window then holds more candidates than one warp
+    stages, and each tile is binned by a whole CTA) -- among 3000 ordinary
+    ones, few per tile, so the scene is binned tile-major.  The binned
+    outputs equal the dense reference's bit for bit."""
+    near = scenes.random_triangles(2500, 0.05, 0.3, jitter, seed=42)
+    tris = np.concatenate([scenes.random_triangles(3000, 1.0, 20.0, 0.02, seed=41), near])
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), scenes.camera())
+    m = vsr.Map(256, 256, 0.32, 0.62, 0.86, 300.0)
+    binned = _gpu_outputs(vsr.raster(m, sc))
+    dense = _gpu_outputs(vsr.raster_dense(m, sc))
+    assert vsr.last_device_status() == 0
+    for k in binned:
+        assert np.array_equal(binned[k].view(np.uint32), dense[k].view(np.uint32)), k
+    assert (binned["id"] != oracle.NO_ID).mean() > 0.3
+
+
+@pytest.mark.parametrize("n", [40000, 200000], ids=["tile_major", "triangle_major"])
+def test_binner_choice_equals_dense(vsr, n):
+    """The same small wide view over few and over many triangles per tile
+    (the scene path bins the first tile-major, the second triangle-major):
+    both equal the dense reference bit for bit."""
+    tris = scenes.random_triangles(n, 1.0, 20.0, 0.02, seed=43)
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), scenes.camera())
+    m = vsr.Map(512, 384, 0.0, 1.0, 1.0, 360.0)
+    binned = _gpu_outputs(vsr.raster(m, sc))
+    dense = _gpu_outputs(vsr.raster_dense(m, sc))
+    assert vsr.last_device_status() == 0
+    for k in binned:
+        assert np.array_equal(binned[k].view(np.uint32), dense[k].view(np.uint32)), k
+
+
+def test_large_map_regenerated_equals_fresh_map(vsr):
+    """A 4096 x 2176 map (34,816 tiles) updated twice with each of two
+    lenses: every frame equals a freshly made map's bit for bit."""
     W, H = 4096, 2176
     lens_a, lens_b = (0.0, 1.0, 1.0, 180.0), (0.32, 0.62, 0.86, 270.0)
     tris = scenes.random_triangles(4000, 1.0, 20.0, 0.05, seed=24)
@@ -262,10 +294,9 @@ def test_large_map_regenerated_into_grid_wide_index(vsr):
                 assert np.array_equal(got[k].view(np.uint32), fresh[k].view(np.uint32)), (lens, k)
 
 
-def test_large_map_grid_wide_tile_index(vsr):
-    """A 4096 x 2176 map has 34,816 tiles, more than the single-CTA tile index
-    takes, so its index is built by the grid-wide kernels: sampled pixels
-    against the oracle."""
+def test_large_map_against_oracle(vsr):
+    """A 4096 x 2176 map (34,816 tiles, 9.1 Mpx): sampled pixels against the
+    oracle."""
     lens = dict(W=4096, H=2176, k=0.0, l=1.0, s=1.0, omega=180.0)
     tris = scenes.random_triangles(2000, 1.0, 20.0, 0.05, seed=21)
     rng = np.random.default_rng(22)

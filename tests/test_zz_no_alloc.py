@@ -82,6 +82,34 @@ def test_noalloc_matches_raster_twice(vsr, workload):
         assert np.isinf(d[~hit]).all()
 
 
+def test_noalloc_after_map_updates(vsr):
+    """The fixed-array path builds the map's tile index on its first use
+    after each generation of the map: through updates of one map with
+    different lenses (and the same lens twice), it matches vsr_raster's
+    outputs every time."""
+    W, H = 640, 360
+    lenses = [(0.32, 0.62, 0.86, 270.0), (-0.5, 0.8, 0.6, 200.0), (-0.5, 0.8, 0.6, 200.0), (1.0, 1.0, 1.0, 100.0)]
+    tris = scenes.random_triangles(3000, 1.0, 20.0, 0.03, seed=23)
+    sc = vsr.Scene(torch.from_numpy(tris).cuda(), scenes.camera())
+    m = vsr.Map(W, H, *lenses[0])
+    outs = _outputs(H, W)
+    status = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    for lens in lenses:
+        m.update(W, H, *lens)
+        ref = vsr.raster(m, sc)
+        assert vsr.last_device_status() == 0
+        for _ in range(2):
+            assert _noalloc(vsr, m, sc, outs, status) == 0
+            torch.cuda.synchronize()
+            assert int(status.item()) == 0
+            ref_id = ref["id"].cpu().numpy().view(np.uint32)
+            assert np.array_equal(outs[0].cpu().numpy().view(np.uint32), ref_id), lens
+            assert np.abs(outs[2].cpu().numpy() - ref["cov"].cpu().numpy()).max() <= COV_TOL
+            hit = ref_id != 0xFFFFFFFF
+            d = outs[1].cpu().numpy()
+            assert np.abs(d[hit] / ref["depth"].cpu().numpy()[hit] - 1).max() <= DEPTH_TOL
+
+
 def test_noalloc_limits(vsr):
     # more tiles than the array holds: refused on the host
     big_map = vsr.Map(4096, 2048, 0.0, 1.0, 1.0, 180.0)
