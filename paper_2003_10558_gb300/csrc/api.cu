@@ -75,10 +75,7 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     m->idx.ntiles = (uint32_t)nt;
     m->idx_built = false;
-    // the widest-ramp word starts below every generation
-    if (cudaMemset(m->idx.hdr, 0, sizeof(TileIndexHdr)) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
-        return VSR_ERR_CUDA;
-    m->hgen = 0;
+    m->hgen = 0;  // the first generation clears the widest-ramp word
     if ((m->spec.flags & VSR_MAP_DERIVATIVES) && (st = dalloc(&m->deriv, 2 * (size_t)W * H)) != VSR_OK) return st;
     return VSR_OK;
 }
@@ -143,14 +140,15 @@ void set_universal_spec(vsr_map m)
     m->lens_grad = true;
 }
 
-// the next generation of the map's widest-ramp word (after 2^32 - 1 of them
-// the word is cleared on st and they count from 1 again)
+// the next generation of the map's widest-ramp word: the first one (of
+// new memory, or after 2^32 - 1 of them) clears the word on st first
 vsr_status next_hgen(vsr_map m, cudaStream_t st)
 {
-    if (++m->hgen == 0) {
+    if (m->hgen == 0 || m->hgen == 0xffffffffu) {
         VSR_CUDA_TRY(cudaMemsetAsync(&m->idx.hdr->h_gen, 0, sizeof(unsigned long long), st));
-        m->hgen = 1;
+        m->hgen = 0;
     }
+    ++m->hgen;
     return VSR_OK;
 }
 

@@ -23,6 +23,7 @@
 #include <math.h>
 #include <stddef.h>
 
+#include <algorithm>
 #include <atomic>
 
 
@@ -889,25 +890,26 @@ struct TileWalk {
     }
 };
 
-// The tiles, one warp each.  A tile whose ranges hold at most
+// The tiles, one warp each (a resident grid: warp w of W takes tiles w,
+// w + W, ...).  A tile whose ranges hold at most
 // BIN_STAGE_HITS entries is binned here: its hits staged in shared memory,
 // its range of the bins taken with one atomic on the cursor.  A larger tile
-// goes to the heavy list for bin_heavy_kernel.
+// goes to the heavy list for bin_heavy_kernel.  With no heavy tile the last
+// CTA to finish stores the total.
 __global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(const float4* __restrict__ geom,
                                                                             const Cone* __restrict__ tiles,
                                                                             int ntiles, TriIndex ti,
                                                                             uint32_t* __restrict__ starts,
                                                                             uint32_t* __restrict__ ends,
                                                                             uint32_t* __restrict__ ids, uint32_t cap,
-                                                                            int* status)
+                                                                            int* status, uint32_t* total_host)
 {
     __shared__ uint32_t s_hit[4][BIN_STAGE_HITS];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * 4 + warp;
     uint32_t* hdr = ti.counts + TRI_HDR;
     const uint32_t lt = (1u << lane) - 1u;
-    if (tile < ntiles) {
+    for (int tile = blockIdx.x * 4 + warp; tile < ntiles; tile += gridDim.x * 4) {
         const float4 g = geom[tile];
         TileWalk tw;
         tw.init(g, g.w >= 0.0f ? tiles[tile] : Cone{}, hdr, lane);
@@ -924,6 +926,7 @@ __global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(cons
             if (lane == 0 && (uint64_t)start + n > cap) raise_status(status, VSR_ERR_BIN_OVERFLOW);
             for (uint32_t j = lane; j < n; j += 32)
                 if (start + j < cap) ids[start + j] = stage[j];
+            __syncwarp();  // the stage is read before the next tile's hits
             if (lane == 0) {
                 starts[tile] = start;
                 ends[tile] = start + n;
@@ -933,6 +936,21 @@ __global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(cons
             if (j < (uint32_t)ntiles) ti.heavy[j] = (uint32_t)tile;
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&hdr[TRI_H_DONE], 1u) == gridDim.x - 1) {
+            __threadfence();
+            if (atomicAdd(&hdr[TRI_H_HEAVY], 0u) == 0u) {
+                const uint32_t total = atomicAdd(&hdr[TRI_H_CURSOR], 0u);
+                starts[ntiles] = total;
+                if (total_host) {  // straight into the host's pinned word (read after an event)
+                    *total_host = total;
+                    __threadfence_system();
+                }
+            }
+        }
+    }
 }
 
 // The heavy tiles, one CTA of BIN_HEAVY_WARPS warps each, the CTAs taking
@@ -940,7 +958,9 @@ __global__ void __launch_bounds__(128, VSR_BIN_TILES_CTAS) bin_tiles_kernel(cons
 // nothing waits).  The warps take the walk's steps in turn: a first walk
 // counts the tile's hits, one atomic takes its range of the bins, a second
 // walk writes them, each step's hits taking their places from a
-// shared-memory counter.  The last CTA to finish stores the total.
+// shared-memory counter.  The last CTA to finish stores the total (when the
+// tile pass left it to this one) and clears the counters and the header for
+// the next binning.
 __global__ void __launch_bounds__(32 * BIN_HEAVY_WARPS) bin_heavy_kernel(const float4* __restrict__ geom,
                                                                         const Cone* __restrict__ tiles, int ntiles,
                                                                         TriIndex ti, uint32_t* __restrict__ starts,
@@ -954,7 +974,13 @@ __global__ void __launch_bounds__(32 * BIN_HEAVY_WARPS) bin_heavy_kernel(const f
     uint32_t* hdr = ti.counts + TRI_HDR;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t nheavy = min(hdr[TRI_H_HEAVY], (uint32_t)ntiles);
-    for (;;) {
+    if (!nheavy) {
+        // nothing reads the cell counters any more: each CTA clears a slice
+        uint4* c4 = reinterpret_cast<uint4*>(ti.counts);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < TRI_HDR / 4; i += gridDim.x * blockDim.x)
+            c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (; nheavy;) {
         __syncthreads();  // the previous tile's counter is read
         if (threadIdx.x == 0) {
             const uint32_t j = atomicAdd(&hdr[TRI_H_NEXT], 1u);
@@ -991,11 +1017,14 @@ __global__ void __launch_bounds__(32 * BIN_HEAVY_WARPS) bin_heavy_kernel(const f
             }
         });
     }
-    // the last CTA to finish stores the total (every tile's range is taken
-    // by then: the tile pass ran before, and each CTA's own before this)
+    // the last CTA to finish (every tile's range is taken by then: the tile
+    // pass ran before, and each CTA's own before this)
+    __shared__ bool s_last;
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&hdr[TRI_H_DONE], 1u) == gridDim.x - 1) {
+        s_last = atomicAdd(&hdr[TRI_H_DONE2], 1u) == gridDim.x - 1;
+        if (s_last && nheavy) {
             __threadfence();
             const uint32_t total = atomicAdd(&hdr[TRI_H_CURSOR], 0u);
             starts[ntiles] = total;
@@ -1004,6 +1033,15 @@ __global__ void __launch_bounds__(32 * BIN_HEAVY_WARPS) bin_heavy_kernel(const f
                 __threadfence_system();
             }
         }
+    }
+    __syncthreads();
+    if (s_last) {
+        // nothing reads the counters any more: clear the rest of them (all,
+        // after heavy tiles) and the header
+        const int from = nheavy ? 0 : TRI_HDR / 4;
+        uint4* c4 = reinterpret_cast<uint4*>(ti.counts);
+        for (int i = from + threadIdx.x; i < TRI_WORDS / 4; i += blockDim.x) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (threadIdx.x < TRI_WORDS % 4) ti.counts[(TRI_WORDS / 4) * 4 + threadIdx.x] = 0u;
     }
 }
 
@@ -1019,7 +1057,10 @@ vsr_status launch_scan(const uint32_t* counts, const uint32_t* extra, int n, con
 
 vsr_status tri_index_alloc(TriIndex* ti, int64_t T, int ntiles)
 {
-    if (!ti->counts) VSR_CUDA_TRY(cudaMalloc(&ti->counts, sizeof(uint32_t) * TRI_WORDS));
+    if (!ti->counts) {
+        VSR_CUDA_TRY(cudaMalloc(&ti->counts, sizeof(uint32_t) * TRI_WORDS));
+        ti->dirty = true;  // cleared by the first binning
+    }
     if (!ti->heavy || ntiles > ti->ntiles) {
         cudaFree(ti->heavy);
         ti->heavy = nullptr;
@@ -1057,23 +1098,36 @@ size_t tri_index_bytes(int64_t T, int ntiles)
 }
 
 vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
-                            const TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap,
-                            int* status, uint32_t* total_host, cudaStream_t st, int pstep)
+                            TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
+                            uint32_t* total_host, cudaStream_t st, int pstep)
 {
     if (T < 0 || (int64_t)T > ti.T || !ti.counts || !ti.cap || ntiles <= 0 || ntiles > ti.ntiles)
         return VSR_ERR_INVALID_ARG;
-    VSR_CUDA_TRY(cudaMemsetAsync(ti.counts, 0, sizeof(uint32_t) * TRI_WORDS, st));
+    // until the clearing kernel is queued, a failure leaves the counters behind
+    const bool was_dirty = ti.dirty;
+    ti.dirty = true;
+    if (was_dirty) VSR_CUDA_TRY(cudaMemsetAsync(ti.counts, 0, sizeof(uint32_t) * TRI_WORDS, st));
     if (T > 0) {
         tri_file_kernel<<<(T + 255) / 256, 256, 0, st>>>(rec, T, idx.hdr, ti, pstep);
         VSR_CUDA_TRY(cudaGetLastError());
     }
-    bin_tiles_kernel<<<(ntiles + 3) / 4, 128, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap, status);
-    VSR_CUDA_TRY(cudaGetLastError());
     const int sms = sm_count();
     if (sms < 0) return VSR_ERR_CUDA;
-    bin_heavy_kernel<<<2 * sms, 32 * BIN_HEAVY_WARPS, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap,
-                                                               status, total_host);
+    // one resident wave (the tile pass's occupancy, looked up once)
+    static std::atomic<int> per_sm{0};
+    int k = per_sm.load();
+    if (k <= 0) {
+        VSR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, bin_tiles_kernel, 128, 0));
+        if (k <= 0) k = 1;
+        per_sm.store(k);
+    }
+    const int grid = std::min((ntiles + 3) / 4, k * sms);
+    bin_tiles_kernel<<<grid, 128, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap, status, total_host);
     VSR_CUDA_TRY(cudaGetLastError());
+    bin_heavy_kernel<<<sms, 32 * BIN_HEAVY_WARPS, 0, st>>>(idx.geom, tiles, ntiles, ti, starts, ends, ids, cap, status,
+                                                           total_host);
+    VSR_CUDA_TRY(cudaGetLastError());
+    ti.dirty = false;
     return VSR_OK;
 }
 

@@ -226,16 +226,18 @@ constexpr int TRI_CELLS = TRI_LARGE + 1;
 constexpr uint32_t TRI_E1 = (uint32_t)TRI_CELLS0 * TRI_K0;
 constexpr uint32_t TRI_E2 = TRI_E1 + (uint32_t)TRI_CELLS1 * TRI_K1;
 
-// Device memory of a triangle index (per scene or view, up to T triangles
-// and ntiles tiles).  Every binning clears the counters and the header first
-// (one memset), so the launches are the same every time and can be captured
-// in a graph.
+// Device memory of a triangle index (per scene, up to T triangles and
+// ntiles tiles).  The counters and the header are zero between binnings:
+// the last kernel of a binning clears them for the next one, so the
+// launches are the same every time and can be captured in a graph (after a
+// failed launch the next binning clears them first).
 constexpr int TRI_HDR = TRI_CELLS;  // header words after the cell counters:
 constexpr int TRI_H_CURSOR = 2;     //   [0..1] largest enlarged cap radius of the fine / coarse grid (float bits),
-constexpr int TRI_H_DONE = 3;       //   bin cursor, finished CTAs of the heavy-tile pass,
+constexpr int TRI_H_DONE = 3;       //   bin cursor, finished CTAs of the tile pass,
 constexpr int TRI_H_HEAVY = 4;      //   heavy tiles listed,
-constexpr int TRI_H_NEXT = 5;       //   heavy tiles taken
-constexpr int TRI_WORDS = TRI_CELLS + 6;
+constexpr int TRI_H_NEXT = 5;       //   heavy tiles taken,
+constexpr int TRI_H_DONE2 = 6;      //   finished CTAs of the heavy-tile pass
+constexpr int TRI_WORDS = TRI_CELLS + 7;
 struct TriIndex {
     // TRI_WORDS: triangles filed per cell (may exceed the cell's capacity)
     // and the list length, then the header
@@ -245,6 +247,7 @@ struct TriIndex {
     float2* cs;       // TRI_E2 + T entries: (sin beta, triangle bits)
     int64_t T;        // capacity of the list
     int ntiles;       // capacity of the heavy list
+    bool dirty;       // host side: a binning may have left the counters behind
 };
 vsr_status tri_index_alloc(TriIndex* ti, int64_t T, int ntiles);
 void tri_index_free(TriIndex* ti);
@@ -257,8 +260,8 @@ size_t tri_index_bytes(int64_t T, int ntiles);
 // total_host (optional): the device address of a pinned host word that
 // also receives the total.
 vsr_status launch_bin_tiles(const float4* rec, int T, const TileIndex& idx, const Cone* tiles, int ntiles,
-                            const TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap,
-                            int* status, uint32_t* total_host, cudaStream_t st, int pstep = 0);
+                            TriIndex& ti, uint32_t* starts, uint32_t* ends, uint32_t* ids, uint32_t cap, int* status,
+                            uint32_t* total_host, cudaStream_t st, int pstep = 0);
 // One view as the raster kernel sees it: its map, tile cones, set-up
 // records, bin offsets (indexed by the view's own tile number), bin ids and
 // outputs.
