@@ -211,9 +211,17 @@ int64_t vsr_scene_size(vsr_scene s);
  * The merge of Sec. 1.4 (m^fc = min(m^f, 1 - m^b), m^b += m^fc) telescopes
  * to min(1, sum m^f), so the result does not depend on fragment order; it is
  * accumulated in 2^-22 fixed point and is bit-reproducible.
- * Scratch (tile bins) is held by the scene handle.  It is sized with one
- * synchronisation of `stream` the first time and whenever the map's tile
- * count or the scene's T changes; otherwise no call synchronises: the bins
+ * Binning (which triangles may cover which 16x16 tile: the enlarged cap of
+ * each triangle against the tile's view cone, the region mask of Sec.
+ * 1.1.3): with at most 64 triangles per tile, tile-major (the triangles
+ * filed by cap cell, then each tile over the cells in its reach), else
+ * triangle-major over the map's tile index (built on the first such
+ * binning after each update of the map); both give the same outputs.
+ * Scratch (tile bins, the triangle index of the tile-major binning: about
+ * 57 MB plus 24 B per triangle) is held by the scene handle.  It is sized
+ * with one synchronisation of `stream` the first time and whenever the
+ * map's tile count or the scene's T changes; otherwise no call
+ * synchronises: the bins
  * grow ahead of need from the pair count of an earlier frame, and a frame
  * that still outgrows them (e.g. after the camera moved) raises
  * VSR_ERR_BIN_OVERFLOW in the device status (vsr_last_device_status) with
@@ -233,8 +241,7 @@ vsr_status vsr_raster_pstep(vsr_map m, vsr_scene s, uint32_t* id_dev, float* dep
                             void* stream);
 
 /* The two halves of vsr_raster, for callers that reuse one binning:
- * vsr_bin builds the tile bins of (m, s) (count, scan, fill; sized as
- * described for vsr_raster);
+ * vsr_bin builds the tile bins of (m, s) (as described for vsr_raster);
  * vsr_raster_tiles runs the tile coverage/depth kernel on the current bins
  * and returns VSR_ERR_INVALID_ARG if they were built for another map or an
  * older set-up of the scene. */

@@ -72,7 +72,6 @@ vsr_status map_alloc(vsr_map m, int W, int H)
     if ((st = dalloc(&m->idx.sorted, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.big, nt)) != VSR_OK) return st;
     if ((st = dalloc(&m->idx.geom, nt)) != VSR_OK) return st;
-    if ((st = dalloc(&m->idx.cell_count, (size_t)IDX_CELLS_MAX)) != VSR_OK) return st;
     m->idx.ntiles = (uint32_t)nt;
     m->idx_built = false;
     m->hgen = 0;  // the first generation clears the widest-ramp word
@@ -90,7 +89,6 @@ void map_release(vsr_map m)
     cudaFree(m->idx.sorted);
     cudaFree(m->idx.big);
     cudaFree(m->idx.geom);
-    cudaFree(m->idx.cell_count);
     cudaFree(m->deriv);
     m->deriv = nullptr;
     m->map = nullptr;

@@ -137,8 +137,7 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
                                                                        TileIndexHdr* __restrict__ hdr,
                                                                        uint32_t* __restrict__ cell_start,
                                                                        Cone* __restrict__ sorted,
-                                                                       Cone* __restrict__ big,
-                                                                       uint32_t* __restrict__ cell_count)
+                                                                       Cone* __restrict__ big)
 {
     extern __shared__ uint32_t s_cell[];  // per-cell counts, then running slots
     // each small tile's home cell (0xffff: big or empty), from step 3 to step 5
@@ -236,8 +235,6 @@ __global__ void __launch_bounds__(IDX_FUSED_THREADS) idx_fused_kernel(const Cone
             if (slot[u] < (uint32_t)ntiles) sorted[slot[u]] = index_entry(cn[u], base + u * IDX_FUSED_THREADS);
     }
     if (tid == 0) *hdr = s_h;
-    // the filing of later generations adds into the global cell counts
-    for (int c = tid; c < IDX_CELLS_MAX; c += IDX_FUSED_THREADS) cell_count[c] = 0u;
 }
 
 // ---- per-triangle binning ---------------------------------------------------
@@ -1145,7 +1142,7 @@ vsr_status launch_tile_index(const Cone* tiles, int ntiles, TileIndex idx, cudaS
         attr_set.fetch_or(bit);
     }
     idx_fused_kernel<<<1, IDX_FUSED_THREADS, IDX_FUSED_SMEM, st>>>(tiles, idx.geom, ntiles, idx.hdr, idx.cell_start,
-                                                                    idx.sorted, idx.big, idx.cell_count);
+                                                                    idx.sorted, idx.big);
     VSR_CUDA_TRY(cudaGetLastError());
     return VSR_OK;
 }

@@ -96,9 +96,9 @@ struct Scene {
 size_t map_bytes(int W, int H)
 {
     const size_t tiles = (size_t)((W + TILE - 1) / TILE) * ((H + TILE - 1) / TILE);
-    // map, cones (tiles, sorted, big), per-tile geometry, cell starts and counts, header
+    // map, cones (tiles, sorted, big), per-tile geometry, cell starts, header
     return (size_t)W * H * sizeof(float4) + tiles * (3 * sizeof(Cone) + sizeof(float4)) +
-           sizeof(uint32_t) * (2 * IDX_CELLS_MAX + 1) + sizeof(TileIndexHdr);
+           sizeof(uint32_t) * (IDX_CELLS_MAX + 1) + sizeof(TileIndexHdr);
 }
 
 // device memory a (slot, scene) workspace will take once used: records,

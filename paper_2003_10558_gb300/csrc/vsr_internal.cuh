@@ -137,7 +137,6 @@ struct TileIndex {
     Cone* big;             // ntiles
     float4* geom;          // ntiles: (alpha, latitude, longitude of the axis, h), h = -1 if the tile is empty;
                            // written with the cones by the map kernels
-    uint32_t* cell_count;  // IDX_CELLS_MAX: scratch of the build
     uint32_t ntiles;       // tiles of the map (the length of sorted, big and geom)
 };
 // The whole index from the tile cones and geometry (any generation).
